@@ -1,0 +1,23 @@
+"""Compile the CPU oracle (plain C, FP64, OpenMP) into oracle/_bi_oracle.so.
+
+Test infrastructure: builds the checker, not the product.
+"""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "bi_oracle.c")
+OUT = os.path.join(HERE, "_bi_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= os.path.getmtime(SRC):
+        return OUT
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", OUT, SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    return OUT
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv))
