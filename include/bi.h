@@ -1,0 +1,159 @@
+/*
+ * bi.h -- C-ABI of the GB300 boundary-integral operator library.
+ *
+ * The library applies the dense boundary-integral matrix C of the coupled HDG-BI
+ * system (Sec. II.D, Eq. 42, lower-right block; entries Eqs. 43-46) to vectors of
+ * RWG coefficients of the equivalent currents J and M on a closed triangulated
+ * surface (Sec. II.B-C), accelerated by a multilevel fast multipole algorithm
+ * (step 2(a) of the hybrid solver, Sec. II.E).  It also solves C X = b with a
+ * device-resident GMRES (Sec. II.E, steps 2-3) and builds the plane-wave right-hand
+ * sides of Eqs. 49-50.
+ *
+ * Conventions (fixed by the ABI):
+ *   - Time dependence exp(j w t); G = exp(-j k0 R) / (4 pi R); fields normalised so
+ *     that E and H carry the same amplitude (Sec. II.A).
+ *   - Mesh: verts[nv][3] (float64, any length unit consistent with k0), tris[nt][3]
+ *     (int32), counter-clockwise seen from outside.  Several disjoint closed
+ *     components are allowed (Sec. II.F, comment 2).
+ *   - RWG functions are the interior edges sorted by (min vertex, max vertex);
+ *     f = (l / 2A+)(r - p+) on T+, (l / 2A-)(p- - r) on T-, where T+ is the
+ *     triangle in which the edge runs from its smaller to its larger vertex.
+ *   - Unknown vectors are column-major [nrhs][n_unknowns]: for op_mode 0 the J
+ *     block (N entries) then the M block (N entries); for op_mode 1 only J.
+ *   - Complex numbers are interleaved (re, im): complex128 for precision 0,
+ *     complex64 for precision 1.
+ *
+ * Ownership: the caller owns every vector it passes (device memory for the
+ * device entry points, host memory for *_host).  The handle owns all internal
+ * device buffers.  A handle is used by one host thread at a time.
+ *
+ * Errors: every entry point returns a bi_status; nothing aborts.  bi_last_error()
+ * gives a one-line description of the last failure on that handle.
+ */
+#ifndef BI_GB300_H
+#define BI_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bi_handle_s* bi_handle;
+
+typedef enum {
+    BI_OK = 0,
+    BI_ERR_ARG = -1,            /* invalid argument or size                          */
+    BI_ERR_MESH = -2,           /* open/non-manifold edge, flipped or degenerate tri */
+    BI_ERR_OOM = -3,            /* device allocation failed                          */
+    BI_ERR_CUDA = -4,           /* a CUDA call failed                                */
+    BI_ERR_NOT_CONVERGED = -5,  /* GMRES stopped before tol; best iterate returned   */
+    BI_ERR_TIMEOUT = -6,        /* a bounded device wait gave up                     */
+    BI_ERR_BUSY = -7            /* serving queue full                                */
+} bi_status;
+
+typedef enum { BI_PREC_FP64 = 0, BI_PREC_FP32 = 1 } bi_precision;
+
+/* op_mode 0: the C block of Eq. 42 (2N unknowns):
+ *     [ G - P     X/2 - Q ] [J]      G = <f_m, f_n>, X = <f_m, n x f_n>,
+ *     [   Q       G/2 - P ] [M]      P = <f_m, C f_n>, Q = <f_m, n x C f_n>,
+ *   with C = 1/2 pi_tau L + 1/2 pi_x Kbar (Eq. 27, alpha = 1/2).
+ * op_mode 1: PEC combined-field equation (Eqs. 24a/24b with M = 0, alpha = 1/2):
+ *     G/4 - P  (N unknowns). */
+typedef enum { BI_MODE_CBLOCK = 0, BI_MODE_PEC = 1 } bi_op_mode;
+
+typedef struct {
+    int digits;             /* MLFMA accuracy digits d0 in the excess-bandwidth rule (default 3) */
+    double leaf_box;        /* leaf box edge in wavelengths 2 pi / k0 (default 0.25) */
+    int levels;             /* octree levels including the root; 0 = smallest root that holds the mesh */
+    int interp_order;       /* Lagrange points per angular dimension between levels (default 10) */
+    int precision;          /* bi_precision (default BI_PREC_FP32) */
+    int op_mode;            /* bi_op_mode (default BI_MODE_CBLOCK) */
+    int max_rhs;            /* largest nrhs of one bi_matvec call; sizes the workspace (default 1) */
+    int gmres_restart;      /* GMRES(m) restart length (default 100) */
+    int gmres_maxit;        /* total GMRES iterations per right-hand side (default 1000) */
+    void* stream;           /* cudaStream_t for all work of this handle; NULL = legacy default stream */
+} bi_params;
+
+typedef struct {
+    int64_t n_rwg;              /* N */
+    int64_t n_unknowns;         /* 2N (op_mode 0) or N (op_mode 1) */
+    int levels;                 /* including the root */
+    int leaf_level;             /* levels - 1 */
+    int boxes[32];              /* non-empty boxes per level */
+    int L[32];                  /* multipole truncation per level (0 where no far field) */
+    int K[32];                  /* directions per level, 2 (L+1)^2 */
+    int64_t near_pairs;         /* RWG pairs stored in the near-field block matrix */
+    int64_t interactions[32];   /* box-to-box translations per level */
+    int64_t device_bytes;       /* device memory held by the handle */
+    double root_size;           /* root box edge */
+    double setup_ms;            /* wall time of bi_setup */
+} bi_info_t;
+
+/* Fill *p with the defaults listed above. */
+void bi_default_params(bi_params* p);
+
+/* Build the operator for mesh (verts, tris) at wavenumber k0 (Sec. II.B-D):
+ * validates the mesh, builds RWG functions, the octree, the near-field block matrix
+ * (singular Galerkin integrals in FP64 on the device), leaf radiation/receive
+ * patterns, translation operators and interpolation tables.
+ * verts, tris: host arrays.  digits overrides opt->digits when > 0.  opt may be NULL.
+ * Returns BI_ERR_MESH for an invalid surface, BI_ERR_OOM / BI_ERR_CUDA on device
+ * failure; *out is NULL on failure. */
+int bi_setup(const double* verts, int nv, const int* tris, int nt, double k0, int digits,
+             const bi_params* opt, bi_handle* out);
+
+/* N (RWG count) and the unknown count of the handle's op_mode. */
+int bi_num_unknowns(bi_handle h, int64_t* n_rwg, int64_t* n_unknowns);
+
+/* RWG order of the ABI: edge_vertex_pairs[N][2] (host) = (min vertex, max vertex). */
+int bi_rwg_edges(bi_handle h, int* edge_vertex_pairs);
+
+/* Sizes and timings of the built operator (host struct). */
+int bi_get_info(bi_handle h, bi_info_t* info);
+
+/* y = C x for nrhs column vectors (step 2(a) of Sec. II.E).  x, y: device pointers,
+ * column-major [nrhs][n_unknowns], complex of the handle's precision; x and y must
+ * not overlap.  1 <= nrhs <= max_rhs.  Work is queued on the handle's stream and
+ * the call returns without synchronising. */
+int bi_matvec(bi_handle h, const void* x, void* y, int nrhs);
+
+/* Same product with host buffers: copies x to the device, multiplies, copies y back
+ * and synchronises the stream before returning. */
+int bi_matvec_host(bi_handle h, const void* x, void* y, int nrhs);
+
+/* Plane-wave right-hand sides of Eqs. 49-50 (op_mode 0) or the PEC combined-field
+ * right-hand side <f, E/2 + n x H/2> (op_mode 1), for E = phat exp(-j k0 khat.r),
+ * H = (khat x phat) exp(-j k0 khat.r) (Sec. III).  khat, phat: host [nrhs][3] unit
+ * vectors.  b: device, column-major [nrhs][n_unknowns], handle precision. */
+int bi_rhs_planewave(bi_handle h, const double* khat, const double* phat, int nrhs, void* b);
+
+/* Solve C x = rhs for nrhs right-hand sides with restarted GMRES (Saad and Schultz
+ * 1986; Sec. II.E), x0 = 0, stopping when ||rhs - C x|| / ||rhs|| <= tol for every
+ * column or at gmres_maxit iterations.  rhs, x: device, column-major [nrhs][n_unknowns].
+ * iters, relres: host arrays [nrhs] (may be NULL).  Returns BI_ERR_NOT_CONVERGED when a
+ * column missed tol (x holds the last iterate). */
+int bi_solve(bi_handle h, const void* rhs, void* x, int nrhs, double tol, int* iters, double* relres);
+
+/* Diagnostics: copy an internal device buffer of h to host memory.
+ *   what 0: leaf radiation patterns F [N_tree][K_leaf][2] complex (tree order, theta/phi)
+ *   what 1: leaf twisted receive patterns RX [N_tree][K_leaf][2]
+ *   what 2: translation operators of `level` [343][K_level] (weights folded in)
+ *   what 3: outgoing patterns U of `level` [boxes][K_level][2 nrhs] (last product)
+ *   what 4: incoming patterns V of `level` [boxes][K_level][2 nrhs] (last product)
+ *   what 5: tree order: int32 [N] user RWG index of each tree position
+ * host: buffer of `bytes` bytes; returns BI_ERR_ARG when it is too small or the buffer
+ * does not exist for that level.  Synchronises the handle's stream. */
+int bi_debug_copy(bi_handle h, int what, int level, void* host, int64_t bytes);
+
+/* Text of the last error on h (or of the last failed bi_setup when h is NULL). */
+const char* bi_last_error(bi_handle h);
+
+/* Release every device buffer of h.  NULL is ignored. */
+void bi_destroy(bi_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BI_GB300_H */

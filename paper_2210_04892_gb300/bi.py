@@ -1,0 +1,227 @@
+"""Thin Python binding of the C-ABI in include/bi.h (argument marshalling only).
+
+Every numerical step runs in libbi_gb300.so; PyTorch provides device memory and the
+CUDA stream.  The library is loaded on first use and a missing or unloadable
+library raises -- there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbi_gb300.so")
+
+BI_OK = 0
+BI_ERR_ARG = -1
+BI_ERR_MESH = -2
+BI_ERR_OOM = -3
+BI_ERR_CUDA = -4
+BI_ERR_NOT_CONVERGED = -5
+BI_ERR_TIMEOUT = -6
+BI_ERR_BUSY = -7
+_NAMES = {0: "BI_OK", -1: "BI_ERR_ARG", -2: "BI_ERR_MESH", -3: "BI_ERR_OOM", -4: "BI_ERR_CUDA",
+          -5: "BI_ERR_NOT_CONVERGED", -6: "BI_ERR_TIMEOUT", -7: "BI_ERR_BUSY"}
+
+# entry points declared in include/bi.h
+EXPORTS = ["bi_default_params", "bi_setup", "bi_num_unknowns", "bi_rwg_edges", "bi_get_info", "bi_matvec",
+           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_debug_copy", "bi_last_error", "bi_destroy"]
+
+
+class BIError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_NAMES.get(code, code), msg))
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("digits", ctypes.c_int), ("leaf_box", ctypes.c_double), ("levels", ctypes.c_int),
+                ("interp_order", ctypes.c_int), ("precision", ctypes.c_int), ("op_mode", ctypes.c_int),
+                ("max_rhs", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_rwg", ctypes.c_int64), ("n_unknowns", ctypes.c_int64), ("levels", ctypes.c_int),
+                ("leaf_level", ctypes.c_int), ("boxes", ctypes.c_int * 32), ("L", ctypes.c_int * 32),
+                ("K", ctypes.c_int * 32), ("near_pairs", ctypes.c_int64), ("interactions", ctypes.c_int64 * 32),
+                ("device_bytes", ctypes.c_int64), ("root_size", ctypes.c_double), ("setup_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libbi_gb300.so not built: run paper_2210_04892_gb300/build.py (or __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    vp, i, d, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    L.bi_default_params.argtypes = [ctypes.POINTER(Params)]
+    L.bi_default_params.restype = None
+    L.bi_setup.argtypes = [vp, i, vp, i, d, i, ctypes.POINTER(Params), ctypes.POINTER(vp)]
+    L.bi_num_unknowns.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.bi_rwg_edges.argtypes = [vp, vp]
+    L.bi_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+    L.bi_matvec.argtypes = [vp, vp, vp, i]
+    L.bi_matvec_host.argtypes = [vp, vp, vp, i]
+    L.bi_rhs_planewave.argtypes = [vp, vp, vp, i, vp]
+    L.bi_solve.argtypes = [vp, vp, vp, i, d, vp, vp]
+    L.bi_debug_copy.argtypes = [vp, i, i, vp, i64]
+    L.bi_last_error.argtypes = [vp]
+    L.bi_last_error.restype = ctypes.c_char_p
+    L.bi_destroy.argtypes = [vp]
+    L.bi_destroy.restype = None
+    _lib = L
+    return L
+
+
+def default_params() -> Params:
+    p = Params()
+    load().bi_default_params(ctypes.byref(p))
+    return p
+
+
+def _check(rc, h=None):
+    if rc != BI_OK:
+        raise BIError(rc, load().bi_last_error(h).decode())
+
+
+class Operator:
+    """The boundary-integral operator C (Eqs. 43-46) of one closed surface, on the GPU.
+
+    op_mode 0: C block (2N unknowns, J then M); op_mode 1: PEC combined field (N).
+    precision "fp32" (complex64 vectors) or "fp64" (complex128)."""
+
+    def __init__(self, verts, tris, k0, digits=3, precision="fp32", op_mode=0, leaf_box=0.25, levels=0,
+                 interp_order=10, max_rhs=1, gmres_restart=100, gmres_maxit=1000, stream=None):
+        import torch
+        L = load()
+        p = default_params()
+        p.digits = int(digits)
+        p.leaf_box = float(leaf_box)
+        p.levels = int(levels)
+        p.interp_order = int(interp_order)
+        p.precision = 0 if precision == "fp64" else 1
+        p.op_mode = int(op_mode)
+        p.max_rhs = int(max_rhs)
+        p.gmres_restart = int(gmres_restart)
+        p.gmres_maxit = int(gmres_maxit)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        p.stream = ctypes.c_void_p(stream.cuda_stream)
+        v = np.ascontiguousarray(verts, np.float64)
+        t = np.ascontiguousarray(tris, np.int32)
+        self._v, self._t = v, t
+        h = ctypes.c_void_p()
+        rc = L.bi_setup(v.ctypes.data, len(v), t.ctypes.data, len(t), float(k0), int(digits), ctypes.byref(p),
+                        ctypes.byref(h))
+        _check(rc, None)
+        self.h = h
+        self.params = p
+        self.precision = precision
+        self.cdtype = torch.complex128 if precision == "fp64" else torch.complex64
+        self.np_cdtype = np.complex128 if precision == "fp64" else np.complex64
+        n, nu = ctypes.c_int64(), ctypes.c_int64()
+        L.bi_num_unknowns(h, ctypes.byref(n), ctypes.byref(nu))
+        self.n_rwg, self.n_unknowns = n.value, nu.value
+        self.max_rhs = int(max_rhs)
+        self.k0 = float(k0)
+
+    # ---------------------------------------------------------------- queries
+    def info(self) -> dict:
+        I = Info()
+        _check(load().bi_get_info(self.h, ctypes.byref(I)), self.h)
+        nl = I.levels
+        return dict(n_rwg=I.n_rwg, n_unknowns=I.n_unknowns, levels=nl, leaf_level=I.leaf_level,
+                    boxes=list(I.boxes[:nl]), L=list(I.L[:nl]), K=list(I.K[:nl]), near_pairs=I.near_pairs,
+                    interactions=list(I.interactions[:nl]), device_bytes=I.device_bytes, root_size=I.root_size,
+                    setup_ms=I.setup_ms)
+
+    def edges(self) -> np.ndarray:
+        e = np.zeros((self.n_rwg, 2), np.int32)
+        _check(load().bi_rwg_edges(self.h, e.ctypes.data), self.h)
+        return e
+
+    # ---------------------------------------------------------------- products
+    def _vec(self, x, nrhs=None):
+        import torch
+        if x.dtype != self.cdtype or not x.is_cuda or not x.is_contiguous():
+            raise TypeError("expected a contiguous CUDA %s tensor" % self.cdtype)
+        if x.dim() == 1:
+            x = x.view(1, -1)
+        if x.shape[-1] != self.n_unknowns:
+            raise ValueError("last dimension must be n_unknowns = %d" % self.n_unknowns)
+        return x
+
+    def matvec(self, x, out=None):
+        """y = C x for x of shape [nrhs, n_unknowns] (CUDA complex tensor); queued on the stream."""
+        import torch
+        x = self._vec(x)
+        if out is None:
+            out = torch.empty_like(x)
+        _check(load().bi_matvec(self.h, x.data_ptr(), out.data_ptr(), x.shape[0]), self.h)
+        return out
+
+    def matvec_host(self, x: np.ndarray) -> np.ndarray:
+        """y = C x with host arrays (copies in and out inside the call)."""
+        x = np.ascontiguousarray(np.atleast_2d(x), self.np_cdtype)
+        y = np.empty_like(x)
+        _check(load().bi_matvec_host(self.h, x.ctypes.data, y.ctypes.data, x.shape[0]), self.h)
+        return y
+
+    def rhs_planewave(self, khat, phat):
+        import torch
+        kh = np.ascontiguousarray(np.atleast_2d(khat), np.float64)
+        ph = np.ascontiguousarray(np.atleast_2d(phat), np.float64)
+        b = torch.empty((len(kh), self.n_unknowns), dtype=self.cdtype, device="cuda")
+        _check(load().bi_rhs_planewave(self.h, kh.ctypes.data, ph.ctypes.data, len(kh), b.data_ptr()), self.h)
+        return b
+
+    def solve(self, b, tol=1e-3):
+        """GMRES solve of C x = b; returns (x, iterations, relative residuals)."""
+        import torch
+        b = self._vec(b)
+        x = torch.empty_like(b)
+        R = b.shape[0]
+        its = np.zeros(R, np.int32)
+        rel = np.zeros(R, np.float64)
+        rc = load().bi_solve(self.h, b.data_ptr(), x.data_ptr(), R, float(tol), its.ctypes.data, rel.ctypes.data)
+        if rc not in (BI_OK, BI_ERR_NOT_CONVERGED):
+            _check(rc, self.h)
+        return x, its, rel
+
+    def debug_buffer(self, what, level=0):
+        """Copy of an internal device buffer (diagnostics; see bi_debug_copy in bi.h)."""
+        inf = self.info()
+        E = 2 * self.max_rhs
+        if what in (0, 1):
+            shape = (self.n_rwg, inf["K"][inf["leaf_level"]], 2)
+        elif what == 2:
+            shape = (343, inf["K"][level])
+        elif what in (3, 4):
+            shape = (inf["boxes"][level], inf["K"][level], E)
+        else:
+            out = np.zeros(self.n_rwg, np.int32)
+            _check(load().bi_debug_copy(self.h, what, level, out.ctypes.data, out.nbytes), self.h)
+            return out
+        out = np.zeros(shape, self.np_cdtype)
+        _check(load().bi_debug_copy(self.h, what, level, out.ctypes.data, out.nbytes), self.h)
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().bi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,261 @@
+// C-ABI entry points (include/bi.h): argument checks, handle lifecycle, error text.
+#include <chrono>
+#include <cstring>
+#include <string>
+
+#include "bi_internal.h"
+
+static thread_local std::string g_setup_error;
+
+void* bi_handle_s::alloc(size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw bi_error{BI_ERR_OOM, "cudaMalloc(" + std::to_string(bytes) + " B): " + cudaGetErrorString(e)};
+    }
+    owned.push_back({p, bytes});
+    info.device_bytes += (int64_t)bytes;
+    return p;
+}
+
+extern "C" void bi_default_params(bi_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->digits = 3;
+    p->leaf_box = 0.25;
+    p->levels = 0;
+    p->interp_order = 10;
+    p->precision = BI_PREC_FP32;
+    p->op_mode = BI_MODE_CBLOCK;
+    p->max_rhs = 1;
+    p->gmres_restart = 100;
+    p->gmres_maxit = 1000;
+    p->stream = nullptr;
+}
+
+static void release(bi_handle_s* h) {
+    if (!h) return;
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    for (auto& b : h->owned) cudaFree(b.p);
+    h->owned.clear();
+    if (h->h_pinned) cudaFreeHost(h->h_pinned);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+}
+
+extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, double k0, int digits, const bi_params* opt,
+                        bi_handle* out) {
+    if (!out) return BI_ERR_ARG;
+    *out = nullptr;
+    if (!verts || !tris || nv < 3 || nt < 4 || !(k0 > 0)) {
+        g_setup_error = "bi_setup: null mesh, fewer than 4 triangles, or k0 <= 0";
+        return BI_ERR_ARG;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    bi_handle_s* h = new bi_handle_s();
+    if (opt) h->prm = *opt;
+    else bi_default_params(&h->prm);
+    if (digits > 0) h->prm.digits = digits;
+    bi_params& P = h->prm;
+    if (P.digits < 1 || P.digits > 8 || !(P.leaf_box > 0) || P.interp_order < 2 || P.interp_order > 32 ||
+        (P.precision != 0 && P.precision != 1) || (P.op_mode != 0 && P.op_mode != 1) || P.max_rhs < 1 ||
+        P.max_rhs > 4096 || P.gmres_restart < 1 || P.gmres_maxit < 1 || P.levels < 0 || P.levels > 21) {
+        g_setup_error = "bi_setup: parameter out of range";
+        delete h;
+        return BI_ERR_ARG;
+    }
+    h->k = k0;
+    h->prec = P.precision;
+    h->csize = P.precision == 0 ? 16 : 8;
+    h->nX = P.op_mode == 0 ? 2 : 1;
+    h->max_rhs = P.max_rhs;
+    h->stream = (cudaStream_t)P.stream;
+    const char* env = std::getenv("BI_NO_GRAPHS");
+    h->use_graphs = !(env && env[0] == '1');
+    try {
+        bi_build_rwg(h, verts, nv, tris, nt);
+        h->nun = h->nX * h->N;
+        bi_build_tree(h, verts);
+        bi_build_sampling(h);
+        bi_build_interp(h);
+        CU(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        CU(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        bi_device_geometry(h, verts, tris);
+        bi_fill_near(h);
+        bi_fill_patterns(h);
+        bi_fill_translations(h);
+        bi_alloc_work(h);
+        CU(cudaStreamSynchronize(h->stream));
+        CU(cudaDeviceSynchronize());
+    } catch (const bi_error& e) {
+        g_setup_error = e.msg;
+        release(h);
+        delete h;
+        return e.code;
+    } catch (const std::exception& e) {
+        g_setup_error = std::string("bi_setup: ") + e.what();
+        release(h);
+        delete h;
+        return BI_ERR_OOM;
+    }
+    bi_info_t& I = h->info;
+    I.n_rwg = h->N;
+    I.n_unknowns = h->nun;
+    I.levels = h->nlev;
+    I.leaf_level = h->leaf;
+    for (int l = 0; l < h->nlev && l < 32; ++l) {
+        I.boxes[l] = h->lev[l].nbox;
+        I.L[l] = h->lev[l].L;
+        I.K[l] = h->lev[l].K;
+        I.interactions[l] = h->lev[l].n_inter;
+    }
+    I.near_pairs = h->near_nnz;
+    I.root_size = h->lev[0].a;
+    I.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return BI_OK;
+}
+
+extern "C" int bi_num_unknowns(bi_handle h, int64_t* n_rwg, int64_t* n_unknowns) {
+    if (!h) return BI_ERR_ARG;
+    if (n_rwg) *n_rwg = h->N;
+    if (n_unknowns) *n_unknowns = h->nun;
+    return BI_OK;
+}
+
+extern "C" int bi_rwg_edges(bi_handle h, int* ev) {
+    if (!h || !ev) return BI_ERR_ARG;
+    std::memcpy(ev, h->edges.data(), sizeof(int) * h->edges.size());
+    return BI_OK;
+}
+
+extern "C" int bi_get_info(bi_handle h, bi_info_t* info) {
+    if (!h || !info) return BI_ERR_ARG;
+    *info = h->info;
+    return BI_OK;
+}
+
+template <typename F>
+static int guarded(bi_handle h, F&& f) {
+    try {
+        return f();
+    } catch (const bi_error& e) {
+        h->err = e.msg;
+        return e.code;
+    }
+}
+
+extern "C" int bi_matvec(bi_handle h, const void* x, void* y, int nrhs) {
+    if (!h) return BI_ERR_ARG;
+    if (!x || !y || nrhs < 1 || nrhs > h->max_rhs) {
+        h->err = "bi_matvec: null vector or nrhs outside [1, max_rhs]";
+        return BI_ERR_ARG;
+    }
+    size_t bytes = (size_t)h->nun * nrhs * h->csize;
+    const char* xa = (const char*)x;
+    const char* ya = (const char*)y;
+    if (xa < ya + bytes && ya < xa + bytes) {
+        h->err = "bi_matvec: x and y overlap";
+        return BI_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        bi_matvec_launch(h, x, y, nrhs, h->stream);
+        return (int)BI_OK;
+    });
+}
+
+extern "C" int bi_matvec_host(bi_handle h, const void* x, void* y, int nrhs) {
+    if (!h) return BI_ERR_ARG;
+    if (!x || !y || nrhs < 1 || nrhs > h->max_rhs) {
+        h->err = "bi_matvec_host: null vector or nrhs outside [1, max_rhs]";
+        return BI_ERR_ARG;
+    }
+    size_t bytes = (size_t)h->nun * nrhs * h->csize;
+    return guarded(h, [&] {
+        CU(cudaMemcpyAsync(h->d_sx, x, bytes, cudaMemcpyHostToDevice, h->stream));
+        bi_matvec_launch(h, h->d_sx, h->d_sy, nrhs, h->stream);
+        CU(cudaMemcpyAsync(y, h->d_sy, bytes, cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        return (int)BI_OK;
+    });
+}
+
+extern "C" int bi_rhs_planewave(bi_handle h, const double* khat, const double* phat, int nrhs, void* b) {
+    if (!h) return BI_ERR_ARG;
+    if (!khat || !phat || !b || nrhs < 1) {
+        h->err = "bi_rhs_planewave: null argument or nrhs < 1";
+        return BI_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        bi_rhs_launch(h, khat, phat, nrhs, b);
+        return (int)BI_OK;
+    });
+}
+
+extern "C" int bi_solve(bi_handle h, const void* rhs, void* x, int nrhs, double tol, int* iters, double* relres) {
+    if (!h) return BI_ERR_ARG;
+    if (!rhs || !x || nrhs < 1 || nrhs > h->max_rhs || !(tol > 0)) {
+        h->err = "bi_solve: null vector, nrhs outside [1, max_rhs] or tol <= 0";
+        return BI_ERR_ARG;
+    }
+    return guarded(h, [&] { return bi_gmres(h, rhs, x, nrhs, tol, iters, relres); });
+}
+
+extern "C" const char* bi_last_error(bi_handle h) { return h ? h->err.c_str() : g_setup_error.c_str(); }
+
+extern "C" void bi_destroy(bi_handle h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    release(h);
+    delete h;
+}
+
+extern "C" int bi_debug_copy(bi_handle h, int what, int level, void* host, int64_t bytes) {
+    if (!h || !host || bytes < 0) return BI_ERR_ARG;
+    const void* src = nullptr;
+    size_t need = 0;
+    const bool far = h->leaf >= 2;
+    const bool lev_ok = far && level >= 2 && level <= h->leaf;
+    const int E = 2 * h->max_rhs;
+    switch (what) {
+        case 0:
+        case 1:
+            if (!far) break;
+            src = what == 0 ? h->d_F : h->d_RX;
+            need = (size_t)h->N * h->lev[h->leaf].K * 2 * h->csize;
+            break;
+        case 2:
+            if (!lev_ok) break;
+            src = h->lev[level].d_T;
+            need = (size_t)343 * h->lev[level].K * h->csize;
+            break;
+        case 3:
+        case 4:
+            if (!lev_ok) break;
+            src = what == 3 ? h->lev[level].d_U : h->lev[level].d_V;
+            need = (size_t)h->lev[level].nbox * h->lev[level].K * E * h->csize;
+            break;
+        case 5:
+            src = h->d_perm;
+            need = sizeof(int) * (size_t)h->N;
+            break;
+        default:
+            break;
+    }
+    if (!src || (size_t)bytes < need) {
+        h->err = "bi_debug_copy: no such buffer or host buffer too small";
+        return BI_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        CU(cudaStreamSynchronize(h->stream));
+        CU(cudaMemcpy(host, src, need, cudaMemcpyDeviceToHost));
+        return (int)BI_OK;
+    });
+}

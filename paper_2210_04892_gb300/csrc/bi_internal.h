@@ -1,0 +1,187 @@
+// Internal data structures of the GB300 boundary-integral operator.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bi.h"
+
+#define BI_MAXLEV 24
+
+// Status propagation: every CUDA call is checked, and a failure becomes BI_ERR_CUDA
+// with the call text in the handle's error string.
+struct bi_error {
+    int code;
+    std::string msg;
+};
+
+#define CU(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            throw bi_error{e_ == cudaErrorMemoryAllocation ? BI_ERR_OOM : BI_ERR_CUDA,                 \
+                           std::string(#call) + ": " + cudaGetErrorString(e_)};                        \
+    } while (0)
+
+// Device pointer with a host-side size, freed by the handle.
+struct dbuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// One level of the octree.
+struct level_t {
+    int nbox = 0;
+    double a = 0;                       // box edge
+    std::vector<int> coords;            // [nbox][3]
+    std::vector<double> center;         // [nbox][3]
+    std::vector<uint64_t> key;          // Morton key at this level, sorted
+    std::vector<int> parent;            // index in level-1
+    std::vector<int> child_ptr;         // CSR into level+1 (children contiguous)
+    // far-field sampling (levels >= 2 when the leaf is >= 2)
+    int L = 0, nth = 0, nph = 0, K = 0;
+    std::vector<double> theta, wtheta;  // [nth], theta ascending, Gauss-Legendre in cos(theta)
+    // interaction list (levels >= 2)
+    std::vector<int> il_ptr, il_src, il_off;
+    // device
+    void* d_T = nullptr;                // translation operators [343][K] complex (weights folded)
+    int* d_il_ptr = nullptr;
+    int* d_il_src = nullptr;
+    int* d_il_off = nullptr;
+    int* d_parent = nullptr;
+    int* d_child_ptr = nullptr;
+    int* d_octant = nullptr;            // octant of each box inside its parent
+    void* d_shift = nullptr;            // [8][K] exp(+jk khat.(c_child - c_parent)) for parent level
+    void* d_U = nullptr;                // outgoing patterns [nbox][K][E]
+    void* d_V = nullptr;                // incoming patterns [nbox][K][E]
+    int64_t n_inter = 0;
+};
+
+// Lagrange interpolation between level l+1 (child) and level l (parent).
+struct interp_t {
+    int p_th = 0, p_ph = 0;
+    // forward theta pass: for every parent theta, p_th taps (child theta index, flip, weight)
+    std::vector<int> th_src, th_flip;
+    std::vector<double> th_w;
+    // forward phi pass: for every parent phi, p_ph taps (child phi index, weight)
+    std::vector<int> ph_src;
+    std::vector<double> ph_w;
+    // transposed (anterpolation) lists
+    std::vector<int> tth_ptr, tth_dst, tth_flip;   // per child theta: parent thetas
+    std::vector<double> tth_w;
+    std::vector<int> tph_ptr, tph_dst;             // per child phi: parent phis
+    std::vector<double> tph_w;
+    // device copies (weights stored in the handle precision)
+    int *d_th_src = nullptr, *d_th_flip = nullptr, *d_ph_src = nullptr;
+    void *d_th_w = nullptr, *d_ph_w = nullptr;
+    int *d_tth_ptr = nullptr, *d_tth_dst = nullptr, *d_tth_flip = nullptr, *d_tph_ptr = nullptr, *d_tph_dst = nullptr;
+    void *d_tth_w = nullptr, *d_tph_w = nullptr;
+    void* d_tmp = nullptr;              // per child box: [nbox_child][nth_parent][nph_child][E]
+};
+
+struct bi_handle_s {
+    bi_params prm{};
+    double k = 0;
+    int N = 0, nt = 0, nv = 0;
+    int nun = 0;      // unknowns
+    int nX = 2;       // currents per RWG (2 for op_mode 0, 1 for op_mode 1)
+    int prec = 1;     // 0 double, 1 float
+    size_t csize = 8; // bytes of one complex
+    std::string err;
+    bi_info_t info{};
+
+    cudaStream_t stream = nullptr;      // user stream (not owned)
+    cudaStream_t side = nullptr;        // owned: near field runs here concurrently with the far field
+    cudaStream_t cap = nullptr;         // owned: graph capture origin
+    bool use_graphs = true;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+
+    // host mesh / RWG in user order
+    std::vector<int> edges;             // [N][2]
+    std::vector<int> tplus, tminus, lplus, lminus;
+    std::vector<int> tri_vid_host;      // [nt][3] copy of the mesh triangles
+    double margin = 0.0;                // bandwidth margin: twice the largest RWG overhang
+    std::vector<double> tri_host, tri_n_host, tri_area_host, rwg_len_user;
+    double* d_leaf_center = nullptr;    // [nbox_leaf][3]
+    // tree order
+    std::vector<int> perm;              // tree index -> user index
+    int nlev = 0, leaf = 0;
+    std::vector<level_t> lev;
+    std::vector<interp_t> itp;          // itp[l] maps level l+1 -> l
+    std::vector<int> leaf_start;        // [nbox_leaf + 1]
+    int max_leaf_count = 0;
+    int64_t near_nnz = 0;
+    std::vector<int> near_ptr, near_src;  // per leaf box: near source boxes
+    std::vector<int64_t> near_blk;        // block offset per (box, near index)
+
+    // device data
+    std::vector<dbuf> owned;
+    int* d_perm = nullptr;
+    int* d_leaf_start = nullptr;
+    int* d_leaf_of = nullptr;           // leaf box of each tree RWG
+    int* d_near_ptr = nullptr;
+    int* d_near_src = nullptr;
+    int64_t* d_near_blk = nullptr;
+    void* d_near = nullptr;             // near blocks: per pair (A, B) complex (mode 0) or A (mode 1)
+    int* d_gram_ptr = nullptr;          // mode 0: Gram correction per tree row
+    int* d_gram_col = nullptr;
+    void* d_gram_val = nullptr;         // [nnz][2] real: (G, X)
+    void* d_F = nullptr;                // leaf radiation patterns [N][K][2]
+    void* d_RX = nullptr;               // leaf twisted receive patterns [N][K][2]
+    // geometry on device (tree order for RWG data)
+    double* d_tri = nullptr;            // [nt][9]
+    double* d_tri_n = nullptr;          // [nt][3]
+    double* d_tri_area = nullptr;       // [nt]
+    int* d_tri_vid = nullptr;           // [nt][3]
+    int* d_rwg_t = nullptr;             // tree order [N][2] (T+, T-)
+    int* d_rwg_l = nullptr;             // tree order [N][2] local free vertex
+    double* d_rwg_len = nullptr;        // tree order [N]
+    // work buffers
+    int max_rhs = 1;
+    void* d_xt = nullptr;               // [N][nX][R]
+    void* d_yt = nullptr;               // [N][nX][R]
+    void* d_yfar = nullptr;             // [N][nX][R]
+    void* d_sx = nullptr;               // staging [R][nun] (host API and GMRES matvec input)
+    void* d_sy = nullptr;               // staging [R][nun] (output)
+    void* h_pinned = nullptr;           // pinned host staging
+    size_t h_pinned_bytes = 0;
+
+    // CUDA graph of one matvec per nrhs value (captured lazily)
+    struct graph_entry {
+        int nrhs;
+        const void* x;
+        void* y;
+        cudaGraphExec_t exec;
+    };
+    std::vector<graph_entry> graphs;
+
+    void* alloc(size_t bytes);
+    template <typename T>
+    T* upload(const std::vector<T>& v) {
+        if (v.empty()) return nullptr;
+        T* p = (T*)alloc(sizeof(T) * v.size());
+        CU(cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+        return p;
+    }
+};
+
+// setup stages (host)
+void bi_build_rwg(bi_handle_s* h, const double* V, int nv, const int* T, int nt);
+void bi_build_tree(bi_handle_s* h, const double* V);
+void bi_build_sampling(bi_handle_s* h);
+void bi_build_interp(bi_handle_s* h);
+
+// device stages
+void bi_device_geometry(bi_handle_s* h, const double* V, const int* T);
+void bi_fill_near(bi_handle_s* h);
+void bi_fill_patterns(bi_handle_s* h);
+void bi_fill_translations(bi_handle_s* h);
+void bi_alloc_work(bi_handle_s* h);
+void bi_matvec_launch(bi_handle_s* h, const void* x, void* y, int nrhs, cudaStream_t s);
+void bi_rhs_launch(bi_handle_s* h, const double* khat, const double* phat, int nrhs, void* b);
+int bi_gmres(bi_handle_s* h, const void* rhs, void* x, int nrhs, double tol, int* iters, double* relres);
+
+// numerical helpers shared by the host setup files of the library (not by the oracle)
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);  // nodes in (-1, 1)

@@ -1,0 +1,199 @@
+"""GPU parity tests: the CUDA path through the C-ABI against the CPU FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_04892_gb300.inputs import SEED_BASE, complex_gaussian, icosphere, sample_rows
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+K0 = 2 * np.pi
+
+
+@pytest.fixture(scope="module")
+def bi():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2210_04892_gb300 import bi as mod
+    mod.load()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def sphere_c1():
+    v, t = icosphere(8, 0.5)
+    return v, t
+
+
+@pytest.fixture(scope="module")
+def Z_c1(sphere_c1):
+    v, t = sphere_c1
+    return {0: oracle.fill(v, t, K0, 0), 1: oracle.fill(v, t, K0, 1)}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_rwg_order_matches_oracle(bi, sphere_c1):
+    v, t = sphere_c1
+    op = bi.Operator(v, t, K0)
+    assert np.array_equal(op.edges(), oracle.rwg(v, t)["edges"])
+    op.close()
+
+
+def test_invalid_mesh_rejected(bi):
+    v, t = icosphere(2, 0.5)
+    with pytest.raises(bi.BIError) as e:
+        bi.Operator(v, t[:-1], K0)
+    assert e.value.code == bi.BI_ERR_MESH
+    t2 = t.copy()
+    t2[3] = t2[3][[0, 2, 1]]
+    with pytest.raises(bi.BIError) as e:
+        bi.Operator(v, t2, K0)
+    assert e.value.code == bi.BI_ERR_MESH
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_near_field_only_matches_dense_oracle(bi, sphere_c1, Z_c1, mode):
+    """With a 0.5-wavelength leaf the 1-wavelength sphere has no far field: the product is
+    the GPU's FP64 singular/near-singular Galerkin integrals alone."""
+    v, t = sphere_c1
+    op = bi.Operator(v, t, K0, precision="fp64", op_mode=mode, leaf_box=0.5, max_rhs=2)
+    assert op.info()["leaf_level"] < 2
+    x = complex_gaussian(op.n_unknowns, 2, seed=SEED_BASE)
+    y = op.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = x @ Z_c1[mode].T
+    assert rel(y, ref) < 2e-5
+    op.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_c1_mlfma_matches_dense_oracle(bi, sphere_c1, Z_c1, precision, mode):
+    """PEC sphere r = 0.5 lambda, 1280 triangles, 3-level MLFMA at 3 digits; x = seeded
+    complex Gaussian plus the plane wave along -z polarised along x (Eqs. 49-50)."""
+    v, t = sphere_c1
+    op = bi.Operator(v, t, K0, digits=3, precision=precision, op_mode=mode, max_rhs=2)
+    assert op.info()["levels"] == 3
+    x0 = complex_gaussian(op.n_unknowns, 1, seed=SEED_BASE)
+    b = oracle.rhs_planewave(v, t, K0, mode, [0, 0, -1.0], [1.0, 0, 0])
+    x = np.concatenate([x0, b], 0)
+    xt = torch.from_numpy(x.astype(op.np_cdtype)).cuda()
+    y = op.matvec(xt).cpu().numpy()
+    ref = x @ Z_c1[mode].T
+    for r in range(2):
+        assert rel(y[r], ref[r]) < 1e-3, (r, rel(y[r], ref[r]))
+    op.close()
+
+
+def test_c1b_small_leaf(bi, sphere_c1, Z_c1):
+    """Same sphere with a 0.125-wavelength leaf (4 levels, interpolation between levels).
+    Boxes this small sit at the low-frequency limit of the diagonal translation, so the
+    4-digit sampling rule is needed to stay within 1e-3."""
+    v, t = sphere_c1
+    op = bi.Operator(v, t, K0, digits=4, precision="fp64", op_mode=0, leaf_box=0.125, max_rhs=1)
+    assert op.info()["levels"] == 4
+    x = complex_gaussian(op.n_unknowns, 1, seed=SEED_BASE)
+    y = op.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y, x @ Z_c1[0].T) < 1e-3
+    op.close()
+
+
+def test_four_level_sphere_sampled_rows(bi):
+    """Sphere r = 1 lambda (5120 triangles), 4 levels at the default 0.25-lambda leaf:
+    interpolation 0.25 -> 0.5 lambda and anterpolation back; 192 sampled rows."""
+    v, t = icosphere(16, 1.0)
+    op = bi.Operator(v, t, K0, digits=3, precision="fp64", op_mode=0, max_rhs=1)
+    assert op.info()["levels"] == 4
+    x = complex_gaussian(op.n_unknowns, 1, seed=SEED_BASE + 3)
+    y = op.matvec(torch.from_numpy(x).cuda()).cpu().numpy()[0]
+    rows = sample_rows(op.n_unknowns, 192, seed=SEED_BASE + 13)
+    ref = oracle.rows(v, t, K0, 0, rows) @ x[0]
+    assert rel(y[rows], ref) < 1e-3
+    op.close()
+
+
+def test_translation_operators_vs_series(bi, sphere_c1):
+    """Leaf translation operators T(khat; X) w(khat) for all 316 far offsets against the
+    series evaluated with scipy's spherical Bessel functions."""
+    from scipy import special
+    v, t = sphere_c1
+    op = bi.Operator(v, t, K0, precision="fp64", max_rhs=1)
+    inf = op.info()
+    lf = inf["leaf_level"]
+    L = inf["L"][lf]
+    T = op.debug_buffer(2, lf)
+    xg, wg = np.polynomial.legendre.leggauss(L + 1)
+    o = np.argsort(-xg)
+    th, wt = np.arccos(xg[o]), wg[o]
+    nph = 2 * (L + 1)
+    TH, PH = np.meshgrid(th, 2 * np.pi * np.arange(nph) / nph, indexing="ij")
+    kh = np.stack([np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)], -1).reshape(-1, 3)
+    W = (wt[:, None] * np.ones(nph)[None] * 2 * np.pi / nph).ravel()
+    a = inf["root_size"] / 2 ** lf
+    worst = 0.0
+    for oi in range(343):
+        off = np.array([oi // 49 - 3, (oi // 7) % 7 - 3, oi % 7 - 3])
+        if np.abs(off).max() <= 1:
+            assert np.abs(T[oi]).max() == 0
+            continue
+        X = off * a
+        Xn = np.linalg.norm(X)
+        cg = kh @ (X / Xn)
+        ref = np.zeros(len(kh), complex)
+        for l in range(L + 1):
+            hl = special.spherical_jn(l, K0 * Xn) - 1j * special.spherical_yn(l, K0 * Xn)
+            ref += (-1j) ** l * (2 * l + 1) * hl * special.eval_legendre(l, cg)
+        worst = max(worst, rel(T[oi], ref * W))
+    assert worst < 1e-10, worst
+    op.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_rhs_planewave_matches_oracle(bi, sphere_c1, mode):
+    v, t = sphere_c1
+    op = bi.Operator(v, t, K0, precision="fp64", op_mode=mode, max_rhs=2)
+    kh = np.array([[0, 0, -1.0], [np.sin(1.0), 0, np.cos(1.0)]])
+    ph = np.array([[1.0, 0, 0], [np.cos(1.0), 0, -np.sin(1.0)]])
+    b = op.rhs_planewave(kh, ph).cpu().numpy()
+    ref = oracle.rhs_planewave(v, t, K0, mode, kh, ph)
+    assert rel(b, ref) < 1e-6
+    op.close()
+
+
+def test_matvec_host_equals_device(bi, sphere_c1):
+    v, t = sphere_c1
+    op = bi.Operator(v, t, K0, max_rhs=3)
+    x = complex_gaussian(op.n_unknowns, 3, seed=5).astype(np.complex64)
+    yd = op.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    yh = op.matvec_host(x)
+    assert np.array_equal(yd, yh)
+    op.close()
+
+
+def test_pec_solve_matches_dense_solution(bi, sphere_c1, Z_c1):
+    v, t = sphere_c1
+    op = bi.Operator(v, t, K0, precision="fp32", op_mode=1, max_rhs=1)
+    b = op.rhs_planewave([0, 0, 1.0], [1.0, 0, 0])
+    x, its, relres = op.solve(b, tol=1e-5)
+    assert relres[0] <= 1e-5 * 1.001
+    xr = np.linalg.solve(Z_c1[1], b.cpu().numpy()[0].astype(np.complex128))
+    assert rel(x.cpu().numpy()[0], xr) < 1e-3
+    op.close()
+
+
+def test_c2_sampled_rows(bi):
+    """Coated-sphere outer surface r = 2 lambda (20480 triangles, 61440 unknowns), 5 levels,
+    FP32, one RHS: 96 seeded sampled rows computed one by one by the oracle."""
+    v, t = icosphere(32, 2.0)
+    op = bi.Operator(v, t, K0, digits=3, precision="fp32", op_mode=0, max_rhs=1)
+    assert op.info()["levels"] == 5
+    x = complex_gaussian(op.n_unknowns, 1, seed=SEED_BASE + 1)
+    y = op.matvec(torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()[0]
+    rows = sample_rows(op.n_unknowns, 96, seed=SEED_BASE + 11)
+    Zr = oracle.rows(v, t, K0, 0, rows)
+    ref = Zr @ x[0]
+    assert rel(y[rows], ref) < 1e-3
+    op.close()
