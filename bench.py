@@ -1,0 +1,304 @@
+#!/usr/bin/env python
+"""Benchmark of the boundary-integral matvec (step 2(a) of the hybrid solver, Sec. II.E).
+
+Workload (default): dielectric-coated-sphere outer surface, radius 2 wavelengths,
+geodesic mesh of 20,480 triangles (30,720 RWG per current, 61,440 unknowns J + M),
+5-level MLFMA at 3 digits, FP32 complex, one seeded complex-Gaussian right-hand
+side, op_mode 0 (the C block of Eq. 42).  One step = one full product y = C x.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU FP64 oracle (plain
+dense Galerkin rows, Eqs. 43-46) on the host cores on a bounded sample of rows of the
+same matrix.  Multi-GPU runs are independent replicas (one operator per GPU, no
+data exchange): value = total unknowns*RHS over the max time across ranks.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BI matvec unknowns*RHS/s at rel.err<=1e-3 vs FP64"
+UNIT = "unknowns*RHS/s"
+WORKLOAD = "coated-sphere outer surface r=2 lambda, 20480 triangles, 61440 unknowns (J+M), 5-level MLFMA 3 digits, FP32, 1 RHS"
+K0 = 2 * np.pi
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-rows", type=int, default=256, help="oracle rows in the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_mesh():
+    from paper_2210_04892_gb300.inputs import workload
+    v, t, meta = workload("sphere_r2_nu32")
+    return v, t, meta
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------- algorithmic bytes
+def stage_bytes(info, nrhs, csize=8):
+    """Algorithmic bytes of each stage of one product (every array touched once)."""
+    N, nun = info["n_rwg"], info["n_unknowns"]
+    lf = info["leaf_level"]
+    E = 2 * nrhs
+    vec = nun * nrhs * csize
+    b = {}
+    b["gather"] = 2 * vec + 4 * N
+    b["near"] = info["near_pairs"] * 2 * csize + 2 * vec          # (A, B) per pair, x read, y write
+    Kl = info["K"][lf]
+    pat = N * Kl * 2 * csize                                         # one pattern array
+    far = lambda l: info["boxes"][l] * info["K"][l] * E * csize
+    b["aggregate"] = pat + vec + far(lf)
+    b["interpolate"] = sum(far(l + 1) + far(l) for l in range(2, lf))
+    b["translate"] = sum(2 * far(l) + 343 * info["K"][l] * csize for l in range(2, lf + 1))
+    b["anterpolate"] = sum(far(l) + 2 * far(l + 1) for l in range(2, lf))
+    b["receive"] = 2 * pat + far(lf) + vec
+    b["scatter"] = 3 * vec + 4 * N
+    return b
+
+
+def launches_per_step(info):
+    lf = info["leaf_level"]
+    if lf < 2:
+        return 3
+    return 1 + 1 + 1 + 2 * (lf - 2) + (lf - 1) + 2 * (lf - 2) + 1 + 1
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------- CPU oracle
+def oracle_rows_rate(v, t, rows, x=None, y=None):
+    """Time the oracle computing the given rows of the C block; returns (rows/s, seconds,
+    rel. error of y on those rows when y is given)."""
+    import oracle
+    t0 = time.perf_counter()
+    Z = oracle.rows(v, t, K0, 0, rows)
+    ref = Z @ x if x is not None else None
+    dt = time.perf_counter() - t0
+    err = None
+    if y is not None:
+        err = float(np.linalg.norm(y[rows] - ref) / np.linalg.norm(ref))
+    return len(rows) / dt, dt, err
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2210_04892_gb300.inputs import SEED_BASE, complex_gaussian, sample_rows
+    v, t, _ = workload_mesh()
+    nun = oracle.num_unknowns(v, t, 0)
+    x = complex_gaussian(nun, 1, seed=SEED_BASE + 1)[0]
+    # calibrate rows per step so the whole run stays within a few minutes
+    probe = sample_rows(nun, 8, seed=SEED_BASE + 21)
+    rate, _, _ = oracle_rows_rate(v, t, probe, x)
+    budget = 150.0
+    per_step = max(1, int(budget * rate / max(1, args.steps + args.warmup)))
+    per_step = min(per_step, 512)
+    rng_rows = [sample_rows(nun, per_step, seed=SEED_BASE + 100 + s) for s in range(args.steps + args.warmup)]
+    for s in range(args.warmup):
+        oracle_rows_rate(v, t, rng_rows[s], x)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle_rows_rate(v, t, rng_rows[args.warmup + s], x)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt          # rows of C x per second = unknowns*RHS/s
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64 complex)",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "host cores"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                            "sample": "%d seeded rows of C per step, matrix-free dense Galerkin rows times x" % per_step},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2210_04892_gb300 import bi
+    from paper_2210_04892_gb300.inputs import SEED_BASE, complex_gaussian, sample_rows
+    v, t, meta = workload_mesh()
+    op = bi.Operator(v, t, K0, digits=3, precision="fp32", op_mode=0, max_rhs=1)
+    info = op.info()
+    nun = op.n_unknowns
+    R = 1
+    x_np = complex_gaussian(nun, R, seed=SEED_BASE + 1).astype(np.complex64)
+    x = torch.from_numpy(x_np).cuda()
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        op.matvec(x, out=y)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        op.matvec(x, out=y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * nun * R / (ms * 1e-3)
+
+    # end to end through the public host-buffer entry point (pinned host memory)
+    xh = torch.from_numpy(x_np).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    for _ in range(max(3, args.warmup // 4)):
+        op.matvec_host(xh, yh)
+    n_e2e = max(10, min(args.steps, 500))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        op.matvec_host(xh, yh)
+    t_e2e = (time.perf_counter() - t0) / n_e2e
+    if dist:
+        tt = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e = {"value": world * nun * R / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 8),
+           "d2h_bytes_per_step": int(yh.numel() * 8), "ms_per_step": 1e3 * t_e2e}
+
+    # live per-stage timing (serialised stages, CUDA events on the handle's stream)
+    stages = op.profile_stages(x, reps=50)
+    sb = stage_bytes(info, R)
+    dom = max((k for k in stages if k in sb), key=lambda k: stages[k])
+    peak, peak_kind = peaks()
+    achieved = sb[dom] / (stages[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                "algorithmic_bytes": sb[dom], "stage_ms": stages,
+                "step_frac": (sum(sb.values()) / (ms * 1e-3) / 1e9) / peak}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c64 (fp32 complex)", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n_unknowns": nun, "nrhs": R, "levels": info["levels"],
+                      "near_pairs": info["near_pairs"], "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "inputs larger than L2 (near blocks + patterns %.0f MB per step)" %
+                            ((sb["near"] + sb["receive"]) / 1e6)},
+           "roofline": roofline, "e2e": e2e, "clocks": clocks,
+           "gpu_launches": launches_per_step(info) * args.steps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        rows = sample_rows(nun, args.cpu_rows, seed=SEED_BASE + 11)
+        yv = y.cpu().numpy()[0].astype(np.complex128)
+        rate, dt, err = oracle_rows_rate(v, t, rows, x_np[0].astype(np.complex128), yv)
+        out["cpu_baseline"] = {"value": rate * R, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                               "sample": "%d seeded rows of C (matrix-free FP64 dense Galerkin rows times x), %.1f s"
+                                         % (len(rows), dt)}
+        out["rel_err_vs_oracle"] = err
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    op.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

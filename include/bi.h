@@ -146,6 +146,14 @@ int bi_solve(bi_handle h, const void* rhs, void* x, int nrhs, double tol, int* i
  * does not exist for that level.  Synchronises the handle's stream. */
 int bi_debug_copy(bi_handle h, int what, int level, void* host, int64_t bytes);
 
+/* Diagnostics: device time of each stage of one product, in milliseconds, averaged over
+ * `reps` products.  Stages run one after another on the handle's stream (no graph and no
+ * near/far overlap), bracketed by CUDA events; stage_ms[8] = gather, near, aggregate,
+ * interpolate, translate, anterpolate, receive, scatter (names from bi_stage_name).
+ * x, y as for bi_matvec.  Synchronises the stream. */
+int bi_profile_stages(bi_handle h, const void* x, void* y, int nrhs, int reps, double* stage_ms);
+const char* bi_stage_name(int i);
+
 /* Text of the last error on h (or of the last failed bi_setup when h is NULL). */
 const char* bi_last_error(bi_handle h);
 

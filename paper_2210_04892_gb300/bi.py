@@ -27,7 +27,8 @@ _NAMES = {0: "BI_OK", -1: "BI_ERR_ARG", -2: "BI_ERR_MESH", -3: "BI_ERR_OOM", -4:
 
 # entry points declared in include/bi.h
 EXPORTS = ["bi_default_params", "bi_setup", "bi_num_unknowns", "bi_rwg_edges", "bi_get_info", "bi_matvec",
-           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_debug_copy", "bi_last_error", "bi_destroy"]
+           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_debug_copy", "bi_profile_stages", "bi_stage_name", "bi_last_error",
+           "bi_destroy"]
 
 
 class BIError(RuntimeError):
@@ -73,6 +74,9 @@ def load(path: str = LIB_PATH):
     L.bi_rhs_planewave.argtypes = [vp, vp, vp, i, vp]
     L.bi_solve.argtypes = [vp, vp, vp, i, d, vp, vp]
     L.bi_debug_copy.argtypes = [vp, i, i, vp, i64]
+    L.bi_profile_stages.argtypes = [vp, vp, vp, i, i, vp]
+    L.bi_stage_name.argtypes = [i]
+    L.bi_stage_name.restype = ctypes.c_char_p
     L.bi_last_error.argtypes = [vp]
     L.bi_last_error.restype = ctypes.c_char_p
     L.bi_destroy.argtypes = [vp]
@@ -169,10 +173,18 @@ class Operator:
         _check(load().bi_matvec(self.h, x.data_ptr(), out.data_ptr(), x.shape[0]), self.h)
         return out
 
-    def matvec_host(self, x: np.ndarray) -> np.ndarray:
-        """y = C x with host arrays (copies in and out inside the call)."""
+    def matvec_host(self, x, out=None):
+        """y = C x with host buffers (numpy arrays, or CPU torch tensors -- pinned for
+        asynchronous copies); the call copies in, multiplies, copies out and synchronises."""
+        if hasattr(x, "data_ptr"):
+            if x.is_cuda or not x.is_contiguous() or x.shape[-1] != self.n_unknowns:
+                raise TypeError("expected a contiguous CPU tensor with last dimension n_unknowns")
+            y = out if out is not None else x.new_empty(x.shape)
+            n = 1 if x.dim() == 1 else x.shape[0]
+            _check(load().bi_matvec_host(self.h, x.data_ptr(), y.data_ptr(), n), self.h)
+            return y
         x = np.ascontiguousarray(np.atleast_2d(x), self.np_cdtype)
-        y = np.empty_like(x)
+        y = np.empty_like(x) if out is None else out
         _check(load().bi_matvec_host(self.h, x.ctypes.data, y.ctypes.data, x.shape[0]), self.h)
         return y
 
@@ -196,6 +208,16 @@ class Operator:
         if rc not in (BI_OK, BI_ERR_NOT_CONVERGED):
             _check(rc, self.h)
         return x, its, rel
+
+    def profile_stages(self, x, reps=10):
+        """Mean device milliseconds of each stage of one product (serialised stages)."""
+        x = self._vec(x)
+        import torch
+        y = torch.empty_like(x)
+        ms = np.zeros(8, np.float64)
+        _check(load().bi_profile_stages(self.h, x.data_ptr(), y.data_ptr(), x.shape[0], int(reps), ms.ctypes.data),
+               self.h)
+        return {load().bi_stage_name(i).decode(): float(ms[i]) for i in range(8)}
 
     def debug_buffer(self, what, level=0):
         """Copy of an internal device buffer (diagnostics; see bi_debug_copy in bi.h)."""

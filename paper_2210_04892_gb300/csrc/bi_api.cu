@@ -259,3 +259,17 @@ extern "C" int bi_debug_copy(bi_handle h, int what, int level, void* host, int64
         return (int)BI_OK;
     });
 }
+
+extern "C" int bi_profile_stages(bi_handle h, const void* x, void* y, int nrhs, int reps, double* stage_ms) {
+    if (!h) return BI_ERR_ARG;
+    if (!x || !y || !stage_ms || nrhs < 1 || nrhs > h->max_rhs || reps < 1) {
+        h->err = "bi_profile_stages: null argument, nrhs outside [1, max_rhs] or reps < 1";
+        return BI_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        bi_profile_impl(h, x, y, nrhs, reps, stage_ms);
+        return (int)BI_OK;
+    });
+}
+
+extern "C" const char* bi_stage_name(int i) { return bi_stage_name_impl(i); }

@@ -9,6 +9,7 @@
 #include "bi.h"
 
 #define BI_MAXLEV 24
+#define BI_NSTAGES 8
 
 // Status propagation: every CUDA call is checked, and a failure becomes BI_ERR_CUDA
 // with the call text in the handle's error string.
@@ -181,6 +182,8 @@ void bi_fill_translations(bi_handle_s* h);
 void bi_alloc_work(bi_handle_s* h);
 void bi_matvec_launch(bi_handle_s* h, const void* x, void* y, int nrhs, cudaStream_t s);
 void bi_rhs_launch(bi_handle_s* h, const double* khat, const double* phat, int nrhs, void* b);
+void bi_profile_impl(bi_handle_s* h, const void* x, void* y, int nrhs, int reps, double* ms);
+const char* bi_stage_name_impl(int i);
 int bi_gmres(bi_handle_s* h, const void* rhs, void* x, int nrhs, double tol, int* iters, double* relres);
 
 // numerical helpers shared by the host setup files of the library (not by the oracle)

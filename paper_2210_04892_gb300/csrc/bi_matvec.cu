@@ -358,8 +358,12 @@ __global__ void k_receive(int N, int K, int R, const int* __restrict__ leaf_of, 
 
 inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) / th); }
 
+// Stage boundaries for bi_profile_stages: when ev is non-null every stage runs on s (no
+// overlap) and ev[i] is recorded after stage i; ev[-1] must be recorded by the caller.
 template <typename T>
-void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s, cudaStream_t side) {
+void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s, cudaStream_t side,
+                cudaEvent_t* ev = nullptr) {
+    if (ev) side = s;
     const int N = h->N, nX = h->nX, nun = h->nun;
     const int E = 2 * R;
     const int th = 256;
@@ -372,9 +376,12 @@ void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s,
     int64_t nvec = (int64_t)N * nX * R;
     k_gather_x<T><<<nblk(nvec, th), th, 0, s>>>(N, nX, R, nun, h->d_perm, x, xt);
     CU(cudaGetLastError());
+    if (ev) CU(cudaEventRecord(ev[0], s));
     // near field on the side stream, concurrent with the far field
-    CU(cudaEventRecord(h->ev_fork, s));
-    CU(cudaStreamWaitEvent(side, h->ev_fork, 0));
+    if (!ev) {
+        CU(cudaEventRecord(h->ev_fork, s));
+        CU(cudaStreamWaitEvent(side, h->ev_fork, 0));
+    }
     const level_t& LF = h->lev[h->leaf];
     if (h->prm.op_mode == 0)
         k_near<T, 0><<<LF.nbox, 128, 0, side>>>(R, h->d_leaf_start, h->d_near_ptr, h->d_near_src, h->d_near_blk,
@@ -383,7 +390,8 @@ void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s,
         k_near<T, 1><<<LF.nbox, 128, 0, side>>>(R, h->d_leaf_start, h->d_near_ptr, h->d_near_src, h->d_near_blk,
                                                 (const C*)h->d_near, nullptr, nullptr, nullptr, xt, yt);
     CU(cudaGetLastError());
-    CU(cudaEventRecord(h->ev_join, side));
+    if (ev) CU(cudaEventRecord(ev[1], s));
+    else CU(cudaEventRecord(h->ev_join, side));
     const bool far = h->leaf >= 2;
     if (far) {
         const int lf = h->leaf;
@@ -397,6 +405,7 @@ void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s,
                 k_aggregate<T, 1><<<g, th, 0, s>>>(L.K, R, h->d_leaf_start, (const C*)h->d_F, xt, (C*)L.d_U);
             CU(cudaGetLastError());
         }
+        if (ev) CU(cudaEventRecord(ev[2], s));
         // upward pass
         for (int l = lf - 1; l >= 2; --l) {
             level_t& P = h->lev[l];
@@ -411,6 +420,7 @@ void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s,
                                               Cc.d_octant, (const C*)P.d_shift, (const C*)I.d_tmp, (C*)P.d_U);
             CU(cudaGetLastError());
         }
+        if (ev) CU(cudaEventRecord(ev[3], s));
         // translations on every level
         for (int l = 2; l <= lf; ++l) {
             level_t& L = h->lev[l];
@@ -419,6 +429,7 @@ void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s,
                                             (C*)L.d_V);
             CU(cudaGetLastError());
         }
+        if (ev) CU(cudaEventRecord(ev[4], s));
         // downward pass
         for (int l = 2; l < lf; ++l) {
             level_t& P = h->lev[l];
@@ -433,6 +444,7 @@ void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s,
                                                 (const T*)I.d_tth_w, (const C*)I.d_tmp, (C*)Cc.d_V);
             CU(cudaGetLastError());
         }
+        if (ev) CU(cudaEventRecord(ev[5], s));
         // leaf receive
         {
             level_t& L = h->lev[lf];
@@ -448,9 +460,16 @@ void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s,
             CU(cudaGetLastError());
         }
     }
-    CU(cudaStreamWaitEvent(s, h->ev_join, 0));
+    if (ev) {
+        if (!far)
+            for (int i = 2; i <= 5; ++i) CU(cudaEventRecord(ev[i], s));
+        CU(cudaEventRecord(ev[6], s));
+    } else {
+        CU(cudaStreamWaitEvent(s, h->ev_join, 0));
+    }
     k_scatter_y<T><<<nblk(nvec, th), th, 0, s>>>(N, nX, R, nun, h->d_perm, yt, far ? yf : nullptr, y);
     CU(cudaGetLastError());
+    if (ev) CU(cudaEventRecord(ev[7], s));
 }
 
 }  // namespace
@@ -492,4 +511,29 @@ void bi_matvec_launch(bi_handle_s* h, const void* x, void* y, int nrhs, cudaStre
     }
     h->graphs.push_back({nrhs, x, y, exec});
     CU(cudaGraphLaunch(exec, s));
+}
+
+static const char* kStageNames[BI_NSTAGES] = {"gather", "near", "aggregate", "interpolate", "translate",
+                                              "anterpolate", "receive", "scatter"};
+
+const char* bi_stage_name_impl(int i) { return (i >= 0 && i < BI_NSTAGES) ? kStageNames[i] : ""; }
+
+// Per-stage device time of `reps` products (serialised stages, CUDA events on the handle's stream).
+void bi_profile_impl(bi_handle_s* h, const void* x, void* y, int nrhs, int reps, double* ms) {
+    cudaEvent_t ev[BI_NSTAGES + 1];
+    for (auto& e : ev) CU(cudaEventCreate(&e));
+    for (int i = 0; i < BI_NSTAGES; ++i) ms[i] = 0.0;
+    cudaStream_t s = h->stream;
+    for (int r = 0; r < reps; ++r) {
+        CU(cudaEventRecord(ev[0], s));
+        if (h->prec == 0) launch_all<double>(h, x, y, nrhs, s, s, ev + 1);
+        else launch_all<float>(h, x, y, nrhs, s, s, ev + 1);
+        CU(cudaEventSynchronize(ev[BI_NSTAGES]));
+        for (int i = 0; i < BI_NSTAGES; ++i) {
+            float t = 0;
+            CU(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+            ms[i] += t / reps;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
 }

@@ -311,10 +311,8 @@ int bi_gmres(bi_handle_s* h, const void* rhs, void* xout, int R, double tol, int
             else k_cvt_from<float><<<nb(nv, th), th, 0, s>>>(nv, (const float*)yout, out);
         };
         int total = 0;
+        std::vector<double> last_true(R, 1e300);
         while (total < maxit) {
-            bool all = true;
-            for (int r = 0; r < R; ++r) all = all && done[r];
-            if (all) break;
             // r0 = b - A x
             matvec64(x64, w);
             k_residual<<<nb(nv, th), th, 0, s>>>(nv, b64, w, w);
@@ -325,11 +323,20 @@ int bi_gmres(bi_handle_s* h, const void* rhs, void* xout, int R, double tol, int
             CU(cudaStreamSynchronize(s));
             std::vector<z2> g0((size_t)R * (m + 1), z2{0, 0});
             std::vector<int> a(R), kcols(R, 0);
+            // the true residual decides at every restart; a column whose true residual did not
+            // drop by 10% over a whole cycle has stagnated (matvec rounding floor) and stops
+            bool any_left = false;
             for (int r = 0; r < R; ++r) {
                 g0[(size_t)r * (m + 1)] = z2{beta[r], 0};
-                if (!done[r] && beta[r] / std::max(bnorm[r], 1e-300) <= tol) done[r] = 1;
-                a[r] = !done[r];
+                double rel = beta[r] / std::max(bnorm[r], 1e-300);
+                if (bnorm[r] == 0.0 || rel <= tol) done[r] = 1;
+                else if (done[r] == 0 && rel > 0.9 * last_true[r]) done[r] = 2;  // stagnated
+                else if (done[r] == 1) done[r] = 0;                              // estimate was optimistic
+                last_true[r] = rel;
+                a[r] = (done[r] == 0);
+                any_left = any_left || a[r];
             }
+            if (!any_left) break;
             CU(cudaMemcpyAsync(g, g0.data(), sizeof(z2) * g0.size(), cudaMemcpyHostToDevice, s));
             CU(cudaMemcpyAsync(act, a.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s));
             int j = 0;
@@ -359,7 +366,7 @@ int bi_gmres(bi_handle_s* h, const void* rhs, void* xout, int R, double tol, int
                     if (a[r]) {
                         kcols[r] = j + 1;
                         its[r] += 1;
-                        if (rr[r] / std::max(bnorm[r], 1e-300) <= tol) { a[r] = 0; done[r] = 1; }
+                        if (rr[r] / std::max(bnorm[r], 1e-300) <= tol) a[r] = 0;
                     }
                 CU(cudaMemcpyAsync(act, a.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s));
             }
@@ -367,7 +374,6 @@ int bi_gmres(bi_handle_s* h, const void* rhs, void* xout, int R, double tol, int
             k_backsolve<<<nb(R, 64), 64, 0, s>>>(R, m, H, g, nk, yv);
             k_update_x<<<nb(nv, th), th, 0, s>>>(nun, R, m, V, nv, yv, nk, x64);
             CU(cudaStreamSynchronize(s));
-            if (j == 0) break;
         }
         // true residual
         matvec64(x64, w);
