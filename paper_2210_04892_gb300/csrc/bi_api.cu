@@ -46,6 +46,11 @@ static void release(bi_handle_s* h) {
     if (h->cap) cudaStreamDestroy(h->cap);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    for (int l = 0; l < BI_MAXLEV; ++l) {
+        if (h->tstream[l]) cudaStreamDestroy(h->tstream[l]);
+        if (h->ev_tfork[l]) cudaEventDestroy(h->ev_tfork[l]);
+        if (h->ev_tjoin[l]) cudaEventDestroy(h->ev_tjoin[l]);
+    }
 }
 
 extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, double k0, int digits, const bi_params* opt,
@@ -77,6 +82,8 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
     h->stream = (cudaStream_t)P.stream;
     const char* env = std::getenv("BI_NO_GRAPHS");
     h->use_graphs = !(env && env[0] == '1');
+    const char* env2 = std::getenv("BI_TWO_PASS");
+    h->use_fast = !(env2 && env2[0] == '1');
     try {
         bi_build_rwg(h, verts, nv, tris, nt);
         h->nun = h->nX * h->N;
@@ -87,6 +94,16 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
         CU(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
         CU(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        for (int l = 3; l < h->nlev && l < BI_MAXLEV; ++l) {
+            CU(cudaStreamCreateWithFlags(&h->tstream[l], cudaStreamNonBlocking));
+            CU(cudaEventCreateWithFlags(&h->ev_tfork[l], cudaEventDisableTiming));
+            CU(cudaEventCreateWithFlags(&h->ev_tjoin[l], cudaEventDisableTiming));
+        }
+        {
+            int dev = 0;
+            CU(cudaGetDevice(&dev));
+            CU(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+        }
         bi_device_geometry(h, verts, tris);
         bi_fill_near(h);
         bi_fill_patterns(h);

@@ -96,7 +96,12 @@ struct bi_handle_s {
     cudaStream_t stream = nullptr;      // user stream (not owned)
     cudaStream_t side = nullptr;        // owned: near field runs here concurrently with the far field
     cudaStream_t cap = nullptr;         // owned: graph capture origin
+    cudaStream_t tstream[BI_MAXLEV] = {};   // owned: translations of level l (l >= 3)
+    cudaEvent_t ev_tfork[BI_MAXLEV] = {}, ev_tjoin[BI_MAXLEV] = {};
     bool use_graphs = true;
+    bool use_fast = true;               // fused kernels (false: two-pass reference kernels)
+    int near_ncol_max = 0;
+    int num_sms = 152;              // widest near segment of a leaf box (columns)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // host mesh / RWG in user order

@@ -90,9 +90,8 @@ __global__ void k_scatter_y(int N, int nX, int R, int nun, const int* __restrict
     y[(int64_t)r * nun + (int64_t)X * N + perm[t]] = v;
 }
 
-// ------------------------------------------------------------------ near field
-// One CTA per test leaf box.  Thread (r, m) accumulates the row of RWG m for RHS r over
-// the box's near blocks; blocks are column-major so consecutive m read consecutive entries.
+// ------------------------------------------------------------------ near field (reference kernel)
+// One thread per (test row, RHS) over the row-major segment of its box; tree-ordered vectors.
 //   C block:  y_J = -(A x_J + B x_M),  y_M = B x_J - A x_M + (X/2) x_J - (G/2) x_M
 //   PEC:      y   = -A x
 template <typename T, int MODE>
@@ -103,16 +102,17 @@ __global__ void __launch_bounds__(128) k_near(int R, const int* __restrict__ lea
                                               const cpx<T>* __restrict__ xt, cpx<T>* __restrict__ yt) {
     const int b = blockIdx.x;
     const int m0 = leaf_start[b], mb = leaf_start[b + 1] - m0;
-    const int nX = MODE == 0 ? 2 : 1;
+    const int64_t seg = near_blk[near_ptr[b]];
+    const int ncol = (int)((near_blk[near_ptr[b + 1]] - seg) / mb);
     for (int idx = threadIdx.x; idx < mb * R; idx += blockDim.x) {
         const int ml = idx % mb, r = idx / mb;
         cpx<T> aJ = czero<T>(), aM = czero<T>();
+        int c = 0;
         for (int q = near_ptr[b]; q < near_ptr[b + 1]; ++q) {
             const int s = near_src[q];
             const int n0 = leaf_start[s], nbs = leaf_start[s + 1] - n0;
-            const int64_t base = near_blk[q];
-            for (int nl = 0; nl < nbs; ++nl) {
-                const int64_t e = base + (int64_t)nl * mb + ml;
+            for (int nl = 0; nl < nbs; ++nl, ++c) {
+                const int64_t e = seg + (int64_t)ml * ncol + c;
                 const int n = n0 + nl;
                 if (MODE == 0) {
                     cpx<T> A = blocks[2 * e], B = blocks[2 * e + 1];
@@ -142,7 +142,6 @@ __global__ void __launch_bounds__(128) k_near(int R, const int* __restrict__ lea
         } else {
             yt[(int64_t)m * R + r] = cpx<T>{-aJ.x, -aJ.y};
         }
-        (void)nX;
     }
 }
 
@@ -179,7 +178,8 @@ __global__ void k_aggregate(int K, int R, const int* __restrict__ leaf_start, co
 
 // ------------------------------------------------------------------ interpolation (upward)
 // theta pass on great circles: tmp[cb][ip][jc][e] = sum_t w (+-) U_c[cb][src][jc or jc+half][e]
-template <typename T>
+// P > 0: compile-time tap count (taps hoisted and unrolled); P = 0: runtime count pth.
+template <typename T, int P>
 __global__ void k_interp_theta(int nthp, int nphc, int Kc, int E, int pth, const int* __restrict__ src,
                                const int* __restrict__ flip, const T* __restrict__ w, const cpx<T>* __restrict__ Uc,
                                cpx<T>* __restrict__ tmp) {
@@ -192,22 +192,36 @@ __global__ void k_interp_theta(int nthp, int nphc, int Kc, int E, int pth, const
     const int ip = (int)(idx / ((int64_t)E * nphc));
     const int half = nphc / 2;
     const cpx<T>* u = Uc + (int64_t)cb * Kc * E;
+    const int np = P > 0 ? P : pth;
     cpx<T> acc = czero<T>();
-    for (int t = 0; t < pth; ++t) {
-        const int i = src[ip * pth + t];
-        const int f = flip[ip * pth + t];
+#pragma unroll
+    for (int t = 0; t < (P > 0 ? P : 1); ++t) {
+        if (P == 0) break;
+        const int i = __ldg(src + ip * np + t);
+        const int f = __ldg(flip + ip * np + t);
         const int j = f ? (jc + half) % nphc : jc;
-        const T ww = f ? -w[ip * pth + t] : w[ip * pth + t];
+        const T ww = f ? -__ldg(w + ip * np + t) : __ldg(w + ip * np + t);
         cpx<T> v = u[((int64_t)i * nphc + j) * E + e];
         acc.x = fma(ww, v.x, acc.x);
         acc.y = fma(ww, v.y, acc.y);
+    }
+    if (P == 0) {
+        for (int t = 0; t < np; ++t) {
+            const int i = src[ip * np + t];
+            const int f = flip[ip * np + t];
+            const int j = f ? (jc + half) % nphc : jc;
+            const T ww = f ? -w[ip * np + t] : w[ip * np + t];
+            cpx<T> v = u[((int64_t)i * nphc + j) * E + e];
+            acc.x = fma(ww, v.x, acc.x);
+            acc.y = fma(ww, v.y, acc.y);
+        }
     }
     tmp[(int64_t)cb * tot + idx] = acc;
 }
 
 // phi pass, phase shift to the parent center and sum over children:
 //   U_p[pb][ip][jp][e] = sum_{cb} shift[oct(cb)][ip, jp] sum_q w tmp[cb][ip][src][e]
-template <typename T>
+template <typename T, int P>
 __global__ void k_interp_phi(int nthp, int nphp, int nphc, int E, int pph, const int* __restrict__ src,
                              const T* __restrict__ w, const int* __restrict__ child_ptr, const int* __restrict__ octant,
                              const cpx<T>* __restrict__ shift, const cpx<T>* __restrict__ tmp, cpx<T>* __restrict__ Up) {
@@ -219,15 +233,34 @@ __global__ void k_interp_phi(int nthp, int nphp, int nphc, int E, int pph, const
     const int kk = (int)(idx / E);
     const int ip = kk / nphp, jp = kk % nphp;
     const int64_t tsz = (int64_t)nthp * nphc * E;
+    const int np = P > 0 ? P : pph;
+    int sj[P > 0 ? P : 1];
+    T sw[P > 0 ? P : 1];
+    if (P > 0) {
+#pragma unroll
+        for (int q = 0; q < (P > 0 ? P : 1); ++q) {
+            sj[q] = __ldg(src + jp * np + q);
+            sw[q] = __ldg(w + jp * np + q);
+        }
+    }
     cpx<T> acc = czero<T>();
     for (int cb = child_ptr[pb]; cb < child_ptr[pb + 1]; ++cb) {
-        const cpx<T>* tt = tmp + (int64_t)cb * tsz + (int64_t)ip * nphc * E;
+        const cpx<T>* tt = tmp + (int64_t)cb * tsz + (int64_t)ip * nphc * E + e;
         cpx<T> s = czero<T>();
-        for (int q = 0; q < pph; ++q) {
-            const T ww = w[jp * pph + q];
-            cpx<T> v = tt[(int64_t)src[jp * pph + q] * E + e];
-            s.x = fma(ww, v.x, s.x);
-            s.y = fma(ww, v.y, s.y);
+        if (P > 0) {
+#pragma unroll
+            for (int q = 0; q < (P > 0 ? P : 1); ++q) {
+                const cpx<T> v = tt[(int64_t)sj[q] * E];
+                s.x = fma(sw[q], v.x, s.x);
+                s.y = fma(sw[q], v.y, s.y);
+            }
+        } else {
+            for (int q = 0; q < np; ++q) {
+                const cpx<T> v = tt[(int64_t)src[jp * np + q] * E];
+                const T ww = w[jp * np + q];
+                s.x = fma(ww, v.x, s.x);
+                s.y = fma(ww, v.y, s.y);
+            }
         }
         cfma(acc, shift[(int64_t)octant[cb] * Kp + kk], s);
     }
@@ -270,6 +303,7 @@ __global__ void k_anterp_phi(int nthp, int nphp, int nphc, int E, const int* __r
     const cpx<T>* vp = Vp + (int64_t)parent[cb] * Kp * E;
     const cpx<T>* sh = shift + (int64_t)octant[cb] * Kp;
     cpx<T> acc = czero<T>();
+#pragma unroll 4
     for (int q = tptr[jc]; q < tptr[jc + 1]; ++q) {
         const int jp = tdst[q];
         const int kk = ip * nphp + jp;
@@ -297,6 +331,7 @@ __global__ void k_anterp_theta(int nthp, int nthc, int nphc, int E, const int* _
     const int64_t tsz = (int64_t)nthp * nphc * E;
     const cpx<T>* tt = tmp + (int64_t)cb * tsz;
     cpx<T> acc = czero<T>();
+#pragma unroll 4
     for (int q = tptr[ic]; q < tptr[ic + 1]; ++q) {
         const int ip = tdst[q];
         const int f = tflip[q];
@@ -356,7 +391,489 @@ __global__ void k_receive(int N, int K, int R, const int* __restrict__ leaf_of, 
     }
 }
 
+// ------------------------------------------------------------------ near field (streaming)
+// One CTA per test leaf box; x of the box's near columns (read through the user permutation)
+// is staged in shared memory, then each warp streams whole rows of the row-major segment:
+// lane j reads columns j, j+32, ... (coalesced 16-byte entries), a shuffle reduction gives the
+// row.  RT right-hand sides per pass.
+__device__ __forceinline__ void load_pair(const cpx<float>* p, cpx<float>& A, cpx<float>& B) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    A = {v.x, v.y};
+    B = {v.z, v.w};
+}
+__device__ __forceinline__ void load_pair(const cpx<double>* p, cpx<double>& A, cpx<double>& B) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    A = {a.x, a.y};
+    B = {b.x, b.y};
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> warp_sum(cpx<T> v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+template <typename T, int MODE, int RT>
+__global__ void __launch_bounds__(256) k_near_stream(int N, int R, int nun, const int* __restrict__ perm,
+                                                     const int* __restrict__ leaf_start, const int* __restrict__ near_ptr,
+                                                     const int* __restrict__ near_src, const int64_t* __restrict__ near_blk,
+                                                     const cpx<T>* __restrict__ blocks, const int* __restrict__ gptr,
+                                                     const int* __restrict__ gcol, const T* __restrict__ gval,
+                                                     const cpx<T>* __restrict__ x, cpx<T>* __restrict__ yt,
+                                                     cpx<T>* __restrict__ yuser) {
+    constexpr int NX = MODE == 0 ? 2 : 1;
+    extern __shared__ unsigned char smem_raw[];
+    cpx<T>* xs = reinterpret_cast<cpx<T>*>(smem_raw);  // [NX][RT][ncol]
+    const int b = blockIdx.x;
+    const int m0 = leaf_start[b], mb = leaf_start[b + 1] - m0;
+    const int q0 = near_ptr[b], q1 = near_ptr[b + 1];
+    const int64_t seg = near_blk[q0];
+    const int ncol = (int)((near_blk[q1] - seg) / mb);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    for (int r0 = 0; r0 < R; r0 += RT) {
+        const int rn = min(RT, R - r0);
+        __syncthreads();
+        for (int q = q0; q < q1; ++q) {
+            const int s = near_src[q];
+            const int n0 = leaf_start[s], nbs = leaf_start[s + 1] - n0;
+            const int c0 = (int)((near_blk[q] - seg) / mb);
+            for (int i = threadIdx.x; i < nbs; i += blockDim.x) {
+                const int u = perm[n0 + i];
+#pragma unroll
+                for (int X = 0; X < NX; ++X)
+#pragma unroll
+                    for (int rr = 0; rr < RT; ++rr)
+                        xs[((size_t)X * RT + rr) * ncol + c0 + i] =
+                            rr < rn ? x[(int64_t)(r0 + rr) * nun + (int64_t)X * N + u] : czero<T>();
+            }
+        }
+        __syncthreads();
+        for (int ml = warp; ml < mb; ml += nwarp) {
+            cpx<T> aJ[RT], aM[RT];
+#pragma unroll
+            for (int rr = 0; rr < RT; ++rr) { aJ[rr] = czero<T>(); aM[rr] = czero<T>(); }
+            const cpx<T>* row = blocks + (MODE == 0 ? 2 : 1) * (seg + (int64_t)ml * ncol);
+#pragma unroll 4
+            for (int c = lane; c < ncol; c += 32) {
+                if (MODE == 0) {
+                    cpx<T> A, B;
+                    load_pair(row + 2 * c, A, B);
+#pragma unroll
+                    for (int rr = 0; rr < RT; ++rr) {
+                        const cpx<T> xJ = xs[(size_t)(0 * RT + rr) * ncol + c], xM = xs[(size_t)(1 * RT + rr) * ncol + c];
+                        cfma(aJ[rr], A, xJ);
+                        cfma(aJ[rr], B, xM);
+                        cfma(aM[rr], B, xJ);
+                        cfma(aM[rr], A, cpx<T>{-xM.x, -xM.y});
+                    }
+                } else {
+                    const cpx<T> A = row[c];
+#pragma unroll
+                    for (int rr = 0; rr < RT; ++rr) cfma(aJ[rr], A, xs[(size_t)rr * ncol + c]);
+                }
+            }
+            const int m = m0 + ml;
+#pragma unroll
+            for (int rr = 0; rr < RT; ++rr) {
+                const cpx<T> sJ = warp_sum(aJ[rr]);
+                cpx<T> sM = MODE == 0 ? warp_sum(aM[rr]) : czero<T>();
+                if (lane == 0 && rr < rn) {
+                    const int r = r0 + rr;
+                    if (MODE == 0) {
+                        for (int qq = gptr[m]; qq < gptr[m + 1]; ++qq) {
+                            const int n = gcol[qq];
+                            const T gg = gval[2 * qq], xx = gval[2 * qq + 1];
+                            const cpx<T> xJ = x[(int64_t)r * nun + perm[n]], xM = x[(int64_t)r * nun + N + perm[n]];
+                            sM.x += T(0.5) * (xx * xJ.x - gg * xM.x);
+                            sM.y += T(0.5) * (xx * xJ.y - gg * xM.y);
+                        }
+                    }
+                    const cpx<T> vJ = {-sJ.x, -sJ.y};
+                    if (yuser) {
+                        yuser[(int64_t)r * nun + perm[m]] = vJ;
+                        if (MODE == 0) yuser[(int64_t)r * nun + N + perm[m]] = sM;
+                    } else {
+                        yt[((int64_t)m * NX + 0) * R + r] = vJ;
+                        if (MODE == 0) yt[((int64_t)m * NX + 1) * R + r] = sM;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ leaf aggregation (fused gather)
+// thread per (direction kk, RHS r): both components from one 16-byte pattern load.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_aggregate2(int N, int K, int R, int nun, const int* __restrict__ perm,
+                                                    const int* __restrict__ leaf_start, const cpx<T>* __restrict__ F,
+                                                    const cpx<T>* __restrict__ x, cpx<T>* __restrict__ U) {
+    // x of the box's RWGs (J then M) for every RHS, staged once per CTA
+    extern __shared__ unsigned char smem_raw[];
+    cpx<T>* xs = reinterpret_cast<cpx<T>*>(smem_raw);  // [nb][2][R]
+    const int b = blockIdx.y;
+    const int n0 = leaf_start[b], nb = leaf_start[b + 1] - n0;
+    for (int i = threadIdx.x; i < nb * 2 * R; i += blockDim.x) {
+        const int r = i % R, X = (i / R) % 2, n = i / (2 * R);
+        xs[i] = (MODE == 0 || X == 0) ? x[(int64_t)r * nun + (int64_t)X * N + perm[n0 + n]] : czero<T>();
+    }
+    __syncthreads();
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= K * R) return;
+    const int kk = idx / R, r = idx % R;
+    const int E = 2 * R;
+    cpx<T> ut = czero<T>(), up = czero<T>();
+    const cpx<T>* f = F + ((int64_t)n0 * K + kk) * 2;
+#pragma unroll 8
+    for (int n = 0; n < nb; ++n) {
+        cpx<T> Ft, Fp;
+        load_pair(f + (int64_t)n * K * 2, Ft, Fp);
+        const cpx<T> xJ = xs[(n * 2 + 0) * R + r];
+        ut = csub(ut, cmul(xJ, Ft));
+        up = csub(up, cmul(xJ, Fp));
+        if (MODE == 0) {
+            const cpx<T> xM = xs[(n * 2 + 1) * R + r];
+            ut = csub(ut, cmul(xM, Fp));
+            up = cadd(up, cmul(xM, Ft));
+        }
+    }
+    cpx<T>* o = U + ((int64_t)b * K + kk) * E;
+    o[r] = ut;
+    o[R + r] = up;
+}
+
+// ------------------------------------------------------------------ fused interpolation (one CTA per parent)
+// U_p = sum_children shift * Interp_phi(Interp_theta(U_c)); child pattern and theta-pass in shared memory,
+// parent outputs accumulated in registers (OPT outputs per thread).
+template <typename T, int OPT>
+__global__ void __launch_bounds__(256) k_interp_fused(int nthc, int nphc, int nthp, int nphp, int E, int pth, int pph,
+                                                      const int* __restrict__ th_src, const int* __restrict__ th_flip,
+                                                      const T* __restrict__ th_w, const int* __restrict__ ph_src,
+                                                      const T* __restrict__ ph_w, const int* __restrict__ child_ptr,
+                                                      const int* __restrict__ octant, const cpx<T>* __restrict__ shift,
+                                                      const cpx<T>* __restrict__ Uc, cpx<T>* __restrict__ Up) {
+    extern __shared__ unsigned char smem_raw[];
+    const int Kc = nthc * nphc, Kp = nthp * nphp;
+    cpx<T>* s1 = reinterpret_cast<cpx<T>*>(smem_raw);   // child [Kc][E]
+    cpx<T>* s2 = s1 + (size_t)Kc * E;                   // theta pass [nthp][nphc][E]
+    const int pb = blockIdx.x;
+    const int half = nphc / 2;
+    const int nout = Kp * E;
+    cpx<T> acc[OPT];
+#pragma unroll
+    for (int i = 0; i < OPT; ++i) acc[i] = czero<T>();
+    for (int cb = child_ptr[pb]; cb < child_ptr[pb + 1]; ++cb) {
+        __syncthreads();
+        const cpx<T>* u = Uc + (int64_t)cb * Kc * E;
+        for (int i = threadIdx.x; i < Kc * E; i += blockDim.x) s1[i] = u[i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < nthp * nphc * E; i += blockDim.x) {
+            const int e = i % E, jc = (i / E) % nphc, ip = i / (E * nphc);
+            cpx<T> a = czero<T>();
+            for (int t = 0; t < pth; ++t) {
+                const int src = th_src[ip * pth + t], f = th_flip[ip * pth + t];
+                const T w = f ? -th_w[ip * pth + t] : th_w[ip * pth + t];
+                const cpx<T> v = s1[((size_t)src * nphc + (f ? (jc + half) % nphc : jc)) * E + e];
+                a.x = fma(w, v.x, a.x);
+                a.y = fma(w, v.y, a.y);
+            }
+            s2[i] = a;
+        }
+        __syncthreads();
+        const cpx<T>* sh = shift + (int64_t)octant[cb] * Kp;
+#pragma unroll
+        for (int o = 0; o < OPT; ++o) {
+            const int i = threadIdx.x + o * blockDim.x;
+            if (i < nout) {
+                const int e = i % E, kk = i / E, ip = kk / nphp, jp = kk % nphp;
+                cpx<T> a = czero<T>();
+                for (int q = 0; q < pph; ++q) {
+                    const T w = ph_w[jp * pph + q];
+                    const cpx<T> v = s2[((size_t)ip * nphc + ph_src[jp * pph + q]) * E + e];
+                    a.x = fma(w, v.x, a.x);
+                    a.y = fma(w, v.y, a.y);
+                }
+                cfma(acc[o], sh[kk], a);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) {
+        const int i = threadIdx.x + o * blockDim.x;
+        if (i < nout) Up[(int64_t)pb * nout + i] = acc[o];
+    }
+}
+
+// ------------------------------------------------------------------ fused anterpolation (one CTA per parent)
+// V_c += Anterp_theta(Anterp_phi(conj(shift) * V_p)) for every child of the parent.
+template <typename T>
+__global__ void __launch_bounds__(256) k_anterp_fused(int nthc, int nphc, int nthp, int nphp, int E,
+                                                      const int* __restrict__ tph_ptr, const int* __restrict__ tph_dst,
+                                                      const T* __restrict__ tph_w, const int* __restrict__ tth_ptr,
+                                                      const int* __restrict__ tth_dst, const int* __restrict__ tth_flip,
+                                                      const T* __restrict__ tth_w, const int* __restrict__ child_ptr,
+                                                      const int* __restrict__ octant, const cpx<T>* __restrict__ shift,
+                                                      const cpx<T>* __restrict__ Vp, cpx<T>* __restrict__ Vc) {
+    extern __shared__ unsigned char smem_raw[];
+    const int Kc = nthc * nphc, Kp = nthp * nphp;
+    cpx<T>* s0 = reinterpret_cast<cpx<T>*>(smem_raw);   // parent [Kp][E]
+    cpx<T>* s2 = s0 + (size_t)Kp * E;                   // [nthp][nphc][E]
+    const int pb = blockIdx.x;
+    const int half = nphc / 2;
+    const cpx<T>* vp = Vp + (int64_t)pb * Kp * E;
+    for (int i = threadIdx.x; i < Kp * E; i += blockDim.x) s0[i] = vp[i];
+    for (int cb = child_ptr[pb]; cb < child_ptr[pb + 1]; ++cb) {
+        __syncthreads();
+        const cpx<T>* sh = shift + (int64_t)octant[cb] * Kp;
+        for (int i = threadIdx.x; i < nthp * nphc * E; i += blockDim.x) {
+            const int e = i % E, jc = (i / E) % nphc, ip = i / (E * nphc);
+            cpx<T> a = czero<T>();
+            for (int q = tph_ptr[jc]; q < tph_ptr[jc + 1]; ++q) {
+                const int kk = ip * nphp + tph_dst[q];
+                const cpx<T> v = cmulc(sh[kk], s0[(size_t)kk * E + e]);
+                const T w = tph_w[q];
+                a.x = fma(w, v.x, a.x);
+                a.y = fma(w, v.y, a.y);
+            }
+            s2[i] = a;
+        }
+        __syncthreads();
+        cpx<T>* vc = Vc + (int64_t)cb * Kc * E;
+        for (int i = threadIdx.x; i < Kc * E; i += blockDim.x) {
+            const int e = i % E, kk = i / E, ic = kk / nphc, jc = kk % nphc;
+            cpx<T> a = czero<T>();
+            for (int q = tth_ptr[ic]; q < tth_ptr[ic + 1]; ++q) {
+                const int f = tth_flip[q];
+                const T w = f ? -tth_w[q] : tth_w[q];
+                const cpx<T> v = s2[((size_t)tth_dst[q] * nphc + (f ? (jc + half) % nphc : jc)) * E + e];
+                a.x = fma(w, v.x, a.x);
+                a.y = fma(w, v.y, a.y);
+            }
+            vc[i] = cadd(vc[i], a);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ per-child interpolation / anterpolation
+// One CTA per child box; the child's pattern, the pass intermediate and the interpolation
+// tables live in shared memory, so every tap is a shared-memory read.
+//  upward:   U_p[parent] += shift(oct) * Interp_phi(Interp_theta(U_c))   (float atomics into U_p,
+//            which the caller zeroes; 8 children per parent)
+//  downward: V_c += Anterp_theta(Anterp_phi(conj(shift(oct)) * V_p[parent]))
+template <typename T>
+__device__ __forceinline__ void atomic_add_c(cpx<T>* p, cpx<T> v) {
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_interp_child(int nthc, int nphc, int nthp, int nphp, int E, int pth, int pph,
+                                                      const int* __restrict__ th_src, const int* __restrict__ th_flip,
+                                                      const T* __restrict__ th_w, const int* __restrict__ ph_src,
+                                                      const T* __restrict__ ph_w, const int* __restrict__ parent,
+                                                      const int* __restrict__ octant, const cpx<T>* __restrict__ shift,
+                                                      const cpx<T>* __restrict__ Uc, cpx<T>* __restrict__ Up) {
+    extern __shared__ unsigned char smem_raw[];
+    const int Kc = nthc * nphc, Kp = nthp * nphp;
+    cpx<T>* s1 = reinterpret_cast<cpx<T>*>(smem_raw);        // [Kc][E]
+    cpx<T>* s2 = s1 + (size_t)Kc * E;                        // [nthp][nphc][E]
+    T* tw = reinterpret_cast<T*>(s2 + (size_t)nthp * nphc * E);  // theta weights (sign folded) [nthp*pth]
+    T* pw = tw + nthp * pth;                                 // phi weights [nphp*pph]
+    int* tsrc = reinterpret_cast<int*>(pw + nphp * pph);     // theta source row*nphc + column shift flag
+    int* psrc = tsrc + nthp * pth;                           // phi source column
+    const int cb = blockIdx.x;
+    const int half = nphc / 2;
+    for (int i = threadIdx.x; i < nthp * pth; i += blockDim.x) {
+        const int f = th_flip[i];
+        tw[i] = f ? -th_w[i] : th_w[i];
+        tsrc[i] = th_src[i] * 2 + f;
+    }
+    for (int i = threadIdx.x; i < nphp * pph; i += blockDim.x) {
+        pw[i] = ph_w[i];
+        psrc[i] = ph_src[i];
+    }
+    const cpx<T>* u = Uc + (int64_t)cb * Kc * E;
+    for (int i = threadIdx.x; i < Kc * E; i += blockDim.x) s1[i] = u[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < nthp * nphc * E; i += blockDim.x) {
+        const int e = i % E, jc = (i / E) % nphc, ip = i / (E * nphc);
+        cpx<T> a = czero<T>();
+        for (int t = 0; t < pth; ++t) {
+            const int code = tsrc[ip * pth + t];
+            const int j = (code & 1) ? (jc + half) % nphc : jc;
+            const cpx<T> v = s1[((size_t)(code >> 1) * nphc + j) * E + e];
+            const T w = tw[ip * pth + t];
+            a.x = fma(w, v.x, a.x);
+            a.y = fma(w, v.y, a.y);
+        }
+        s2[i] = a;
+    }
+    __syncthreads();
+    const cpx<T>* sh = shift + (int64_t)octant[cb] * Kp;
+    cpx<T>* up = Up + (int64_t)parent[cb] * Kp * E;
+    for (int i = threadIdx.x; i < Kp * E; i += blockDim.x) {
+        const int e = i % E, kk = i / E, ip = kk / nphp, jp = kk % nphp;
+        cpx<T> a = czero<T>();
+        for (int q = 0; q < pph; ++q) {
+            const cpx<T> v = s2[((size_t)ip * nphc + psrc[jp * pph + q]) * E + e];
+            const T w = pw[jp * pph + q];
+            a.x = fma(w, v.x, a.x);
+            a.y = fma(w, v.y, a.y);
+        }
+        atomic_add_c(up + i, cmul(sh[kk], a));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_anterp_child(int nthc, int nphc, int nthp, int nphp, int E, int ntph, int ntth,
+                                                      const int* __restrict__ tph_ptr, const int* __restrict__ tph_dst,
+                                                      const T* __restrict__ tph_w, const int* __restrict__ tth_ptr,
+                                                      const int* __restrict__ tth_dst, const int* __restrict__ tth_flip,
+                                                      const T* __restrict__ tth_w, const int* __restrict__ parent,
+                                                      const int* __restrict__ octant, const cpx<T>* __restrict__ shift,
+                                                      const cpx<T>* __restrict__ Vp, cpx<T>* __restrict__ Vc) {
+    extern __shared__ unsigned char smem_raw[];
+    const int Kc = nthc * nphc, Kp = nthp * nphp;
+    cpx<T>* s0 = reinterpret_cast<cpx<T>*>(smem_raw);        // conj(shift) * V_p  [Kp][E]
+    cpx<T>* s2 = s0 + (size_t)Kp * E;                        // [nthp][nphc][E]
+    T* pw = reinterpret_cast<T*>(s2 + (size_t)nthp * nphc * E);   // [ntph]
+    T* tw = pw + ntph;                                            // [ntth] (sign folded)
+    int* pptr = reinterpret_cast<int*>(tw + ntth);                // [nphc + 1]
+    int* pdst = pptr + nphc + 1;                                  // [ntph]
+    int* tptr = pdst + ntph;                                      // [nthc + 1]
+    int* tdst = tptr + nthc + 1;                                  // [ntth]: parent row * 2 + flip
+    const int cb = blockIdx.x;
+    const int half = nphc / 2;
+    for (int i = threadIdx.x; i < ntph; i += blockDim.x) { pw[i] = tph_w[i]; pdst[i] = tph_dst[i]; }
+    for (int i = threadIdx.x; i < ntth; i += blockDim.x) {
+        const int f = tth_flip[i];
+        tw[i] = f ? -tth_w[i] : tth_w[i];
+        tdst[i] = tth_dst[i] * 2 + f;
+    }
+    for (int i = threadIdx.x; i <= nphc; i += blockDim.x) pptr[i] = tph_ptr[i];
+    for (int i = threadIdx.x; i <= nthc; i += blockDim.x) tptr[i] = tth_ptr[i];
+    const cpx<T>* sh = shift + (int64_t)octant[cb] * Kp;
+    const cpx<T>* vp = Vp + (int64_t)parent[cb] * Kp * E;
+    for (int i = threadIdx.x; i < Kp * E; i += blockDim.x) s0[i] = cmulc(sh[i / E], vp[i]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nthp * nphc * E; i += blockDim.x) {
+        const int e = i % E, jc = (i / E) % nphc, ip = i / (E * nphc);
+        cpx<T> a = czero<T>();
+        for (int q = pptr[jc]; q < pptr[jc + 1]; ++q) {
+            const cpx<T> v = s0[((size_t)ip * nphp + pdst[q]) * E + e];
+            a.x = fma(pw[q], v.x, a.x);
+            a.y = fma(pw[q], v.y, a.y);
+        }
+        s2[i] = a;
+    }
+    __syncthreads();
+    cpx<T>* vc = Vc + (int64_t)cb * Kc * E;
+    for (int i = threadIdx.x; i < Kc * E; i += blockDim.x) {
+        const int e = i % E, kk = i / E, ic = kk / nphc, jc = kk % nphc;
+        cpx<T> a = czero<T>();
+        for (int q = tptr[ic]; q < tptr[ic + 1]; ++q) {
+            const int code = tdst[q];
+            const int j = (code & 1) ? (jc + half) % nphc : jc;
+            const cpx<T> v = s2[((size_t)(code >> 1) * nphc + j) * E + e];
+            a.x = fma(tw[q], v.x, a.x);
+            a.y = fma(tw[q], v.y, a.y);
+        }
+        vc[i] = cadd(vc[i], a);
+    }
+}
+
+// ------------------------------------------------------------------ leaf receive with the final permutation
+// y_user[perm[m]] = y_near[m] + far part (the near result in tree order is added here).
+template <typename T, int MODE>
+__global__ void k_receive2(int N, int K, int R, int nun, const int* __restrict__ perm, const int* __restrict__ leaf_of,
+                           const cpx<T>* __restrict__ F, const cpx<T>* __restrict__ RX, const cpx<T>* __restrict__ V, T c,
+                           const cpx<T>* __restrict__ yt, cpx<T>* __restrict__ y) {
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= N * R) return;
+    const int m = warp / R, r = warp % R;
+    const int b = leaf_of[m];
+    const int E = 2 * R;
+    cpx<T> sJ = czero<T>(), sM = czero<T>();
+#pragma unroll 4
+    for (int kk = lane; kk < K; kk += 32) {
+        cpx<T> Ft, Fp, Xt, Xp;
+        load_pair(F + ((int64_t)m * K + kk) * 2, Ft, Fp);
+        load_pair(RX + ((int64_t)m * K + kk) * 2, Xt, Xp);
+        const cpx<T> Vt = V[((int64_t)b * K + kk) * E + r], Vp = V[((int64_t)b * K + kk) * E + R + r];
+        cpx<T> RV = cadd(cmulc(Ft, Vt), cmulc(Fp, Vp));
+        cpx<T> XkV = csub(cmul(Xp, Vt), cmul(Xt, Vp));
+        sJ = cadd(sJ, csub(RV, XkV));
+        if (MODE == 0) {
+            cpx<T> t = csub(cmulc(Ft, Vp), cmulc(Fp, Vt));
+            t = csub(t, cmul(Xt, Vt));
+            t = csub(t, cmul(Xp, Vp));
+            sM = cadd(sM, t);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sJ.x += __shfl_xor_sync(0xffffffffu, sJ.x, o);
+        sJ.y += __shfl_xor_sync(0xffffffffu, sJ.y, o);
+        if (MODE == 0) {
+            sM.x += __shfl_xor_sync(0xffffffffu, sM.x, o);
+            sM.y += __shfl_xor_sync(0xffffffffu, sM.y, o);
+        }
+    }
+    if (lane == 0) {
+        const int u = perm[m];
+        if (MODE == 0) {
+            y[(int64_t)r * nun + u] = cadd(yt[((int64_t)m * 2 + 0) * R + r], cscale(sJ, -c));
+            y[(int64_t)r * nun + N + u] = cadd(yt[((int64_t)m * 2 + 1) * R + r], cscale(sM, c));
+        } else {
+            y[(int64_t)r * nun + u] = cadd(yt[(int64_t)m * R + r], cscale(sJ, -c));
+        }
+    }
+}
+
 inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) / th); }
+
+template <typename T>
+void launch_interp_two_pass(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    level_t& P = h->lev[l];
+    level_t& Cc = h->lev[l + 1];
+    interp_t& I = h->itp[l];
+    const int th = 256;
+    typedef cpx<T> C;
+    dim3 g1(nblk((int64_t)P.nth * Cc.nph * E, th), Cc.nbox);
+    dim3 g2(nblk((int64_t)P.K * E, th), P.nbox);
+#define BI_TH(PP) k_interp_theta<T, PP><<<g1, th, 0, s>>>(P.nth, Cc.nph, Cc.K, E, I.p_th, I.d_th_src, I.d_th_flip, \
+                                                          (const T*)I.d_th_w, (const C*)Cc.d_U, (C*)I.d_tmp)
+#define BI_PH(PP) k_interp_phi<T, PP><<<g2, th, 0, s>>>(P.nth, P.nph, Cc.nph, E, I.p_ph, I.d_ph_src, (const T*)I.d_ph_w, \
+                                                        P.d_child_ptr, Cc.d_octant, (const C*)P.d_shift, \
+                                                        (const C*)I.d_tmp, (C*)P.d_U)
+    switch (I.p_th) {
+        case 4: BI_TH(4); break;
+        case 6: BI_TH(6); break;
+        case 8: BI_TH(8); break;
+        case 10: BI_TH(10); break;
+        case 12: BI_TH(12); break;
+        case 16: BI_TH(16); break;
+        default: BI_TH(0); break;
+    }
+    CU(cudaGetLastError());
+    switch (I.p_ph) {
+        case 4: BI_PH(4); break;
+        case 6: BI_PH(6); break;
+        case 8: BI_PH(8); break;
+        case 10: BI_PH(10); break;
+        case 12: BI_PH(12); break;
+        case 16: BI_PH(16); break;
+        default: BI_PH(0); break;
+    }
+#undef BI_TH
+#undef BI_PH
+    CU(cudaGetLastError());
+}
+
+
 
 // Stage boundaries for bi_profile_stages: when ev is non-null every stage runs on s (no
 // overlap) and ev[i] is recorded after stage i; ev[-1] must be recorded by the caller.
@@ -411,14 +928,8 @@ void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s,
             level_t& P = h->lev[l];
             level_t& Cc = h->lev[l + 1];
             interp_t& I = h->itp[l];
-            dim3 g1(nblk((int64_t)P.nth * Cc.nph * E, th), Cc.nbox);
-            k_interp_theta<T><<<g1, th, 0, s>>>(P.nth, Cc.nph, Cc.K, E, I.p_th, I.d_th_src, I.d_th_flip, (const T*)I.d_th_w,
-                                                (const C*)Cc.d_U, (C*)I.d_tmp);
-            CU(cudaGetLastError());
-            dim3 g2(nblk((int64_t)P.K * E, th), P.nbox);
-            k_interp_phi<T><<<g2, th, 0, s>>>(P.nth, P.nph, Cc.nph, E, I.p_ph, I.d_ph_src, (const T*)I.d_ph_w, P.d_child_ptr,
-                                              Cc.d_octant, (const C*)P.d_shift, (const C*)I.d_tmp, (C*)P.d_U);
-            CU(cudaGetLastError());
+            (void)P; (void)Cc; (void)I;
+            launch_interp_two_pass<T>(h, l, E, s);
         }
         if (ev) CU(cudaEventRecord(ev[3], s));
         // translations on every level
@@ -472,14 +983,246 @@ void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s,
     if (ev) CU(cudaEventRecord(ev[7], s));
 }
 
+
+template <typename T, int MODE, int RT>
+void launch_near_stream(bi_handle_s* h, const cpx<T>* x, cpx<T>* yt, cpx<T>* yuser, int R, cudaStream_t s) {
+    const int NX = MODE == 0 ? 2 : 1;
+    size_t smem = (size_t)h->near_ncol_max * NX * RT * sizeof(cpx<T>);
+    auto kern = k_near_stream<T, MODE, RT>;
+    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<h->lev[h->leaf].nbox, 256, smem, s>>>(h->N, R, h->nun, h->d_perm, h->d_leaf_start, h->d_near_ptr, h->d_near_src,
+                                                 h->d_near_blk, (const cpx<T>*)h->d_near, h->d_gram_ptr, h->d_gram_col,
+                                                 (const T*)h->d_gram_val, x, yt, yuser);
+    CU(cudaGetLastError());
+}
+
+template <typename T, int MODE>
+void launch_near_any(bi_handle_s* h, const cpx<T>* x, cpx<T>* yt, cpx<T>* yuser, int R, cudaStream_t s) {
+    if ((size_t)h->near_ncol_max * 2 * sizeof(cpx<T>) > 160 * 1024) {
+        // rows of one box exceed the CTA: the row-per-thread kernel on tree-ordered vectors
+        const int64_t nvec = (int64_t)h->N * h->nX * R;
+        k_gather_x<T><<<nblk(nvec, 256), 256, 0, s>>>(h->N, h->nX, R, h->nun, h->d_perm, x, (cpx<T>*)h->d_xt);
+        k_near<T, MODE><<<h->lev[h->leaf].nbox, 128, 0, s>>>(R, h->d_leaf_start, h->d_near_ptr, h->d_near_src, h->d_near_blk,
+                                                            (const cpx<T>*)h->d_near, h->d_gram_ptr, h->d_gram_col,
+                                                            (const T*)h->d_gram_val, (const cpx<T>*)h->d_xt, yt);
+        if (yuser)
+            k_scatter_y<T><<<nblk(nvec, 256), 256, 0, s>>>(h->N, h->nX, R, h->nun, h->d_perm, yt, nullptr, yuser);
+        CU(cudaGetLastError());
+        return;
+    }
+    if (R == 1) launch_near_stream<T, MODE, 1>(h, x, yt, yuser, R, s);
+    else if (R == 2) launch_near_stream<T, MODE, 2>(h, x, yt, yuser, R, s);
+    else launch_near_stream<T, MODE, 4>(h, x, yt, yuser, R, s);
+}
+
+template <typename T, int OPT>
+bool try_interp_fused(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    level_t& P = h->lev[l];
+    level_t& C = h->lev[l + 1];
+    interp_t& I = h->itp[l];
+    if ((int64_t)P.K * E > (int64_t)256 * OPT) return false;
+    size_t smem = ((size_t)C.K * E + (size_t)P.nth * C.nph * E) * sizeof(cpx<T>);
+    if (smem > 160 * 1024) return false;
+    auto kern = k_interp_fused<T, OPT>;
+    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<P.nbox, 256, smem, s>>>(C.nth, C.nph, P.nth, P.nph, E, I.p_th, I.p_ph, I.d_th_src, I.d_th_flip,
+                                   (const T*)I.d_th_w, I.d_ph_src, (const T*)I.d_ph_w, P.d_child_ptr, C.d_octant,
+                                   (const cpx<T>*)P.d_shift, (const cpx<T>*)C.d_U, (cpx<T>*)P.d_U);
+    CU(cudaGetLastError());
+    return true;
+}
+
+template <typename T>
+bool interp_fused(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    return try_interp_fused<T, 1>(h, l, E, s) || try_interp_fused<T, 2>(h, l, E, s) || try_interp_fused<T, 4>(h, l, E, s) ||
+           try_interp_fused<T, 8>(h, l, E, s) || try_interp_fused<T, 16>(h, l, E, s);
+}
+
+template <typename T>
+bool anterp_fused(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    level_t& P = h->lev[l];
+    level_t& C = h->lev[l + 1];
+    interp_t& I = h->itp[l];
+    size_t smem = ((size_t)P.K * E + (size_t)P.nth * C.nph * E) * sizeof(cpx<T>);
+    if (smem > 160 * 1024) return false;
+    auto kern = k_anterp_fused<T>;
+    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<P.nbox, 256, smem, s>>>(C.nth, C.nph, P.nth, P.nph, E, I.d_tph_ptr, I.d_tph_dst, (const T*)I.d_tph_w,
+                                   I.d_tth_ptr, I.d_tth_dst, I.d_tth_flip, (const T*)I.d_tth_w, P.d_child_ptr, C.d_octant,
+                                   (const cpx<T>*)P.d_shift, (const cpx<T>*)P.d_V, (cpx<T>*)C.d_V);
+    CU(cudaGetLastError());
+    return true;
+}
+
+
+template <typename T>
+size_t interp_child_smem(bi_handle_s* h, int l, int E) {
+    const level_t& P = h->lev[l];
+    const level_t& C = h->lev[l + 1];
+    const interp_t& I = h->itp[l];
+    return ((size_t)C.K * E + (size_t)P.nth * C.nph * E) * sizeof(cpx<T>) +
+           ((size_t)P.nth * I.p_th + (size_t)P.nph * I.p_ph) * (sizeof(T) + sizeof(int));
+}
+template <typename T>
+size_t anterp_child_smem(bi_handle_s* h, int l, int E) {
+    const level_t& P = h->lev[l];
+    const level_t& C = h->lev[l + 1];
+    const interp_t& I = h->itp[l];
+    return ((size_t)P.K * E + (size_t)P.nth * C.nph * E) * sizeof(cpx<T>) +
+           (I.tph_dst.size() + I.tth_dst.size()) * (sizeof(T) + sizeof(int)) + (size_t)(C.nph + C.nth + 2) * sizeof(int);
+}
+
+template <typename T>
+bool interp_child(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    level_t& P = h->lev[l];
+    level_t& C = h->lev[l + 1];
+    interp_t& I = h->itp[l];
+    size_t smem = interp_child_smem<T>(h, l, E);
+    if (smem > 180 * 1024) return false;
+    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(k_interp_child<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CU(cudaMemsetAsync(P.d_U, 0, (size_t)P.nbox * P.K * E * sizeof(cpx<T>), s));
+    k_interp_child<T><<<C.nbox, 256, smem, s>>>(C.nth, C.nph, P.nth, P.nph, E, I.p_th, I.p_ph, I.d_th_src, I.d_th_flip,
+                                                (const T*)I.d_th_w, I.d_ph_src, (const T*)I.d_ph_w, C.d_parent, C.d_octant,
+                                                (const cpx<T>*)P.d_shift, (const cpx<T>*)C.d_U, (cpx<T>*)P.d_U);
+    CU(cudaGetLastError());
+    return true;
+}
+
+template <typename T>
+bool anterp_child(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    level_t& P = h->lev[l];
+    level_t& C = h->lev[l + 1];
+    interp_t& I = h->itp[l];
+    size_t smem = anterp_child_smem<T>(h, l, E);
+    if (smem > 180 * 1024) return false;
+    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(k_anterp_child<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_anterp_child<T><<<C.nbox, 256, smem, s>>>(C.nth, C.nph, P.nth, P.nph, E, (int)I.tph_dst.size(), (int)I.tth_dst.size(),
+                                                I.d_tph_ptr, I.d_tph_dst, (const T*)I.d_tph_w, I.d_tth_ptr, I.d_tth_dst,
+                                                I.d_tth_flip, (const T*)I.d_tth_w, C.d_parent, C.d_octant,
+                                                (const cpx<T>*)P.d_shift, (const cpx<T>*)P.d_V, (cpx<T>*)C.d_V);
+    CU(cudaGetLastError());
+    return true;
+}
+
+// The product with fused kernels: near (side stream) || aggregate -> interpolate -> translate
+// -> anterpolate -> receive (+ near result, + permutation to user order).
+template <typename T>
+void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s, cudaStream_t side, cudaEvent_t* ev) {
+    if (ev) side = s;
+    typedef cpx<T> C;
+    const C* x = (const C*)xv;
+    C* y = (C*)yv;
+    C* yt = (C*)h->d_yt;
+    const int N = h->N, nun = h->nun, E = 2 * R, th = 256;
+    const bool far = h->leaf >= 2;
+    if (ev) CU(cudaEventRecord(ev[0], s));
+    if (!ev) {
+        CU(cudaEventRecord(h->ev_fork, s));
+        CU(cudaStreamWaitEvent(side, h->ev_fork, 0));
+    }
+    if (h->prm.op_mode == 0) launch_near_any<T, 0>(h, x, yt, far ? nullptr : y, R, side);
+    else launch_near_any<T, 1>(h, x, yt, far ? nullptr : y, R, side);
+    if (ev) CU(cudaEventRecord(ev[1], s));
+    else CU(cudaEventRecord(h->ev_join, side));
+    if (!far) {
+        if (ev)
+            for (int i = 2; i < BI_NSTAGES; ++i) CU(cudaEventRecord(ev[i], s));
+        else
+            CU(cudaStreamWaitEvent(s, h->ev_join, 0));
+        return;
+    }
+    const int lf = h->leaf;
+    {
+        level_t& L = h->lev[lf];
+        dim3 g(nblk((int64_t)L.K * R, th), L.nbox);
+        size_t smem = (size_t)h->max_leaf_count * 2 * R * sizeof(C);
+        if (smem > 48 * 1024) {
+            CU(cudaFuncSetAttribute(k_aggregate2<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            CU(cudaFuncSetAttribute(k_aggregate2<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        }
+        if (h->prm.op_mode == 0)
+            k_aggregate2<T, 0><<<g, th, smem, s>>>(N, L.K, R, nun, h->d_perm, h->d_leaf_start, (const C*)h->d_F, x, (C*)L.d_U);
+        else
+            k_aggregate2<T, 1><<<g, th, smem, s>>>(N, L.K, R, nun, h->d_perm, h->d_leaf_start, (const C*)h->d_F, x, (C*)L.d_U);
+        CU(cudaGetLastError());
+    }
+    if (ev) CU(cudaEventRecord(ev[2], s));
+    // Translations of level l only need U_l: the finer levels run on their own streams while
+    // the upward pass continues, and join before the downward pass adds into V_l.
+    auto translate = [&](int l, cudaStream_t st) {
+        level_t& L = h->lev[l];
+        dim3 g(nblk((int64_t)L.K * E, th), L.nbox);
+        k_translate<T><<<g, th, 0, st>>>(L.K, E, L.d_il_ptr, L.d_il_src, L.d_il_off, (const C*)L.d_T, (const C*)L.d_U,
+                                         (C*)L.d_V);
+        CU(cudaGetLastError());
+    };
+    auto fork_translate = [&](int l) {
+        if (ev) return;  // profiling: translations are timed as one serial stage below
+        cudaStream_t st = h->tstream[l];
+        CU(cudaEventRecord(h->ev_tfork[l], s));
+        CU(cudaStreamWaitEvent(st, h->ev_tfork[l], 0));
+        translate(l, st);
+        CU(cudaEventRecord(h->ev_tjoin[l], st));
+    };
+    if (lf > 2) fork_translate(lf);
+    for (int l = lf - 1; l >= 2; --l) {
+        // one CTA per parent only pays off when the level has enough parents to fill the GPU
+        if (!interp_child<T>(h, l, E, s)) launch_interp_two_pass<T>(h, l, E, s);
+        if (l > 2) fork_translate(l);
+    }
+    if (ev) CU(cudaEventRecord(ev[3], s));
+    if (ev)
+        for (int l = 2; l <= lf; ++l) translate(l, s);
+    else
+        translate(2, s);
+    if (ev) CU(cudaEventRecord(ev[4], s));
+    for (int l = 2; l < lf; ++l) {
+        if (!ev) CU(cudaStreamWaitEvent(s, h->ev_tjoin[l + 1], 0));
+        if (anterp_child<T>(h, l, E, s)) continue;
+        level_t& P = h->lev[l];
+        level_t& Cc = h->lev[l + 1];
+        interp_t& I = h->itp[l];
+        dim3 g1(nblk((int64_t)P.nth * Cc.nph * E, th), Cc.nbox);
+        k_anterp_phi<T><<<g1, th, 0, s>>>(P.nth, P.nph, Cc.nph, E, I.d_tph_ptr, I.d_tph_dst, (const T*)I.d_tph_w,
+                                          Cc.d_parent, Cc.d_octant, (const C*)P.d_shift, (const C*)P.d_V, (C*)I.d_tmp);
+        CU(cudaGetLastError());
+        dim3 g2(nblk((int64_t)Cc.K * E, th), Cc.nbox);
+        k_anterp_theta<T><<<g2, th, 0, s>>>(P.nth, Cc.nth, Cc.nph, E, I.d_tth_ptr, I.d_tth_dst, I.d_tth_flip,
+                                            (const T*)I.d_tth_w, (const C*)I.d_tmp, (C*)Cc.d_V);
+        CU(cudaGetLastError());
+    }
+    if (ev) CU(cudaEventRecord(ev[5], s));
+    else CU(cudaStreamWaitEvent(s, h->ev_join, 0));
+    {
+        level_t& L = h->lev[lf];
+        const double pi = 3.14159265358979323846;
+        T c = (T)(h->k * h->k / (32.0 * pi * pi));
+        int64_t nthreads = (int64_t)N * R * 32;
+        if (h->prm.op_mode == 0)
+            k_receive2<T, 0><<<nblk(nthreads, th), th, 0, s>>>(N, L.K, R, nun, h->d_perm, h->d_leaf_of, (const C*)h->d_F,
+                                                                (const C*)h->d_RX, (const C*)L.d_V, c, yt, y);
+        else
+            k_receive2<T, 1><<<nblk(nthreads, th), th, 0, s>>>(N, L.K, R, nun, h->d_perm, h->d_leaf_of, (const C*)h->d_F,
+                                                                (const C*)h->d_RX, (const C*)L.d_V, c, yt, y);
+        CU(cudaGetLastError());
+    }
+    if (ev) {
+        CU(cudaEventRecord(ev[6], s));
+        CU(cudaEventRecord(ev[7], s));
+    }
+}
+
 }  // namespace
 
 // Enqueue one product on stream s (no graph).
 static void matvec_enqueue(bi_handle_s* h, const void* x, void* y, int nrhs, cudaStream_t s, cudaStream_t side) {
-    if (h->prec == 0)
-        launch_all<double>(h, x, y, nrhs, s, side);
-    else
-        launch_all<float>(h, x, y, nrhs, s, side);
+    if (h->use_fast) {
+        if (h->prec == 0) launch_fast<double>(h, x, y, nrhs, s, side, nullptr);
+        else launch_fast<float>(h, x, y, nrhs, s, side, nullptr);
+    } else {
+        if (h->prec == 0) launch_all<double>(h, x, y, nrhs, s, side);
+        else launch_all<float>(h, x, y, nrhs, s, side);
+    }
 }
 
 // One product: replayed from a CUDA graph captured on first use for this (x, y, nrhs).
@@ -526,8 +1269,13 @@ void bi_profile_impl(bi_handle_s* h, const void* x, void* y, int nrhs, int reps,
     cudaStream_t s = h->stream;
     for (int r = 0; r < reps; ++r) {
         CU(cudaEventRecord(ev[0], s));
-        if (h->prec == 0) launch_all<double>(h, x, y, nrhs, s, s, ev + 1);
-        else launch_all<float>(h, x, y, nrhs, s, s, ev + 1);
+        if (h->use_fast) {
+            if (h->prec == 0) launch_fast<double>(h, x, y, nrhs, s, s, ev + 1);
+            else launch_fast<float>(h, x, y, nrhs, s, s, ev + 1);
+        } else {
+            if (h->prec == 0) launch_all<double>(h, x, y, nrhs, s, s, ev + 1);
+            else launch_all<float>(h, x, y, nrhs, s, s, ev + 1);
+        }
         CU(cudaEventSynchronize(ev[BI_NSTAGES]));
         for (int i = 0; i < BI_NSTAGES; ++i) {
             float t = 0;

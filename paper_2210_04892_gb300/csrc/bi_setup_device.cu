@@ -375,7 +375,8 @@ __device__ raw4 tri_pair(const dtri& Tm, int i, const dtri& Tn, int j, double k)
 // One CTA per near block (test leaf box b, source box s); threads loop over the block's
 // entries, column-major (source column outer, test row inner).
 template <typename T>
-__global__ void k_near_fill(int nblk, const int* __restrict__ blk_box, const int* __restrict__ near_src,
+__global__ void k_near_fill(int nblk, const int* __restrict__ blk_box, const int* __restrict__ near_ptr,
+                            const int* __restrict__ near_src,
                             const int64_t* __restrict__ near_blk, const int* __restrict__ leaf_start,
                             const int* __restrict__ rwg_t, const int* __restrict__ rwg_l, const double* __restrict__ rwg_len,
                             const double* __restrict__ tri, const double* __restrict__ nrm, const double* __restrict__ area,
@@ -385,7 +386,10 @@ __global__ void k_near_fill(int nblk, const int* __restrict__ blk_box, const int
     int b = blk_box[q], s = near_src[q];
     int m0 = leaf_start[b], mb = leaf_start[b + 1] - m0;
     int n0 = leaf_start[s], nbs = leaf_start[s + 1] - n0;
-    int64_t base = near_blk[q];
+    // the test box's blocks form one row-major mb x ncol segment (columns: near source RWGs)
+    const int64_t seg = near_blk[near_ptr[b]];
+    const int ncol = (int)((near_blk[near_ptr[b + 1]] - seg) / mb);
+    const int c0 = (int)((near_blk[q] - seg) / mb);
     int cnt = mb * nbs;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
         int ml = e % mb, nl = e / mb;
@@ -429,7 +433,7 @@ __global__ void k_near_fill(int nblk, const int* __restrict__ blk_box, const int
         double gA = (mode == 0) ? 1.0 : 0.25;
         zd A = zmk(P.x - gA * G, P.y);
         zd B = zmk(Q.x - 0.5 * X, Q.y);
-        int64_t o = base + e;
+        int64_t o = seg + (int64_t)ml * ncol + c0 + nl;
         if (mode == 0) {
             out[4 * o + 0] = (T)A.x;
             out[4 * o + 1] = (T)A.y;
@@ -720,12 +724,12 @@ void bi_fill_near(bi_handle_s* h) {
     h->d_near = h->alloc(per * (size_t)std::max<int64_t>(h->near_nnz, 1));
     if (nblk > 0) {
         if (h->prec == 0)
-            k_near_fill<double><<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_src, h->d_near_blk, h->d_leaf_start,
+            k_near_fill<double><<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_ptr, h->d_near_src, h->d_near_blk, h->d_leaf_start,
                                                               h->d_rwg_t, h->d_rwg_l, h->d_rwg_len, h->d_tri, h->d_tri_n,
                                                               h->d_tri_area, h->d_tri_vid, h->k, h->prm.op_mode,
                                                               (double*)h->d_near);
         else
-            k_near_fill<float><<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_src, h->d_near_blk, h->d_leaf_start,
+            k_near_fill<float><<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_ptr, h->d_near_src, h->d_near_blk, h->d_leaf_start,
                                                              h->d_rwg_t, h->d_rwg_l, h->d_rwg_len, h->d_tri, h->d_tri_n,
                                                              h->d_tri_area, h->d_tri_vid, h->k, h->prm.op_mode,
                                                              (float*)h->d_near);

@@ -262,6 +262,12 @@ void bi_build_tree(bi_handle_s* h, const double* V) {
         }
         h->near_nnz = off;
         h->near_blk.push_back(off);
+        h->near_ncol_max = 0;
+        for (int b = 0; b < LF.nbox; ++b) {
+            int mb = h->leaf_start[b + 1] - h->leaf_start[b];
+            int ncol = (int)((h->near_blk[h->near_ptr[b + 1]] - h->near_blk[h->near_ptr[b]]) / mb);
+            h->near_ncol_max = std::max(h->near_ncol_max, ncol);
+        }
     }
     // interaction lists on levels 2..leaf: children of the parent's neighbours that do not touch
     for (int l = 2; l < nlev; ++l) {

@@ -214,3 +214,20 @@ def test_c2_sampled_rows(bi):
     ref = Zr @ x[0]
     assert rel(y[rows], ref) < 1e-3
     op.close()
+
+
+@pytest.mark.parametrize("mode,nrhs", [(0, 1), (0, 3), (1, 5)])
+def test_fused_kernels_match_two_pass_kernels(bi, mode, nrhs, monkeypatch):
+    """The fused/streaming kernels and the two-pass reference kernels give the same product
+    (FP64; 4 levels so the interpolation and anterpolation kernels run)."""
+    v, t = icosphere(16, 1.0)
+    x = None
+    ys = []
+    for two_pass in ("0", "1"):
+        monkeypatch.setenv("BI_TWO_PASS", two_pass)
+        op = bi.Operator(v, t, K0, precision="fp64", op_mode=mode, max_rhs=nrhs)
+        if x is None:
+            x = complex_gaussian(op.n_unknowns, nrhs, seed=SEED_BASE + 5)
+        ys.append(op.matvec(torch.from_numpy(x).cuda()).cpu().numpy())
+        op.close()
+    assert rel(ys[0], ys[1]) < 1e-12
