@@ -135,6 +135,15 @@ int bi_rhs_planewave(bi_handle h, const double* khat, const double* phat, int nr
  * column missed tol (x holds the last iterate). */
 int bi_solve(bi_handle h, const void* rhs, void* x, int nrhs, double tol, int* iters, double* relres);
 
+/* Far field of the currents x (Eq. 22a in the far zone, time factor exp(-jkr)/r removed):
+ *   F(rhat) = -jk/(4 pi) [ (I - rhat rhat) N_J - rhat x N_M ],  N_X = sum_n x_X,n int f_n exp(+jk rhat.r') ds',
+ * so that sigma(rhat) = 4 pi |F(rhat)|^2 for a unit incident field (RCS of Sec. III, Eq. 5-25).
+ * x: device, column-major [nrhs][n_unknowns] in the handle precision (op_mode 1: M = 0).
+ * dirs: device float64 [ndir][3] unit vectors.  F: device complex128 [nrhs][ndir][3].
+ * Partial sums go to scratch memory that the handle allocates on first use (and grows
+ * when a later call needs more) and keeps until bi_destroy.  Queued on the handle's stream. */
+int bi_farfield(bi_handle h, const void* x, int nrhs, const double* dirs, int ndir, void* F);
+
 /* Diagnostics: copy an internal device buffer of h to host memory.
  *   what 0: leaf radiation patterns F [N_tree][K_leaf][2] complex (tree order, theta/phi)
  *   what 1: leaf twisted receive patterns RX [N_tree][K_leaf][2]

@@ -27,7 +27,7 @@ _NAMES = {0: "BI_OK", -1: "BI_ERR_ARG", -2: "BI_ERR_MESH", -3: "BI_ERR_OOM", -4:
 
 # entry points declared in include/bi.h
 EXPORTS = ["bi_default_params", "bi_setup", "bi_num_unknowns", "bi_rwg_edges", "bi_get_info", "bi_matvec",
-           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_debug_copy", "bi_profile_stages", "bi_stage_name", "bi_last_error",
+           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_farfield", "bi_debug_copy", "bi_profile_stages", "bi_stage_name", "bi_last_error",
            "bi_destroy"]
 
 
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
     L.bi_matvec_host.argtypes = [vp, vp, vp, i]
     L.bi_rhs_planewave.argtypes = [vp, vp, vp, i, vp]
     L.bi_solve.argtypes = [vp, vp, vp, i, d, vp, vp]
+    L.bi_farfield.argtypes = [vp, vp, i, vp, i, vp]
     L.bi_debug_copy.argtypes = [vp, i, i, vp, i64]
     L.bi_profile_stages.argtypes = [vp, vp, vp, i, i, vp]
     L.bi_stage_name.argtypes = [i]
@@ -236,6 +237,20 @@ class Operator:
         out = np.zeros(shape, self.np_cdtype)
         _check(load().bi_debug_copy(self.h, what, level, out.ctypes.data, out.nbytes), self.h)
         return out
+
+    def farfield(self, x, dirs):
+        """Far-field vectors F [nrhs, ndir, 3] (complex128, CUDA) of currents x; sigma = 4 pi |F|^2."""
+        import torch
+        x = self._vec(x)
+        d = torch.as_tensor(np.ascontiguousarray(np.atleast_2d(dirs), np.float64)).cuda()
+        F = torch.empty((x.shape[0], d.shape[0], 3), dtype=torch.complex128, device="cuda")
+        _check(load().bi_farfield(self.h, x.data_ptr(), x.shape[0], d.data_ptr(), d.shape[0], F.data_ptr()), self.h)
+        return F
+
+    def rcs(self, x, dirs):
+        """Bistatic RCS sigma [nrhs, ndir] (area units) of currents x."""
+        F = self.farfield(x, dirs)
+        return (4 * np.pi * (F.abs() ** 2).sum(-1)).cpu().numpy()
 
     def close(self):
         if getattr(self, "h", None):

@@ -290,3 +290,22 @@ extern "C" int bi_profile_stages(bi_handle h, const void* x, void* y, int nrhs, 
 }
 
 extern "C" const char* bi_stage_name(int i) { return bi_stage_name_impl(i); }
+
+extern "C" int bi_farfield(bi_handle h, const void* x, int nrhs, const double* dirs, int ndir, void* F) {
+    if (!h) return BI_ERR_ARG;
+    if (!x || !dirs || !F || nrhs < 1 || ndir < 1 || nrhs > 65535 || ndir > 65535) {
+        h->err = "bi_farfield: null argument or nrhs/ndir outside [1, 65535]";
+        return BI_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        size_t need = bi_farfield_scratch_bytes(h, nrhs, ndir);
+        if (need > h->ffscratch_bytes) {
+            // scratch is kept by the handle and reused by later calls
+            CU(cudaStreamSynchronize(h->stream));
+            h->d_ffscratch = h->alloc(need);
+            h->ffscratch_bytes = need;
+        }
+        bi_farfield_launch(h, x, nrhs, dirs, ndir, F, (double*)h->d_ffscratch, h->stream);
+        return (int)BI_OK;
+    });
+}

@@ -101,6 +101,8 @@ struct bi_handle_s {
     bool use_graphs = true;
     bool use_fast = true;               // fused kernels (false: two-pass reference kernels)
     int near_ncol_max = 0;
+    int near_nwork = 0;                 // work items of the streaming near kernel (box, first row)
+    int* d_near_work = nullptr;
     int num_sms = 152;              // widest near segment of a leaf box (columns)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
@@ -133,6 +135,7 @@ struct bi_handle_s {
     void* d_near = nullptr;             // near blocks: per pair (A, B) complex (mode 0) or A (mode 1)
     int* d_gram_ptr = nullptr;          // mode 0: Gram correction per tree row
     int* d_gram_col = nullptr;
+    int* d_gram_seg = nullptr;          // column of the neighbour in the test box's near segment
     void* d_gram_val = nullptr;         // [nnz][2] real: (G, X)
     void* d_F = nullptr;                // leaf radiation patterns [N][K][2]
     void* d_RX = nullptr;               // leaf twisted receive patterns [N][K][2]
@@ -151,6 +154,8 @@ struct bi_handle_s {
     void* d_yfar = nullptr;             // [N][nX][R]
     void* d_sx = nullptr;               // staging [R][nun] (host API and GMRES matvec input)
     void* d_sy = nullptr;               // staging [R][nun] (output)
+    void* d_ffscratch = nullptr;        // far-field partial sums (grown on demand)
+    size_t ffscratch_bytes = 0;
     void* h_pinned = nullptr;           // pinned host staging
     size_t h_pinned_bytes = 0;
 
@@ -189,6 +194,9 @@ void bi_matvec_launch(bi_handle_s* h, const void* x, void* y, int nrhs, cudaStre
 void bi_rhs_launch(bi_handle_s* h, const double* khat, const double* phat, int nrhs, void* b);
 void bi_profile_impl(bi_handle_s* h, const void* x, void* y, int nrhs, int reps, double* ms);
 const char* bi_stage_name_impl(int i);
+size_t bi_farfield_scratch_bytes(const bi_handle_s* h, int nrhs, int ndir);
+void bi_farfield_launch(bi_handle_s* h, const void* x, int nrhs, const double* dirs, int ndir, void* F, double* part,
+                        cudaStream_t s);
 int bi_gmres(bi_handle_s* h, const void* rhs, void* x, int nrhs, double tol, int* iters, double* relres);
 
 // numerical helpers shared by the host setup files of the library (not by the oracle)

@@ -418,21 +418,24 @@ __device__ __forceinline__ cpx<T> warp_sum(cpx<T> v) {
 
 template <typename T, int MODE, int RT>
 __global__ void __launch_bounds__(256) k_near_stream(int N, int R, int nun, const int* __restrict__ perm,
+                                                     const int2* __restrict__ work,
                                                      const int* __restrict__ leaf_start, const int* __restrict__ near_ptr,
                                                      const int* __restrict__ near_src, const int64_t* __restrict__ near_blk,
                                                      const cpx<T>* __restrict__ blocks, const int* __restrict__ gptr,
-                                                     const int* __restrict__ gcol, const T* __restrict__ gval,
+                                                     const int* __restrict__ gseg, const T* __restrict__ gval,
                                                      const cpx<T>* __restrict__ x, cpx<T>* __restrict__ yt,
                                                      cpx<T>* __restrict__ yuser) {
     constexpr int NX = MODE == 0 ? 2 : 1;
     extern __shared__ unsigned char smem_raw[];
     cpx<T>* xs = reinterpret_cast<cpx<T>*>(smem_raw);  // [NX][RT][ncol]
-    const int b = blockIdx.x;
+    // work item: test box and its first row; a CTA covers up to 2 * (blockDim / 32) rows
+    const int b = work[blockIdx.x].x, row0 = work[blockIdx.x].y;
     const int m0 = leaf_start[b], mb = leaf_start[b + 1] - m0;
     const int q0 = near_ptr[b], q1 = near_ptr[b + 1];
     const int64_t seg = near_blk[q0];
     const int ncol = (int)((near_blk[q1] - seg) / mb);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const int row_end = min(mb, row0 + 2 * nwarp);
     for (int r0 = 0; r0 < R; r0 += RT) {
         const int rn = min(RT, R - r0);
         __syncthreads();
@@ -451,53 +454,82 @@ __global__ void __launch_bounds__(256) k_near_stream(int N, int R, int nun, cons
             }
         }
         __syncthreads();
-        for (int ml = warp; ml < mb; ml += nwarp) {
-            cpx<T> aJ[RT], aM[RT];
+        // each warp streams two rows at once (independent loads in flight for both)
+        {
+            const int mlA = row0 + 2 * warp, mlB = mlA + 1;
+            const bool hasA = mlA < row_end, hasB = mlB < row_end;
+            cpx<T> aJ[2][RT], aM[2][RT];
 #pragma unroll
-            for (int rr = 0; rr < RT; ++rr) { aJ[rr] = czero<T>(); aM[rr] = czero<T>(); }
-            const cpx<T>* row = blocks + (MODE == 0 ? 2 : 1) * (seg + (int64_t)ml * ncol);
+            for (int h2 = 0; h2 < 2; ++h2)
+#pragma unroll
+                for (int rr = 0; rr < RT; ++rr) { aJ[h2][rr] = czero<T>(); aM[h2][rr] = czero<T>(); }
+            const int stride = (MODE == 0 ? 2 : 1);
+            const cpx<T>* rowA = blocks + stride * (seg + (int64_t)(hasA ? mlA : 0) * ncol);
+            const cpx<T>* rowB = blocks + stride * (seg + (int64_t)(hasB ? mlB : 0) * ncol);
+            if (hasA) {
 #pragma unroll 4
-            for (int c = lane; c < ncol; c += 32) {
-                if (MODE == 0) {
-                    cpx<T> A, B;
-                    load_pair(row + 2 * c, A, B);
-#pragma unroll
-                    for (int rr = 0; rr < RT; ++rr) {
-                        const cpx<T> xJ = xs[(size_t)(0 * RT + rr) * ncol + c], xM = xs[(size_t)(1 * RT + rr) * ncol + c];
-                        cfma(aJ[rr], A, xJ);
-                        cfma(aJ[rr], B, xM);
-                        cfma(aM[rr], B, xJ);
-                        cfma(aM[rr], A, cpx<T>{-xM.x, -xM.y});
-                    }
-                } else {
-                    const cpx<T> A = row[c];
-#pragma unroll
-                    for (int rr = 0; rr < RT; ++rr) cfma(aJ[rr], A, xs[(size_t)rr * ncol + c]);
-                }
-            }
-            const int m = m0 + ml;
-#pragma unroll
-            for (int rr = 0; rr < RT; ++rr) {
-                const cpx<T> sJ = warp_sum(aJ[rr]);
-                cpx<T> sM = MODE == 0 ? warp_sum(aM[rr]) : czero<T>();
-                if (lane == 0 && rr < rn) {
-                    const int r = r0 + rr;
+                for (int c = lane; c < ncol; c += 32) {
                     if (MODE == 0) {
-                        for (int qq = gptr[m]; qq < gptr[m + 1]; ++qq) {
-                            const int n = gcol[qq];
-                            const T gg = gval[2 * qq], xx = gval[2 * qq + 1];
-                            const cpx<T> xJ = x[(int64_t)r * nun + perm[n]], xM = x[(int64_t)r * nun + N + perm[n]];
-                            sM.x += T(0.5) * (xx * xJ.x - gg * xM.x);
-                            sM.y += T(0.5) * (xx * xJ.y - gg * xM.y);
+                        cpx<T> A0, B0, A1 = czero<T>(), B1 = czero<T>();
+                        load_pair(rowA + 2 * c, A0, B0);
+                        if (hasB) load_pair(rowB + 2 * c, A1, B1);
+#pragma unroll
+                        for (int rr = 0; rr < RT; ++rr) {
+                            const cpx<T> xJ = xs[(size_t)(0 * RT + rr) * ncol + c], xM = xs[(size_t)(1 * RT + rr) * ncol + c];
+                            const cpx<T> nxM = {-xM.x, -xM.y};
+                            cfma(aJ[0][rr], A0, xJ);
+                            cfma(aJ[0][rr], B0, xM);
+                            cfma(aM[0][rr], B0, xJ);
+                            cfma(aM[0][rr], A0, nxM);
+                            cfma(aJ[1][rr], A1, xJ);
+                            cfma(aJ[1][rr], B1, xM);
+                            cfma(aM[1][rr], B1, xJ);
+                            cfma(aM[1][rr], A1, nxM);
+                        }
+                    } else {
+                        const cpx<T> A0 = rowA[c];
+                        const cpx<T> A1 = hasB ? rowB[c] : czero<T>();
+#pragma unroll
+                        for (int rr = 0; rr < RT; ++rr) {
+                            cfma(aJ[0][rr], A0, xs[(size_t)rr * ncol + c]);
+                            cfma(aJ[1][rr], A1, xs[(size_t)rr * ncol + c]);
                         }
                     }
-                    const cpx<T> vJ = {-sJ.x, -sJ.y};
-                    if (yuser) {
-                        yuser[(int64_t)r * nun + perm[m]] = vJ;
-                        if (MODE == 0) yuser[(int64_t)r * nun + N + perm[m]] = sM;
-                    } else {
-                        yt[((int64_t)m * NX + 0) * R + r] = vJ;
-                        if (MODE == 0) yt[((int64_t)m * NX + 1) * R + r] = sM;
+                }
+            }
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const int ml = h2 == 0 ? mlA : mlB;
+                if (ml >= row_end) continue;
+                const int m = m0 + ml;
+                if (MODE == 0) {
+                    // Gram correction of the M row, (X/2) x_J - (G/2) x_M: one neighbour per lane, x from shared memory
+                    const int g0 = gptr[m], gn = gptr[m + 1] - g0;
+                    for (int qq = lane; qq < gn; qq += 32) {
+                        const int c = gseg[g0 + qq];
+                        const T gg = gval[2 * (g0 + qq)], xx = gval[2 * (g0 + qq) + 1];
+#pragma unroll
+                        for (int rr = 0; rr < RT; ++rr) {
+                            const cpx<T> xJ = xs[(size_t)(0 * RT + rr) * ncol + c], xM = xs[(size_t)(1 * RT + rr) * ncol + c];
+                            aM[h2][rr].x += T(0.5) * (xx * xJ.x - gg * xM.x);
+                            aM[h2][rr].y += T(0.5) * (xx * xJ.y - gg * xM.y);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int rr = 0; rr < RT; ++rr) {
+                    const cpx<T> sJ = warp_sum(aJ[h2][rr]);
+                    const cpx<T> sM = MODE == 0 ? warp_sum(aM[h2][rr]) : czero<T>();
+                    if (lane == 0 && rr < rn) {
+                        const int r = r0 + rr;
+                        const cpx<T> vJ = {-sJ.x, -sJ.y};
+                        if (yuser) {
+                            yuser[(int64_t)r * nun + perm[m]] = vJ;
+                            if (MODE == 0) yuser[(int64_t)r * nun + N + perm[m]] = sM;
+                        } else {
+                            yt[((int64_t)m * NX + 0) * R + r] = vJ;
+                            if (MODE == 0) yt[((int64_t)m * NX + 1) * R + r] = sM;
+                        }
                     }
                 }
             }
@@ -511,9 +543,11 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_aggregate2(int N, int K, int R, int nun, const int* __restrict__ perm,
                                                     const int* __restrict__ leaf_start, const cpx<T>* __restrict__ F,
                                                     const cpx<T>* __restrict__ x, cpx<T>* __restrict__ U) {
-    // x of the box's RWGs (J then M) for every RHS, staged once per CTA
+    // CTA = (box, 64 direction-RHS slots); the box's RWGs are split over 4 thread groups whose
+    // partial sums meet in shared memory.  x of the box is staged once per CTA.
     extern __shared__ unsigned char smem_raw[];
     cpx<T>* xs = reinterpret_cast<cpx<T>*>(smem_raw);  // [nb][2][R]
+    __shared__ cpx<T> red[4][64][2];
     const int b = blockIdx.y;
     const int n0 = leaf_start[b], nb = leaf_start[b + 1] - n0;
     for (int i = threadIdx.x; i < nb * 2 * R; i += blockDim.x) {
@@ -521,28 +555,39 @@ __global__ void __launch_bounds__(256) k_aggregate2(int N, int K, int R, int nun
         xs[i] = (MODE == 0 || X == 0) ? x[(int64_t)r * nun + (int64_t)X * N + perm[n0 + n]] : czero<T>();
     }
     __syncthreads();
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= K * R) return;
-    const int kk = idx / R, r = idx % R;
-    const int E = 2 * R;
+    const int slot = threadIdx.x & 63, grp = threadIdx.x >> 6;
+    const int idx = blockIdx.x * 64 + slot;
+    const bool ok = idx < K * R;
+    const int kk = ok ? idx / R : 0, r = ok ? idx % R : 0;
     cpx<T> ut = czero<T>(), up = czero<T>();
-    const cpx<T>* f = F + ((int64_t)n0 * K + kk) * 2;
-#pragma unroll 8
-    for (int n = 0; n < nb; ++n) {
-        cpx<T> Ft, Fp;
-        load_pair(f + (int64_t)n * K * 2, Ft, Fp);
-        const cpx<T> xJ = xs[(n * 2 + 0) * R + r];
-        ut = csub(ut, cmul(xJ, Ft));
-        up = csub(up, cmul(xJ, Fp));
-        if (MODE == 0) {
-            const cpx<T> xM = xs[(n * 2 + 1) * R + r];
-            ut = csub(ut, cmul(xM, Fp));
-            up = cadd(up, cmul(xM, Ft));
+    if (ok) {
+        const cpx<T>* f = F + ((int64_t)n0 * K + kk) * 2;
+#pragma unroll 4
+        for (int n = grp; n < nb; n += 4) {
+            cpx<T> Ft, Fp;
+            load_pair(f + (int64_t)n * K * 2, Ft, Fp);
+            const cpx<T> xJ = xs[(n * 2 + 0) * R + r];
+            ut = csub(ut, cmul(xJ, Ft));
+            up = csub(up, cmul(xJ, Fp));
+            if (MODE == 0) {
+                const cpx<T> xM = xs[(n * 2 + 1) * R + r];
+                ut = csub(ut, cmul(xM, Fp));
+                up = cadd(up, cmul(xM, Ft));
+            }
         }
     }
-    cpx<T>* o = U + ((int64_t)b * K + kk) * E;
-    o[r] = ut;
-    o[R + r] = up;
+    red[grp][slot][0] = ut;
+    red[grp][slot][1] = up;
+    __syncthreads();
+    if (grp == 0 && ok) {
+        for (int g2 = 1; g2 < 4; ++g2) {
+            ut = cadd(ut, red[g2][slot][0]);
+            up = cadd(up, red[g2][slot][1]);
+        }
+        cpx<T>* o = U + ((int64_t)b * K + kk) * (2 * R);
+        o[r] = ut;
+        o[R + r] = up;
+    }
 }
 
 // ------------------------------------------------------------------ fused interpolation (one CTA per parent)
@@ -698,32 +743,48 @@ __global__ void __launch_bounds__(256) k_interp_child(int nthc, int nphc, int nt
     const cpx<T>* u = Uc + (int64_t)cb * Kc * E;
     for (int i = threadIdx.x; i < Kc * E; i += blockDim.x) s1[i] = u[i];
     __syncthreads();
-    for (int i = threadIdx.x; i < nthp * nphc * E; i += blockDim.x) {
-        const int e = i % E, jc = (i / E) % nphc, ip = i / (E * nphc);
-        cpx<T> a = czero<T>();
-        for (int t = 0; t < pth; ++t) {
-            const int code = tsrc[ip * pth + t];
-            const int j = (code & 1) ? (jc + half) % nphc : jc;
-            const cpx<T> v = s1[((size_t)(code >> 1) * nphc + j) * E + e];
-            const T w = tw[ip * pth + t];
-            a.x = fma(w, v.x, a.x);
-            a.y = fma(w, v.y, a.y);
+    // theta pass: thread owns one (column, component) slot of a row and walks the rows
+    const int W = nphc * E, Wp = nphp * E;
+    for (int cbase = 0; cbase < W; cbase += blockDim.x) {
+        const int lanes = min(W - cbase, (int)blockDim.x);
+        const int rpp = blockDim.x / lanes;
+        const int col = cbase + threadIdx.x % lanes, r0 = threadIdx.x / lanes;
+        if (r0 >= rpp) continue;
+        const int jc = col / E, e = col - jc * E;
+        const int off0 = col, off1 = ((jc + half) % nphc) * E + e;
+        for (int ip = r0; ip < nthp; ip += rpp) {
+            cpx<T> a = czero<T>();
+            for (int t = 0; t < pth; ++t) {
+                const int code = tsrc[ip * pth + t];
+                const cpx<T> v = s1[(code >> 1) * W + ((code & 1) ? off1 : off0)];
+                const T w = tw[ip * pth + t];
+                a.x = fma(w, v.x, a.x);
+                a.y = fma(w, v.y, a.y);
+            }
+            s2[ip * W + col] = a;
         }
-        s2[i] = a;
     }
     __syncthreads();
     const cpx<T>* sh = shift + (int64_t)octant[cb] * Kp;
     cpx<T>* up = Up + (int64_t)parent[cb] * Kp * E;
-    for (int i = threadIdx.x; i < Kp * E; i += blockDim.x) {
-        const int e = i % E, kk = i / E, ip = kk / nphp, jp = kk % nphp;
-        cpx<T> a = czero<T>();
-        for (int q = 0; q < pph; ++q) {
-            const cpx<T> v = s2[((size_t)ip * nphc + psrc[jp * pph + q]) * E + e];
-            const T w = pw[jp * pph + q];
-            a.x = fma(w, v.x, a.x);
-            a.y = fma(w, v.y, a.y);
+    for (int cbase = 0; cbase < Wp; cbase += blockDim.x) {
+        const int lanes = min(Wp - cbase, (int)blockDim.x);
+        const int rpp = blockDim.x / lanes;
+        const int col = cbase + threadIdx.x % lanes, r0 = threadIdx.x / lanes;
+        if (r0 >= rpp) continue;
+        const int jp = col / E, e = col - jp * E;
+        const int* ps = psrc + jp * pph;
+        const T* pwj = pw + jp * pph;
+        for (int ip = r0; ip < nthp; ip += rpp) {
+            const cpx<T>* row = s2 + ip * W + e;
+            cpx<T> a = czero<T>();
+            for (int q = 0; q < pph; ++q) {
+                const cpx<T> v = row[ps[q] * E];
+                a.x = fma(pwj[q], v.x, a.x);
+                a.y = fma(pwj[q], v.y, a.y);
+            }
+            atomic_add_c(up + ip * Wp + col, cmul(sh[ip * nphp + jp], a));
         }
-        atomic_add_c(up + i, cmul(sh[kk], a));
     }
 }
 
@@ -759,38 +820,55 @@ __global__ void __launch_bounds__(256) k_anterp_child(int nthc, int nphc, int nt
     const cpx<T>* vp = Vp + (int64_t)parent[cb] * Kp * E;
     for (int i = threadIdx.x; i < Kp * E; i += blockDim.x) s0[i] = cmulc(sh[i / E], vp[i]);
     __syncthreads();
-    for (int i = threadIdx.x; i < nthp * nphc * E; i += blockDim.x) {
-        const int e = i % E, jc = (i / E) % nphc, ip = i / (E * nphc);
-        cpx<T> a = czero<T>();
-        for (int q = pptr[jc]; q < pptr[jc + 1]; ++q) {
-            const cpx<T> v = s0[((size_t)ip * nphp + pdst[q]) * E + e];
-            a.x = fma(pw[q], v.x, a.x);
-            a.y = fma(pw[q], v.y, a.y);
+    const int W = nphc * E, Wp = nphp * E;
+    for (int cbase = 0; cbase < W; cbase += blockDim.x) {
+        const int lanes = min(W - cbase, (int)blockDim.x);
+        const int rpp = blockDim.x / lanes;
+        const int col = cbase + threadIdx.x % lanes, r0 = threadIdx.x / lanes;
+        if (r0 >= rpp) continue;
+        const int jc = col / E, e = col - jc * E;
+        const int q0 = pptr[jc], q1 = pptr[jc + 1];
+        for (int ip = r0; ip < nthp; ip += rpp) {
+            const cpx<T>* row = s0 + ip * Wp + e;
+            cpx<T> a = czero<T>();
+            for (int q = q0; q < q1; ++q) {
+                const cpx<T> v = row[pdst[q] * E];
+                a.x = fma(pw[q], v.x, a.x);
+                a.y = fma(pw[q], v.y, a.y);
+            }
+            s2[ip * W + col] = a;
         }
-        s2[i] = a;
     }
     __syncthreads();
     cpx<T>* vc = Vc + (int64_t)cb * Kc * E;
-    for (int i = threadIdx.x; i < Kc * E; i += blockDim.x) {
-        const int e = i % E, kk = i / E, ic = kk / nphc, jc = kk % nphc;
-        cpx<T> a = czero<T>();
-        for (int q = tptr[ic]; q < tptr[ic + 1]; ++q) {
-            const int code = tdst[q];
-            const int j = (code & 1) ? (jc + half) % nphc : jc;
-            const cpx<T> v = s2[((size_t)(code >> 1) * nphc + j) * E + e];
-            a.x = fma(tw[q], v.x, a.x);
-            a.y = fma(tw[q], v.y, a.y);
+    for (int cbase = 0; cbase < W; cbase += blockDim.x) {
+        const int lanes = min(W - cbase, (int)blockDim.x);
+        const int rpp = blockDim.x / lanes;
+        const int col = cbase + threadIdx.x % lanes, r0 = threadIdx.x / lanes;
+        if (r0 >= rpp) continue;
+        const int jc = col / E, e = col - jc * E;
+        const int off0 = col, off1 = ((jc + half) % nphc) * E + e;
+        for (int ic = r0; ic < nthc; ic += rpp) {
+            cpx<T> a = czero<T>();
+            for (int q = tptr[ic]; q < tptr[ic + 1]; ++q) {
+                const int code = tdst[q];
+                const cpx<T> v = s2[(code >> 1) * W + ((code & 1) ? off1 : off0)];
+                a.x = fma(tw[q], v.x, a.x);
+                a.y = fma(tw[q], v.y, a.y);
+            }
+            vc[ic * W + col] = cadd(vc[ic * W + col], a);
         }
-        vc[i] = cadd(vc[i], a);
     }
 }
 
 // ------------------------------------------------------------------ leaf receive with the final permutation
 // y_user[perm[m]] = y_near[m] + far part (the near result in tree order is added here).
 template <typename T, int MODE>
-__global__ void k_receive2(int N, int K, int R, int nun, const int* __restrict__ perm, const int* __restrict__ leaf_of,
-                           const cpx<T>* __restrict__ F, const cpx<T>* __restrict__ RX, const cpx<T>* __restrict__ V, T c,
-                           const cpx<T>* __restrict__ yt, cpx<T>* __restrict__ y) {
+__global__ void __launch_bounds__(256) k_receive2(int N, int K, int R, int nun, const int* __restrict__ perm,
+                                                  const int* __restrict__ leaf_of, const cpx<T>* __restrict__ F,
+                                                  const cpx<T>* __restrict__ RX, const cpx<T>* __restrict__ V, T c,
+                                                  const cpx<T>* __restrict__ yt, cpx<T>* __restrict__ y) {
+    // one warp per (tree RWG m, RHS r); lanes stride over directions, then a shuffle reduction
     const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (warp >= N * R) return;
@@ -804,24 +882,16 @@ __global__ void k_receive2(int N, int K, int R, int nun, const int* __restrict__
         load_pair(F + ((int64_t)m * K + kk) * 2, Ft, Fp);
         load_pair(RX + ((int64_t)m * K + kk) * 2, Xt, Xp);
         const cpx<T> Vt = V[((int64_t)b * K + kk) * E + r], Vp = V[((int64_t)b * K + kk) * E + R + r];
-        cpx<T> RV = cadd(cmulc(Ft, Vt), cmulc(Fp, Vp));
-        cpx<T> XkV = csub(cmul(Xp, Vt), cmul(Xt, Vp));
-        sJ = cadd(sJ, csub(RV, XkV));
+        // R.V - RX.(khat x V) with R = conj(F), (khat x V) = (-V_phi, V_theta)
+        sJ = cadd(sJ, csub(cadd(cmulc(Ft, Vt), cmulc(Fp, Vp)), csub(cmul(Xp, Vt), cmul(Xt, Vp))));
         if (MODE == 0) {
-            cpx<T> t = csub(cmulc(Ft, Vp), cmulc(Fp, Vt));
-            t = csub(t, cmul(Xt, Vt));
-            t = csub(t, cmul(Xp, Vp));
-            sM = cadd(sM, t);
+            // -R.(khat x V) - RX.V
+            const cpx<T> t = csub(cmulc(Ft, Vp), cmulc(Fp, Vt));
+            sM = cadd(sM, csub(t, cadd(cmul(Xt, Vt), cmul(Xp, Vp))));
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        sJ.x += __shfl_xor_sync(0xffffffffu, sJ.x, o);
-        sJ.y += __shfl_xor_sync(0xffffffffu, sJ.y, o);
-        if (MODE == 0) {
-            sM.x += __shfl_xor_sync(0xffffffffu, sM.x, o);
-            sM.y += __shfl_xor_sync(0xffffffffu, sM.y, o);
-        }
-    }
+    sJ = warp_sum(sJ);
+    if (MODE == 0) sM = warp_sum(sM);
     if (lane == 0) {
         const int u = perm[m];
         if (MODE == 0) {
@@ -990,8 +1060,9 @@ void launch_near_stream(bi_handle_s* h, const cpx<T>* x, cpx<T>* yt, cpx<T>* yus
     size_t smem = (size_t)h->near_ncol_max * NX * RT * sizeof(cpx<T>);
     auto kern = k_near_stream<T, MODE, RT>;
     if (smem > 48 * 1024) CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<h->lev[h->leaf].nbox, 256, smem, s>>>(h->N, R, h->nun, h->d_perm, h->d_leaf_start, h->d_near_ptr, h->d_near_src,
-                                                 h->d_near_blk, (const cpx<T>*)h->d_near, h->d_gram_ptr, h->d_gram_col,
+    kern<<<h->near_nwork, 256, smem, s>>>(h->N, R, h->nun, h->d_perm, (const int2*)h->d_near_work, h->d_leaf_start,
+                                          h->d_near_ptr, h->d_near_src,
+                                                 h->d_near_blk, (const cpx<T>*)h->d_near, h->d_gram_ptr, h->d_gram_seg,
                                                  (const T*)h->d_gram_val, x, yt, yuser);
     CU(cudaGetLastError());
 }
@@ -1134,7 +1205,7 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
     const int lf = h->leaf;
     {
         level_t& L = h->lev[lf];
-        dim3 g(nblk((int64_t)L.K * R, th), L.nbox);
+        dim3 g(nblk((int64_t)L.K * R, 64), L.nbox);
         size_t smem = (size_t)h->max_leaf_count * 2 * R * sizeof(C);
         if (smem > 48 * 1024) {
             CU(cudaFuncSetAttribute(k_aggregate2<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -636,6 +636,17 @@ void bi_device_geometry(bi_handle_s* h, const double* V, const int* Tm) {
     h->d_near_ptr = h->upload(h->near_ptr);
     h->d_near_src = h->upload(h->near_src);
     h->d_near_blk = h->upload(h->near_blk);
+    {
+        // streaming near kernel work items: up to 16 rows (8 warps x 2 rows) of one test box
+        std::vector<int> work;
+        for (int b = 0; b < LF.nbox; ++b)
+            for (int r0 = 0; r0 < h->leaf_start[b + 1] - h->leaf_start[b]; r0 += 16) {
+                work.push_back(b);
+                work.push_back(r0);
+            }
+        h->near_nwork = (int)(work.size() / 2);
+        h->d_near_work = h->upload(work);
+    }
     std::vector<double> cen = LF.center;
     h->d_leaf_center = h->upload(cen);
     h->tri_host = tri;
@@ -781,11 +792,25 @@ void bi_fill_near(bi_handle_s* h) {
                     rx[m][pos] += c * gx;
                 }
         }
-        std::vector<int> ptr(N + 1, 0), col;
+        // column of each Gram neighbour inside its test box's near segment (x is staged there)
+        const level_t& LFb = h->lev[h->leaf];
+        std::vector<int> leaf_of_t(N);
+        for (int b = 0; b < LFb.nbox; ++b)
+            for (int t = h->leaf_start[b]; t < h->leaf_start[b + 1]; ++t) leaf_of_t[t] = b;
+        std::vector<int> ptr(N + 1, 0), col, segc;
         std::vector<double> val;
         for (int m = 0; m < N; ++m) {
+            const int b = leaf_of_t[m];
+            const int mb = h->leaf_start[b + 1] - h->leaf_start[b];
+            const int64_t seg = h->near_blk[h->near_ptr[b]];
             for (size_t q = 0; q < rc[m].size(); ++q) {
-                col.push_back(rc[m][q]);
+                const int n = rc[m][q], sb = leaf_of_t[n];
+                int c = -1;
+                for (int qq = h->near_ptr[b]; qq < h->near_ptr[b + 1]; ++qq)
+                    if (h->near_src[qq] == sb) c = (int)((h->near_blk[qq] - seg) / mb) + (n - h->leaf_start[sb]);
+                if (c < 0) throw bi_error{BI_ERR_MESH, "Gram neighbour outside the near field (mesh too coarse for the leaf box)"};
+                col.push_back(n);
+                segc.push_back(c);
                 val.push_back(rg[m][q]);
                 val.push_back(rx[m][q]);
             }
@@ -793,6 +818,7 @@ void bi_fill_near(bi_handle_s* h) {
         }
         h->d_gram_ptr = h->upload(ptr);
         h->d_gram_col = h->upload(col);
+        h->d_gram_seg = h->upload(segc);
         if (h->prec == 0) {
             h->d_gram_val = h->upload(val);
         } else {

@@ -231,3 +231,38 @@ def test_fused_kernels_match_two_pass_kernels(bi, mode, nrhs, monkeypatch):
         ys.append(op.matvec(torch.from_numpy(x).cuda()).cpu().numpy())
         op.close()
     assert rel(ys[0], ys[1]) < 1e-12
+
+
+def test_farfield_matches_oracle(bi, sphere_c1):
+    v, t = sphere_c1
+    op = bi.Operator(v, t, K0, precision="fp64", op_mode=0, max_rhs=2)
+    x = complex_gaussian(op.n_unknowns, 2, seed=SEED_BASE + 7)
+    th = np.deg2rad(np.arange(0, 181, 3))
+    dirs = np.stack([np.sin(th), 0 * th, np.cos(th)], 1)
+    F = op.farfield(torch.from_numpy(x).cuda(), dirs).cpu().numpy()
+    for r in range(2):
+        ref = oracle.farfield(v, t, K0, 0, x[r], dirs)
+        assert rel(F[r], ref) < 1e-5
+    op.close()
+
+
+@pytest.mark.parametrize("nu,radius,tol", [(8, 0.5, 1e-4), (32, 2.0, 1e-4)])
+def test_pec_sphere_solve_rcs_vs_mie(bi, nu, radius, tol):
+    """PEC combined-field solve (GMRES on the GPU, FP32 MLFMA) of a plane wave along +z
+    polarised along x, RCS from the GPU far field against the Mie series (Sec. III.A
+    metric): within 0.5 dB where sigma >= max - 20 dB.  radius 2 lambda is the 20,480-triangle
+    sphere of the coated-sphere outer surface."""
+    from oracle import mie
+    v, t = icosphere(nu, radius)
+    op = bi.Operator(v, t, K0, precision="fp32", op_mode=1, max_rhs=1)
+    b = op.rhs_planewave([0, 0, 1.0], [1.0, 0, 0])
+    x, its, relres = op.solve(b, tol=tol)
+    assert relres[0] <= tol * 1.001
+    th = np.deg2rad(np.arange(0, 181))
+    dirs = np.stack([np.sin(th), 0 * th, np.cos(th)], 1)
+    s = op.rcs(x, dirs)[0]
+    sm = mie.rcs_pec(K0, radius, th)
+    mask = 10 * np.log10(sm) >= 10 * np.log10(sm.max()) - 20
+    assert np.abs(10 * np.log10(s / sm))[mask].max() < 0.5
+    assert oracle.rcs_error(s, sm) < 0.1
+    op.close()
