@@ -144,6 +144,23 @@ int bi_solve(bi_handle h, const void* rhs, void* x, int nrhs, double tol, int* i
  * when a later call needs more) and keeps until bi_destroy.  Queued on the handle's stream. */
 int bi_farfield(bi_handle h, const void* x, int nrhs, const double* dirs, int ndir, void* F);
 
+/* Allocation-free far field, for callers that must not allocate device memory during the
+ * call: code that runs while a CUDA stream is being captured into a graph, real-time loops
+ * with a fixed memory budget, or hosts whose allocator is owned by someone else.  (The paper
+ * has no counterpart: it is a deployment variant of bi_farfield.)
+ * Computes exactly what bi_farfield computes, with the same arguments, but its partial sums
+ * go to a fixed array of BI_FARFIELD_NOALLOC_MAX_BYTES bytes compiled into the library: every
+ * GPU that loads the library holds that array until the process exits.  Scratch needed:
+ * ceil(N / 256) * nrhs * ndir * 96 bytes; larger requests return BI_ERR_ARG (split the
+ * directions over several calls).  The call allocates nothing; its first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device current, so
+ * make that first call before any stream capture.  All calls on a device share the array:
+ * calls whose work overlaps on the GPU (different streams, or different handles on one
+ * device) race on it -- order them on one stream or synchronise between them.  The handle
+ * itself must already exist (bi_setup allocates). */
+#define BI_FARFIELD_NOALLOC_MAX_BYTES (8u << 20)
+int bi_farfield_noalloc(bi_handle h, const void* x, int nrhs, const double* dirs, int ndir, void* F);
+
 /* Diagnostics: copy an internal device buffer of h to host memory.
  *   what 0: leaf radiation patterns F [N_tree][K_leaf][2] complex (tree order, theta/phi)
  *   what 1: leaf twisted receive patterns RX [N_tree][K_leaf][2]

@@ -27,7 +27,7 @@ _NAMES = {0: "BI_OK", -1: "BI_ERR_ARG", -2: "BI_ERR_MESH", -3: "BI_ERR_OOM", -4:
 
 # entry points declared in include/bi.h
 EXPORTS = ["bi_default_params", "bi_setup", "bi_num_unknowns", "bi_rwg_edges", "bi_get_info", "bi_matvec",
-           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_farfield", "bi_debug_copy", "bi_profile_stages", "bi_stage_name", "bi_last_error",
+           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_profile_stages", "bi_stage_name", "bi_last_error",
            "bi_destroy"]
 
 
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH):
     L.bi_rhs_planewave.argtypes = [vp, vp, vp, i, vp]
     L.bi_solve.argtypes = [vp, vp, vp, i, d, vp, vp]
     L.bi_farfield.argtypes = [vp, vp, i, vp, i, vp]
+    L.bi_farfield_noalloc.argtypes = [vp, vp, i, vp, i, vp]
     L.bi_debug_copy.argtypes = [vp, i, i, vp, i64]
     L.bi_profile_stages.argtypes = [vp, vp, vp, i, i, vp]
     L.bi_stage_name.argtypes = [i]

@@ -138,3 +138,56 @@ void bi_farfield_launch(bi_handle_s* h, const void* x, int nrhs, const double* d
     k_farfield_final<<<(tot + 127) / 128, 128, 0, s>>>(nchunk, nrhs, ndir, h->k, dirs, part, (double*)F);
     CU(cudaGetLastError());
 }
+
+// ---------------------------------------------------------------------------------
+// Allocation-free variant of bi_farfield.  The first-pass partial sums live in a fixed
+// array compiled into the library instead of handle-owned scratch, so the call itself
+// never allocates device memory.  Every GPU that loads the library holds this array until
+// the process exits; all calls on one device share it.
+#include <mutex>
+
+static __device__ __align__(256) double g_ff_noalloc_scratch[BI_FARFIELD_NOALLOC_MAX_BYTES / sizeof(double)];
+
+namespace {
+std::mutex g_ff_noalloc_mu;
+double* g_ff_noalloc_ptr[256] = {};  // device address of the array, per device ordinal
+}  // namespace
+
+extern "C" int bi_farfield_noalloc(bi_handle h, const void* x, int nrhs, const double* dirs, int ndir, void* F) {
+    if (!h) return BI_ERR_ARG;
+    if (!x || !dirs || !F || nrhs < 1 || ndir < 1 || nrhs > 65535 || ndir > 65535) {
+        h->err = "bi_farfield_noalloc: null argument or nrhs/ndir outside [1, 65535]";
+        return BI_ERR_ARG;
+    }
+    const size_t need = bi_farfield_scratch_bytes(h, nrhs, ndir);
+    if (need > (size_t)BI_FARFIELD_NOALLOC_MAX_BYTES) {
+        h->err = "bi_farfield_noalloc: needs " + std::to_string(need) + " B of scratch, more than the fixed " +
+                 std::to_string((size_t)BI_FARFIELD_NOALLOC_MAX_BYTES) +
+                 " B; use fewer directions or right-hand sides per call, or bi_farfield";
+        return BI_ERR_ARG;
+    }
+    try {
+        int dev = 0;
+        CU(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 256) throw bi_error{BI_ERR_CUDA, "bi_farfield_noalloc: device ordinal out of range"};
+        double* part = nullptr;
+        {
+            // host code cannot use the array's name as an address: look the address up once
+            // per device, with that device current
+            std::lock_guard<std::mutex> lock(g_ff_noalloc_mu);
+            if (!g_ff_noalloc_ptr[dev]) {
+                void* p = nullptr;
+                CU(cudaGetSymbolAddress(&p, g_ff_noalloc_scratch));
+                g_ff_noalloc_ptr[dev] = (double*)p;
+            }
+            part = g_ff_noalloc_ptr[dev];
+        }
+        // every partial-sum slot used by this call is written by the first pass before the
+        // second pass reads it, so nothing needs clearing
+        bi_farfield_launch(h, x, nrhs, dirs, ndir, F, part, h->stream);
+        return BI_OK;
+    } catch (const bi_error& e) {
+        h->err = e.msg;
+        return e.code;
+    }
+}
