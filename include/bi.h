@@ -88,6 +88,9 @@ typedef struct {
     int64_t device_bytes;       /* device memory held by the handle */
     double root_size;           /* root box edge */
     double setup_ms;            /* wall time of bi_setup */
+    double setup_near_regular_ms;   /* near-field fill: separated triangle pairs (FP32) */
+    double setup_near_special_ms;   /* near-field fill: singular / near-singular pairs (FP64) */
+    int64_t near_special_entries;   /* triangle pairs of the near field integrated in FP64 (singular / near-singular) */
 } bi_info_t;
 
 /* Fill *p with the defaults listed above. */

@@ -48,7 +48,9 @@ class Info(ctypes.Structure):
     _fields_ = [("n_rwg", ctypes.c_int64), ("n_unknowns", ctypes.c_int64), ("levels", ctypes.c_int),
                 ("leaf_level", ctypes.c_int), ("boxes", ctypes.c_int * 32), ("L", ctypes.c_int * 32),
                 ("K", ctypes.c_int * 32), ("near_pairs", ctypes.c_int64), ("interactions", ctypes.c_int64 * 32),
-                ("device_bytes", ctypes.c_int64), ("root_size", ctypes.c_double), ("setup_ms", ctypes.c_double)]
+                ("device_bytes", ctypes.c_int64), ("root_size", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("setup_near_regular_ms", ctypes.c_double), ("setup_near_special_ms", ctypes.c_double),
+                ("near_special_entries", ctypes.c_int64)]
 
 
 _lib = None
@@ -148,7 +150,8 @@ class Operator:
         return dict(n_rwg=I.n_rwg, n_unknowns=I.n_unknowns, levels=nl, leaf_level=I.leaf_level,
                     boxes=list(I.boxes[:nl]), L=list(I.L[:nl]), K=list(I.K[:nl]), near_pairs=I.near_pairs,
                     interactions=list(I.interactions[:nl]), device_bytes=I.device_bytes, root_size=I.root_size,
-                    setup_ms=I.setup_ms)
+                    setup_ms=I.setup_ms, setup_near_regular_ms=I.setup_near_regular_ms,
+                    setup_near_special_ms=I.setup_near_special_ms, near_special_entries=I.near_special_entries)
 
     def edges(self) -> np.ndarray:
         e = np.zeros((self.n_rwg, 2), np.int32)

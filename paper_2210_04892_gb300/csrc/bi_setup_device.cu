@@ -16,7 +16,9 @@
 //   - the grad-Phi part of <f_m, n x L f_n> is integrated by parts onto the edges of the
 //     test triangle for close pairs (n x f_m is divergence free on a flat triangle).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "bi_internal.h"
@@ -307,7 +309,7 @@ __device__ raw4 tri_pair(const dtri& Tm, int i, const dtri& Tn, int j, double k)
     double dc[3] = {Tm.c[0] - Tn.c[0], Tm.c[1] - Tn.c[1], Tm.c[2] - Tn.c[2]};
     double dist = sqrt(dot3(dc, dc));
     double dm = fmax(Tm.diam, Tn.diam);
-    if (ns == 0 && dist >= 3.0 * dm) {
+    if (ns == 0 && dist >= 2.0 * dm) {
         for (int q = 0; q < 7; ++q) {
             double b0, b1, b2, w;
             radon7(q, b0, b1, b2, w);
@@ -370,6 +372,287 @@ __device__ raw4 tri_pair(const dtri& Tm, int i, const dtri& Tn, int j, double k)
     }
     nl_edges(Tm, Tn, i, k, acc);
     return acc;
+}
+
+// Regular triangle pairs (no shared vertex, centroids at least three diameters apart): plain
+// 7-point rules on both triangles, evaluated in FP32.
+// Triangle-pair classes of the near-field fill:
+//   0 separated by >= 4 diameters: 7 x 7 point rules, FP32
+//   1 separated by 2..4 diameters: 28 x 28 point composite rules, FP32
+//   2 closer than 2 diameters, no shared vertex: singularity subtraction, FP64
+//   3 one shared vertex, 4 shared edge, 5 same triangle: singularity subtraction with graded rules, FP64
+__device__ __forceinline__ int pair_class(const dtri& Tm, const dtri& Tn) {
+    int ns = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            if (Tm.vid[a] == Tn.vid[b]) ++ns;
+    if (ns > 0) return 2 + ns;
+    double dc[3] = {Tm.c[0] - Tn.c[0], Tm.c[1] - Tn.c[1], Tm.c[2] - Tn.c[2]};
+    const double d = sqrt(dot3(dc, dc)), dm = fmax(Tm.diam, Tn.diam);
+    return d >= 4.0 * dm ? 0 : (d >= 2.0 * dm ? 1 : 2);
+}
+
+struct zf {
+    float x, y;
+};
+__device__ __forceinline__ zf fadd(zf a, zf b) { return zf{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ zf fmul(zf a, zf b) { return zf{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ zf fsc(zf a, float s) { return zf{a.x * s, a.y * s}; }
+
+// returns (P_raw, Q_raw) = (1/2)(L + NK), (1/2)(NL - K) for half-bases g_i (test), g_j (source)
+template <int NSUB>
+__device__ void tri_pair_regular_f32(const dtri& Tm, int i, const dtri& Tn, int j, float k, zf& Pr, zf& Qr) {
+    // coordinates relative to the test centroid keep FP32 accurate for large meshes
+    float pm[3][3], pn[3][3], nm[3];
+    for (int a = 0; a < 3; ++a)
+        for (int d = 0; d < 3; ++d) {
+            pm[a][d] = (float)(Tm.p[a][d] - Tm.c[d]);
+            pn[a][d] = (float)(Tn.p[a][d] - Tm.c[d]);
+        }
+    for (int d = 0; d < 3; ++d) nm[d] = (float)Tm.n[d];
+    const float Am = (float)Tm.area, An = (float)Tn.area;
+    const float i4pi = 0.0795774715459477f;
+    const float s15 = 3.8729833f;
+    const float a1 = (6.0f - s15) / 21.0f, a2 = (6.0f + s15) / 21.0f;
+    const float w1 = (155.0f - s15) / 1200.0f, w2 = (155.0f + s15) / 1200.0f;
+    // 7-point rule on NSUB sub-triangles (midpoint subdivision when NSUB = 4)
+    constexpr int NQ = 7 * NSUB;
+    float bq[NQ][3], wq[NQ];
+    {
+        float b7[7][3], w7[7];
+        b7[0][0] = b7[0][1] = b7[0][2] = 1.0f / 3.0f;
+        w7[0] = 9.0f / 40.0f;
+        for (int q = 1; q < 7; ++q) {
+            const float a = (q <= 3) ? a1 : a2;
+            w7[q] = (q <= 3) ? w1 : w2;
+            b7[q][0] = b7[q][1] = b7[q][2] = a;
+            b7[q][(q - 1) % 3] = 1.0f - 2.0f * a;
+        }
+        const float sub[4][3][3] = {{{1, 0, 0}, {.5f, .5f, 0}, {.5f, 0, .5f}},
+                                    {{.5f, .5f, 0}, {0, 1, 0}, {0, .5f, .5f}},
+                                    {{.5f, 0, .5f}, {0, .5f, .5f}, {0, 0, 1}},
+                                    {{.5f, .5f, 0}, {0, .5f, .5f}, {.5f, 0, .5f}}};
+        for (int sb = 0; sb < NSUB; ++sb)
+            for (int q = 0; q < 7; ++q) {
+                for (int d = 0; d < 3; ++d)
+                    bq[sb * 7 + q][d] = NSUB == 1 ? b7[q][d]
+                                                   : b7[q][0] * sub[sb][0][d] + b7[q][1] * sub[sb][1][d] + b7[q][2] * sub[sb][2][d];
+                wq[sb * 7 + q] = w7[q] / NSUB;
+            }
+    }
+    zf L = {0, 0}, NL = {0, 0}, K = {0, 0}, NK = {0, 0};
+    for (int qo = 0; qo < NQ; ++qo) {
+        float r[3];
+        for (int d = 0; d < 3; ++d) r[d] = bq[qo][0] * pm[0][d] + bq[qo][1] * pm[1][d] + bq[qo][2] * pm[2][d];
+        zf Sg = {0, 0}, Sr[3] = {{0, 0}, {0, 0}, {0, 0}}, Kv[3] = {{0, 0}, {0, 0}, {0, 0}};
+        for (int qi = 0; qi < NQ; ++qi) {
+            float dd[3];
+            for (int d = 0; d < 3; ++d)
+                dd[d] = bq[qi][0] * pn[0][d] + bq[qi][1] * pn[1][d] + bq[qi][2] * pn[2][d] - r[d];
+            const float R2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+            const float iR = rsqrtf(R2);
+            const float R = R2 * iR;
+            float sn, cs;
+            sincosf(-k * R, &sn, &cs);
+            const float ww = wq[qi] * An * i4pi * iR;
+            const zf G = {cs * ww, sn * ww};
+            // (1 + jkR) e^{-jkR} / R^2 (times the 1/R of ww)
+            const zf gt = fsc(fmul(zf{1.0f, k * R}, zf{cs, sn}), ww * iR * iR);
+            Sg = fadd(Sg, G);
+            for (int d = 0; d < 3; ++d) {
+                Sr[d] = fadd(Sr[d], fsc(G, dd[d]));
+                Kv[d] = fadd(Kv[d], fsc(gt, dd[d]));
+            }
+        }
+        const float W = wq[qo] * Am;
+        float gi[3], gj[3], ngi[3], ngj[3];
+        for (int d = 0; d < 3; ++d) { gi[d] = r[d] - pm[i][d]; gj[d] = r[d] - pn[j][d]; }
+        ngi[0] = nm[1] * gi[2] - nm[2] * gi[1]; ngi[1] = nm[2] * gi[0] - nm[0] * gi[2]; ngi[2] = nm[0] * gi[1] - nm[1] * gi[0];
+        ngj[0] = nm[1] * gj[2] - nm[2] * gj[1]; ngj[1] = nm[2] * gj[0] - nm[0] * gj[2]; ngj[2] = nm[0] * gj[1] - nm[1] * gj[0];
+        zf giSr = {0, 0}, ngiSr = {0, 0}, ngiKv = {0, 0}, kk = {0, 0}, kgi = {0, 0}, kn = {0, 0};
+        float gjxgi[3] = {gj[1] * gi[2] - gj[2] * gi[1], gj[2] * gi[0] - gj[0] * gi[2], gj[0] * gi[1] - gj[1] * gi[0]};
+        for (int d = 0; d < 3; ++d) {
+            giSr = fadd(giSr, fsc(Sr[d], gi[d]));
+            ngiSr = fadd(ngiSr, fsc(Sr[d], ngi[d]));
+            ngiKv = fadd(ngiKv, fsc(Kv[d], ngi[d]));
+            kk = fadd(kk, fsc(Kv[d], gjxgi[d]));
+            kgi = fadd(kgi, fsc(Kv[d], gi[d]));
+            kn = fadd(kn, fsc(Kv[d], nm[d]));
+        }
+        const float gg = gi[0] * gj[0] + gi[1] * gj[1] + gi[2] * gj[2];
+        const float gngj = gi[0] * ngj[0] + gi[1] * ngj[1] + gi[2] * ngj[2];
+        const zf tL = fadd(giSr, fsc(Sg, gg - 4.0f / (k * k)));
+        L = fadd(L, fsc(fmul(zf{0.0f, -k}, tL), W));
+        const zf tN = fadd(fsc(ngiSr, -1.0f), fsc(Sg, gngj));
+        NL = fadd(NL, fsc(fadd(fmul(zf{0.0f, -k}, tN), fmul(zf{0.0f, 2.0f / k}, ngiKv)), W));
+        K = fadd(K, fsc(kk, W));
+        const float ngjn = nm[0] * gj[0] + nm[1] * gj[1] + nm[2] * gj[2];
+        NK = fadd(NK, fsc(fadd(fsc(kgi, ngjn), fsc(kn, -gg)), W));
+    }
+    Pr = fsc(fadd(L, NK), 0.5f);
+    Qr = fsc(fadd(NL, fsc(K, -1.0f)), 0.5f);
+}
+
+// Pass 1: one CTA per near block, one thread per entry: the separated triangle pairs
+// (classes 0, 1) in FP32; every other triangle pair of the entry is appended to the list of
+// its class for pass 2.  Entry = (A, B) with A = P, B = Q at this point.
+struct special_item {
+    int lo, hi;   // entry offset (split in two 31-bit halves)
+    int m, n;     // tree RWG indices
+    int sides;    // sm | (sn << 1)
+    int pad;
+};
+template <typename T>
+__global__ void __launch_bounds__(128) k_near_regular(int nblk, const int* __restrict__ blk_box, const int* __restrict__ near_ptr,
+                                                      const int* __restrict__ near_src, const int64_t* __restrict__ near_blk,
+                                                      const int* __restrict__ leaf_start, const int* __restrict__ rwg_t,
+                                                      const int* __restrict__ rwg_l, const double* __restrict__ rwg_len,
+                                                      const double* __restrict__ tri, const double* __restrict__ nrm,
+                                                      const double* __restrict__ area, const int* __restrict__ vid, double k,
+                                                      int mode, T* __restrict__ out, special_item* __restrict__ lists,
+                                                      unsigned long long* __restrict__ count,
+                                                      const unsigned long long* __restrict__ cap,
+                                                      const unsigned long long* __restrict__ base) {
+    int q = blockIdx.x;
+    if (q >= nblk) return;
+    int b = blk_box[q], s = near_src[q];
+    int m0 = leaf_start[b], mb = leaf_start[b + 1] - m0;
+    int n0 = leaf_start[s], nbs = leaf_start[s + 1] - n0;
+    const int64_t seg = near_blk[near_ptr[b]];
+    const int ncol = (int)((near_blk[near_ptr[b + 1]] - seg) / mb);
+    const int c0 = (int)((near_blk[q] - seg) / mb);
+    for (int e = threadIdx.x; e < mb * nbs; e += blockDim.x) {
+        const int ml = e % mb, nl = e / mb;
+        const int m = m0 + ml, n = n0 + nl;
+        const int64_t o = seg + (int64_t)ml * ncol + c0 + nl;
+        zf P = {0, 0}, Q = {0, 0};
+        for (int sm = 0; sm < 2; ++sm) {
+            dtri Tm;
+            load_tri(tri, nrm, area, vid, rwg_t[2 * m + sm], Tm);
+            const int i = rwg_l[2 * m + sm];
+            const float cm = (float)((sm == 0 ? 1.0 : -1.0) * rwg_len[m] / (2.0 * Tm.area));
+            for (int sn = 0; sn < 2; ++sn) {
+                dtri Tn;
+                load_tri(tri, nrm, area, vid, rwg_t[2 * n + sn], Tn);
+                const int cls = pair_class(Tm, Tn);
+                if (cls >= 2) {
+                    const unsigned long long slot = atomicAdd(count + (cls - 2), 1ull);
+                    if (slot < cap[cls - 2]) {
+                        special_item it;
+                        it.lo = (int)(o & 0x7fffffff);
+                        it.hi = (int)(o >> 31);
+                        it.m = m;
+                        it.n = n;
+                        it.sides = sm | (sn << 1);
+                        it.pad = 0;
+                        lists[base[cls - 2] + slot] = it;
+                    }
+                    continue;
+                }
+                const int j = rwg_l[2 * n + sn];
+                const float cn = (float)((sn == 0 ? 1.0 : -1.0) * rwg_len[n] / (2.0 * Tn.area));
+                zf pr, qr;
+                if (cls == 0) tri_pair_regular_f32<1>(Tm, i, Tn, j, (float)k, pr, qr);
+                else tri_pair_regular_f32<4>(Tm, i, Tn, j, (float)k, pr, qr);
+                P = fadd(P, fsc(pr, cm * cn));
+                Q = fadd(Q, fsc(qr, cm * cn));
+            }
+        }
+        if (mode == 0) {
+            out[4 * o + 0] = (T)P.x;
+            out[4 * o + 1] = (T)P.y;
+            out[4 * o + 2] = (T)Q.x;
+            out[4 * o + 3] = (T)Q.y;
+        } else {
+            out[2 * o + 0] = (T)P.x;
+            out[2 * o + 1] = (T)P.y;
+        }
+    }
+}
+
+// Counting pass: how many triangle pairs of each special class (2..5) the near entries hold,
+// so the lists of pass 1 are allocated exactly.
+__global__ void __launch_bounds__(128) k_near_count(int nblk, const int* __restrict__ blk_box, const int* __restrict__ near_src,
+                                                    const int* __restrict__ leaf_start, const int* __restrict__ rwg_t,
+                                                    const double* __restrict__ tri, const double* __restrict__ nrm,
+                                                    const double* __restrict__ area, const int* __restrict__ vid,
+                                                    unsigned long long* __restrict__ count) {
+    int q = blockIdx.x;
+    if (q >= nblk) return;
+    int b = blk_box[q], s = near_src[q];
+    int m0 = leaf_start[b], mb = leaf_start[b + 1] - m0;
+    int n0 = leaf_start[s], nbs = leaf_start[s + 1] - n0;
+    unsigned long long c[4] = {0, 0, 0, 0};
+    for (int e = threadIdx.x; e < mb * nbs; e += blockDim.x) {
+        const int m = m0 + e % mb, n = n0 + e / mb;
+        for (int sm = 0; sm < 2; ++sm) {
+            dtri Tm;
+            load_tri(tri, nrm, area, vid, rwg_t[2 * m + sm], Tm);
+            for (int sn = 0; sn < 2; ++sn) {
+                dtri Tn;
+                load_tri(tri, nrm, area, vid, rwg_t[2 * n + sn], Tn);
+                const int cls = pair_class(Tm, Tn);
+                if (cls >= 2) ++c[cls - 2];
+            }
+        }
+    }
+    for (int k = 0; k < 4; ++k)
+        if (c[k]) atomicAdd(count + k, c[k]);
+}
+
+// Pass 2: one thread per listed triangle pair of one class (so a warp follows one path):
+// the pair's contribution in FP64 with singularity extraction, plus its Gram terms for the
+// same-triangle class, added atomically to the entry (at most four pairs per entry):
+// A += P - g G, B += Q - X/2.
+template <typename T>
+__global__ void __launch_bounds__(128) k_near_special(unsigned long long nlist, const special_item* __restrict__ list,
+                                                      const int* __restrict__ rwg_t, const int* __restrict__ rwg_l,
+                                                      const double* __restrict__ rwg_len, const double* __restrict__ tri,
+                                                      const double* __restrict__ nrm, const double* __restrict__ area,
+                                                      const int* __restrict__ vid, double k, int mode, T* __restrict__ out) {
+    const unsigned long long it = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= nlist) return;
+    const special_item w = list[it];
+    const int64_t o = (int64_t)(unsigned)w.lo | ((int64_t)w.hi << 31);
+    const int m = w.m, n = w.n, sm = w.sides & 1, sn = (w.sides >> 1) & 1;
+    dtri Tm, Tn;
+    const int tm = rwg_t[2 * m + sm], i = rwg_l[2 * m + sm];
+    const int tn = rwg_t[2 * n + sn], j = rwg_l[2 * n + sn];
+    load_tri(tri, nrm, area, vid, tm, Tm);
+    load_tri(tri, nrm, area, vid, tn, Tn);
+    const double cm = (sm == 0 ? 1.0 : -1.0) * rwg_len[m] / (2.0 * Tm.area);
+    const double cn = (sn == 0 ? 1.0 : -1.0) * rwg_len[n] / (2.0 * Tn.area);
+    raw4 r = tri_pair(Tm, i, Tn, j, k);
+    const double c = 0.5 * cm * cn;
+    zd P = zscale(zadd(r.L, r.NK), c);
+    zd Q = zscale(zadd(r.NL, zscale(r.K, -1.0)), c);
+    double G = 0, X = 0;
+    if (tm == tn) {
+        double gg = 0, gx = 0;
+        for (int e2 = 0; e2 < 3; ++e2) {
+            double x[3], gi[3], gj[3], ngj[3];
+            for (int d = 0; d < 3; ++d) {
+                x[d] = 0.5 * (Tm.p[e2][d] + Tm.p[(e2 + 1) % 3][d]);
+                gi[d] = x[d] - Tm.p[i][d];
+                gj[d] = x[d] - Tm.p[j][d];
+            }
+            cross3(Tm.n, gj, ngj);
+            gg += dot3(gi, gj) / 3.0;
+            gx += dot3(gi, ngj) / 3.0;
+        }
+        G = cm * cn * gg * Tm.area;
+        X = cm * cn * gx * Tm.area;
+    }
+    const double gA = (mode == 0) ? 1.0 : 0.25;
+    if (mode == 0) {
+        atomicAdd(out + 4 * o + 0, (T)(P.x - gA * G));
+        atomicAdd(out + 4 * o + 1, (T)P.y);
+        atomicAdd(out + 4 * o + 2, (T)(Q.x - 0.5 * X));
+        atomicAdd(out + 4 * o + 3, (T)Q.y);
+    } else {
+        atomicAdd(out + 2 * o + 0, (T)(P.x - gA * G));
+        atomicAdd(out + 2 * o + 1, (T)P.y);
+    }
 }
 
 // One CTA per near block (test leaf box b, source box s); threads loop over the block's
@@ -733,7 +1016,66 @@ void bi_fill_near(bi_handle_s* h) {
     int* d_blk_box = h->upload(blk_box);
     size_t per = (h->prm.op_mode == 0 ? 2 : 1) * h->csize;
     h->d_near = h->alloc(per * (size_t)std::max<int64_t>(h->near_nnz, 1));
-    if (nblk > 0) {
+    const char* env_fill = std::getenv("BI_NEAR_FILL_SINGLE_PASS");
+    const bool two_pass = !(env_fill && env_fill[0] == '1');
+    if (nblk > 0 && two_pass) {
+        // per-class lists of singular / near-singular triangle pairs, counted first and sized exactly
+        unsigned long long* d_count = nullptr;
+        CU(cudaMalloc(&d_count, 12 * sizeof(unsigned long long)));
+        CU(cudaMemsetAsync(d_count, 0, 12 * sizeof(unsigned long long), h->stream));
+        k_near_count<<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_src, h->d_leaf_start, h->d_rwg_t, h->d_tri,
+                                                   h->d_tri_n, h->d_tri_area, h->d_tri_vid, d_count);
+        CU(cudaGetLastError());
+        unsigned long long capv[4], basev[4];
+        CU(cudaMemcpyAsync(capv, d_count, sizeof(capv), cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        unsigned long long tot_cap = 0;
+        for (int c = 0; c < 4; ++c) { basev[c] = tot_cap; tot_cap += capv[c]; }
+        CU(cudaMemcpyAsync(d_count + 4, capv, sizeof(capv), cudaMemcpyHostToDevice, h->stream));
+        CU(cudaMemcpyAsync(d_count + 8, basev, sizeof(basev), cudaMemcpyHostToDevice, h->stream));
+        CU(cudaMemsetAsync(d_count, 0, 4 * sizeof(unsigned long long), h->stream));
+        special_item* d_list = nullptr;
+        CU(cudaMalloc(&d_list, sizeof(special_item) * std::max<unsigned long long>(tot_cap, 1)));
+        auto t0 = std::chrono::steady_clock::now();
+        if (h->prec == 0)
+            k_near_regular<double><<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_ptr, h->d_near_src, h->d_near_blk,
+                                                                 h->d_leaf_start, h->d_rwg_t, h->d_rwg_l, h->d_rwg_len,
+                                                                 h->d_tri, h->d_tri_n, h->d_tri_area, h->d_tri_vid, h->k,
+                                                                 h->prm.op_mode, (double*)h->d_near, d_list, d_count, d_count + 4, d_count + 8);
+        else
+            k_near_regular<float><<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_ptr, h->d_near_src, h->d_near_blk,
+                                                                h->d_leaf_start, h->d_rwg_t, h->d_rwg_l, h->d_rwg_len,
+                                                                h->d_tri, h->d_tri_n, h->d_tri_area, h->d_tri_vid, h->k,
+                                                                h->prm.op_mode, (float*)h->d_near, d_list, d_count, d_count + 4, d_count + 8);
+        CU(cudaGetLastError());
+        unsigned long long nlist[4] = {0, 0, 0, 0};
+        CU(cudaMemcpyAsync(nlist, d_count, sizeof(nlist), cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        auto t1 = std::chrono::steady_clock::now();
+        unsigned long long total = 0;
+        for (int c = 0; c < 4; ++c) {
+            if (nlist[c] != capv[c]) throw bi_error{BI_ERR_CUDA, "near-field special list count mismatch"};
+            total += nlist[c];
+            if (nlist[c] == 0) continue;
+            const unsigned nb = (unsigned)((nlist[c] + 127) / 128);
+            if (h->prec == 0)
+                k_near_special<double><<<nb, 128, 0, h->stream>>>(nlist[c], d_list + basev[c], h->d_rwg_t, h->d_rwg_l,
+                                                                  h->d_rwg_len, h->d_tri, h->d_tri_n, h->d_tri_area,
+                                                                  h->d_tri_vid, h->k, h->prm.op_mode, (double*)h->d_near);
+            else
+                k_near_special<float><<<nb, 128, 0, h->stream>>>(nlist[c], d_list + basev[c], h->d_rwg_t, h->d_rwg_l,
+                                                                 h->d_rwg_len, h->d_tri, h->d_tri_n, h->d_tri_area,
+                                                                 h->d_tri_vid, h->k, h->prm.op_mode, (float*)h->d_near);
+            CU(cudaGetLastError());
+        }
+        CU(cudaStreamSynchronize(h->stream));
+        auto t2 = std::chrono::steady_clock::now();
+        cudaFree(d_list);
+        cudaFree(d_count);
+        h->info.setup_near_regular_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        h->info.setup_near_special_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
+        h->info.near_special_entries = (int64_t)total;
+    } else if (nblk > 0) {
         if (h->prec == 0)
             k_near_fill<double><<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_ptr, h->d_near_src, h->d_near_blk, h->d_leaf_start,
                                                               h->d_rwg_t, h->d_rwg_l, h->d_rwg_len, h->d_tri, h->d_tri_n,

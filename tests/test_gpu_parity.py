@@ -266,3 +266,20 @@ def test_pec_sphere_solve_rcs_vs_mie(bi, nu, radius, tol):
     assert np.abs(10 * np.log10(s / sm))[mask].max() < 0.5
     assert oracle.rcs_error(s, sm) < 0.1
     op.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_two_pass_near_fill_matches_single_pass(bi, mode, monkeypatch):
+    """The default near-field fill (separated triangle pairs in FP32, the rest in FP64) against
+    the single-pass all-FP64 fill: the products agree to FP32 rounding of the separated pairs."""
+    v, t = icosphere(8, 0.5)
+    ys = []
+    for single in ("0", "1"):
+        monkeypatch.setenv("BI_NEAR_FILL_SINGLE_PASS", single)
+        op = bi.Operator(v, t, K0, precision="fp64", op_mode=mode, leaf_box=0.5, max_rhs=1)
+        x = complex_gaussian(op.n_unknowns, 1, seed=SEED_BASE + 9)
+        ys.append(op.matvec(torch.from_numpy(x).cuda()).cpu().numpy())
+        if single == "0":
+            assert op.info()["near_special_entries"] > 0
+        op.close()
+    assert rel(ys[0], ys[1]) < 2e-5
