@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-rows", type=int, default=256, help="oracle rows in the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", type=int, default=64, help="RHS of the batched monostatic-sweep section (0: skip)")
     return ap.parse_args()
 
 
@@ -191,6 +192,57 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------- batched sweep
+def run_batched(args):
+    """Batched monostatic sweep on the cube-with-cylinder surface (~93k RWG, 186k unknowns):
+    one product of C with args.batched plane-wave columns (phi in 2-degree steps at
+    theta = 90 deg), FP32.  Reported beside the main line; not the headline metric."""
+    import torch
+    from paper_2210_04892_gb300 import bi
+    from paper_2210_04892_gb300.inputs import cube_with_cylinder
+    R = args.batched
+    v, t = cube_with_cylinder()
+    op = bi.Operator(v, t, K0, digits=3, precision="fp32", op_mode=0, max_rhs=R)
+    info = op.info()
+    ph = np.deg2rad(2.0 * np.arange(R))
+    kh = -np.stack([np.cos(ph), np.sin(ph), 0 * ph], 1)
+    pp = np.tile([0.0, 0.0, 1.0], (R, 1))
+    b = op.rhs_planewave(kh, pp)
+    y = torch.empty_like(b)
+    for _ in range(3):
+        op.matvec(b, out=y)
+    torch.cuda.synchronize()
+    steps = 20
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        op.matvec(b, out=y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    stages = op.profile_stages(b, reps=5)
+    # the same operator one column at a time (the plain one-RHS form)
+    y1 = torch.empty_like(b[:1])
+    b1 = b[:1].contiguous()
+    for _ in range(3):
+        op.matvec(b1, out=y1)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        op.matvec(b1, out=y1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1) / steps
+    out = {"workload": "cube 5 lambda + cylinder, %d RWG (%d unknowns), %d levels, FP32" %
+                       (info["n_rwg"], info["n_unknowns"], info["levels"]),
+           "nrhs": R, "ms_per_product": ms, "value": info["n_unknowns"] * R / (ms * 1e-3), "unit": UNIT,
+           "one_rhs_value": info["n_unknowns"] / (ms1 * 1e-3), "setup_ms": info["setup_ms"],
+           "stage_ms": stages}
+    op.close()
+    return out
+
+
 # ---------------------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
@@ -276,6 +328,8 @@ def run_gpu(args):
                             ((sb["near"] + sb["receive"]) / 1e6)},
            "roofline": roofline, "e2e": e2e, "clocks": clocks,
            "gpu_launches": launches_per_step(info) * args.steps}
+    if args.batched and rank == 0:
+        out["batched"] = run_batched(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         rows = sample_rows(nun, args.cpu_rows, seed=SEED_BASE + 11)

@@ -590,6 +590,123 @@ __global__ void __launch_bounds__(256) k_aggregate2(int N, int K, int R, int nun
     }
 }
 
+// ------------------------------------------------------------------ many right-hand sides: per-box tiles
+// Aggregation as a small product per leaf box, U[k][c][r] = sum_n F[n][k][.] x[n][.][r]:
+// CTA = (box, 32 directions); the box's patterns for those directions and its x for all RHS
+// are staged in shared memory, so every pattern entry is read from HBM once per product.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_aggregate_tile(int N, int K, int R, int nun, const int* __restrict__ perm,
+                                                        const int* __restrict__ leaf_start, const cpx<T>* __restrict__ F,
+                                                        const cpx<T>* __restrict__ x, cpx<T>* __restrict__ U) {
+    constexpr int KT = 32;
+    extern __shared__ unsigned char smem_raw[];
+    const int b = blockIdx.y, k0 = blockIdx.x * KT;
+    const int n0 = leaf_start[b], nb = leaf_start[b + 1] - n0;
+    cpx<T>* fs = reinterpret_cast<cpx<T>*>(smem_raw);      // [nb][KT][2]
+    cpx<T>* xs = fs + (size_t)nb * KT * 2;                   // [nb][2][R]
+    for (int i = threadIdx.x; i < nb * KT; i += blockDim.x) {
+        const int n = i / KT, kk = k0 + i % KT;
+        cpx<T> a = czero<T>(), c = czero<T>();
+        if (kk < K) load_pair(F + ((int64_t)(n0 + n) * K + kk) * 2, a, c);
+        fs[2 * i] = a;
+        fs[2 * i + 1] = c;
+    }
+    for (int i = threadIdx.x; i < nb * 2 * R; i += blockDim.x) {
+        const int r = i % R, X = (i / R) % 2, n = i / (2 * R);
+        xs[i] = (MODE == 0 || X == 0) ? x[(int64_t)r * nun + (int64_t)X * N + perm[n0 + n]] : czero<T>();
+    }
+    __syncthreads();
+    const int E = 2 * R;
+    for (int o = threadIdx.x; o < KT * R; o += blockDim.x) {
+        const int kl = o / R, r = o % R, kk = k0 + kl;
+        if (kk >= K) continue;
+        cpx<T> ut = czero<T>(), up = czero<T>();
+        for (int n = 0; n < nb; ++n) {
+            const cpx<T> Ft = fs[(n * KT + kl) * 2], Fp = fs[(n * KT + kl) * 2 + 1];
+            const cpx<T> xJ = xs[(n * 2 + 0) * R + r];
+            ut = csub(ut, cmul(xJ, Ft));
+            up = csub(up, cmul(xJ, Fp));
+            if (MODE == 0) {
+                const cpx<T> xM = xs[(n * 2 + 1) * R + r];
+                ut = csub(ut, cmul(xM, Fp));
+                up = cadd(up, cmul(xM, Ft));
+            }
+        }
+        cpx<T>* out = U + ((int64_t)b * K + kk) * E;
+        out[r] = ut;
+        out[R + r] = up;
+    }
+}
+
+// Receive as a small product per leaf box: y[m][r] = sum_k (F, RX)[m][k] . V[k][r]:
+// CTA = one leaf box; directions in tiles of 32 staged in shared memory (patterns of the
+// box's RWGs and V for all RHS), each thread accumulating a few (m, r) outputs.
+template <typename T, int MODE, int OPT>
+__global__ void __launch_bounds__(256) k_receive_tile(int N, int K, int R, int RC, int nun, const int* __restrict__ perm,
+                                                      const int* __restrict__ leaf_start, const cpx<T>* __restrict__ F,
+                                                      const cpx<T>* __restrict__ RX, const cpx<T>* __restrict__ V, T c,
+                                                      const cpx<T>* __restrict__ yt, cpx<T>* __restrict__ y) {
+    constexpr int KT = 32;
+    extern __shared__ unsigned char smem_raw[];
+    const int b = blockIdx.x;
+    const int r0 = blockIdx.y * RC, rc = min(RC, R - r0);     // this CTA's right-hand sides
+    const int n0 = leaf_start[b], nb = leaf_start[b + 1] - n0;
+    const int E = 2 * R;
+    cpx<T>* fs = reinterpret_cast<cpx<T>*>(smem_raw);       // [nb][KT][4]: Ft Fp Xt Xp
+    cpx<T>* vs = fs + (size_t)nb * KT * 4;                    // [KT][2][RC]
+    cpx<T> aJ[OPT], aM[OPT];
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) { aJ[o] = czero<T>(); aM[o] = czero<T>(); }
+    for (int k0 = 0; k0 < K; k0 += KT) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < nb * KT; i += blockDim.x) {
+            const int n = i / KT, kk = k0 + i % KT;
+            cpx<T> a = czero<T>(), bb = czero<T>(), cc = czero<T>(), dd = czero<T>();
+            if (kk < K) {
+                load_pair(F + ((int64_t)(n0 + n) * K + kk) * 2, a, bb);
+                load_pair(RX + ((int64_t)(n0 + n) * K + kk) * 2, cc, dd);
+            }
+            fs[4 * i] = a;
+            fs[4 * i + 1] = bb;
+            fs[4 * i + 2] = cc;
+            fs[4 * i + 3] = dd;
+        }
+        for (int i = threadIdx.x; i < KT * 2 * RC; i += blockDim.x) {
+            const int kl = i / (2 * RC), cpt = (i / RC) % 2, rr = i % RC, kk = k0 + kl;
+            vs[i] = (kk < K && rr < rc) ? V[((int64_t)b * K + kk) * E + cpt * R + r0 + rr] : czero<T>();
+        }
+        __syncthreads();
+        const int kn = min(KT, K - k0);
+#pragma unroll
+        for (int o = 0; o < OPT; ++o) {
+            const int it = threadIdx.x + o * blockDim.x;
+            if (it >= nb * rc) continue;
+            const int n = it / rc, r = it % rc;
+            for (int kl = 0; kl < kn; ++kl) {
+                const cpx<T>* f = fs + (n * KT + kl) * 4;
+                const cpx<T> Vt = vs[(kl * 2 + 0) * RC + r], Vp = vs[(kl * 2 + 1) * RC + r];
+                aJ[o] = cadd(aJ[o], csub(cadd(cmulc(f[0], Vt), cmulc(f[1], Vp)), csub(cmul(f[3], Vt), cmul(f[2], Vp))));
+                if (MODE == 0) {
+                    const cpx<T> t = csub(cmulc(f[0], Vp), cmulc(f[1], Vt));
+                    aM[o] = cadd(aM[o], csub(t, cadd(cmul(f[2], Vt), cmul(f[3], Vp))));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) {
+        const int it = threadIdx.x + o * blockDim.x;
+        if (it >= nb * rc) continue;
+        const int n = it / rc, r = r0 + it % rc, m = n0 + n, u = perm[m];
+        if (MODE == 0) {
+            y[(int64_t)r * nun + u] = cadd(yt[((int64_t)m * 2 + 0) * R + r], cscale(aJ[o], -c));
+            y[(int64_t)r * nun + N + u] = cadd(yt[((int64_t)m * 2 + 1) * R + r], cscale(aM[o], c));
+        } else {
+            y[(int64_t)r * nun + u] = cadd(yt[(int64_t)m * R + r], cscale(aJ[o], -c));
+        }
+    }
+}
+
 // ------------------------------------------------------------------ fused interpolation (one CTA per parent)
 // U_p = sum_children shift * Interp_phi(Interp_theta(U_c)); child pattern and theta-pass in shared memory,
 // parent outputs accumulated in registers (OPT outputs per thread).
@@ -1083,7 +1200,8 @@ void launch_near_any(bi_handle_s* h, const cpx<T>* x, cpx<T>* yt, cpx<T>* yuser,
     }
     if (R == 1) launch_near_stream<T, MODE, 1>(h, x, yt, yuser, R, s);
     else if (R == 2) launch_near_stream<T, MODE, 2>(h, x, yt, yuser, R, s);
-    else launch_near_stream<T, MODE, 4>(h, x, yt, yuser, R, s);
+    else if (R <= 4 || (size_t)h->near_ncol_max * 2 * 8 * sizeof(cpx<T>) > 160 * 1024) launch_near_stream<T, MODE, 4>(h, x, yt, yuser, R, s);
+    else launch_near_stream<T, MODE, 8>(h, x, yt, yuser, R, s);
 }
 
 template <typename T, int OPT>
@@ -1175,6 +1293,42 @@ bool anterp_child(bi_handle_s* h, int l, int E, cudaStream_t s) {
     return true;
 }
 
+
+template <typename T, int OPT>
+bool launch_receive_tile_opt(bi_handle_s* h, cpx<T>* y, int R, cudaStream_t s) {
+    level_t& L = h->lev[h->leaf];
+    // right-hand sides per CTA so that one thread holds at most OPT outputs
+    int RC = std::min(R, (256 * OPT) / std::max(1, h->max_leaf_count));
+    if (RC < 1) return false;
+    size_t smem = ((size_t)h->max_leaf_count * 32 * 4 + (size_t)32 * 2 * RC) * sizeof(cpx<T>);
+    if (smem > 200 * 1024) return false;
+    const double pi = 3.14159265358979323846;
+    const T c = (T)(h->k * h->k / (32.0 * pi * pi));
+    if (h->prm.op_mode == 0) {
+        if (smem > 48 * 1024)
+            CU(cudaFuncSetAttribute(k_receive_tile<T, 0, OPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_receive_tile<T, 0, OPT><<<dim3(L.nbox, (R + RC - 1) / RC), 256, smem, s>>>(h->N, L.K, R, RC, h->nun, h->d_perm,
+                                                                                   h->d_leaf_start,
+                                                            (const cpx<T>*)h->d_F, (const cpx<T>*)h->d_RX,
+                                                            (const cpx<T>*)L.d_V, c, (const cpx<T>*)h->d_yt, y);
+    } else {
+        if (smem > 48 * 1024)
+            CU(cudaFuncSetAttribute(k_receive_tile<T, 1, OPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_receive_tile<T, 1, OPT><<<dim3(L.nbox, (R + RC - 1) / RC), 256, smem, s>>>(h->N, L.K, R, RC, h->nun, h->d_perm,
+                                                                                   h->d_leaf_start,
+                                                            (const cpx<T>*)h->d_F, (const cpx<T>*)h->d_RX,
+                                                            (const cpx<T>*)L.d_V, c, (const cpx<T>*)h->d_yt, y);
+    }
+    CU(cudaGetLastError());
+    return true;
+}
+
+template <typename T>
+bool launch_receive_tile(bi_handle_s* h, const cpx<T>* x, cpx<T>* y, int R, cudaStream_t s) {
+    (void)x;
+    return launch_receive_tile_opt<T, 8>(h, y, R, s);
+}
+
 // The product with fused kernels: near (side stream) || aggregate -> interpolate -> translate
 // -> anterpolate -> receive (+ near result, + permutation to user order).
 template <typename T>
@@ -1203,7 +1357,22 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
         return;
     }
     const int lf = h->leaf;
-    {
+    if (R >= 8) {
+        level_t& L = h->lev[lf];
+        dim3 g(nblk(L.K, 32), L.nbox);
+        size_t smem = ((size_t)h->max_leaf_count * 32 * 2 + (size_t)h->max_leaf_count * 2 * R) * sizeof(C);
+        if (smem > 48 * 1024) {
+            CU(cudaFuncSetAttribute(k_aggregate_tile<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            CU(cudaFuncSetAttribute(k_aggregate_tile<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        }
+        if (h->prm.op_mode == 0)
+            k_aggregate_tile<T, 0><<<g, 256, smem, s>>>(N, L.K, R, nun, h->d_perm, h->d_leaf_start, (const C*)h->d_F, x,
+                                                        (C*)L.d_U);
+        else
+            k_aggregate_tile<T, 1><<<g, 256, smem, s>>>(N, L.K, R, nun, h->d_perm, h->d_leaf_start, (const C*)h->d_F, x,
+                                                        (C*)L.d_U);
+        CU(cudaGetLastError());
+    } else {
         level_t& L = h->lev[lf];
         dim3 g(nblk((int64_t)L.K * R, 64), L.nbox);
         size_t smem = (size_t)h->max_leaf_count * 2 * R * sizeof(C);
@@ -1264,7 +1433,8 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
     }
     if (ev) CU(cudaEventRecord(ev[5], s));
     else CU(cudaStreamWaitEvent(s, h->ev_join, 0));
-    {
+    if (R >= 8 && launch_receive_tile<T>(h, x, y, R, s)) {
+    } else {
         level_t& L = h->lev[lf];
         const double pi = 3.14159265358979323846;
         T c = (T)(h->k * h->k / (32.0 * pi * pi));

@@ -121,20 +121,38 @@ def _box_surface(lo, hi, spacing_fn):
     return V, _orient_outward(V, T, center=(lo + hi) / 2)
 
 
+def _zip_rings(outer, inner, phi_o, phi_i, tris):
+    """Triangulate the band between two closed rings (vertex ids with their angles), both
+    counter-clockwise in angle, by advancing along whichever ring has the smaller next angle."""
+    no, ni = len(outer), len(inner)
+    i = j = 0
+    while i < no or j < ni:
+        ao = phi_o[i] + (2 * np.pi if i >= no else 0) if i < no else np.inf
+        ai = phi_i[j] if j < ni else np.inf
+        next_o = phi_o[(i + 1) % no] + (2 * np.pi if i + 1 >= no else 0)
+        next_i = phi_i[(j + 1) % ni] + (2 * np.pi if j + 1 >= ni else 0)
+        if (i < no) and (j >= ni or next_o <= next_i):
+            tris.append([outer[i % no], outer[(i + 1) % no], inner[j % ni]])
+            i += 1
+        else:
+            tris.append([outer[i % no], inner[(j + 1) % ni], inner[j % ni]])
+            j += 1
+
+
 def _cylinder_surface(center, radius, height, h):
-    """Closed cylinder (axis z) with flat caps, triangle size about ``h``."""
+    """Closed cylinder (axis z) with flat caps, triangle size about ``h``: a structured side
+    and caps made of concentric rings whose point counts follow their circumference."""
     center = np.asarray(center, float)
     nphi = max(8, int(np.ceil(2 * np.pi * radius / h)))
     nz = max(2, int(np.ceil(height / h)))
-    nr = max(1, int(np.ceil(radius / h)))
+    nr = max(1, int(round(radius / h)))
     vlist, tris = [], []
 
     def add(p):
-        vlist.append(p)
+        vlist.append(np.asarray(p, float))
         return len(vlist) - 1
 
     phis = 2 * np.pi * np.arange(nphi) / nphi
-    z0 = center[2] - height / 2
     ring = [[add(center + np.array([radius * np.cos(p), radius * np.sin(p), -height / 2 + height * k / nz]))
              for p in phis] for k in range(nz + 1)]
     for k in range(nz):
@@ -142,44 +160,37 @@ def _cylinder_surface(center, radius, height, h):
             b = (a + 1) % nphi
             tris.append([ring[k][a], ring[k][b], ring[k + 1][b]])
             tris.append([ring[k][a], ring[k + 1][b], ring[k + 1][a]])
-    for cap, zk in ((0, 0), (1, nz)):
-        rings = [ring[zk]]
+    for zk in (0, nz):
+        zc = center[2] - height / 2 + height * zk / nz
+        outer, phi_o = ring[zk], phis
         for r in range(nr - 1, 0, -1):
             rr = radius * r / nr
-            zc = center[2] - height / 2 + height * zk / nz
-            rings.append([add(np.array([center[0] + rr * np.cos(p), center[1] + rr * np.sin(p), zc])) for p in phis])
-        ctr = add(np.array([center[0], center[1], center[2] - height / 2 + height * zk / nz]))
-        for r in range(len(rings) - 1):
-            o, i = rings[r], rings[r + 1]
-            for a in range(nphi):
-                b = (a + 1) % nphi
-                tris.append([o[a], o[b], i[b]])
-                tris.append([o[a], i[b], i[a]])
-        inner = rings[-1]
-        for a in range(nphi):
-            tris.append([inner[a], inner[(a + 1) % nphi], ctr])
+            m = max(6, int(round(2 * np.pi * rr / h)))
+            off = np.pi / m * (r % 2)
+            phi_i = off + 2 * np.pi * np.arange(m) / m
+            inner = [add([center[0] + rr * np.cos(p), center[1] + rr * np.sin(p), zc]) for p in phi_i]
+            _zip_rings(outer, inner, phi_o, phi_i, tris)
+            outer, phi_o = inner, phi_i
+        ctr = add([center[0], center[1], zc])
+        for a in range(len(outer)):
+            tris.append([outer[a], outer[(a + 1) % len(outer)], ctr])
     V = np.array(vlist)
     T = np.array(tris, dtype=np.int64)
     return V, _orient_outward(V, T, center=center)
 
 
-def cube_with_cylinder(size=5.0, h_face=1 / 8, h_edge=1 / 12, cyl_radius=1.0, cyl_height=3.0, h_cyl=1 / 12):
-    """Two disjoint closed components: a cube of side ``size`` whose grid is
-    graded from ``h_face`` (face centers) to ``h_edge`` (near cube edges), and a
-    coaxial closed cylinder strictly inside it (a layered-cube-like object with an
-    embedded body, Sec. III.E shape)."""
+def cube_with_cylinder(size=5.0, h_face=1 / 10.7, h_edge=1 / 16, cyl_radius=1.0, cyl_height=3.0, h_cyl=1 / 16):
+    """Two disjoint closed components: a cube of side ``size`` on tensor grids graded
+    smoothly from ``h_face`` (face centres) to ``h_edge`` (cube edges), and a closed coaxial
+    cylinder strictly inside it (the shape of a layered cube with an embedded body, Sec. III.E).
+    The defaults give about 100k RWG functions."""
 
     def graded(length):
-        # spacing grows from h_edge at both ends to h_face in the middle
-        xs = [0.0]
-        while xs[-1] < length - 1e-12:
-            x = xs[-1]
-            t = min(x, length - x) / (length / 2)
-            step = h_edge + (h_face - h_edge) * min(1.0, t * 2)
-            xs.append(min(length, x + step))
-        xs = np.array(xs)
-        # rescale so the last node lands exactly on length
-        return xs * (length / xs[-1])
+        # x(s) = L (s - a sin(2 pi s) / (2 pi)): spacing (1 - a) h0 at the ends, (1 + a) h0 mid-face
+        a = (h_face - h_edge) / (h_face + h_edge)
+        n = max(2, int(round(length * (1 - a) / h_edge)))
+        sgrid = np.arange(n + 1) / n
+        return length * (sgrid - a * np.sin(2 * np.pi * sgrid) / (2 * np.pi))
 
     half = size / 2
     Vc, Tc = _box_surface((-half, -half, -half), (half, half, half), graded)
