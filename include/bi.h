@@ -183,6 +183,43 @@ int bi_debug_copy(bi_handle h, int what, int level, void* host, int64_t bytes);
 int bi_profile_stages(bi_handle h, const void* x, void* y, int nrhs, int reps, double* stage_ms);
 const char* bi_stage_name(int i);
 
+/* ---- Serving: continuous batching of solves ------------------------------------------
+ * A server owns two host threads.  bi_submit queues a solve request (mesh, k0, parameters,
+ * nrhs plane waves, tolerance); requests are admitted in arrival order while fewer than
+ * max_active are running and the device-memory estimate fits mem_budget_bytes.  An admitted
+ * request gets its own stream, operator (bi_setup, run on a setup thread so that setups
+ * overlap running solves) and GMRES state; the serving thread advances every running solve
+ * by one iteration per pass, so their matvecs and Krylov kernels overlap on the device, and
+ * requests join or leave between passes.  Latency = submit to solution on the host. */
+typedef struct bi_server_s* bi_server;
+typedef struct {
+    int64_t mem_budget_bytes;   /* device bytes for admitted requests; 0 = 80% of free memory */
+    int max_active;             /* requests set up or iterating at once (default 8) */
+    int queue_capacity;         /* waiting requests before bi_submit returns BI_ERR_BUSY (default 4096) */
+} bi_server_params;
+
+void bi_server_default_params(bi_server_params* p);
+/* Create a server on the current CUDA device. */
+int bi_server_create(const bi_server_params* prm, bi_server* out);
+/* Queue a solve of C x = b for nrhs plane waves (khat, phat: host [nrhs][3]) on the surface
+ * (verts, tris) at k0; opt as for bi_setup (stream ignored).  Copies every input.  *req
+ * receives the request id.  BI_ERR_BUSY: queue full; BI_ERR_OOM: larger than the budget. */
+int bi_submit(bi_server s, const double* verts, int nv, const int* tris, int nt, double k0, const bi_params* opt,
+              int nrhs, const double* khat, const double* phat, double tol, int64_t* req);
+/* *done = 1 once the request finished; *status = its bi_status then. */
+int bi_poll(bi_server s, int64_t req, int* done, int* status);
+/* Result of a finished request: x_host [nrhs][n_unknowns] complex of the request precision
+ * (x_bytes = buffer size), GMRES iterations and relative residuals [nrhs], latency (submit
+ * to result) and setup time in ms.  Returns the request's status, or BI_ERR_BUSY if it is not
+ * finished.  Any output pointer may be NULL. */
+int bi_result(bi_server s, int64_t req, void* x_host, int64_t x_bytes, int* iters, double* relres, double* latency_ms,
+              double* setup_ms);
+/* Forget a finished request (frees its host result). */
+int bi_release(bi_server s, int64_t req);
+const char* bi_server_last_error(bi_server s);
+/* Stop the threads and free every request and buffer. */
+void bi_server_destroy(bi_server s);
+
 /* Text of the last error on h (or of the last failed bi_setup when h is NULL). */
 const char* bi_last_error(bi_handle h);
 

@@ -28,7 +28,8 @@ _NAMES = {0: "BI_OK", -1: "BI_ERR_ARG", -2: "BI_ERR_MESH", -3: "BI_ERR_OOM", -4:
 # entry points declared in include/bi.h
 EXPORTS = ["bi_default_params", "bi_setup", "bi_num_unknowns", "bi_rwg_edges", "bi_get_info", "bi_matvec",
            "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_profile_stages", "bi_stage_name", "bi_last_error",
-           "bi_destroy"]
+           "bi_destroy", "bi_server_default_params", "bi_server_create", "bi_submit", "bi_poll", "bi_result",
+           "bi_release", "bi_server_last_error", "bi_server_destroy"]
 
 
 class BIError(RuntimeError):
@@ -51,6 +52,10 @@ class Info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("root_size", ctypes.c_double), ("setup_ms", ctypes.c_double),
                 ("setup_near_regular_ms", ctypes.c_double), ("setup_near_special_ms", ctypes.c_double),
                 ("near_special_entries", ctypes.c_int64)]
+
+
+class ServerParams(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_active", ctypes.c_int), ("queue_capacity", ctypes.c_int)]
 
 
 _lib = None
@@ -85,6 +90,17 @@ def load(path: str = LIB_PATH):
     L.bi_last_error.restype = ctypes.c_char_p
     L.bi_destroy.argtypes = [vp]
     L.bi_destroy.restype = None
+    L.bi_server_default_params.argtypes = [ctypes.POINTER(ServerParams)]
+    L.bi_server_default_params.restype = None
+    L.bi_server_create.argtypes = [ctypes.POINTER(ServerParams), ctypes.POINTER(vp)]
+    L.bi_submit.argtypes = [vp, vp, i, vp, i, d, ctypes.POINTER(Params), i, vp, vp, d, ctypes.POINTER(i64)]
+    L.bi_poll.argtypes = [vp, i64, ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.bi_result.argtypes = [vp, i64, vp, i64, vp, vp, ctypes.POINTER(d), ctypes.POINTER(d)]
+    L.bi_release.argtypes = [vp, i64]
+    L.bi_server_last_error.argtypes = [vp]
+    L.bi_server_last_error.restype = ctypes.c_char_p
+    L.bi_server_destroy.argtypes = [vp]
+    L.bi_server_destroy.restype = None
     _lib = L
     return L
 
@@ -259,6 +275,90 @@ class Operator:
     def close(self):
         if getattr(self, "h", None):
             load().bi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching solve server (bi_server_* in include/bi.h)."""
+
+    def __init__(self, mem_budget_bytes=0, max_active=8, queue_capacity=4096):
+        L = load()
+        p = ServerParams()
+        L.bi_server_default_params(ctypes.byref(p))
+        p.mem_budget_bytes = int(mem_budget_bytes)
+        p.max_active = int(max_active)
+        p.queue_capacity = int(queue_capacity)
+        h = ctypes.c_void_p()
+        rc = L.bi_server_create(ctypes.byref(p), ctypes.byref(h))
+        if rc != BI_OK:
+            raise BIError(rc, "bi_server_create failed")
+        self.h = h
+        self._meta = {}
+
+    def submit(self, verts, tris, k0, khat, phat, tol=1e-3, digits=3, precision="fp32", op_mode=1, leaf_box=0.25,
+               levels=0, interp_order=10, gmres_restart=100, gmres_maxit=1000):
+        L = load()
+        p = default_params()
+        p.digits, p.leaf_box, p.levels, p.interp_order = int(digits), float(leaf_box), int(levels), int(interp_order)
+        p.precision = 0 if precision == "fp64" else 1
+        p.op_mode = int(op_mode)
+        p.gmres_restart, p.gmres_maxit = int(gmres_restart), int(gmres_maxit)
+        v = np.ascontiguousarray(verts, np.float64)
+        t = np.ascontiguousarray(tris, np.int32)
+        kh = np.ascontiguousarray(np.atleast_2d(khat), np.float64)
+        ph = np.ascontiguousarray(np.atleast_2d(phat), np.float64)
+        req = ctypes.c_int64()
+        rc = L.bi_submit(self.h, v.ctypes.data, len(v), t.ctypes.data, len(t), float(k0), ctypes.byref(p), len(kh),
+                         kh.ctypes.data, ph.ctypes.data, float(tol), ctypes.byref(req))
+        if rc != BI_OK:
+            raise BIError(rc, L.bi_server_last_error(self.h).decode())
+        nt = len(t)
+        nrwg = 3 * nt // 2
+        self._meta[req.value] = (len(kh), nrwg * (2 if op_mode == 0 else 1), np.complex128 if precision == "fp64"
+                                 else np.complex64)
+        return req.value
+
+    def poll(self, req):
+        done, st = ctypes.c_int(), ctypes.c_int()
+        rc = load().bi_poll(self.h, int(req), ctypes.byref(done), ctypes.byref(st))
+        if rc != BI_OK:
+            raise BIError(rc, "bi_poll")
+        return bool(done.value), st.value
+
+    def result(self, req):
+        nrhs, nun, dt = self._meta[req]
+        x = np.zeros((nrhs, nun), dt)
+        its = np.zeros(nrhs, np.int32)
+        rel = np.zeros(nrhs, np.float64)
+        lat, st = ctypes.c_double(), ctypes.c_double()
+        rc = load().bi_result(self.h, int(req), x.ctypes.data, x.nbytes, its.ctypes.data, rel.ctypes.data,
+                              ctypes.byref(lat), ctypes.byref(st))
+        return dict(status=rc, x=x, iters=its, relres=rel, latency_ms=lat.value, setup_ms=st.value)
+
+    def wait(self, req, timeout=600.0):
+        import time
+        t0 = time.time()
+        while True:
+            done, st = self.poll(req)
+            if done:
+                return self.result(req)
+            if time.time() - t0 > timeout:
+                raise TimeoutError("request %d not finished" % req)
+            time.sleep(0.002)
+
+    def release(self, req):
+        load().bi_release(self.h, int(req))
+        self._meta.pop(req, None)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().bi_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -110,7 +110,6 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
         bi_fill_translations(h);
         bi_alloc_work(h);
         CU(cudaStreamSynchronize(h->stream));
-        CU(cudaDeviceSynchronize());
     } catch (const bi_error& e) {
         g_setup_error = e.msg;
         release(h);

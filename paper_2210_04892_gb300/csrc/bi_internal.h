@@ -198,6 +198,14 @@ size_t bi_farfield_scratch_bytes(const bi_handle_s* h, int nrhs, int ndir);
 void bi_farfield_launch(bi_handle_s* h, const void* x, int nrhs, const double* dirs, int ndir, void* F, double* part,
                         cudaStream_t s);
 int bi_gmres(bi_handle_s* h, const void* rhs, void* x, int nrhs, double tol, int* iters, double* relres);
+// resumable GMRES (serving loop)
+struct gmres_ctx;
+gmres_ctx* bi_gmres_create(bi_handle_s* h, const void* rhs, int nrhs, double tol, cudaStream_t s);
+int bi_gmres_advance(gmres_ctx* c);
+int bi_gmres_finish(gmres_ctx* c, void* xout, int* iters, double* relres);
+void bi_gmres_destroy(gmres_ctx* c);
+int64_t bi_gmres_bytes(gmres_ctx* c);
+int64_t bi_gmres_estimate_bytes(int64_t nun, int R, int m);
 
 // numerical helpers shared by the host setup files of the library (not by the oracle)
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);  // nodes in (-1, 1)

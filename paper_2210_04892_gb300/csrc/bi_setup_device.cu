@@ -1021,7 +1021,7 @@ void bi_fill_near(bi_handle_s* h) {
     if (nblk > 0 && two_pass) {
         // per-class lists of singular / near-singular triangle pairs, counted first and sized exactly
         unsigned long long* d_count = nullptr;
-        CU(cudaMalloc(&d_count, 12 * sizeof(unsigned long long)));
+        CU(cudaMallocAsync((void**)&d_count, 12 * sizeof(unsigned long long), h->stream));
         CU(cudaMemsetAsync(d_count, 0, 12 * sizeof(unsigned long long), h->stream));
         k_near_count<<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_src, h->d_leaf_start, h->d_rwg_t, h->d_tri,
                                                    h->d_tri_n, h->d_tri_area, h->d_tri_vid, d_count);
@@ -1035,7 +1035,7 @@ void bi_fill_near(bi_handle_s* h) {
         CU(cudaMemcpyAsync(d_count + 8, basev, sizeof(basev), cudaMemcpyHostToDevice, h->stream));
         CU(cudaMemsetAsync(d_count, 0, 4 * sizeof(unsigned long long), h->stream));
         special_item* d_list = nullptr;
-        CU(cudaMalloc(&d_list, sizeof(special_item) * std::max<unsigned long long>(tot_cap, 1)));
+        CU(cudaMallocAsync((void**)&d_list, sizeof(special_item) * std::max<unsigned long long>(tot_cap, 1), h->stream));
         auto t0 = std::chrono::steady_clock::now();
         if (h->prec == 0)
             k_near_regular<double><<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_ptr, h->d_near_src, h->d_near_blk,
@@ -1070,8 +1070,8 @@ void bi_fill_near(bi_handle_s* h) {
         }
         CU(cudaStreamSynchronize(h->stream));
         auto t2 = std::chrono::steady_clock::now();
-        cudaFree(d_list);
-        cudaFree(d_count);
+        CU(cudaFreeAsync(d_list, h->stream));
+        CU(cudaFreeAsync(d_count, h->stream));
         h->info.setup_near_regular_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
         h->info.setup_near_special_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
         h->info.near_special_entries = (int64_t)total;

@@ -258,141 +258,255 @@ void bi_rhs_launch(bi_handle_s* h, const double* khat, const double* phat, int n
     // the small parameter buffer is released with the handle's other scratch at bi_destroy
 }
 
-int bi_gmres(bi_handle_s* h, const void* rhs, void* xout, int R, double tol, int* iters, double* relres) {
-    const int nun = h->nun;
-    const int m = std::max(1, h->prm.gmres_restart);
-    const int maxit = std::max(1, h->prm.gmres_maxit);
-    const int64_t nv = (int64_t)nun * R;
-    cudaStream_t s = h->stream;
-    // FP64 Krylov state (allocated per solve, released at the end)
-    std::vector<void*> tmp;
-    auto A = [&](size_t bytes) {
+// ---------------------------------------------------------------------------------
+// Resumable GMRES: one context per solve.  The serving loop interleaves the iterations of
+// many contexts (each on its own stream); bi_solve drives one context synchronously.
+namespace {
+__global__ void k_add_inplace(int64_t n, z2* __restrict__ a, const z2* __restrict__ b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { a[i].x += b[i].x; a[i].y += b[i].y; }
+}
+}  // namespace
+
+struct gmres_ctx_impl {
+    bi_handle_s* h = nullptr;
+    int R = 1, m = 1, maxit = 1;
+    double tol = 1e-3;
+    int64_t nun = 0, nv = 0;
+    cudaStream_t s = nullptr;
+    std::vector<void*> mem;
+    z2 *V = nullptr, *w = nullptr, *b64 = nullptr, *x64 = nullptr, *hc = nullptr, *hc2 = nullptr, *H = nullptr,
+       *g = nullptr, *yv = nullptr, *sn = nullptr;
+    double *cs = nullptr, *nrm = nullptr, *res = nullptr;
+    int *act = nullptr, *nk = nullptr;
+    void *xin = nullptr, *yout = nullptr;
+    double* h_res = nullptr;  // pinned
+    cudaEvent_t ev = nullptr;
+    std::vector<double> bnorm, last_true;
+    std::vector<int> done, its, a, kcols;
+    int j = 0, total = 0;
+    bool in_cycle = false, finished = false;
+    int64_t bytes = 0;
+
+    void* A(size_t n) {
         void* p = nullptr;
-        CU(cudaMalloc(&p, bytes));
-        tmp.push_back(p);
+        CU(cudaMalloc(&p, n));
+        mem.push_back(p);
+        bytes += (int64_t)n;
         return p;
-    };
-    int status = BI_OK;
-    try {
-        z2* V = (z2*)A(sizeof(z2) * nv * (m + 1));
-        z2* w = (z2*)A(sizeof(z2) * nv);
-        z2* b64 = (z2*)A(sizeof(z2) * nv);
-        z2* x64 = (z2*)A(sizeof(z2) * nv);
-        z2* hc = (z2*)A(sizeof(z2) * (size_t)(m + 1) * R);
-        z2* hc2 = (z2*)A(sizeof(z2) * (size_t)(m + 1) * R);
-        z2* H = (z2*)A(sizeof(z2) * (size_t)R * (m + 1) * m);
-        z2* g = (z2*)A(sizeof(z2) * (size_t)R * (m + 1));
-        z2* yv = (z2*)A(sizeof(z2) * (size_t)R * m);
-        double* cs = (double*)A(sizeof(double) * (size_t)R * m);
-        z2* sn = (z2*)A(sizeof(z2) * (size_t)R * m);
-        double* nrm = (double*)A(sizeof(double) * R);
-        double* res = (double*)A(sizeof(double) * R);
-        int* act = (int*)A(sizeof(int) * R);
-        int* nk = (int*)A(sizeof(int) * R);
-        // fixed staging buffers of the handle, so the captured matvec graph is reused
-        void* xin = h->d_sx;
-        void* yout = h->d_sy;
+    }
+    ~gmres_ctx_impl() {
+        for (void* p : mem) cudaFree(p);
+        if (h_res) cudaFreeHost(h_res);
+        if (ev) cudaEventDestroy(ev);
+    }
+    static int64_t estimate_bytes(int64_t nun, int R, int m) {
+        return (int64_t)sizeof(z2) * nun * R * (m + 5) + (int64_t)R * (m + 2) * (m + 4) * 32 + 2 * nun * R * 16;
+    }
+    void matvec64(const z2* in, z2* out) {
+        const int th = 256;
+        if (h->prec == 0) k_cvt_to<double><<<nb(nv, th), th, 0, s>>>(nv, in, (double*)xin);
+        else k_cvt_to<float><<<nb(nv, th), th, 0, s>>>(nv, in, (float*)xin);
+        bi_matvec_launch(h, xin, yout, R, s);
+        if (h->prec == 0) k_cvt_from<double><<<nb(nv, th), th, 0, s>>>(nv, (const double*)yout, out);
+        else k_cvt_from<float><<<nb(nv, th), th, 0, s>>>(nv, (const float*)yout, out);
+    }
+    // allocate, x0 = 0, |b| (synchronises the stream once)
+    void init(bi_handle_s* hh, const void* rhs, int nrhs, double tol_, cudaStream_t st, void* xin_, void* yout_) {
+        h = hh;
+        R = nrhs;
+        tol = tol_;
+        s = st;
+        m = std::max(1, h->prm.gmres_restart);
+        maxit = std::max(1, h->prm.gmres_maxit);
+        nun = h->nun;
+        nv = nun * R;
+        V = (z2*)A(sizeof(z2) * nv * (m + 1));
+        w = (z2*)A(sizeof(z2) * nv);
+        b64 = (z2*)A(sizeof(z2) * nv);
+        x64 = (z2*)A(sizeof(z2) * nv);
+        hc = (z2*)A(sizeof(z2) * (size_t)(m + 1) * R);
+        hc2 = (z2*)A(sizeof(z2) * (size_t)(m + 1) * R);
+        H = (z2*)A(sizeof(z2) * (size_t)R * (m + 1) * m);
+        g = (z2*)A(sizeof(z2) * (size_t)R * (m + 1));
+        yv = (z2*)A(sizeof(z2) * (size_t)R * m);
+        cs = (double*)A(sizeof(double) * (size_t)R * m);
+        sn = (z2*)A(sizeof(z2) * (size_t)R * m);
+        nrm = (double*)A(sizeof(double) * R);
+        res = (double*)A(sizeof(double) * R);
+        act = (int*)A(sizeof(int) * R);
+        nk = (int*)A(sizeof(int) * R);
+        xin = xin_ ? xin_ : A(h->csize * nv);
+        yout = yout_ ? yout_ : A(h->csize * nv);
+        CU(cudaMallocHost(&h_res, sizeof(double) * 2 * R));
+        CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         const int th = 256;
         if (h->prec == 0) k_cvt_from<double><<<nb(nv, th), th, 0, s>>>(nv, (const double*)rhs, b64);
         else k_cvt_from<float><<<nb(nv, th), th, 0, s>>>(nv, (const float*)rhs, b64);
         CU(cudaMemsetAsync(x64, 0, sizeof(z2) * nv, s));
         k_norms<<<R, 256, 0, s>>>(nun, b64, nrm);
-        std::vector<double> bnorm(R), rr(R);
+        bnorm.assign(R, 0.0);
         CU(cudaMemcpyAsync(bnorm.data(), nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
-        std::vector<int> done(R, 0), its(R, 0);
+        last_true.assign(R, 1e300);
+        done.assign(R, 0);
+        its.assign(R, 0);
+        a.assign(R, 0);
+        kcols.assign(R, 0);
         for (int r = 0; r < R; ++r)
             if (bnorm[r] == 0.0) done[r] = 1;
-        auto matvec64 = [&](const z2* in, z2* out) {
-            if (h->prec == 0) k_cvt_to<double><<<nb(nv, th), th, 0, s>>>(nv, in, (double*)xin);
-            else k_cvt_to<float><<<nb(nv, th), th, 0, s>>>(nv, in, (float*)xin);
-            bi_matvec_launch(h, xin, yout, R, s);
-            if (h->prec == 0) k_cvt_from<double><<<nb(nv, th), th, 0, s>>>(nv, (const double*)yout, out);
-            else k_cvt_from<float><<<nb(nv, th), th, 0, s>>>(nv, (const float*)yout, out);
-        };
-        int total = 0;
-        std::vector<double> last_true(R, 1e300);
-        while (total < maxit) {
-            // r0 = b - A x
-            matvec64(x64, w);
-            k_residual<<<nb(nv, th), th, 0, s>>>(nv, b64, w, w);
-            k_norms<<<R, 256, 0, s>>>(nun, w, nrm);
-            k_scale_into<<<nb(nv, th), th, 0, s>>>(nun, R, w, nrm, V);
-            std::vector<double> beta(R);
-            CU(cudaMemcpyAsync(beta.data(), nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
-            CU(cudaStreamSynchronize(s));
-            std::vector<z2> g0((size_t)R * (m + 1), z2{0, 0});
-            std::vector<int> a(R), kcols(R, 0);
-            // the true residual decides at every restart; a column whose true residual did not
-            // drop by 10% over a whole cycle has stagnated (matvec rounding floor) and stops
-            bool any_left = false;
-            for (int r = 0; r < R; ++r) {
-                g0[(size_t)r * (m + 1)] = z2{beta[r], 0};
-                double rel = beta[r] / std::max(bnorm[r], 1e-300);
-                if (bnorm[r] == 0.0 || rel <= tol) done[r] = 1;
-                else if (done[r] == 0 && rel > 0.9 * last_true[r]) done[r] = 2;  // stagnated
-                else if (done[r] == 1) done[r] = 0;                              // estimate was optimistic
-                last_true[r] = rel;
-                a[r] = (done[r] == 0);
-                any_left = any_left || a[r];
-            }
-            if (!any_left) break;
-            CU(cudaMemcpyAsync(g, g0.data(), sizeof(z2) * g0.size(), cudaMemcpyHostToDevice, s));
-            CU(cudaMemcpyAsync(act, a.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s));
-            int j = 0;
-            for (; j < m && total < maxit; ++j, ++total) {
-                bool any = false;
-                for (int r = 0; r < R; ++r) any = any || a[r];
-                if (!any) break;
-                matvec64(V + (int64_t)j * nv, w);
-                // two passes of classical Gram-Schmidt
-                k_dots<<<dim3(R, j + 1), 256, 0, s>>>(nun, R, V, nv, w, hc);
-                k_orth_update<<<nb(nv, th), th, 0, s>>>(nun, R, j + 1, V, nv, hc, w);
-                k_dots<<<dim3(R, j + 1), 256, 0, s>>>(nun, R, V, nv, w, hc2);
-                k_orth_update<<<nb(nv, th), th, 0, s>>>(nun, R, j + 1, V, nv, hc2, w);
-                // hc += hc2 (on the host side of the small arrays)
-                std::vector<z2> h1((size_t)(j + 1) * R), h2((size_t)(j + 1) * R);
-                CU(cudaMemcpyAsync(h1.data(), hc, sizeof(z2) * h1.size(), cudaMemcpyDeviceToHost, s));
-                CU(cudaMemcpyAsync(h2.data(), hc2, sizeof(z2) * h2.size(), cudaMemcpyDeviceToHost, s));
-                k_norms<<<R, 256, 0, s>>>(nun, w, nrm);
-                k_scale_into<<<nb(nv, th), th, 0, s>>>(nun, R, w, nrm, V + (int64_t)(j + 1) * nv);
-                CU(cudaStreamSynchronize(s));
-                for (size_t q = 0; q < h1.size(); ++q) { h1[q].x += h2[q].x; h1[q].y += h2[q].y; }
-                CU(cudaMemcpyAsync(hc, h1.data(), sizeof(z2) * h1.size(), cudaMemcpyHostToDevice, s));
-                k_givens<<<nb(R, 64), 64, 0, s>>>(R, m, j, hc, nrm, H, cs, sn, g, res, act);
-                CU(cudaMemcpyAsync(rr.data(), res, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
-                CU(cudaStreamSynchronize(s));
-                for (int r = 0; r < R; ++r)
-                    if (a[r]) {
-                        kcols[r] = j + 1;
-                        its[r] += 1;
-                        if (rr[r] / std::max(bnorm[r], 1e-300) <= tol) a[r] = 0;
-                    }
-                CU(cudaMemcpyAsync(act, a.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s));
-            }
-            CU(cudaMemcpyAsync(nk, kcols.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s));
-            k_backsolve<<<nb(R, 64), 64, 0, s>>>(R, m, H, g, nk, yv);
-            k_update_x<<<nb(nv, th), th, 0, s>>>(nun, R, m, V, nv, yv, nk, x64);
-            CU(cudaStreamSynchronize(s));
-        }
-        // true residual
+    }
+    // Start a restart cycle from the true residual; false when no column is left to solve.
+    bool start_cycle() {
+        const int th = 256;
+        if (total >= maxit) return false;
         matvec64(x64, w);
         k_residual<<<nb(nv, th), th, 0, s>>>(nv, b64, w, w);
         k_norms<<<R, 256, 0, s>>>(nun, w, nrm);
+        k_scale_into<<<nb(nv, th), th, 0, s>>>(nun, R, w, nrm, V);
+        std::vector<double> beta(R);
+        CU(cudaMemcpyAsync(beta.data(), nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        std::vector<z2> g0((size_t)R * (m + 1), z2{0, 0});
+        bool any_left = false;
+        for (int r = 0; r < R; ++r) {
+            g0[(size_t)r * (m + 1)] = z2{beta[r], 0};
+            double rel = beta[r] / std::max(bnorm[r], 1e-300);
+            // the true residual decides; a column whose true residual did not drop over a
+            // whole cycle by 1% has stagnated (matvec rounding floor) and stops
+            if (bnorm[r] == 0.0 || rel <= tol) done[r] = 1;
+            else if (done[r] == 0 && rel > 0.99 * last_true[r]) done[r] = 2;
+            else if (done[r] == 1) done[r] = 0;
+            last_true[r] = rel;
+            a[r] = (done[r] == 0);
+            kcols[r] = 0;
+            any_left = any_left || a[r];
+        }
+        if (!any_left) return false;
+        CU(cudaMemcpyAsync(g, g0.data(), sizeof(z2) * g0.size(), cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(act, a.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s));
+        CU(cudaStreamSynchronize(s));
+        j = 0;
+        in_cycle = true;
+        return true;
+    }
+    // Queue one Arnoldi step (classical Gram-Schmidt twice, FP64) and the Givens update; the
+    // residual estimates are copied to pinned memory and `ev` marks completion.
+    void enqueue_iteration() {
+        const int th = 256;
+        matvec64(V + (int64_t)j * nv, w);
+        k_dots<<<dim3(R, j + 1), 256, 0, s>>>(nun, R, V, nv, w, hc);
+        k_orth_update<<<nb(nv, th), th, 0, s>>>(nun, R, j + 1, V, nv, hc, w);
+        k_dots<<<dim3(R, j + 1), 256, 0, s>>>(nun, R, V, nv, w, hc2);
+        k_orth_update<<<nb(nv, th), th, 0, s>>>(nun, R, j + 1, V, nv, hc2, w);
+        k_add_inplace<<<nb((int64_t)(j + 1) * R, 128), 128, 0, s>>>((int64_t)(j + 1) * R, hc, hc2);
+        k_norms<<<R, 256, 0, s>>>(nun, w, nrm);
+        k_scale_into<<<nb(nv, th), th, 0, s>>>(nun, R, w, nrm, V + (int64_t)(j + 1) * nv);
+        k_givens<<<nb(R, 64), 64, 0, s>>>(R, m, j, hc, nrm, H, cs, sn, g, res, act);
+        CU(cudaMemcpyAsync(h_res, res, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+        CU(cudaEventRecord(ev, s));
+        CU(cudaGetLastError());
+    }
+    bool iteration_ready() {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaErrorNotReady) return false;
+        CU(e);
+        return true;
+    }
+    // Host update after an iteration completed; true when the cycle must end.
+    bool complete_iteration() {
+        ++total;
+        bool any = false;
+        for (int r = 0; r < R; ++r)
+            if (a[r]) {
+                kcols[r] = j + 1;
+                its[r] += 1;
+                if (h_res[r] / std::max(bnorm[r], 1e-300) <= tol) a[r] = 0;
+                any = any || a[r];
+            }
+        ++j;
+        if (any) CU(cudaMemcpyAsync(act, a.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s));
+        return !any || j >= m || total >= maxit;
+    }
+    // x += V y for the columns of this cycle (queued)
+    void end_cycle() {
+        const int th = 256;
+        CU(cudaMemcpyAsync(nk, kcols.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s));
+        k_backsolve<<<nb(R, 64), 64, 0, s>>>(R, m, H, g, nk, yv);
+        k_update_x<<<nb(nv, th), th, 0, s>>>(nun, R, m, V, nv, yv, nk, x64);
+        CU(cudaGetLastError());
+        CU(cudaStreamSynchronize(s));
+        in_cycle = false;
+    }
+    // True residual, x out (device, handle precision); synchronises.
+    int finish(void* xout, int* iters, double* relres) {
+        const int th = 256;
+        matvec64(x64, w);
+        k_residual<<<nb(nv, th), th, 0, s>>>(nv, b64, w, w);
+        k_norms<<<R, 256, 0, s>>>(nun, w, nrm);
+        std::vector<double> rr(R);
         CU(cudaMemcpyAsync(rr.data(), nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
         if (h->prec == 0) k_cvt_to<double><<<nb(nv, th), th, 0, s>>>(nv, x64, (double*)xout);
         else k_cvt_to<float><<<nb(nv, th), th, 0, s>>>(nv, x64, (float*)xout);
         CU(cudaStreamSynchronize(s));
+        int status = BI_OK;
         for (int r = 0; r < R; ++r) {
             double rel = bnorm[r] > 0 ? rr[r] / bnorm[r] : 0.0;
             if (iters) iters[r] = its[r];
             if (relres) relres[r] = rel;
             if (rel > tol * 1.0001 + 1e-12) status = BI_ERR_NOT_CONVERGED;
         }
+        finished = true;
+        return status;
+    }
+};
+
+gmres_ctx* bi_gmres_create(bi_handle_s* h, const void* rhs, int nrhs, double tol, cudaStream_t s) {
+    gmres_ctx_impl* c = new gmres_ctx_impl();
+    try {
+        c->init(h, rhs, nrhs, tol, s, nullptr, nullptr);
     } catch (...) {
-        for (void* p : tmp) cudaFree(p);
+        delete c;
         throw;
     }
-    for (void* p : tmp) cudaFree(p);
-    return status;
+    return reinterpret_cast<gmres_ctx*>(c);
+}
+void bi_gmres_destroy(gmres_ctx* c) { delete reinterpret_cast<gmres_ctx_impl*>(c); }
+int64_t bi_gmres_bytes(gmres_ctx* c) { return reinterpret_cast<gmres_ctx_impl*>(c)->bytes; }
+int64_t bi_gmres_estimate_bytes(int64_t nun, int R, int m) { return gmres_ctx_impl::estimate_bytes(nun, R, m); }
+
+// Advance a context without blocking on other work: returns 1 when the solve is finished
+// (then bi_gmres_finish), 0 when it needs more calls.
+int bi_gmres_advance(gmres_ctx* cc) {
+    gmres_ctx_impl* c = reinterpret_cast<gmres_ctx_impl*>(cc);
+    if (c->finished) return 1;
+    if (!c->in_cycle) {
+        if (!c->start_cycle()) return 1;
+        c->enqueue_iteration();
+        return 0;
+    }
+    if (!c->iteration_ready()) return 0;
+    if (c->complete_iteration()) {
+        c->end_cycle();
+        return 0;
+    }
+    c->enqueue_iteration();
+    return 0;
+}
+int bi_gmres_finish(gmres_ctx* cc, void* xout, int* iters, double* relres) {
+    return reinterpret_cast<gmres_ctx_impl*>(cc)->finish(xout, iters, relres);
+}
+
+int bi_gmres(bi_handle_s* h, const void* rhs, void* xout, int R, double tol, int* iters, double* relres) {
+    gmres_ctx_impl c;
+    c.init(h, rhs, R, tol, h->stream, h->d_sx, h->d_sy);
+    while (c.start_cycle()) {
+        for (;;) {
+            c.enqueue_iteration();
+            CU(cudaEventSynchronize(c.ev));
+            if (c.complete_iteration()) break;
+        }
+        c.end_cycle();
+    }
+    return c.finish(xout, iters, relres);
 }

@@ -1,0 +1,99 @@
+"""Continuous-batching solve server: results equal direct solves, the same request gives the
+same result alone and in a mix of concurrent requests, and admission limits are enforced."""
+import numpy as np
+import pytest
+
+from paper_2210_04892_gb300.inputs import ellipsoid, icosphere
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+K0 = 2 * np.pi
+TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def bi():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2210_04892_gb300 import bi as mod
+    mod.load()
+    return mod
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _requests():
+    """(mesh, op_mode, nrhs) mix: PEC sphere with 2 incidences, PEC ellipsoid, C-block sphere."""
+    s1 = icosphere(8, 0.5)
+    e1 = ellipsoid(12, (1.0, 0.75, 0.5))
+    s2 = icosphere(6, 0.6)
+    kh2 = np.array([[0, 0, 1.0], [1.0, 0, 0]])
+    ph2 = np.array([[1.0, 0, 0], [0, 0, 1.0]])
+    return [
+        dict(mesh=s1, op_mode=1, khat=kh2, phat=ph2),
+        dict(mesh=e1, op_mode=1, khat=kh2[:1], phat=ph2[:1]),
+        dict(mesh=s2, op_mode=0, khat=kh2[1:], phat=ph2[1:]),
+    ]
+
+
+def _submit(srv, q):
+    v, t = q["mesh"]
+    return srv.submit(v, t, K0, q["khat"], q["phat"], tol=TOL, op_mode=q["op_mode"])
+
+
+def test_server_results_match_direct_solves(bi):
+    qs = _requests()
+    srv = bi.Server(max_active=4)
+    ids = [_submit(srv, q) for q in qs]
+    res = [srv.wait(i) for i in ids]
+    srv.close()
+    for q, r in zip(qs, res):
+        assert r["status"] == bi.BI_OK
+        assert np.all(r["relres"] <= TOL * 1.001)
+        assert r["latency_ms"] >= r["setup_ms"] > 0
+        v, t = q["mesh"]
+        op = bi.Operator(v, t, K0, op_mode=q["op_mode"], max_rhs=len(q["khat"]))
+        b = op.rhs_planewave(q["khat"], q["phat"])
+        x, its, relres = op.solve(b, tol=TOL)
+        assert rel(r["x"], x.cpu().numpy()) < 10 * TOL
+        op.close()
+
+
+def test_same_result_alone_and_in_the_mix(bi):
+    qs = _requests()
+    alone = bi.Server(max_active=1)
+    a = alone.wait(_submit(alone, qs[0]))
+    alone.close()
+    mix = bi.Server(max_active=8)
+    ids = [_submit(mix, q) for q in (qs[1], qs[0], qs[2], qs[1], qs[0])]
+    res = [mix.wait(i) for i in ids]
+    mix.close()
+    for r in res:
+        assert r["status"] == bi.BI_OK
+    for r in (res[1], res[4]):
+        assert rel(r["x"], a["x"]) < 10 * TOL
+        assert np.all(r["relres"] <= TOL * 1.001)
+
+
+def test_admission_limits(bi):
+    v, t = icosphere(8, 0.5)
+    small = bi.Server(mem_budget_bytes=1 << 20, max_active=2)
+    with pytest.raises(bi.BIError) as e:
+        small.submit(v, t, K0, [0, 0, 1.0], [1.0, 0, 0], tol=TOL)
+    assert e.value.code == bi.BI_ERR_OOM
+    small.close()
+    srv = bi.Server(max_active=1, queue_capacity=1)
+    codes = []
+    ids = []
+    for _ in range(4):
+        try:
+            ids.append(srv.submit(v, t, K0, [0, 0, 1.0], [1.0, 0, 0], tol=TOL, op_mode=1))
+        except bi.BIError as err:
+            codes.append(err.code)
+    assert bi.BI_ERR_BUSY in codes
+    for i in ids:
+        assert srv.wait(i)["status"] == bi.BI_OK
+    srv.close()
