@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=256, help="oracle rows in the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=64, help="RHS of the batched monostatic-sweep section (0: skip)")
+    ap.add_argument("--serving", type=int, default=32, help="requests of the serving section (0: skip)")
+    ap.add_argument("--serving-max-unknowns", type=int, default=40000)
+    ap.add_argument("--serving-max-rhs", type=int, default=8)
     return ap.parse_args()
 
 
@@ -192,6 +195,20 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------- replicas
+def aggregate_ranks(ms, units_per_rank, dist=None, device="cpu"):
+    """Replicas on N GPUs: the step time is the slowest rank's, the value is the units all
+    ranks processed per second of that time (weak scaling)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        tt = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    return ms, world * units_per_rank / (ms * 1e-3)
+
+
 # ---------------------------------------------------------------------------- batched sweep
 def run_batched(args):
     """Batched monostatic sweep on the cube-with-cylinder surface (~93k RWG, 186k unknowns):
@@ -243,6 +260,65 @@ def run_batched(args):
     return out
 
 
+# ---------------------------------------------------------------------------- serving stream
+def _serve(bi, reqs, arrivals, max_active, split_rhs, tol):
+    """Submit requests at the given arrival times (s) and wait for all; returns per-request
+    latency (s, from arrival to the last solved column), makespan (s) and setup ms."""
+    srv = bi.Server(max_active=max_active)
+    t0 = time.perf_counter()
+    pending = {}
+    order = []
+    for i, (q, ta) in enumerate(zip(reqs, arrivals)):
+        while time.perf_counter() - t0 < ta:
+            time.sleep(0.0005)
+        cols = [(q["khat"][c:c + 1], q["phat"][c:c + 1]) for c in range(len(q["khat"]))] if split_rhs else \
+            [(q["khat"], q["phat"])]
+        for kh, ph in cols:
+            rid = srv.submit(q["verts"], q["tris"], q["k0"], kh, ph, tol=tol, op_mode=q["op_mode"])
+            pending[rid] = i
+            order.append(rid)
+    done_at = {}
+    setup = []
+    status_ok = True
+    for rid in order:
+        r = srv.wait(rid, timeout=3600)
+        status_ok = status_ok and r["status"] in (bi.BI_OK, bi.BI_ERR_NOT_CONVERGED)
+        i = pending[rid]
+        # latency of a request = submission (its arrival) to its last solved column; in the
+        # split form all of a request's columns are submitted at its arrival
+        done_at[i] = max(done_at.get(i, 0.0), r["latency_ms"] / 1e3)
+        setup.append(r["setup_ms"])
+    makespan = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([done_at[i] for i in range(len(reqs))])
+    return lat, makespan, float(np.mean(setup)), status_ok
+
+
+def run_serving(args):
+    """Serving stream (Poisson arrivals at about 75% of the measured capacity): p50/p99
+    latency and solved unknowns*RHS per second of the continuous-batching server, against the
+    plain form (one request at a time, one right-hand side at a time) on the same arrivals."""
+    from paper_2210_04892_gb300 import bi
+    from paper_2210_04892_gb300.inputs import serving_requests
+    reqs = serving_requests(args.serving, 2000, args.serving_max_unknowns, args.serving_max_rhs)
+    tol = 1e-3
+    work = sum((len(q["tris"]) * 3 // 2) * (2 if q["op_mode"] == 0 else 1) * len(q["khat"]) for q in reqs)
+    # capacity: everything submitted at once
+    lat0, span0, _, _ = _serve(bi, reqs, [0.0] * len(reqs), 8, False, tol)
+    rate = 0.75 * len(reqs) / span0
+    rng = np.random.default_rng(20221011 + 31)
+    arrivals = list(np.cumsum(rng.exponential(1.0 / rate, len(reqs))))
+    arrivals = [a - arrivals[0] for a in arrivals]
+    lat, span, setup_ms, ok = _serve(bi, reqs, arrivals, 8, False, tol)
+    lat_p, span_p, _, ok_p = _serve(bi, reqs, arrivals, 1, True, tol)
+    return {"requests": len(reqs), "unknowns_range": [2000, args.serving_max_unknowns], "max_rhs": args.serving_max_rhs,
+            "tol": tol, "arrival_rate_per_s": rate, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)), "throughput": work / span, "unit": "unknowns*RHS solved/s",
+            "mean_setup_ms": setup_ms, "all_converged_or_reported": bool(ok and ok_p),
+            "plain": {"p50_ms": 1e3 * float(np.percentile(lat_p, 50)), "p99_ms": 1e3 * float(np.percentile(lat_p, 99)),
+                      "throughput": work / span_p, "form": "one request at a time, one RHS at a time"}}
+
+
 # ---------------------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
@@ -283,11 +359,7 @@ def run_gpu(args):
         dist.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * nun * R / (ms * 1e-3)
+    ms, value = aggregate_ranks(ms, nun * R, dist, device="cuda")
 
     # end to end through the public host-buffer entry point (pinned host memory)
     xh = torch.from_numpy(x_np).pin_memory()
@@ -330,6 +402,8 @@ def run_gpu(args):
            "gpu_launches": launches_per_step(info) * args.steps}
     if args.batched and rank == 0:
         out["batched"] = run_batched(args)
+    if args.serving and rank == 0:
+        out["serving"] = run_serving(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         rows = sample_rows(nun, args.cpu_rows, seed=SEED_BASE + 11)

@@ -205,6 +205,45 @@ def ellipsoid(nu: int, axes=(1.0, 0.75, 0.5)):
     return (v * np.asarray(axes)[None, :]).astype(np.float64), t
 
 
+def cube(n_per_side: int, size: float = 1.0):
+    """Closed cube surface of side ``size`` on a uniform n x n grid per face."""
+    half = size / 2
+    V, T = _box_surface((-half, -half, -half), (half, half, half), lambda L: np.linspace(0.0, L, n_per_side + 1))
+    return V.astype(np.float64), T.astype(np.int32)
+
+
+def serving_requests(count: int, min_unknowns: int, max_unknowns: int, max_rhs: int, seed: int = SEED_BASE + 3):
+    """Requests of a serving stream: shape uniform over {sphere, ellipsoid 1:0.75:0.5, cube},
+    unknowns log-uniform in [min, max], mode PEC (N unknowns) or C block (2N unknowns) with
+    probability 1/2, nrhs uniform in 1..max_rhs, plane waves with random directions and
+    polarisations, k0 chosen so that the mean edge is lambda/10.  Returns dicts with
+    verts, tris, k0, op_mode, khat, phat."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        shape = ["sphere", "ellipsoid", "cube"][rng.integers(3)]
+        op_mode = int(rng.integers(2))
+        unknowns = float(np.exp(rng.uniform(np.log(min_unknowns), np.log(max_unknowns))))
+        n_rwg = unknowns / (2 if op_mode == 0 else 1)
+        if shape == "cube":
+            n = max(2, int(round(np.sqrt(n_rwg / 18.0))))     # 6 faces x 2 n^2 triangles, 1.5 edges per triangle
+            v, t = cube(n, 1.0)
+        else:
+            nu = max(2, int(round(np.sqrt(n_rwg / 30.0))))    # 30 nu^2 edges
+            v, t = icosphere(nu, 1.0) if shape == "sphere" else ellipsoid(nu, (1.0, 0.75, 0.5))
+        p = v[t]
+        mean_edge = float(np.mean(np.linalg.norm(p - np.roll(p, 1, axis=1), axis=2)))
+        k0 = 2 * np.pi / (10.0 * mean_edge)
+        nrhs = int(rng.integers(1, max_rhs + 1))
+        kh = rng.standard_normal((nrhs, 3))
+        kh /= np.linalg.norm(kh, axis=1, keepdims=True)
+        ph = rng.standard_normal((nrhs, 3))
+        ph -= np.sum(ph * kh, axis=1, keepdims=True) * kh
+        ph /= np.linalg.norm(ph, axis=1, keepdims=True)
+        out.append(dict(shape=shape, verts=v, tris=t, k0=k0, op_mode=op_mode, khat=kh, phat=ph))
+    return out
+
+
 def complex_gaussian(n: int, nrhs: int = 1, seed: int = SEED_BASE):
     """x = (N(0,1) + j N(0,1)) / sqrt(2), column-major [nrhs][n], complex128."""
     rng = np.random.default_rng(seed)
