@@ -790,11 +790,18 @@ int or_fill_rows(int nv, const double* V, int nt, const int* T, double k, int mo
         if (need[t]) list[nl++] = t;
     rules_t* R = rules_make(level);
 
+    /* work items: (test triangle, block of source triangles), so that a few rows of a large
+       mesh still spread over all cores */
+    const int sblk = 512;
+    const int nsb = (M.nt + sblk - 1) / sblk;
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int li = 0; li < nl; ++li) {
+    for (long long item = 0; item < (long long)nl * nsb; ++item) {
+        int li = (int)(item / nsb);
         int tmi = list[li];
         const tri_t* Tm = &M.tris[tmi];
-        for (int tni = 0; tni < M.nt; ++tni) {
+        int t0 = (int)(item % nsb) * sblk;
+        int t1 = t0 + sblk < M.nt ? t0 + sblk : M.nt;
+        for (int tni = t0; tni < t1; ++tni) {
             const tri_t* Tn = &M.tris[tni];
             blocks_t B;
             pair_blocks(Tm, Tn, R, k, &B);

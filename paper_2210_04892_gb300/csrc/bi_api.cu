@@ -90,12 +90,16 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
         bi_build_tree(h, verts);
         bi_build_sampling(h);
         bi_build_interp(h);
-        CU(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-        CU(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+        // the far-field chain is the latency-critical path of a product: its streams get the
+        // highest priority, the bandwidth-bound near-field product (side stream) the lowest
+        int prio_lo = 0, prio_hi = 0;
+        CU(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        CU(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_lo));
+        CU(cudaStreamCreateWithPriority(&h->cap, cudaStreamNonBlocking, prio_hi));
         CU(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
         for (int l = 3; l < h->nlev && l < BI_MAXLEV; ++l) {
-            CU(cudaStreamCreateWithFlags(&h->tstream[l], cudaStreamNonBlocking));
+            CU(cudaStreamCreateWithPriority(&h->tstream[l], cudaStreamNonBlocking, prio_hi));
             CU(cudaEventCreateWithFlags(&h->ev_tfork[l], cudaEventDisableTiming));
             CU(cudaEventCreateWithFlags(&h->ev_tjoin[l], cudaEventDisableTiming));
         }

@@ -54,6 +54,7 @@ struct level_t {
     int* d_parent = nullptr;
     int* d_child_ptr = nullptr;
     int* d_octant = nullptr;            // octant of each box inside its parent
+    int* d_child_order = nullptr;       // boxes ordered by (slot in parent, parent): siblings far apart in a grid
     void* d_shift = nullptr;            // [8][K] exp(+jk khat.(c_child - c_parent)) for parent level
     void* d_U = nullptr;                // outgoing patterns [nbox][K][E]
     void* d_V = nullptr;                // incoming patterns [nbox][K][E]

@@ -150,9 +150,9 @@ __global__ void __launch_bounds__(128) k_near(int R, const int* __restrict__ lea
 template <typename T, int MODE>
 __global__ void k_aggregate(int K, int R, const int* __restrict__ leaf_start, const cpx<T>* __restrict__ F,
                             const cpx<T>* __restrict__ xt, cpx<T>* __restrict__ U) {
-    const int b = blockIdx.y;
+    const int b = blockIdx.x;
     const int E = 2 * R;
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t idx = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)K * E) return;
     const int kk = (int)(idx / E), e = (int)(idx % E);
     const int c = e / R, r = e % R;
@@ -183,8 +183,8 @@ template <typename T, int P>
 __global__ void k_interp_theta(int nthp, int nphc, int Kc, int E, int pth, const int* __restrict__ src,
                                const int* __restrict__ flip, const T* __restrict__ w, const cpx<T>* __restrict__ Uc,
                                cpx<T>* __restrict__ tmp) {
-    const int cb = blockIdx.y;
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int cb = blockIdx.x;
+    int64_t idx = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     int64_t tot = (int64_t)nthp * nphc * E;
     if (idx >= tot) return;
     const int e = (int)(idx % E);
@@ -225,8 +225,8 @@ template <typename T, int P>
 __global__ void k_interp_phi(int nthp, int nphp, int nphc, int E, int pph, const int* __restrict__ src,
                              const T* __restrict__ w, const int* __restrict__ child_ptr, const int* __restrict__ octant,
                              const cpx<T>* __restrict__ shift, const cpx<T>* __restrict__ tmp, cpx<T>* __restrict__ Up) {
-    const int pb = blockIdx.y;
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int pb = blockIdx.x;
+    int64_t idx = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     const int Kp = nthp * nphp;
     if (idx >= (int64_t)Kp * E) return;
     const int e = (int)(idx % E);
@@ -273,8 +273,8 @@ template <typename T>
 __global__ void k_translate(int K, int E, const int* __restrict__ il_ptr, const int* __restrict__ il_src,
                             const int* __restrict__ il_off, const cpx<T>* __restrict__ Top, const cpx<T>* __restrict__ U,
                             cpx<T>* __restrict__ V) {
-    const int b = blockIdx.y;
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.x;
+    int64_t idx = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)K * E) return;
     const int kk = (int)(idx / E);
     cpx<T> acc = czero<T>();
@@ -292,8 +292,8 @@ template <typename T>
 __global__ void k_anterp_phi(int nthp, int nphp, int nphc, int E, const int* __restrict__ tptr, const int* __restrict__ tdst,
                              const T* __restrict__ tw, const int* __restrict__ parent, const int* __restrict__ octant,
                              const cpx<T>* __restrict__ shift, const cpx<T>* __restrict__ Vp, cpx<T>* __restrict__ tmp) {
-    const int cb = blockIdx.y;
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int cb = blockIdx.x;
+    int64_t idx = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     const int64_t tot = (int64_t)nthp * nphc * E;
     if (idx >= tot) return;
     const int e = (int)(idx % E);
@@ -320,8 +320,8 @@ template <typename T>
 __global__ void k_anterp_theta(int nthp, int nthc, int nphc, int E, const int* __restrict__ tptr,
                                const int* __restrict__ tdst, const int* __restrict__ tflip, const T* __restrict__ tw,
                                const cpx<T>* __restrict__ tmp, cpx<T>* __restrict__ Vc) {
-    const int cb = blockIdx.y;
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int cb = blockIdx.x;
+    int64_t idx = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     const int Kc = nthc * nphc;
     if (idx >= (int64_t)Kc * E) return;
     const int e = (int)(idx % E);
@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(256) k_aggregate2(int N, int K, int R, int nun
     extern __shared__ unsigned char smem_raw[];
     cpx<T>* xs = reinterpret_cast<cpx<T>*>(smem_raw);  // [nb][2][R]
     __shared__ cpx<T> red[4][64][2];
-    const int b = blockIdx.y;
+    const int b = blockIdx.x;
     const int n0 = leaf_start[b], nb = leaf_start[b + 1] - n0;
     for (int i = threadIdx.x; i < nb * 2 * R; i += blockDim.x) {
         const int r = i % R, X = (i / R) % 2, n = i / (2 * R);
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(256) k_aggregate2(int N, int K, int R, int nun
     }
     __syncthreads();
     const int slot = threadIdx.x & 63, grp = threadIdx.x >> 6;
-    const int idx = blockIdx.x * 64 + slot;
+    const int idx = blockIdx.y * 64 + slot;
     const bool ok = idx < K * R;
     const int kk = ok ? idx / R : 0, r = ok ? idx % R : 0;
     cpx<T> ut = czero<T>(), up = czero<T>();
@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(256) k_aggregate_tile(int N, int K, int R, int
                                                         const cpx<T>* __restrict__ x, cpx<T>* __restrict__ U) {
     constexpr int KT = 32;
     extern __shared__ unsigned char smem_raw[];
-    const int b = blockIdx.y, k0 = blockIdx.x * KT;
+    const int b = blockIdx.x, k0 = blockIdx.y * KT;
     const int n0 = leaf_start[b], nb = leaf_start[b + 1] - n0;
     cpx<T>* fs = reinterpret_cast<cpx<T>*>(smem_raw);      // [nb][KT][2]
     cpx<T>* xs = fs + (size_t)nb * KT * 2;                   // [nb][2][R]
@@ -825,8 +825,10 @@ __global__ void __launch_bounds__(256) k_anterp_fused(int nthc, int nphc, int nt
 //  upward:   U_p[parent] += shift(oct) * Interp_phi(Interp_theta(U_c))   (float atomics into U_p,
 //            which the caller zeroes; 8 children per parent)
 //  downward: V_c += Anterp_theta(Anterp_phi(conj(shift(oct)) * V_p[parent]))
-template <typename T>
-__device__ __forceinline__ void atomic_add_c(cpx<T>* p, cpx<T> v) {
+__device__ __forceinline__ void atomic_add_c(cpx<float>* p, cpx<float> v) {
+    atomicAdd(reinterpret_cast<float2*>(p), make_float2(v.x, v.y));
+}
+__device__ __forceinline__ void atomic_add_c(cpx<double>* p, cpx<double> v) {
     atomicAdd(&p->x, v.x);
     atomicAdd(&p->y, v.y);
 }
@@ -837,6 +839,7 @@ __global__ void __launch_bounds__(256) k_interp_child(int nthc, int nphc, int nt
                                                       const T* __restrict__ th_w, const int* __restrict__ ph_src,
                                                       const T* __restrict__ ph_w, const int* __restrict__ parent,
                                                       const int* __restrict__ octant, const cpx<T>* __restrict__ shift,
+                                                      const int* __restrict__ order,
                                                       const cpx<T>* __restrict__ Uc, cpx<T>* __restrict__ Up) {
     extern __shared__ unsigned char smem_raw[];
     const int Kc = nthc * nphc, Kp = nthp * nphp;
@@ -846,7 +849,7 @@ __global__ void __launch_bounds__(256) k_interp_child(int nthc, int nphc, int nt
     T* pw = tw + nthp * pth;                                 // phi weights [nphp*pph]
     int* tsrc = reinterpret_cast<int*>(pw + nphp * pph);     // theta source row*nphc + column shift flag
     int* psrc = tsrc + nthp * pth;                           // phi source column
-    const int cb = blockIdx.x;
+    const int cb = order[blockIdx.x];
     const int half = nphc / 2;
     for (int i = threadIdx.x; i < nthp * pth; i += blockDim.x) {
         const int f = th_flip[i];
@@ -1029,8 +1032,8 @@ void launch_interp_two_pass(bi_handle_s* h, int l, int E, cudaStream_t s) {
     interp_t& I = h->itp[l];
     const int th = 256;
     typedef cpx<T> C;
-    dim3 g1(nblk((int64_t)P.nth * Cc.nph * E, th), Cc.nbox);
-    dim3 g2(nblk((int64_t)P.K * E, th), P.nbox);
+    dim3 g1(Cc.nbox, nblk((int64_t)P.nth * Cc.nph * E, th));
+    dim3 g2(P.nbox, nblk((int64_t)P.K * E, th));
 #define BI_TH(PP) k_interp_theta<T, PP><<<g1, th, 0, s>>>(P.nth, Cc.nph, Cc.K, E, I.p_th, I.d_th_src, I.d_th_flip, \
                                                           (const T*)I.d_th_w, (const C*)Cc.d_U, (C*)I.d_tmp)
 #define BI_PH(PP) k_interp_phi<T, PP><<<g2, th, 0, s>>>(P.nth, P.nph, Cc.nph, E, I.p_ph, I.d_ph_src, (const T*)I.d_ph_w, \
@@ -1102,7 +1105,7 @@ void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s,
         // leaf aggregation
         {
             level_t& L = h->lev[lf];
-            dim3 g(nblk((int64_t)L.K * E, th), L.nbox);
+            dim3 g(L.nbox, nblk((int64_t)L.K * E, th));
             if (h->prm.op_mode == 0)
                 k_aggregate<T, 0><<<g, th, 0, s>>>(L.K, R, h->d_leaf_start, (const C*)h->d_F, xt, (C*)L.d_U);
             else
@@ -1122,7 +1125,7 @@ void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s,
         // translations on every level
         for (int l = 2; l <= lf; ++l) {
             level_t& L = h->lev[l];
-            dim3 g(nblk((int64_t)L.K * E, th), L.nbox);
+            dim3 g(L.nbox, nblk((int64_t)L.K * E, th));
             k_translate<T><<<g, th, 0, s>>>(L.K, E, L.d_il_ptr, L.d_il_src, L.d_il_off, (const C*)L.d_T, (const C*)L.d_U,
                                             (C*)L.d_V);
             CU(cudaGetLastError());
@@ -1133,11 +1136,11 @@ void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s,
             level_t& P = h->lev[l];
             level_t& Cc = h->lev[l + 1];
             interp_t& I = h->itp[l];
-            dim3 g1(nblk((int64_t)P.nth * Cc.nph * E, th), Cc.nbox);
+            dim3 g1(Cc.nbox, nblk((int64_t)P.nth * Cc.nph * E, th));
             k_anterp_phi<T><<<g1, th, 0, s>>>(P.nth, P.nph, Cc.nph, E, I.d_tph_ptr, I.d_tph_dst, (const T*)I.d_tph_w,
                                               Cc.d_parent, Cc.d_octant, (const C*)P.d_shift, (const C*)P.d_V, (C*)I.d_tmp);
             CU(cudaGetLastError());
-            dim3 g2(nblk((int64_t)Cc.K * E, th), Cc.nbox);
+            dim3 g2(Cc.nbox, nblk((int64_t)Cc.K * E, th));
             k_anterp_theta<T><<<g2, th, 0, s>>>(P.nth, Cc.nth, Cc.nph, E, I.d_tth_ptr, I.d_tth_dst, I.d_tth_flip,
                                                 (const T*)I.d_tth_w, (const C*)I.d_tmp, (C*)Cc.d_V);
             CU(cudaGetLastError());
@@ -1272,7 +1275,8 @@ bool interp_child(bi_handle_s* h, int l, int E, cudaStream_t s) {
     CU(cudaMemsetAsync(P.d_U, 0, (size_t)P.nbox * P.K * E * sizeof(cpx<T>), s));
     k_interp_child<T><<<C.nbox, 256, smem, s>>>(C.nth, C.nph, P.nth, P.nph, E, I.p_th, I.p_ph, I.d_th_src, I.d_th_flip,
                                                 (const T*)I.d_th_w, I.d_ph_src, (const T*)I.d_ph_w, C.d_parent, C.d_octant,
-                                                (const cpx<T>*)P.d_shift, (const cpx<T>*)C.d_U, (cpx<T>*)P.d_U);
+                                                (const cpx<T>*)P.d_shift, C.d_child_order, (const cpx<T>*)C.d_U,
+                                                (cpx<T>*)P.d_U);
     CU(cudaGetLastError());
     return true;
 }
@@ -1359,7 +1363,7 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
     const int lf = h->leaf;
     if (R >= 8) {
         level_t& L = h->lev[lf];
-        dim3 g(nblk(L.K, 32), L.nbox);
+        dim3 g(L.nbox, nblk(L.K, 32));
         size_t smem = ((size_t)h->max_leaf_count * 32 * 2 + (size_t)h->max_leaf_count * 2 * R) * sizeof(C);
         if (smem > 48 * 1024) {
             CU(cudaFuncSetAttribute(k_aggregate_tile<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1374,7 +1378,7 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
         CU(cudaGetLastError());
     } else {
         level_t& L = h->lev[lf];
-        dim3 g(nblk((int64_t)L.K * R, 64), L.nbox);
+        dim3 g(L.nbox, nblk((int64_t)L.K * R, 64));
         size_t smem = (size_t)h->max_leaf_count * 2 * R * sizeof(C);
         if (smem > 48 * 1024) {
             CU(cudaFuncSetAttribute(k_aggregate2<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1391,7 +1395,7 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
     // the upward pass continues, and join before the downward pass adds into V_l.
     auto translate = [&](int l, cudaStream_t st) {
         level_t& L = h->lev[l];
-        dim3 g(nblk((int64_t)L.K * E, th), L.nbox);
+        dim3 g(L.nbox, nblk((int64_t)L.K * E, th));
         k_translate<T><<<g, th, 0, st>>>(L.K, E, L.d_il_ptr, L.d_il_src, L.d_il_off, (const C*)L.d_T, (const C*)L.d_U,
                                          (C*)L.d_V);
         CU(cudaGetLastError());
@@ -1422,11 +1426,11 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
         level_t& P = h->lev[l];
         level_t& Cc = h->lev[l + 1];
         interp_t& I = h->itp[l];
-        dim3 g1(nblk((int64_t)P.nth * Cc.nph * E, th), Cc.nbox);
+        dim3 g1(Cc.nbox, nblk((int64_t)P.nth * Cc.nph * E, th));
         k_anterp_phi<T><<<g1, th, 0, s>>>(P.nth, P.nph, Cc.nph, E, I.d_tph_ptr, I.d_tph_dst, (const T*)I.d_tph_w,
                                           Cc.d_parent, Cc.d_octant, (const C*)P.d_shift, (const C*)P.d_V, (C*)I.d_tmp);
         CU(cudaGetLastError());
-        dim3 g2(nblk((int64_t)Cc.K * E, th), Cc.nbox);
+        dim3 g2(Cc.nbox, nblk((int64_t)Cc.K * E, th));
         k_anterp_theta<T><<<g2, th, 0, s>>>(P.nth, Cc.nth, Cc.nph, E, I.d_tth_ptr, I.d_tth_dst, I.d_tth_flip,
                                             (const T*)I.d_tth_w, (const C*)I.d_tmp, (C*)Cc.d_V);
         CU(cudaGetLastError());

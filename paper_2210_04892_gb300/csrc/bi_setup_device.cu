@@ -1248,6 +1248,14 @@ void bi_fill_translations(bi_handle_s* h) {
             oct[b] = (L.coords[3 * b] & 1) | ((L.coords[3 * b + 1] & 1) << 1) | ((L.coords[3 * b + 2] & 1) << 2);
         L.d_octant = h->upload(oct);
         L.d_parent = h->upload(L.parent);
+        {
+            // slot of each box among its siblings; order = by slot, then by parent
+            std::vector<int> slot(L.nbox, 0), ord(L.nbox);
+            for (int b = 1; b < L.nbox; ++b) slot[b] = (L.parent[b] == L.parent[b - 1]) ? slot[b - 1] + 1 : 0;
+            for (int b = 0; b < L.nbox; ++b) ord[b] = b;
+            std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return slot[x] < slot[y]; });
+            L.d_child_order = h->upload(ord);
+        }
     }
     // interpolation tables (weights in the handle precision)
     for (int l = 2; l + 1 <= h->leaf; ++l) {
