@@ -120,7 +120,7 @@ def stage_bytes(info, nrhs, csize=8):
     b["gather"] = 2 * vec + 4 * N
     b["near"] = info["near_pairs"] * 2 * csize + 2 * vec          # (A, B) per pair, x read, y write
     Kl = info["K"][lf]
-    pat = N * Kl * 2 * csize                                         # one pattern array
+    pat = N * (Kl // 2) * 2 * csize                                  # one pattern array (one of each antipodal pair)
     far = lambda l: info["boxes"][l] * info["K"][l] * E * csize
     b["aggregate"] = pat + vec + far(lf)
     b["interpolate"] = sum(far(l + 1) + far(l) for l in range(2, lf))

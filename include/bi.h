@@ -165,8 +165,10 @@ int bi_farfield(bi_handle h, const void* x, int nrhs, const double* dirs, int nd
 int bi_farfield_noalloc(bi_handle h, const void* x, int nrhs, const double* dirs, int ndir, void* F);
 
 /* Diagnostics: copy an internal device buffer of h to host memory.
- *   what 0: leaf radiation patterns F [N_tree][K_leaf][2] complex (tree order, theta/phi)
- *   what 1: leaf twisted receive patterns RX [N_tree][K_leaf][2]
+ *   what 0: leaf radiation patterns F [N_tree][K_leaf/2][2] complex (tree order, theta/phi;
+ *           the first K_leaf/2 directions in theta-major order, one of each antipodal pair:
+ *           the antipode holds (conj F_theta, -conj F_phi))
+ *   what 1: leaf twisted receive patterns RX [N_tree][K_leaf/2][2], same convention
  *   what 2: translation operators of `level` [343][K_level] (weights folded in)
  *   what 3: outgoing patterns U of `level` [boxes][K_level][2 nrhs] (last product)
  *   what 4: incoming patterns V of `level` [boxes][K_level][2 nrhs] (last product)

@@ -245,7 +245,7 @@ class Operator:
         inf = self.info()
         E = 2 * self.max_rhs
         if what in (0, 1):
-            shape = (self.n_rwg, inf["K"][inf["leaf_level"]], 2)
+            shape = (self.n_rwg, inf["K"][inf["leaf_level"]] // 2, 2)
         elif what == 2:
             shape = (343, inf["K"][level])
         elif what in (3, 4):

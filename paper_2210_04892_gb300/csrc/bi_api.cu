@@ -249,7 +249,7 @@ extern "C" int bi_debug_copy(bi_handle h, int what, int level, void* host, int64
         case 1:
             if (!far) break;
             src = what == 0 ? h->d_F : h->d_RX;
-            need = (size_t)h->N * h->lev[h->leaf].K * 2 * h->csize;
+            need = (size_t)h->N * (h->lev[h->leaf].K / 2) * 2 * h->csize;
             break;
         case 2:
             if (!lev_ok) break;

@@ -138,8 +138,8 @@ struct bi_handle_s {
     int* d_gram_col = nullptr;
     int* d_gram_seg = nullptr;          // column of the neighbour in the test box's near segment
     void* d_gram_val = nullptr;         // [nnz][2] real: (G, X)
-    void* d_F = nullptr;                // leaf radiation patterns [N][K][2]
-    void* d_RX = nullptr;               // leaf twisted receive patterns [N][K][2]
+    void* d_F = nullptr;                // leaf radiation patterns [N][K/2][2] (one direction of each antipodal pair)
+    void* d_RX = nullptr;               // leaf twisted receive patterns [N][K/2][2]
     // geometry on device (tree order for RWG data)
     double* d_tri = nullptr;            // [nt][9]
     double* d_tri_n = nullptr;          // [nt][3]

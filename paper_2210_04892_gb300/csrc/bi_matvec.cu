@@ -63,6 +63,34 @@ __device__ __forceinline__ cpx<T> czero() {
     return {T(0), T(0)};
 }
 
+// Antipodal pairs of directions: (it, jp) <-> (nth - 1 - it, jp + nph/2 mod nph).  The leaf
+// pattern arrays hold the first K/2 directions of the theta-major numbering, one of each pair;
+// a stored (theta, phi) pair (a, b) reads (conj a, -conj b) at the antipode (real basis
+// functions; the antipodal map keeps theta-hat and reverses phi-hat).
+__device__ __forceinline__ int antipode(int kk, int K, int nph) {
+    const int it = kk / nph, jp = kk - it * nph, jm = jp + (nph >> 1);
+    return (K / nph - 1 - it) * nph + (jm >= nph ? jm - nph : jm);
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> cconj(cpx<T> a) {
+    return {a.x, -a.y};
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> cnegconj(cpx<T> a) {
+    return {-a.x, a.y};
+}
+// One direction's receive terms (R = conj(F), khat x V = (-V_phi, V_theta)):
+//   J += R.V - RX.(khat x V),  M += -R.(khat x V) - RX.V
+template <typename T, int MODE>
+__device__ __forceinline__ void recv_terms(cpx<T> Ft, cpx<T> Fp, cpx<T> Xt, cpx<T> Xp, cpx<T> Vt, cpx<T> Vp, cpx<T>& sJ,
+                                           cpx<T>& sM) {
+    sJ = cadd(sJ, csub(cadd(cmulc(Ft, Vt), cmulc(Fp, Vp)), csub(cmul(Xp, Vt), cmul(Xt, Vp))));
+    if (MODE == 0) {
+        const cpx<T> t = csub(cmulc(Ft, Vp), cmulc(Fp, Vt));
+        sM = cadd(sM, csub(t, cadd(cmul(Xt, Vt), cmul(Xp, Vp))));
+    }
+}
+
 // ------------------------------------------------------------------ permutations
 template <typename T>
 __global__ void k_gather_x(int N, int nX, int R, int nun, const int* __restrict__ perm, const cpx<T>* __restrict__ x,
@@ -148,17 +176,23 @@ __global__ void __launch_bounds__(128) k_near(int R, const int* __restrict__ lea
 // ------------------------------------------------------------------ leaf aggregation
 // U_b(k) = sum_{n in b} ( -x_J,n F_n(k) + x_M,n khat x F_n(k) ),  (khat x F) = (-F_phi, F_theta)
 template <typename T, int MODE>
-__global__ void k_aggregate(int K, int R, const int* __restrict__ leaf_start, const cpx<T>* __restrict__ F,
+__global__ void k_aggregate(int K, int nph, int R, const int* __restrict__ leaf_start, const cpx<T>* __restrict__ F,
                             const cpx<T>* __restrict__ xt, cpx<T>* __restrict__ U) {
     const int b = blockIdx.x;
-    const int E = 2 * R;
+    const int E = 2 * R, Kh = K / 2;
     int64_t idx = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)K * E) return;
     const int kk = (int)(idx / E), e = (int)(idx % E);
     const int c = e / R, r = e % R;
+    const bool stored = kk < Kh;
+    const int ks = stored ? kk : antipode(kk, K, nph);
     cpx<T> acc = czero<T>();
     for (int n = leaf_start[b]; n < leaf_start[b + 1]; ++n) {
-        cpx<T> Ft = F[((int64_t)n * K + kk) * 2 + 0], Fp = F[((int64_t)n * K + kk) * 2 + 1];
+        cpx<T> Ft = F[((int64_t)n * Kh + ks) * 2 + 0], Fp = F[((int64_t)n * Kh + ks) * 2 + 1];
+        if (!stored) {
+            Ft = cconj(Ft);
+            Fp = cnegconj(Fp);
+        }
         if (MODE == 0) {
             cpx<T> xJ = xt[((int64_t)n * 2 + 0) * R + r], xM = xt[((int64_t)n * 2 + 1) * R + r];
             if (c == 0) {  // -xJ Ft - xM Fp
@@ -348,7 +382,7 @@ __global__ void k_anterp_theta(int nthp, int nthc, int nphc, int E, const int* _
 // ------------------------------------------------------------------ leaf receive
 // One warp per (tree RWG m, RHS r); lanes stride over directions, then a shuffle reduction.
 template <typename T, int MODE>
-__global__ void k_receive(int N, int K, int R, const int* __restrict__ leaf_of, const cpx<T>* __restrict__ F,
+__global__ void k_receive(int N, int K, int nph, int R, const int* __restrict__ leaf_of, const cpx<T>* __restrict__ F,
                           const cpx<T>* __restrict__ RX, const cpx<T>* __restrict__ V, T c, cpx<T>* __restrict__ yf) {
     const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -357,9 +391,18 @@ __global__ void k_receive(int N, int K, int R, const int* __restrict__ leaf_of, 
     const int b = leaf_of[m];
     const int E = 2 * R;
     cpx<T> sJ = czero<T>(), sM = czero<T>();
+    const int Kh = K / 2;
     for (int kk = lane; kk < K; kk += 32) {
-        const cpx<T> Ft = F[((int64_t)m * K + kk) * 2], Fp = F[((int64_t)m * K + kk) * 2 + 1];
-        const cpx<T> Xt = RX[((int64_t)m * K + kk) * 2], Xp = RX[((int64_t)m * K + kk) * 2 + 1];
+        const bool stored = kk < Kh;
+        const int ks = stored ? kk : antipode(kk, K, nph);
+        cpx<T> Ft = F[((int64_t)m * Kh + ks) * 2], Fp = F[((int64_t)m * Kh + ks) * 2 + 1];
+        cpx<T> Xt = RX[((int64_t)m * Kh + ks) * 2], Xp = RX[((int64_t)m * Kh + ks) * 2 + 1];
+        if (!stored) {
+            Ft = cconj(Ft);
+            Fp = cnegconj(Fp);
+            Xt = cconj(Xt);
+            Xp = cnegconj(Xp);
+        }
         const cpx<T> Vt = V[((int64_t)b * K + kk) * E + r], Vp = V[((int64_t)b * K + kk) * E + R + r];
         // R.V = conj(Ft) Vt + conj(Fp) Vp ; RX.(khat x V) = -Xt Vp + Xp Vt
         cpx<T> RV = cadd(cmulc(Ft, Vt), cmulc(Fp, Vp));
@@ -538,17 +581,19 @@ __global__ void __launch_bounds__(256) k_near_stream(int N, int R, int nun, cons
 }
 
 // ------------------------------------------------------------------ leaf aggregation (fused gather)
-// thread per (direction kk, RHS r): both components from one 16-byte pattern load.
+// thread per (stored direction kk, RHS r): both components from one 16-byte pattern load give
+// U at kk and at its antipode.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_aggregate2(int N, int K, int R, int nun, const int* __restrict__ perm,
+__global__ void __launch_bounds__(256) k_aggregate2(int N, int K, int nph, int R, int nun, const int* __restrict__ perm,
                                                     const int* __restrict__ leaf_start, const cpx<T>* __restrict__ F,
                                                     const cpx<T>* __restrict__ x, cpx<T>* __restrict__ U) {
     // CTA = (box, 64 direction-RHS slots); the box's RWGs are split over 4 thread groups whose
     // partial sums meet in shared memory.  x of the box is staged once per CTA.
     extern __shared__ unsigned char smem_raw[];
     cpx<T>* xs = reinterpret_cast<cpx<T>*>(smem_raw);  // [nb][2][R]
-    __shared__ cpx<T> red[4][64][2];
+    __shared__ cpx<T> red[4][64][4];
     const int b = blockIdx.x;
+    const int Kh = K / 2;
     const int n0 = leaf_start[b], nb = leaf_start[b + 1] - n0;
     for (int i = threadIdx.x; i < nb * 2 * R; i += blockDim.x) {
         const int r = i % R, X = (i / R) % 2, n = i / (2 * R);
@@ -557,36 +602,48 @@ __global__ void __launch_bounds__(256) k_aggregate2(int N, int K, int R, int nun
     __syncthreads();
     const int slot = threadIdx.x & 63, grp = threadIdx.x >> 6;
     const int idx = blockIdx.y * 64 + slot;
-    const bool ok = idx < K * R;
+    const bool ok = idx < Kh * R;
     const int kk = ok ? idx / R : 0, r = ok ? idx % R : 0;
-    cpx<T> ut = czero<T>(), up = czero<T>();
+    // (ut, up) at kk; (vt, vp) at the antipode, where the pattern reads (conj Ft, -conj Fp)
+    cpx<T> ut = czero<T>(), up = czero<T>(), vt = czero<T>(), vp = czero<T>();
     if (ok) {
-        const cpx<T>* f = F + ((int64_t)n0 * K + kk) * 2;
+        const cpx<T>* f = F + ((int64_t)n0 * Kh + kk) * 2;
 #pragma unroll 4
         for (int n = grp; n < nb; n += 4) {
             cpx<T> Ft, Fp;
-            load_pair(f + (int64_t)n * K * 2, Ft, Fp);
+            load_pair(f + (int64_t)n * Kh * 2, Ft, Fp);
             const cpx<T> xJ = xs[(n * 2 + 0) * R + r];
             ut = csub(ut, cmul(xJ, Ft));
             up = csub(up, cmul(xJ, Fp));
+            vt = csub(vt, cmulc(Ft, xJ));
+            vp = cadd(vp, cmulc(Fp, xJ));
             if (MODE == 0) {
                 const cpx<T> xM = xs[(n * 2 + 1) * R + r];
                 ut = csub(ut, cmul(xM, Fp));
                 up = cadd(up, cmul(xM, Ft));
+                vt = cadd(vt, cmulc(Fp, xM));
+                vp = cadd(vp, cmulc(Ft, xM));
             }
         }
     }
     red[grp][slot][0] = ut;
     red[grp][slot][1] = up;
+    red[grp][slot][2] = vt;
+    red[grp][slot][3] = vp;
     __syncthreads();
     if (grp == 0 && ok) {
         for (int g2 = 1; g2 < 4; ++g2) {
             ut = cadd(ut, red[g2][slot][0]);
             up = cadd(up, red[g2][slot][1]);
+            vt = cadd(vt, red[g2][slot][2]);
+            vp = cadd(vp, red[g2][slot][3]);
         }
         cpx<T>* o = U + ((int64_t)b * K + kk) * (2 * R);
         o[r] = ut;
         o[R + r] = up;
+        cpx<T>* oa = U + ((int64_t)b * K + antipode(kk, K, nph)) * (2 * R);
+        oa[r] = vt;
+        oa[R + r] = vp;
     }
 }
 
@@ -595,10 +652,11 @@ __global__ void __launch_bounds__(256) k_aggregate2(int N, int K, int R, int nun
 // CTA = (box, 32 directions); the box's patterns for those directions and its x for all RHS
 // are staged in shared memory, so every pattern entry is read from HBM once per product.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_aggregate_tile(int N, int K, int R, int nun, const int* __restrict__ perm,
+__global__ void __launch_bounds__(256) k_aggregate_tile(int N, int K, int nph, int R, int nun, const int* __restrict__ perm,
                                                         const int* __restrict__ leaf_start, const cpx<T>* __restrict__ F,
                                                         const cpx<T>* __restrict__ x, cpx<T>* __restrict__ U) {
     constexpr int KT = 32;
+    const int Kh = K / 2;
     extern __shared__ unsigned char smem_raw[];
     const int b = blockIdx.x, k0 = blockIdx.y * KT;
     const int n0 = leaf_start[b], nb = leaf_start[b + 1] - n0;
@@ -607,7 +665,7 @@ __global__ void __launch_bounds__(256) k_aggregate_tile(int N, int K, int R, int
     for (int i = threadIdx.x; i < nb * KT; i += blockDim.x) {
         const int n = i / KT, kk = k0 + i % KT;
         cpx<T> a = czero<T>(), c = czero<T>();
-        if (kk < K) load_pair(F + ((int64_t)(n0 + n) * K + kk) * 2, a, c);
+        if (kk < Kh) load_pair(F + ((int64_t)(n0 + n) * Kh + kk) * 2, a, c);
         fs[2 * i] = a;
         fs[2 * i + 1] = c;
     }
@@ -619,22 +677,30 @@ __global__ void __launch_bounds__(256) k_aggregate_tile(int N, int K, int R, int
     const int E = 2 * R;
     for (int o = threadIdx.x; o < KT * R; o += blockDim.x) {
         const int kl = o / R, r = o % R, kk = k0 + kl;
-        if (kk >= K) continue;
-        cpx<T> ut = czero<T>(), up = czero<T>();
+        if (kk >= Kh) continue;
+        // (ut, up) at kk, (vt, vp) at its antipode
+        cpx<T> ut = czero<T>(), up = czero<T>(), vt = czero<T>(), vp = czero<T>();
         for (int n = 0; n < nb; ++n) {
             const cpx<T> Ft = fs[(n * KT + kl) * 2], Fp = fs[(n * KT + kl) * 2 + 1];
             const cpx<T> xJ = xs[(n * 2 + 0) * R + r];
             ut = csub(ut, cmul(xJ, Ft));
             up = csub(up, cmul(xJ, Fp));
+            vt = csub(vt, cmulc(Ft, xJ));
+            vp = cadd(vp, cmulc(Fp, xJ));
             if (MODE == 0) {
                 const cpx<T> xM = xs[(n * 2 + 1) * R + r];
                 ut = csub(ut, cmul(xM, Fp));
                 up = cadd(up, cmul(xM, Ft));
+                vt = cadd(vt, cmulc(Fp, xM));
+                vp = cadd(vp, cmulc(Ft, xM));
             }
         }
         cpx<T>* out = U + ((int64_t)b * K + kk) * E;
         out[r] = ut;
         out[R + r] = up;
+        cpx<T>* oa = U + ((int64_t)b * K + antipode(kk, K, nph)) * E;
+        oa[r] = vt;
+        oa[R + r] = vp;
     }
 }
 
@@ -642,7 +708,7 @@ __global__ void __launch_bounds__(256) k_aggregate_tile(int N, int K, int R, int
 // CTA = one leaf box; directions in tiles of 32 staged in shared memory (patterns of the
 // box's RWGs and V for all RHS), each thread accumulating a few (m, r) outputs.
 template <typename T, int MODE, int OPT>
-__global__ void __launch_bounds__(256) k_receive_tile(int N, int K, int R, int RC, int nun, const int* __restrict__ perm,
+__global__ void __launch_bounds__(256) k_receive_tile(int N, int K, int nph, int R, int RC, int nun, const int* __restrict__ perm,
                                                       const int* __restrict__ leaf_start, const cpx<T>* __restrict__ F,
                                                       const cpx<T>* __restrict__ RX, const cpx<T>* __restrict__ V, T c,
                                                       const cpx<T>* __restrict__ yt, cpx<T>* __restrict__ y) {
@@ -652,31 +718,37 @@ __global__ void __launch_bounds__(256) k_receive_tile(int N, int K, int R, int R
     const int r0 = blockIdx.y * RC, rc = min(RC, R - r0);     // this CTA's right-hand sides
     const int n0 = leaf_start[b], nb = leaf_start[b + 1] - n0;
     const int E = 2 * R;
-    cpx<T>* fs = reinterpret_cast<cpx<T>*>(smem_raw);       // [nb][KT][4]: Ft Fp Xt Xp
-    cpx<T>* vs = fs + (size_t)nb * KT * 4;                    // [KT][2][RC]
+    const int Kh = K / 2;
+    cpx<T>* fs = reinterpret_cast<cpx<T>*>(smem_raw);       // [nb][KT][4]: Ft Fp Xt Xp (stored directions)
+    cpx<T>* vs = fs + (size_t)nb * KT * 4;                    // [KT][4][RC]: V at kk (t, p), at its antipode (t, p)
     cpx<T> aJ[OPT], aM[OPT];
 #pragma unroll
     for (int o = 0; o < OPT; ++o) { aJ[o] = czero<T>(); aM[o] = czero<T>(); }
-    for (int k0 = 0; k0 < K; k0 += KT) {
+    for (int k0 = 0; k0 < Kh; k0 += KT) {
         __syncthreads();
         for (int i = threadIdx.x; i < nb * KT; i += blockDim.x) {
             const int n = i / KT, kk = k0 + i % KT;
             cpx<T> a = czero<T>(), bb = czero<T>(), cc = czero<T>(), dd = czero<T>();
-            if (kk < K) {
-                load_pair(F + ((int64_t)(n0 + n) * K + kk) * 2, a, bb);
-                load_pair(RX + ((int64_t)(n0 + n) * K + kk) * 2, cc, dd);
+            if (kk < Kh) {
+                load_pair(F + ((int64_t)(n0 + n) * Kh + kk) * 2, a, bb);
+                load_pair(RX + ((int64_t)(n0 + n) * Kh + kk) * 2, cc, dd);
             }
             fs[4 * i] = a;
             fs[4 * i + 1] = bb;
             fs[4 * i + 2] = cc;
             fs[4 * i + 3] = dd;
         }
-        for (int i = threadIdx.x; i < KT * 2 * RC; i += blockDim.x) {
-            const int kl = i / (2 * RC), cpt = (i / RC) % 2, rr = i % RC, kk = k0 + kl;
-            vs[i] = (kk < K && rr < rc) ? V[((int64_t)b * K + kk) * E + cpt * R + r0 + rr] : czero<T>();
+        for (int i = threadIdx.x; i < KT * 4 * RC; i += blockDim.x) {
+            const int kl = i / (4 * RC), q = (i / RC) % 4, rr = i % RC, kk = k0 + kl;
+            cpx<T> v = czero<T>();
+            if (kk < Kh && rr < rc) {
+                const int kd = q < 2 ? kk : antipode(kk, K, nph);
+                v = V[((int64_t)b * K + kd) * E + (q & 1) * R + r0 + rr];
+            }
+            vs[i] = v;
         }
         __syncthreads();
-        const int kn = min(KT, K - k0);
+        const int kn = min(KT, Kh - k0);
 #pragma unroll
         for (int o = 0; o < OPT; ++o) {
             const int it = threadIdx.x + o * blockDim.x;
@@ -684,12 +756,10 @@ __global__ void __launch_bounds__(256) k_receive_tile(int N, int K, int R, int R
             const int n = it / rc, r = it % rc;
             for (int kl = 0; kl < kn; ++kl) {
                 const cpx<T>* f = fs + (n * KT + kl) * 4;
-                const cpx<T> Vt = vs[(kl * 2 + 0) * RC + r], Vp = vs[(kl * 2 + 1) * RC + r];
-                aJ[o] = cadd(aJ[o], csub(cadd(cmulc(f[0], Vt), cmulc(f[1], Vp)), csub(cmul(f[3], Vt), cmul(f[2], Vp))));
-                if (MODE == 0) {
-                    const cpx<T> t = csub(cmulc(f[0], Vp), cmulc(f[1], Vt));
-                    aM[o] = cadd(aM[o], csub(t, cadd(cmul(f[2], Vt), cmul(f[3], Vp))));
-                }
+                const cpx<T>* v = vs + kl * 4 * RC + r;
+                recv_terms<T, MODE>(f[0], f[1], f[2], f[3], v[0], v[RC], aJ[o], aM[o]);
+                recv_terms<T, MODE>(cconj(f[0]), cnegconj(f[1]), cconj(f[2]), cnegconj(f[3]), v[2 * RC], v[3 * RC], aJ[o],
+                                    aM[o]);
             }
         }
     }
@@ -984,7 +1054,7 @@ __global__ void __launch_bounds__(256) k_anterp_child(int nthc, int nphc, int nt
 // ------------------------------------------------------------------ leaf receive with the final permutation
 // y_user[perm[m]] = y_near[m] + far part (the near result in tree order is added here).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_receive2(int N, int K, int R, int nun, const int* __restrict__ perm,
+__global__ void __launch_bounds__(256) k_receive2(int N, int K, int nph, int R, int nun, const int* __restrict__ perm,
                                                   const int* __restrict__ leaf_of, const cpx<T>* __restrict__ F,
                                                   const cpx<T>* __restrict__ RX, const cpx<T>* __restrict__ V, T c,
                                                   const cpx<T>* __restrict__ yt, cpx<T>* __restrict__ y) {
@@ -995,20 +1065,19 @@ __global__ void __launch_bounds__(256) k_receive2(int N, int K, int R, int nun, 
     const int m = warp / R, r = warp % R;
     const int b = leaf_of[m];
     const int E = 2 * R;
+    const int Kh = K / 2;
     cpx<T> sJ = czero<T>(), sM = czero<T>();
-#pragma unroll 4
-    for (int kk = lane; kk < K; kk += 32) {
+    // lanes over the stored directions; each pattern load serves kk and its antipode
+#pragma unroll 2
+    for (int kk = lane; kk < Kh; kk += 32) {
         cpx<T> Ft, Fp, Xt, Xp;
-        load_pair(F + ((int64_t)m * K + kk) * 2, Ft, Fp);
-        load_pair(RX + ((int64_t)m * K + kk) * 2, Xt, Xp);
+        load_pair(F + ((int64_t)m * Kh + kk) * 2, Ft, Fp);
+        load_pair(RX + ((int64_t)m * Kh + kk) * 2, Xt, Xp);
+        const int ka = antipode(kk, K, nph);
         const cpx<T> Vt = V[((int64_t)b * K + kk) * E + r], Vp = V[((int64_t)b * K + kk) * E + R + r];
-        // R.V - RX.(khat x V) with R = conj(F), (khat x V) = (-V_phi, V_theta)
-        sJ = cadd(sJ, csub(cadd(cmulc(Ft, Vt), cmulc(Fp, Vp)), csub(cmul(Xp, Vt), cmul(Xt, Vp))));
-        if (MODE == 0) {
-            // -R.(khat x V) - RX.V
-            const cpx<T> t = csub(cmulc(Ft, Vp), cmulc(Fp, Vt));
-            sM = cadd(sM, csub(t, cadd(cmul(Xt, Vt), cmul(Xp, Vp))));
-        }
+        const cpx<T> Wt = V[((int64_t)b * K + ka) * E + r], Wp = V[((int64_t)b * K + ka) * E + R + r];
+        recv_terms<T, MODE>(Ft, Fp, Xt, Xp, Vt, Vp, sJ, sM);
+        recv_terms<T, MODE>(cconj(Ft), cnegconj(Fp), cconj(Xt), cnegconj(Xp), Wt, Wp, sJ, sM);
     }
     sJ = warp_sum(sJ);
     if (MODE == 0) sM = warp_sum(sM);
@@ -1107,9 +1176,9 @@ void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s,
             level_t& L = h->lev[lf];
             dim3 g(L.nbox, nblk((int64_t)L.K * E, th));
             if (h->prm.op_mode == 0)
-                k_aggregate<T, 0><<<g, th, 0, s>>>(L.K, R, h->d_leaf_start, (const C*)h->d_F, xt, (C*)L.d_U);
+                k_aggregate<T, 0><<<g, th, 0, s>>>(L.K, L.nph, R, h->d_leaf_start, (const C*)h->d_F, xt, (C*)L.d_U);
             else
-                k_aggregate<T, 1><<<g, th, 0, s>>>(L.K, R, h->d_leaf_start, (const C*)h->d_F, xt, (C*)L.d_U);
+                k_aggregate<T, 1><<<g, th, 0, s>>>(L.K, L.nph, R, h->d_leaf_start, (const C*)h->d_F, xt, (C*)L.d_U);
             CU(cudaGetLastError());
         }
         if (ev) CU(cudaEventRecord(ev[2], s));
@@ -1153,10 +1222,10 @@ void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s,
             T c = (T)(h->k * h->k / (32.0 * pi * pi));
             int64_t nthreads = (int64_t)N * R * 32;
             if (h->prm.op_mode == 0)
-                k_receive<T, 0><<<nblk(nthreads, th), th, 0, s>>>(N, L.K, R, h->d_leaf_of, (const C*)h->d_F,
+                k_receive<T, 0><<<nblk(nthreads, th), th, 0, s>>>(N, L.K, L.nph, R, h->d_leaf_of, (const C*)h->d_F,
                                                                    (const C*)h->d_RX, (const C*)L.d_V, c, yf);
             else
-                k_receive<T, 1><<<nblk(nthreads, th), th, 0, s>>>(N, L.K, R, h->d_leaf_of, (const C*)h->d_F,
+                k_receive<T, 1><<<nblk(nthreads, th), th, 0, s>>>(N, L.K, L.nph, R, h->d_leaf_of, (const C*)h->d_F,
                                                                    (const C*)h->d_RX, (const C*)L.d_V, c, yf);
             CU(cudaGetLastError());
         }
@@ -1304,21 +1373,21 @@ bool launch_receive_tile_opt(bi_handle_s* h, cpx<T>* y, int R, cudaStream_t s) {
     // right-hand sides per CTA so that one thread holds at most OPT outputs
     int RC = std::min(R, (256 * OPT) / std::max(1, h->max_leaf_count));
     if (RC < 1) return false;
-    size_t smem = ((size_t)h->max_leaf_count * 32 * 4 + (size_t)32 * 2 * RC) * sizeof(cpx<T>);
+    size_t smem = ((size_t)h->max_leaf_count * 32 * 4 + (size_t)32 * 4 * RC) * sizeof(cpx<T>);
     if (smem > 200 * 1024) return false;
     const double pi = 3.14159265358979323846;
     const T c = (T)(h->k * h->k / (32.0 * pi * pi));
     if (h->prm.op_mode == 0) {
         if (smem > 48 * 1024)
             CU(cudaFuncSetAttribute(k_receive_tile<T, 0, OPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_receive_tile<T, 0, OPT><<<dim3(L.nbox, (R + RC - 1) / RC), 256, smem, s>>>(h->N, L.K, R, RC, h->nun, h->d_perm,
+        k_receive_tile<T, 0, OPT><<<dim3(L.nbox, (R + RC - 1) / RC), 256, smem, s>>>(h->N, L.K, L.nph, R, RC, h->nun, h->d_perm,
                                                                                    h->d_leaf_start,
                                                             (const cpx<T>*)h->d_F, (const cpx<T>*)h->d_RX,
                                                             (const cpx<T>*)L.d_V, c, (const cpx<T>*)h->d_yt, y);
     } else {
         if (smem > 48 * 1024)
             CU(cudaFuncSetAttribute(k_receive_tile<T, 1, OPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_receive_tile<T, 1, OPT><<<dim3(L.nbox, (R + RC - 1) / RC), 256, smem, s>>>(h->N, L.K, R, RC, h->nun, h->d_perm,
+        k_receive_tile<T, 1, OPT><<<dim3(L.nbox, (R + RC - 1) / RC), 256, smem, s>>>(h->N, L.K, L.nph, R, RC, h->nun, h->d_perm,
                                                                                    h->d_leaf_start,
                                                             (const cpx<T>*)h->d_F, (const cpx<T>*)h->d_RX,
                                                             (const cpx<T>*)L.d_V, c, (const cpx<T>*)h->d_yt, y);
@@ -1363,31 +1432,31 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
     const int lf = h->leaf;
     if (R >= 8) {
         level_t& L = h->lev[lf];
-        dim3 g(L.nbox, nblk(L.K, 32));
+        dim3 g(L.nbox, nblk(L.K / 2, 32));
         size_t smem = ((size_t)h->max_leaf_count * 32 * 2 + (size_t)h->max_leaf_count * 2 * R) * sizeof(C);
         if (smem > 48 * 1024) {
             CU(cudaFuncSetAttribute(k_aggregate_tile<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             CU(cudaFuncSetAttribute(k_aggregate_tile<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         }
         if (h->prm.op_mode == 0)
-            k_aggregate_tile<T, 0><<<g, 256, smem, s>>>(N, L.K, R, nun, h->d_perm, h->d_leaf_start, (const C*)h->d_F, x,
+            k_aggregate_tile<T, 0><<<g, 256, smem, s>>>(N, L.K, L.nph, R, nun, h->d_perm, h->d_leaf_start, (const C*)h->d_F, x,
                                                         (C*)L.d_U);
         else
-            k_aggregate_tile<T, 1><<<g, 256, smem, s>>>(N, L.K, R, nun, h->d_perm, h->d_leaf_start, (const C*)h->d_F, x,
+            k_aggregate_tile<T, 1><<<g, 256, smem, s>>>(N, L.K, L.nph, R, nun, h->d_perm, h->d_leaf_start, (const C*)h->d_F, x,
                                                         (C*)L.d_U);
         CU(cudaGetLastError());
     } else {
         level_t& L = h->lev[lf];
-        dim3 g(L.nbox, nblk((int64_t)L.K * R, 64));
+        dim3 g(L.nbox, nblk((int64_t)(L.K / 2) * R, 64));
         size_t smem = (size_t)h->max_leaf_count * 2 * R * sizeof(C);
         if (smem > 48 * 1024) {
             CU(cudaFuncSetAttribute(k_aggregate2<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             CU(cudaFuncSetAttribute(k_aggregate2<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         }
         if (h->prm.op_mode == 0)
-            k_aggregate2<T, 0><<<g, th, smem, s>>>(N, L.K, R, nun, h->d_perm, h->d_leaf_start, (const C*)h->d_F, x, (C*)L.d_U);
+            k_aggregate2<T, 0><<<g, th, smem, s>>>(N, L.K, L.nph, R, nun, h->d_perm, h->d_leaf_start, (const C*)h->d_F, x, (C*)L.d_U);
         else
-            k_aggregate2<T, 1><<<g, th, smem, s>>>(N, L.K, R, nun, h->d_perm, h->d_leaf_start, (const C*)h->d_F, x, (C*)L.d_U);
+            k_aggregate2<T, 1><<<g, th, smem, s>>>(N, L.K, L.nph, R, nun, h->d_perm, h->d_leaf_start, (const C*)h->d_F, x, (C*)L.d_U);
         CU(cudaGetLastError());
     }
     if (ev) CU(cudaEventRecord(ev[2], s));
@@ -1444,10 +1513,10 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
         T c = (T)(h->k * h->k / (32.0 * pi * pi));
         int64_t nthreads = (int64_t)N * R * 32;
         if (h->prm.op_mode == 0)
-            k_receive2<T, 0><<<nblk(nthreads, th), th, 0, s>>>(N, L.K, R, nun, h->d_perm, h->d_leaf_of, (const C*)h->d_F,
+            k_receive2<T, 0><<<nblk(nthreads, th), th, 0, s>>>(N, L.K, L.nph, R, nun, h->d_perm, h->d_leaf_of, (const C*)h->d_F,
                                                                 (const C*)h->d_RX, (const C*)L.d_V, c, yt, y);
         else
-            k_receive2<T, 1><<<nblk(nthreads, th), th, 0, s>>>(N, L.K, R, nun, h->d_perm, h->d_leaf_of, (const C*)h->d_F,
+            k_receive2<T, 1><<<nblk(nthreads, th), th, 0, s>>>(N, L.K, L.nph, R, nun, h->d_perm, h->d_leaf_of, (const C*)h->d_F,
                                                                 (const C*)h->d_RX, (const C*)L.d_V, c, yt, y);
         CU(cudaGetLastError());
     }

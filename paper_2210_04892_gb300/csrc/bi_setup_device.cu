@@ -731,15 +731,19 @@ __global__ void k_near_fill(int nblk, const int* __restrict__ blk_box, const int
 
 // Leaf patterns, one thread per (tree RWG n, direction kk):
 //   F_n(k)  = int f_n exp(+jk khat.(r - c)) ds,  RX_n(k) = int (n x f_n) exp(-jk khat.(r - c)) ds,
-// theta and phi components, c = center of the RWG's leaf box.
+// theta and phi components, c = center of the RWG's leaf box.  f_n is real, so the pattern at
+// the antipode -khat is the conjugate vector, and theta-hat(-khat) = theta-hat(khat),
+// phi-hat(-khat) = -phi-hat(khat): only the first K/2 directions (theta-major: one of each
+// antipodal pair) are stored, [N][K/2][2].
 template <typename T>
 __global__ void k_patterns(int N, int K, int nph, const double* __restrict__ theta, const int* __restrict__ leaf_of,
                            const double* __restrict__ centers, const int* __restrict__ rwg_t, const int* __restrict__ rwg_l,
                            const double* __restrict__ rwg_len, const double* __restrict__ tri, const double* __restrict__ nrm,
                            const double* __restrict__ area, double k, T* __restrict__ F, T* __restrict__ RX) {
+    const int Kh = K / 2;
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)N * K) return;
-    int n = (int)(idx / K), kk = (int)(idx % K);
+    if (idx >= (int64_t)N * Kh) return;
+    int n = (int)(idx / Kh), kk = (int)(idx % Kh);
     int it = kk / nph, jp = kk % nph;
     double th = theta[it], ph = 2.0 * kPiD * jp / nph;
     double st, ct, sp, cp;
@@ -1174,10 +1178,10 @@ void bi_fill_patterns(bi_handle_s* h) {
     if (h->leaf < 2) return;
     const level_t& LF = h->lev[h->leaf];
     double* d_theta = h->upload(LF.theta);
-    size_t nel = (size_t)h->N * LF.K * 2;
+    size_t nel = (size_t)h->N * (LF.K / 2) * 2;
     h->d_F = h->alloc(nel * h->csize);
     h->d_RX = h->alloc(nel * h->csize);
-    int64_t tot = (int64_t)h->N * LF.K;
+    int64_t tot = (int64_t)h->N * (LF.K / 2);
     int th = 256;
     int64_t nb = (tot + th - 1) / th;
     if (h->prec == 0)
