@@ -225,6 +225,13 @@ void bi_server_destroy(bi_server s);
 /* Text of the last error on h (or of the last failed bi_setup when h is NULL). */
 const char* bi_last_error(bi_handle h);
 
+/* Device status of h (implementation health, no counterpart in the paper): synchronises
+ * the handle's stream, then returns BI_ERR_TIMEOUT if a product kernel gave up a bounded
+ * wait on one of its bulk copies since the last check (the products enqueued before then
+ * are invalid), else BI_OK; the status is cleared by the call.  bi_matvec_host and
+ * bi_solve make the same check before they return. */
+int bi_device_status(bi_handle h);
+
 /* Release every device buffer of h.  NULL is ignored. */
 void bi_destroy(bi_handle h);
 

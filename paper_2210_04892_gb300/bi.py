@@ -27,7 +27,7 @@ _NAMES = {0: "BI_OK", -1: "BI_ERR_ARG", -2: "BI_ERR_MESH", -3: "BI_ERR_OOM", -4:
 
 # entry points declared in include/bi.h
 EXPORTS = ["bi_default_params", "bi_setup", "bi_num_unknowns", "bi_rwg_edges", "bi_get_info", "bi_matvec",
-           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_profile_stages", "bi_stage_name", "bi_last_error",
+           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_profile_stages", "bi_stage_name", "bi_last_error", "bi_device_status",
            "bi_destroy", "bi_server_default_params", "bi_server_create", "bi_submit", "bi_poll", "bi_result",
            "bi_release", "bi_server_last_error", "bi_server_destroy"]
 
@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH):
     L.bi_stage_name.restype = ctypes.c_char_p
     L.bi_last_error.argtypes = [vp]
     L.bi_last_error.restype = ctypes.c_char_p
+    L.bi_device_status.argtypes = [vp]
     L.bi_destroy.argtypes = [vp]
     L.bi_destroy.restype = None
     L.bi_server_default_params.argtypes = [ctypes.POINTER(ServerParams)]
@@ -239,6 +240,10 @@ class Operator:
         _check(load().bi_profile_stages(self.h, x.data_ptr(), y.data_ptr(), x.shape[0], int(reps), ms.ctypes.data),
                self.h)
         return {load().bi_stage_name(i).decode(): float(ms[i]) for i in range(8)}
+
+    def status(self):
+        """Synchronise and raise BIError if a product kernel gave up a bounded device wait."""
+        _check(load().bi_device_status(self.h), self.h)
 
     def debug_buffer(self, what, level=0):
         """Copy of an internal device buffer (diagnostics; see bi_debug_copy in bi.h)."""

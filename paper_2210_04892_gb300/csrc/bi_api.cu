@@ -84,6 +84,8 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
     h->use_graphs = !(env && env[0] == '1');
     const char* env2 = std::getenv("BI_TWO_PASS");
     h->use_fast = !(env2 && env2[0] == '1');
+    const char* env3 = std::getenv("BI_LEAF_BULK");
+    h->use_leaf_bulk = !(env3 && env3[0] == '0');
     try {
         bi_build_rwg(h, verts, nv, tris, nt);
         h->nun = h->nX * h->N;
@@ -172,6 +174,25 @@ static int guarded(bi_handle h, F&& f) {
     }
 }
 
+// Read and clear the device status word (the caller has synchronised the work it checks).
+int bi_take_device_status(bi_handle_s* h) {
+    if (!h->d_status) return BI_OK;
+    int st = 0;
+    CU(cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st == 0) return BI_OK;
+    CU(cudaMemset(h->d_status, 0, sizeof(int)));
+    h->err = "a bounded wait on a bulk copy gave up in a product kernel (results of that product are invalid)";
+    return BI_ERR_TIMEOUT;
+}
+
+extern "C" int bi_device_status(bi_handle h) {
+    if (!h) return BI_ERR_ARG;
+    return guarded(h, [&] {
+        CU(cudaStreamSynchronize(h->stream));
+        return bi_take_device_status(h);
+    });
+}
+
 extern "C" int bi_matvec(bi_handle h, const void* x, void* y, int nrhs) {
     if (!h) return BI_ERR_ARG;
     if (!x || !y || nrhs < 1 || nrhs > h->max_rhs) {
@@ -203,7 +224,7 @@ extern "C" int bi_matvec_host(bi_handle h, const void* x, void* y, int nrhs) {
         bi_matvec_launch(h, h->d_sx, h->d_sy, nrhs, h->stream);
         CU(cudaMemcpyAsync(y, h->d_sy, bytes, cudaMemcpyDeviceToHost, h->stream));
         CU(cudaStreamSynchronize(h->stream));
-        return (int)BI_OK;
+        return bi_take_device_status(h);
     });
 }
 

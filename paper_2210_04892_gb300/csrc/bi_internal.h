@@ -101,6 +101,8 @@ struct bi_handle_s {
     cudaEvent_t ev_tfork[BI_MAXLEV] = {}, ev_tjoin[BI_MAXLEV] = {};
     bool use_graphs = true;
     bool use_fast = true;               // fused kernels (false: two-pass reference kernels)
+    bool use_leaf_bulk = true;          // bulk-copy pipelines for leaf aggregation and receive
+    int* d_status = nullptr;            // device status word (0: healthy; see bi_tma.cuh)
     int near_ncol_max = 0;
     int near_nwork = 0;                 // work items of the streaming near kernel (box, first row)
     int* d_near_work = nullptr;
@@ -130,6 +132,7 @@ struct bi_handle_s {
     int* d_perm = nullptr;
     int* d_leaf_start = nullptr;
     int* d_leaf_of = nullptr;           // leaf box of each tree RWG
+    int* d_leaf_order = nullptr;        // leaf boxes by decreasing RWG count (launch order of per-box CTAs)
     int* d_near_ptr = nullptr;
     int* d_near_src = nullptr;
     int64_t* d_near_blk = nullptr;
@@ -195,6 +198,9 @@ void bi_matvec_launch(bi_handle_s* h, const void* x, void* y, int nrhs, cudaStre
 void bi_rhs_launch(bi_handle_s* h, const double* khat, const double* phat, int nrhs, void* b);
 void bi_profile_impl(bi_handle_s* h, const void* x, void* y, int nrhs, int reps, double* ms);
 const char* bi_stage_name_impl(int i);
+bool bi_leaf_aggregate_bulk(bi_handle_s* h, const void* x, int R, cudaStream_t s);
+bool bi_leaf_receive_bulk(bi_handle_s* h, void* y, int R, cudaStream_t s);
+int bi_take_device_status(bi_handle_s* h);
 size_t bi_farfield_scratch_bytes(const bi_handle_s* h, int nrhs, int ndir);
 void bi_farfield_launch(bi_handle_s* h, const void* x, int nrhs, const double* dirs, int ndir, void* F, double* part,
                         cudaStream_t s);

@@ -23,73 +23,10 @@
 #include <algorithm>
 #include <cstdio>
 
+#include "bi_cpx.cuh"
 #include "bi_internal.h"
 
 namespace {
-
-template <typename T>
-struct cpx {
-    T x, y;
-};
-template <typename T>
-__device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
-    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
-}
-template <typename T>
-__device__ __forceinline__ cpx<T> cmulc(cpx<T> a, cpx<T> b) {  // conj(a) * b
-    return {a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x};
-}
-template <typename T>
-__device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) {
-    return {a.x + b.x, a.y + b.y};
-}
-template <typename T>
-__device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) {
-    return {a.x - b.x, a.y - b.y};
-}
-template <typename T>
-__device__ __forceinline__ cpx<T> cscale(cpx<T> a, T s) {
-    return {a.x * s, a.y * s};
-}
-template <typename T>
-__device__ __forceinline__ void cfma(cpx<T>& acc, cpx<T> a, cpx<T> b) {
-    acc.x = fma(a.x, b.x, acc.x);
-    acc.x = fma(-a.y, b.y, acc.x);
-    acc.y = fma(a.x, b.y, acc.y);
-    acc.y = fma(a.y, b.x, acc.y);
-}
-template <typename T>
-__device__ __forceinline__ cpx<T> czero() {
-    return {T(0), T(0)};
-}
-
-// Antipodal pairs of directions: (it, jp) <-> (nth - 1 - it, jp + nph/2 mod nph).  The leaf
-// pattern arrays hold the first K/2 directions of the theta-major numbering, one of each pair;
-// a stored (theta, phi) pair (a, b) reads (conj a, -conj b) at the antipode (real basis
-// functions; the antipodal map keeps theta-hat and reverses phi-hat).
-__device__ __forceinline__ int antipode(int kk, int K, int nph) {
-    const int it = kk / nph, jp = kk - it * nph, jm = jp + (nph >> 1);
-    return (K / nph - 1 - it) * nph + (jm >= nph ? jm - nph : jm);
-}
-template <typename T>
-__device__ __forceinline__ cpx<T> cconj(cpx<T> a) {
-    return {a.x, -a.y};
-}
-template <typename T>
-__device__ __forceinline__ cpx<T> cnegconj(cpx<T> a) {
-    return {-a.x, a.y};
-}
-// One direction's receive terms (R = conj(F), khat x V = (-V_phi, V_theta)):
-//   J += R.V - RX.(khat x V),  M += -R.(khat x V) - RX.V
-template <typename T, int MODE>
-__device__ __forceinline__ void recv_terms(cpx<T> Ft, cpx<T> Fp, cpx<T> Xt, cpx<T> Xp, cpx<T> Vt, cpx<T> Vp, cpx<T>& sJ,
-                                           cpx<T>& sM) {
-    sJ = cadd(sJ, csub(cadd(cmulc(Ft, Vt), cmulc(Fp, Vp)), csub(cmul(Xp, Vt), cmul(Xt, Vp))));
-    if (MODE == 0) {
-        const cpx<T> t = csub(cmulc(Ft, Vp), cmulc(Fp, Vt));
-        sM = cadd(sM, csub(t, cadd(cmul(Xt, Vt), cmul(Xp, Vp))));
-    }
-}
 
 // ------------------------------------------------------------------ permutations
 template <typename T>
@@ -439,26 +376,6 @@ __global__ void k_receive(int N, int K, int nph, int R, const int* __restrict__ 
 // is staged in shared memory, then each warp streams whole rows of the row-major segment:
 // lane j reads columns j, j+32, ... (coalesced 16-byte entries), a shuffle reduction gives the
 // row.  RT right-hand sides per pass.
-__device__ __forceinline__ void load_pair(const cpx<float>* p, cpx<float>& A, cpx<float>& B) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    A = {v.x, v.y};
-    B = {v.z, v.w};
-}
-__device__ __forceinline__ void load_pair(const cpx<double>* p, cpx<double>& A, cpx<double>& B) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-    A = {a.x, a.y};
-    B = {b.x, b.y};
-}
-template <typename T>
-__device__ __forceinline__ cpx<T> warp_sum(cpx<T> v) {
-    for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-    }
-    return v;
-}
-
 template <typename T, int MODE, int RT>
 __global__ void __launch_bounds__(256) k_near_stream(int N, int R, int nun, const int* __restrict__ perm,
                                                      const int2* __restrict__ work,
@@ -1430,7 +1347,8 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
         return;
     }
     const int lf = h->leaf;
-    if (R >= 8) {
+    if (R < 8 && bi_leaf_aggregate_bulk(h, x, R, s)) {
+    } else if (R >= 8) {
         level_t& L = h->lev[lf];
         dim3 g(L.nbox, nblk(L.K / 2, 32));
         size_t smem = ((size_t)h->max_leaf_count * 32 * 2 + (size_t)h->max_leaf_count * 2 * R) * sizeof(C);
@@ -1507,6 +1425,7 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
     if (ev) CU(cudaEventRecord(ev[5], s));
     else CU(cudaStreamWaitEvent(s, h->ev_join, 0));
     if (R >= 8 && launch_receive_tile<T>(h, x, y, R, s)) {
+    } else if (R < 8 && bi_leaf_receive_bulk(h, y, R, s)) {
     } else {
         level_t& L = h->lev[lf];
         const double pi = 3.14159265358979323846;

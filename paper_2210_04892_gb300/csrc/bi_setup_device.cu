@@ -1288,6 +1288,18 @@ void bi_fill_translations(bi_handle_s* h) {
 
 void bi_alloc_work(bi_handle_s* h) {
     const int R = h->max_rhs;
+    h->d_status = (int*)h->alloc(sizeof(int));
+    CU(cudaMemset(h->d_status, 0, sizeof(int)));
+    {
+        // largest leaf boxes first: per-box CTAs then finish close together
+        const int nb = (int)h->leaf_start.size() - 1;
+        std::vector<int> order(std::max(nb, 0));
+        for (int b = 0; b < nb; ++b) order[b] = b;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return h->leaf_start[a + 1] - h->leaf_start[a] > h->leaf_start[b + 1] - h->leaf_start[b];
+        });
+        h->d_leaf_order = h->upload(order);
+    }
     size_t vec = (size_t)h->N * h->nX * R * h->csize;
     h->d_xt = h->alloc(vec);
     h->d_yt = h->alloc(vec);

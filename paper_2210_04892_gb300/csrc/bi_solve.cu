@@ -449,12 +449,12 @@ struct gmres_ctx_impl {
         if (h->prec == 0) k_cvt_to<double><<<nb(nv, th), th, 0, s>>>(nv, x64, (double*)xout);
         else k_cvt_to<float><<<nb(nv, th), th, 0, s>>>(nv, x64, (float*)xout);
         CU(cudaStreamSynchronize(s));
-        int status = BI_OK;
+        int status = bi_take_device_status(h);
         for (int r = 0; r < R; ++r) {
             double rel = bnorm[r] > 0 ? rr[r] / bnorm[r] : 0.0;
             if (iters) iters[r] = its[r];
             if (relres) relres[r] = rel;
-            if (rel > tol * 1.0001 + 1e-12) status = BI_ERR_NOT_CONVERGED;
+            if (status == BI_OK && rel > tol * 1.0001 + 1e-12) status = BI_ERR_NOT_CONVERGED;
         }
         finished = true;
         return status;
