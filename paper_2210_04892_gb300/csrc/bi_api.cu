@@ -114,6 +114,7 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
         bi_fill_near(h);
         bi_fill_patterns(h);
         bi_fill_translations(h);
+        bi_build_translate_lists(h);
         bi_alloc_work(h);
         CU(cudaStreamSynchronize(h->stream));
     } catch (const bi_error& e) {

@@ -59,6 +59,13 @@ struct level_t {
     void* d_U = nullptr;                // outgoing patterns [nbox][K][E]
     void* d_V = nullptr;                // incoming patterns [nbox][K][E]
     int64_t n_inter = 0;
+    // parent-centred interaction lists (translation level l, parents at l - 1): per parent its
+    // children range, and per source box the offset codes to each child (0xFFFF: near or none)
+    int tp_np = 0;
+    int* d_tp_cptr = nullptr;           // [np + 1] children of each parent (level-l indices)
+    int* d_tp_ptr = nullptr;            // [np + 1] source entries of each parent
+    int* d_tp_src = nullptr;            // [entries] source box
+    void* d_tp_code = nullptr;          // [entries][8] uint16 offset code per child slot
 };
 
 // Lagrange interpolation between level l+1 (child) and level l (parent).
@@ -81,6 +88,13 @@ struct interp_t {
     int *d_tth_ptr = nullptr, *d_tth_dst = nullptr, *d_tth_flip = nullptr, *d_tph_ptr = nullptr, *d_tph_dst = nullptr;
     void *d_tth_w = nullptr, *d_tph_w = nullptr;
     void* d_tmp = nullptr;              // per child box: [nbox_child][nth_parent][nph_child][E]
+    // packed taps (index, weight in the handle precision) for the unrolled kernels:
+    //   th_tap [nth_parent][p_th]: code = child row * 2 + flip, weight with the flip sign folded
+    //   ph_tap [nph_parent][p_ph]: child column
+    //   tth_pad [nth_child][pt_th]: code = parent row * 2 + flip (zero-padded lists)
+    //   tph_pad [nph_child][pt_ph]: parent column (zero-padded lists)
+    int pt_th = 0, pt_ph = 0;
+    void *d_th_tap = nullptr, *d_ph_tap = nullptr, *d_tth_pad = nullptr, *d_tph_pad = nullptr;
 };
 
 struct bi_handle_s {
@@ -199,6 +213,11 @@ void bi_rhs_launch(bi_handle_s* h, const double* khat, const double* phat, int n
 void bi_profile_impl(bi_handle_s* h, const void* x, void* y, int nrhs, int reps, double* ms);
 const char* bi_stage_name_impl(int i);
 bool bi_leaf_aggregate_bulk(bi_handle_s* h, const void* x, int R, cudaStream_t s);
+bool bi_interp_level(bi_handle_s* h, int l, int E, cudaStream_t s);
+bool bi_anterp_level(bi_handle_s* h, int l, int E, cudaStream_t s);
+void bi_upload_taps(bi_handle_s* h);
+bool bi_translate_level(bi_handle_s* h, int l, int E, cudaStream_t s);
+void bi_build_translate_lists(bi_handle_s* h);
 bool bi_leaf_receive_bulk(bi_handle_s* h, void* y, int R, cudaStream_t s);
 int bi_take_device_status(bi_handle_s* h);
 size_t bi_farfield_scratch_bytes(const bi_handle_s* h, int nrhs, int ndir);

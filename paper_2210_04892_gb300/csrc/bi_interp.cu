@@ -1,0 +1,430 @@
+// Interpolation (upward pass) and anterpolation (downward pass) between octree levels of
+// the multilevel product, with compile-time tap counts.
+//
+// Upward, for a parent box p with children c (level l+1 -> l):
+//   U_p(k) = sum_c exp(+jk khat.(c_c - c_p)) [Phi Theta U_c](k)
+// Theta: local Lagrange interpolation in theta along great circles (a tap across a pole reads
+// the column half a turn away with both components negated); Phi: local Lagrange
+// interpolation in phi on the periodic grid.  One CTA per (parent, block of parent theta
+// rows) computes the theta pass of every child for those rows into shared memory, then each
+// thread sums one parent sample over the children: no atomics and no zeroing of U_p.
+//
+// Downward (anterpolation, the transpose), for each child c of p:
+//   V_c += Theta^T Phi^T [ conj(exp(+jk khat.(c_c - c_p))) V_p ]
+// One CTA per child: the shifted parent field, then the transposed phi pass for every parent
+// row, then the transposed theta pass, each from shared memory with zero-padded tap lists.
+//
+// With one right-hand side (E = 2) each thread carries both components of a sample as one
+// 16-byte vector; the general kernels handle any E one component at a time.
+#include <algorithm>
+#include <vector>
+
+#include "bi_cpx.cuh"
+#include "bi_internal.h"
+
+namespace {
+
+template <typename T>
+struct tap {
+    int c;  // index code
+    T w;    // weight
+};
+
+// o / d for 0 <= o < 2^22 via a float reciprocal, corrected to the exact quotient
+__device__ __forceinline__ int fdiv(int o, int d, float inv) {
+    int q = __float2int_rz((float)o * inv);
+    if (q * d > o) --q;
+    else if ((q + 1) * d <= o) ++q;
+    return q;
+}
+
+template <typename T>
+__device__ __forceinline__ cpx<T> ldg_c(const cpx<T>* p) {
+    cpx<T> v;
+    v.x = __ldg(&p->x);
+    v.y = __ldg(&p->y);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ void sts_pair(cpx<T>* p, cpx<T> a, cpx<T> b) {
+    p[0] = a;
+    p[1] = b;
+}
+template <typename T>
+__device__ __forceinline__ void fma_pair(T w, cpx<T> a, cpx<T> b, cpx<T>& s, cpx<T>& t) {
+    s.x = fma(w, a.x, s.x);
+    s.y = fma(w, a.y, s.y);
+    t.x = fma(w, b.x, t.x);
+    t.y = fma(w, b.y, t.y);
+}
+
+// ---------------------------------------------------------------- general E
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_interp_pb(int nthc, int nphc, int nthp, int nphp, int E, int RB,
+                                                   const int* __restrict__ child_ptr, const int* __restrict__ octant,
+                                                   const tap<T>* __restrict__ th_tap, const tap<T>* __restrict__ ph_tap,
+                                                   const cpx<T>* __restrict__ shift, const cpx<T>* __restrict__ Uc,
+                                                   cpx<T>* __restrict__ Up) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int p = blockIdx.x, ip0 = blockIdx.y * RB, nr = min(RB, nthp - ip0);
+    const int c0 = child_ptr[p], nc = child_ptr[p + 1] - c0;
+    const int W = nphc * E, Wp = nphp * E, Kc = nthc * nphc, Kp = nthp * nphp, half = nphc / 2;
+    tap<T>* tt = reinterpret_cast<tap<T>*>(smem_raw);  // [RB][P]
+    tap<T>* pt = tt + RB * P;                          // [nphp][P]
+    int* oc = reinterpret_cast<int*>(pt + nphp * P);   // [8]
+    cpx<T>* s2 = reinterpret_cast<cpx<T>*>(oc + 8);    // [nc][nr][W]
+    for (int i = threadIdx.x; i < nr * P; i += blockDim.x) tt[i] = th_tap[ip0 * P + i];
+    for (int i = threadIdx.x; i < nphp * P; i += blockDim.x) pt[i] = ph_tap[i];
+    if (threadIdx.x < nc) oc[threadIdx.x] = octant[c0 + threadIdx.x];
+    __syncthreads();
+    const float invE = 1.0f / E, invW = 1.0f / W, invRW = 1.0f / (nr * W), invWp = 1.0f / Wp;
+    for (int o = threadIdx.x; o < nc * nr * W; o += blockDim.x) {
+        const int c = fdiv(o, nr * W, invRW);
+        const int rem = o - c * nr * W;
+        const int ipl = fdiv(rem, W, invW);
+        const int col = rem - ipl * W;
+        const int jc = fdiv(col, E, invE), e = col - jc * E;
+        const int jf = jc + half < nphc ? jc + half : jc + half - nphc;
+        const int off0 = col, off1 = jf * E + e;
+        const cpx<T>* u = Uc + (int64_t)(c0 + c) * Kc * E;
+        cpx<T> a = czero<T>();
+#pragma unroll
+        for (int t = 0; t < P; ++t) {
+            const tap<T> q = tt[ipl * P + t];
+            const cpx<T> v = ldg_c(u + (q.c >> 1) * W + ((q.c & 1) ? off1 : off0));
+            a.x = fma(q.w, v.x, a.x);
+            a.y = fma(q.w, v.y, a.y);
+        }
+        s2[o] = a;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < nr * Wp; o += blockDim.x) {
+        const int ipl = fdiv(o, Wp, invWp);
+        const int colp = o - ipl * Wp;
+        const int jp = fdiv(colp, E, invE), e = colp - jp * E;
+        const int ip = ip0 + ipl;
+        cpx<T> acc = czero<T>();
+        for (int c = 0; c < nc; ++c) {
+            const cpx<T>* row = s2 + ((int64_t)c * nr + ipl) * W + e;
+            cpx<T> a = czero<T>();
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const tap<T> tq = pt[jp * P + q];
+                const cpx<T> v = row[tq.c * E];
+                a.x = fma(tq.w, v.x, a.x);
+                a.y = fma(tq.w, v.y, a.y);
+            }
+            cfma(acc, ldg_c(shift + (int64_t)oc[c] * Kp + ip * nphp + jp), a);
+        }
+        Up[((int64_t)p * Kp + ip * nphp) * E + colp] = acc;
+    }
+}
+
+template <typename T, int PT, int PP>
+__global__ void __launch_bounds__(256) k_anterp_cb(int nthc, int nphc, int nthp, int nphp, int E,
+                                                   const int* __restrict__ parent, const int* __restrict__ octant,
+                                                   const tap<T>* __restrict__ tth_pad, const tap<T>* __restrict__ tph_pad,
+                                                   const cpx<T>* __restrict__ shift, const cpx<T>* __restrict__ Vp,
+                                                   cpx<T>* __restrict__ Vc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int c = blockIdx.x;
+    const int pb = parent[c], oct = octant[c];
+    const int W = nphc * E, Wp = nphp * E, Kc = nthc * nphc, Kp = nthp * nphp, half = nphc / 2;
+    tap<T>* tt = reinterpret_cast<tap<T>*>(smem_raw);       // [nthc][PT]
+    tap<T>* pt = tt + nthc * PT;                             // [nphc][PP]
+    cpx<T>* S = reinterpret_cast<cpx<T>*>(pt + nphc * PP);  // [Kp][E] conj(shift) V_p
+    cpx<T>* t1 = S + (int64_t)Kp * E;                        // [nthp][W] transposed phi pass
+    for (int i = threadIdx.x; i < nthc * PT; i += blockDim.x) tt[i] = tth_pad[i];
+    for (int i = threadIdx.x; i < nphc * PP; i += blockDim.x) pt[i] = tph_pad[i];
+    const cpx<T>* sh = shift + (int64_t)oct * Kp;
+    const cpx<T>* vp = Vp + (int64_t)pb * Kp * E;
+    const float invE = 1.0f / E, invW = 1.0f / W;
+    for (int i = threadIdx.x; i < Kp * E; i += blockDim.x) S[i] = cmulc(ldg_c(sh + fdiv(i, E, invE)), ldg_c(vp + i));
+    __syncthreads();
+    // t1[ip][jc][e] = sum over parent columns jp that interpolate child column jc
+    for (int o = threadIdx.x; o < nthp * W; o += blockDim.x) {
+        const int ip = fdiv(o, W, invW);
+        const int col = o - ip * W;
+        const int jc = fdiv(col, E, invE), e = col - jc * E;
+        const cpx<T>* row = S + (int64_t)ip * Wp + e;
+        cpx<T> a = czero<T>();
+#pragma unroll
+        for (int q = 0; q < PP; ++q) {
+            const tap<T> tq = pt[jc * PP + q];
+            const cpx<T> v = row[tq.c * E];
+            a.x = fma(tq.w, v.x, a.x);
+            a.y = fma(tq.w, v.y, a.y);
+        }
+        t1[o] = a;
+    }
+    __syncthreads();
+    // V_c[ic][col] += sum over parent rows ip that interpolate child row ic (pole taps read the
+    // column half a turn away, sign folded into the weight)
+    cpx<T>* vc = Vc + (int64_t)c * Kc * E;
+    for (int o = threadIdx.x; o < nthc * W; o += blockDim.x) {
+        const int ic = fdiv(o, W, invW);
+        const int col = o - ic * W;
+        const int jc = fdiv(col, E, invE), e = col - jc * E;
+        const int jf = jc + half < nphc ? jc + half : jc + half - nphc;
+        const int off0 = col, off1 = jf * E + e;
+        cpx<T> a = czero<T>();
+#pragma unroll
+        for (int q = 0; q < PT; ++q) {
+            const tap<T> tq = tt[ic * PT + q];
+            const cpx<T> v = t1[(tq.c >> 1) * W + ((tq.c & 1) ? off1 : off0)];
+            a.x = fma(tq.w, v.x, a.x);
+            a.y = fma(tq.w, v.y, a.y);
+        }
+        vc[o] = cadd(vc[o], a);
+    }
+}
+
+// ---------------------------------------------------------------- one right-hand side (E = 2)
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_interp_pb1(int nthc, int nphc, int nthp, int nphp, int RB,
+                                                    const int* __restrict__ child_ptr, const int* __restrict__ octant,
+                                                    const tap<T>* __restrict__ th_tap, const tap<T>* __restrict__ ph_tap,
+                                                    const cpx<T>* __restrict__ shift, const cpx<T>* __restrict__ Uc,
+                                                    cpx<T>* __restrict__ Up) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int p = blockIdx.x, ip0 = blockIdx.y * RB, nr = min(RB, nthp - ip0);
+    const int c0 = child_ptr[p], nc = child_ptr[p + 1] - c0;
+    const int Kc = nthc * nphc, Kp = nthp * nphp, half = nphc / 2;
+    tap<T>* tt = reinterpret_cast<tap<T>*>(smem_raw);  // [RB][P]
+    tap<T>* pt = tt + RB * P;                          // [nphp][P]
+    int* oc = reinterpret_cast<int*>(pt + nphp * P);   // [8]
+    cpx<T>* s2 = reinterpret_cast<cpx<T>*>(oc + 8);    // [nc][nr][nphc][2]
+    for (int i = threadIdx.x; i < nr * P; i += blockDim.x) tt[i] = th_tap[ip0 * P + i];
+    for (int i = threadIdx.x; i < nphp * P; i += blockDim.x) pt[i] = ph_tap[i];
+    if (threadIdx.x < nc) oc[threadIdx.x] = octant[c0 + threadIdx.x];
+    __syncthreads();
+    // theta pass: one (child, row, column) per thread, both components
+    const float invC = 1.0f / nphc, invRC = 1.0f / (nr * nphc);
+    for (int o = threadIdx.x; o < nc * nr * nphc; o += blockDim.x) {
+        const int c = fdiv(o, nr * nphc, invRC);
+        const int rem = o - c * nr * nphc;
+        const int ipl = fdiv(rem, nphc, invC);
+        const int jc = rem - ipl * nphc;
+        const int jf = jc + half < nphc ? jc + half : jc + half - nphc;
+        const cpx<T>* u = Uc + (int64_t)(c0 + c) * Kc * 2;
+        cpx<T> a = czero<T>(), b = czero<T>();
+#pragma unroll
+        for (int t = 0; t < P; ++t) {
+            const tap<T> q = tt[ipl * P + t];
+            cpx<T> va, vb;
+            load_pair(u + ((q.c >> 1) * nphc + ((q.c & 1) ? jf : jc)) * 2, va, vb);
+            fma_pair(q.w, va, vb, a, b);
+        }
+        sts_pair(s2 + 2 * o, a, b);
+    }
+    __syncthreads();
+    // phi pass and sum over children: one parent sample per thread, its taps in registers for
+    // every child
+    for (int o = threadIdx.x; o < nr * nphp; o += blockDim.x) {
+        const int ipl = o / nphp;
+        const int jp = o - ipl * nphp;
+        const int ip = ip0 + ipl;
+        int src[P];
+        T w[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const tap<T> tq = pt[jp * P + q];
+            src[q] = tq.c;
+            w[q] = tq.w;
+        }
+        cpx<T> A = czero<T>(), B = czero<T>();
+        for (int c = 0; c < nc; ++c) {
+            const cpx<T>* row = s2 + (((int64_t)c * nr + ipl) * nphc) * 2;
+            cpx<T> a = czero<T>(), b = czero<T>();
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                cpx<T> va, vb;
+                lds_pair(row + 2 * src[q], va, vb);
+                fma_pair(w[q], va, vb, a, b);
+            }
+            const cpx<T> sh = ldg_c(shift + (int64_t)oc[c] * Kp + ip * nphp + jp);
+            cfma(A, sh, a);
+            cfma(B, sh, b);
+        }
+        cpx<T>* out = Up + ((int64_t)p * Kp + ip * nphp + jp) * 2;
+        out[0] = A;
+        out[1] = B;
+    }
+}
+
+template <typename T, int PT>
+__global__ void __launch_bounds__(256) k_anterp_cb1(int nthc, int nphc, int nthp, int nphp,
+                                                    const int* __restrict__ parent, const int* __restrict__ octant,
+                                                    const tap<T>* __restrict__ tth_pad, const tap<T>* __restrict__ tph_pad,
+                                                    const cpx<T>* __restrict__ shift, const cpx<T>* __restrict__ Vp,
+                                                    cpx<T>* __restrict__ Vc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int c = blockIdx.x;
+    const int pb = parent[c], oct = octant[c];
+    const int Kc = nthc * nphc, Kp = nthp * nphp, half = nphc / 2;
+    tap<T>* tt = reinterpret_cast<tap<T>*>(smem_raw);       // [nthc][PT]
+    tap<T>* pt = tt + nthc * PT;                             // [nphc][PT]
+    cpx<T>* S = reinterpret_cast<cpx<T>*>(pt + nphc * PT);  // [Kp][2] conj(shift) V_p
+    cpx<T>* t1 = S + (int64_t)Kp * 2;                        // [nthp][nphc][2]
+    for (int i = threadIdx.x; i < nthc * PT; i += blockDim.x) tt[i] = tth_pad[i];
+    for (int i = threadIdx.x; i < nphc * PT; i += blockDim.x) pt[i] = tph_pad[i];
+    const cpx<T>* sh = shift + (int64_t)oct * Kp;
+    const cpx<T>* vp = Vp + (int64_t)pb * Kp * 2;
+    for (int i = threadIdx.x; i < Kp; i += blockDim.x) {
+        cpx<T> a, b;
+        load_pair(vp + 2 * i, a, b);
+        const cpx<T> s = ldg_c(sh + i);
+        sts_pair(S + 2 * i, cmulc(s, a), cmulc(s, b));
+    }
+    __syncthreads();
+    // transposed phi pass: one (parent row, child column) per thread
+    for (int o = threadIdx.x; o < nphc * nthp; o += blockDim.x) {
+        const int ip = o / nphc;
+        const int jc = o - ip * nphc;
+        const cpx<T>* row = S + (int64_t)ip * nphp * 2;
+        cpx<T> a = czero<T>(), b = czero<T>();
+#pragma unroll
+        for (int q = 0; q < PT; ++q) {
+            const tap<T> tq = pt[jc * PT + q];
+            cpx<T> va, vb;
+            lds_pair(row + 2 * tq.c, va, vb);
+            fma_pair(tq.w, va, vb, a, b);
+        }
+        sts_pair(t1 + 2 * o, a, b);
+    }
+    __syncthreads();
+    // transposed theta pass: one child sample per thread (taps of its row shared by the warp)
+    cpx<T>* vc = Vc + (int64_t)c * Kc * 2;
+    for (int o = threadIdx.x; o < Kc; o += blockDim.x) {
+        const int ic = o / nphc;
+        const int jc = o - ic * nphc;
+        const int jf = jc + half < nphc ? jc + half : jc + half - nphc;
+        cpx<T> a = czero<T>(), b = czero<T>();
+#pragma unroll
+        for (int q = 0; q < PT; ++q) {
+            const tap<T> tq = tt[ic * PT + q];
+            cpx<T> va, vb;
+            lds_pair(t1 + ((tq.c >> 1) * nphc + ((tq.c & 1) ? jf : jc)) * 2, va, vb);
+            fma_pair(tq.w, va, vb, a, b);
+        }
+        cpx<T> ga, gb;
+        load_pair(vc + 2 * o, ga, gb);
+        sts_pair(vc + 2 * o, cadd(ga, a), cadd(gb, b));
+    }
+}
+
+template <typename T>
+void upload_taps_t(bi_handle_s* h) {
+    for (int l = 2; l + 1 <= h->leaf; ++l) {
+        interp_t& I = h->itp[l];
+        const level_t& C = h->lev[l + 1];
+        std::vector<tap<T>> th(I.th_src.size()), ph(I.ph_src.size());
+        for (size_t i = 0; i < th.size(); ++i)
+            th[i] = {I.th_src[i] * 2 + I.th_flip[i], (T)(I.th_flip[i] ? -I.th_w[i] : I.th_w[i])};
+        for (size_t i = 0; i < ph.size(); ++i) ph[i] = {I.ph_src[i], (T)I.ph_w[i]};
+        int mt = 0, mp = 0;
+        for (int i = 0; i < C.nth; ++i) mt = std::max(mt, I.tth_ptr[i + 1] - I.tth_ptr[i]);
+        for (int j = 0; j < C.nph; ++j) mp = std::max(mp, I.tph_ptr[j + 1] - I.tph_ptr[j]);
+        // one padded width for both lists (the kernels are instantiated for 16 and 24)
+        const int m = std::max(mt, mp);
+        I.pt_th = I.pt_ph = m <= 16 ? 16 : m <= 24 ? 24 : m;
+        std::vector<tap<T>> tth((size_t)C.nth * I.pt_th, tap<T>{0, T(0)}), tph((size_t)C.nph * I.pt_ph, tap<T>{0, T(0)});
+        for (int i = 0; i < C.nth; ++i)
+            for (int q = I.tth_ptr[i]; q < I.tth_ptr[i + 1]; ++q)
+                tth[(size_t)i * I.pt_th + (q - I.tth_ptr[i])] = {I.tth_dst[q] * 2 + I.tth_flip[q],
+                                                                 (T)(I.tth_flip[q] ? -I.tth_w[q] : I.tth_w[q])};
+        for (int j = 0; j < C.nph; ++j)
+            for (int q = I.tph_ptr[j]; q < I.tph_ptr[j + 1]; ++q)
+                tph[(size_t)j * I.pt_ph + (q - I.tph_ptr[j])] = {I.tph_dst[q], (T)I.tph_w[q]};
+        I.d_th_tap = h->upload(th);
+        I.d_ph_tap = h->upload(ph);
+        I.d_tth_pad = h->upload(tth);
+        I.d_tph_pad = h->upload(tph);
+    }
+}
+
+template <typename T, int P>
+bool interp_t_p(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    level_t& Pl = h->lev[l];
+    level_t& C = h->lev[l + 1];
+    interp_t& I = h->itp[l];
+    const int W = C.nph * E;
+    // rows per CTA: shared memory for 8 children, and at least ~2 CTAs per SM overall
+    const size_t per_row = (size_t)8 * W * sizeof(cpx<T>);
+    int RB = (int)std::max<size_t>(1, (64 * 1024) / per_row);
+    const int want_blocks = (2 * h->num_sms + Pl.nbox - 1) / Pl.nbox;
+    RB = std::min(RB, std::max(1, (Pl.nth + want_blocks - 1) / want_blocks));
+    RB = std::min(RB, Pl.nth);
+    const size_t smem = (size_t)(RB + Pl.nph) * P * sizeof(tap<T>) + 8 * sizeof(int) + (size_t)RB * per_row;
+    if (smem > 160 * 1024) return false;
+    dim3 g(Pl.nbox, (Pl.nth + RB - 1) / RB);
+    if (E == 2) {
+        auto k1 = k_interp_pb1<T, P>;
+        if (smem > 48 * 1024) CU(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k1<<<g, 256, smem, s>>>(C.nth, C.nph, Pl.nth, Pl.nph, RB, Pl.d_child_ptr, C.d_octant, (const tap<T>*)I.d_th_tap,
+                                (const tap<T>*)I.d_ph_tap, (const cpx<T>*)Pl.d_shift, (const cpx<T>*)C.d_U,
+                                (cpx<T>*)Pl.d_U);
+        CU(cudaGetLastError());
+        return true;
+    }
+    auto kern = k_interp_pb<T, P>;
+    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<g, 256, smem, s>>>(C.nth, C.nph, Pl.nth, Pl.nph, E, RB, Pl.d_child_ptr, C.d_octant, (const tap<T>*)I.d_th_tap,
+                              (const tap<T>*)I.d_ph_tap, (const cpx<T>*)Pl.d_shift, (const cpx<T>*)C.d_U,
+                              (cpx<T>*)Pl.d_U);
+    CU(cudaGetLastError());
+    return true;
+}
+
+template <typename T, int PT, int PP>
+bool anterp_t_p(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    level_t& Pl = h->lev[l];
+    level_t& C = h->lev[l + 1];
+    interp_t& I = h->itp[l];
+    const size_t smem = (size_t)(C.nth * PT + C.nph * PP) * sizeof(tap<T>) +
+                        ((size_t)Pl.K * E + (size_t)Pl.nth * C.nph * E) * sizeof(cpx<T>);
+    if (smem > 160 * 1024) return false;
+    if (E == 2) {
+        auto k1 = k_anterp_cb1<T, PT>;
+        if (smem > 48 * 1024) CU(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k1<<<C.nbox, 256, smem, s>>>(C.nth, C.nph, Pl.nth, Pl.nph, C.d_parent, C.d_octant, (const tap<T>*)I.d_tth_pad,
+                                     (const tap<T>*)I.d_tph_pad, (const cpx<T>*)Pl.d_shift, (const cpx<T>*)Pl.d_V,
+                                     (cpx<T>*)C.d_V);
+        CU(cudaGetLastError());
+        return true;
+    }
+    auto kern = k_anterp_cb<T, PT, PP>;
+    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<C.nbox, 256, smem, s>>>(C.nth, C.nph, Pl.nth, Pl.nph, E, C.d_parent, C.d_octant, (const tap<T>*)I.d_tth_pad,
+                                   (const tap<T>*)I.d_tph_pad, (const cpx<T>*)Pl.d_shift, (const cpx<T>*)Pl.d_V,
+                                   (cpx<T>*)C.d_V);
+    CU(cudaGetLastError());
+    return true;
+}
+
+template <typename T>
+bool anterp_t(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    const interp_t& I = h->itp[l];
+    if (I.pt_th == 16 && I.pt_ph == 16) return anterp_t_p<T, 16, 16>(h, l, E, s);
+    if (I.pt_th == 24 && I.pt_ph == 24) return anterp_t_p<T, 24, 24>(h, l, E, s);
+    return false;
+}
+
+}  // namespace
+
+void bi_upload_taps(bi_handle_s* h) {
+    if (h->prec == 0) upload_taps_t<double>(h);
+    else upload_taps_t<float>(h);
+}
+
+bool bi_interp_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    const interp_t& I = h->itp[l];
+    if (I.p_th != 10 || I.p_ph != 10 || !I.d_th_tap) return false;
+    return h->prec == 0 ? interp_t_p<double, 10>(h, l, E, s) : interp_t_p<float, 10>(h, l, E, s);
+}
+
+bool bi_anterp_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    if (!h->itp[l].d_tth_pad) return false;
+    return h->prec == 0 ? anterp_t<double>(h, l, E, s) : anterp_t<float>(h, l, E, s);
+}

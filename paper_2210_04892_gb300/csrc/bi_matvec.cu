@@ -1381,6 +1381,7 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
     // Translations of level l only need U_l: the finer levels run on their own streams while
     // the upward pass continues, and join before the downward pass adds into V_l.
     auto translate = [&](int l, cudaStream_t st) {
+        if (bi_translate_level(h, l, E, st)) return;
         level_t& L = h->lev[l];
         dim3 g(L.nbox, nblk((int64_t)L.K * E, th));
         k_translate<T><<<g, th, 0, st>>>(L.K, E, L.d_il_ptr, L.d_il_src, L.d_il_off, (const C*)L.d_T, (const C*)L.d_U,
@@ -1398,7 +1399,7 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
     if (lf > 2) fork_translate(lf);
     for (int l = lf - 1; l >= 2; --l) {
         // one CTA per parent only pays off when the level has enough parents to fill the GPU
-        if (!interp_child<T>(h, l, E, s)) launch_interp_two_pass<T>(h, l, E, s);
+        if (!bi_interp_level(h, l, E, s) && !interp_child<T>(h, l, E, s)) launch_interp_two_pass<T>(h, l, E, s);
         if (l > 2) fork_translate(l);
     }
     if (ev) CU(cudaEventRecord(ev[3], s));
@@ -1409,7 +1410,7 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
     if (ev) CU(cudaEventRecord(ev[4], s));
     for (int l = 2; l < lf; ++l) {
         if (!ev) CU(cudaStreamWaitEvent(s, h->ev_tjoin[l + 1], 0));
-        if (anterp_child<T>(h, l, E, s)) continue;
+        if (bi_anterp_level(h, l, E, s) || anterp_child<T>(h, l, E, s)) continue;
         level_t& P = h->lev[l];
         level_t& Cc = h->lev[l + 1];
         interp_t& I = h->itp[l];

@@ -1284,6 +1284,7 @@ void bi_fill_translations(bi_handle_s* h) {
             I.d_tph_w = h->upload(std::vector<float>(I.tph_w.begin(), I.tph_w.end()));
         }
     }
+    bi_upload_taps(h);
 }
 
 void bi_alloc_work(bi_handle_s* h) {

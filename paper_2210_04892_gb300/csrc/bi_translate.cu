@@ -1,0 +1,158 @@
+// Diagonal translations of one level (the M2L step of the multilevel product):
+//   V_b(k) = sum_{s in IL(b)} T[off(b, s)](k) U_s(k)     (quadrature weights folded into T)
+// with IL(b) the children of the neighbours of b's parent that do not touch b.
+//
+// Parent-centred form: one CTA per (parent box p, 32 directions) computes V for every child of
+// p.  The sources of all children of p are the children of p's neighbours; each source
+// pattern U_s(k) is loaded once into registers and applied to every child that has s in its
+// interaction list, the per-child offset codes coming from a host-built table (one 16-byte
+// record of eight codes per (parent, source)).  The CTA's warps split the sources and meet
+// in shared memory; every child's V is written once, without atomics.  One right-hand side
+// (E = 2): each lane carries both components of its direction.
+#include <algorithm>
+#include <cstdlib>
+#include <unordered_map>
+#include <vector>
+
+#include "bi_cpx.cuh"
+#include "bi_internal.h"
+
+namespace {
+
+constexpr int kWarps = 4;
+constexpr unsigned short kNone = 0xFFFF;
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kWarps) k_translate_pc(int K, const int* __restrict__ cptr,
+                                                              const int* __restrict__ tptr, const int* __restrict__ src,
+                                                              const uint4* __restrict__ codes,
+                                                              const cpx<T>* __restrict__ Top,
+                                                              const cpx<T>* __restrict__ U, cpx<T>* __restrict__ V) {
+    __shared__ cpx<T> red[kWarps][8][2][32];
+    const int p = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = blockIdx.y * 32 + lane;
+    const bool ok = k < K;
+    const int kk = ok ? k : 0;
+    const int c0 = cptr[p], nc = cptr[p + 1] - c0;
+    cpx<T> a0[8], a1[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a0[j] = a1[j] = czero<T>();
+    for (int q = tptr[p] + warp; q < tptr[p + 1]; q += kWarps) {
+        const int s = src[q];
+        const uint4 cw = codes[q];
+        const unsigned cc[4] = {cw.x, cw.y, cw.z, cw.w};
+        cpx<T> u0, u1;
+        load_pair(U + ((int64_t)s * K + kk) * 2, u0, u1);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const unsigned code = (cc[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
+            if (code != kNone) {
+                cpx<T> t;
+                t.x = __ldg(&Top[(int64_t)code * K + kk].x);
+                t.y = __ldg(&Top[(int64_t)code * K + kk].y);
+                cfma(a0[j], t, u0);
+                cfma(a1[j], t, u1);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        red[warp][j][0][lane] = a0[j];
+        red[warp][j][1][lane] = a1[j];
+    }
+    __syncthreads();
+    // thread -> (child j, lane): sum the warps' partials and write both components
+    for (int t = threadIdx.x; t < nc * 32; t += blockDim.x) {
+        const int j = t >> 5, l = t & 31;
+        const int kd = blockIdx.y * 32 + l;
+        if (kd >= K) continue;
+        cpx<T> s0 = czero<T>(), s1 = czero<T>();
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            s0 = cadd(s0, red[w][j][0][l]);
+            s1 = cadd(s1, red[w][j][1][l]);
+        }
+        cpx<T>* out = V + ((int64_t)(c0 + j) * K + kd) * 2;
+        out[0] = s0;
+        out[1] = s1;
+    }
+}
+
+template <typename T>
+void launch_t(bi_handle_s* h, int l, cudaStream_t s) {
+    level_t& L = h->lev[l];
+    dim3 g(L.tp_np, (L.K + 31) / 32);
+    k_translate_pc<T><<<g, 32 * kWarps, 0, s>>>(L.K, L.d_tp_cptr, L.d_tp_ptr, L.d_tp_src, (const uint4*)L.d_tp_code,
+                                               (const cpx<T>*)L.d_T, (const cpx<T>*)L.d_U, (cpx<T>*)L.d_V);
+    CU(cudaGetLastError());
+}
+
+inline uint64_t ckey(int x, int y, int z) {
+    return ((uint64_t)(uint32_t)x << 42) | ((uint64_t)(uint32_t)y << 21) | (uint64_t)(uint32_t)z;
+}
+
+}  // namespace
+
+void bi_build_translate_lists(bi_handle_s* h) {
+    for (int l = 2; l <= h->leaf; ++l) {
+        level_t& C = h->lev[l];
+        const level_t& P = h->lev[l - 1];
+        std::unordered_map<uint64_t, int> pidx;
+        pidx.reserve(P.nbox * 2);
+        for (int b = 0; b < P.nbox; ++b) pidx[ckey(P.coords[3 * b], P.coords[3 * b + 1], P.coords[3 * b + 2])] = b;
+        const int pside = 1 << (l - 1);
+        std::vector<int> tptr(P.nbox + 1, 0), src;
+        std::vector<unsigned short> code;
+        for (int p = 0; p < P.nbox; ++p) {
+            const int c0 = P.child_ptr[p], nc = P.child_ptr[p + 1] - c0;
+            if (nc > 8) throw bi_error{BI_ERR_ARG, "octree parent with more than 8 children"};
+            for (int dx = -1; dx <= 1; ++dx)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dz = -1; dz <= 1; ++dz) {
+                        const int x = P.coords[3 * p] + dx, y = P.coords[3 * p + 1] + dy, z = P.coords[3 * p + 2] + dz;
+                        if (x < 0 || y < 0 || z < 0 || x >= pside || y >= pside || z >= pside) continue;
+                        auto it = pidx.find(ckey(x, y, z));
+                        if (it == pidx.end()) continue;
+                        const int qb = it->second;
+                        for (int s = P.child_ptr[qb]; s < P.child_ptr[qb + 1]; ++s) {
+                            unsigned short cs[8];
+                            bool any = false;
+                            for (int j = 0; j < 8; ++j) {
+                                cs[j] = kNone;
+                                if (j >= nc) continue;
+                                const int b = c0 + j;
+                                const int ox = C.coords[3 * b] - C.coords[3 * s];
+                                const int oy = C.coords[3 * b + 1] - C.coords[3 * s + 1];
+                                const int oz = C.coords[3 * b + 2] - C.coords[3 * s + 2];
+                                if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
+                                cs[j] = (unsigned short)((ox + 3) * 49 + (oy + 3) * 7 + (oz + 3));
+                                any = true;
+                            }
+                            if (!any) continue;
+                            src.push_back(s);
+                            code.insert(code.end(), cs, cs + 8);
+                        }
+                    }
+            tptr[p + 1] = (int)src.size();
+        }
+        std::vector<int> cptr(P.child_ptr.begin(), P.child_ptr.end());
+        C.tp_np = P.nbox;
+        C.d_tp_cptr = h->upload(cptr);
+        C.d_tp_ptr = h->upload(tptr);
+        if (!src.empty()) {
+            C.d_tp_src = h->upload(src);
+            C.d_tp_code = h->upload(code);
+        } else {
+            C.d_tp_src = (int*)h->alloc(sizeof(int));
+            C.d_tp_code = h->alloc(16);
+        }
+    }
+}
+
+bool bi_translate_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    if (E != 2 || !h->lev[l].d_tp_ptr) return false;
+    if (h->prec == 0) launch_t<double>(h, l, s);
+    else launch_t<float>(h, l, s);
+    return true;
+}
