@@ -138,6 +138,21 @@ def launches_per_step(info):
     return 1 + 1 + 1 + 2 * (lf - 2) + (lf - 1) + 2 * (lf - 2) + 1 + 1
 
 
+def measured_traffic():
+    """Per-launch DRAM bytes of the HBM-bound kernels from the committed ncu summary
+    (lines `traffic: <stage> <kernel> <bytes>`); {} when absent."""
+    out = {}
+    p = os.path.join(ROOT, "profiles", "dram_matvec_sphere_r2_61440.md")
+    try:
+        for line in open(p):
+            if line.startswith("traffic:"):
+                _, stage, kernel, nbytes = line.split()
+                out[stage] = (kernel, int(nbytes))
+    except OSError:
+        pass
+    return out
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -387,8 +402,10 @@ def run_gpu(args):
     dom = max((k for k in stages if k in sb), key=lambda k: stages[k])
     peak, peak_kind = peaks()
     achieved = sb[dom] / (stages[dom] * 1e-3) / 1e9
+    tr = measured_traffic().get(dom)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": tr[1] if tr else None,
+                "traffic_kernel": tr[0] if tr else None,
                 "algorithmic_bytes": sb[dom], "stage_ms": stages,
                 "step_frac": (sum(sb.values()) / (ms * 1e-3) / 1e9) / peak}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
