@@ -377,7 +377,7 @@ __global__ void k_receive(int N, int K, int nph, int R, const int* __restrict__ 
 // lane j reads columns j, j+32, ... (coalesced 16-byte entries), a shuffle reduction gives the
 // row.  RT right-hand sides per pass.
 template <typename T, int MODE, int RT>
-__global__ void __launch_bounds__(256) k_near_stream(int N, int R, int nun, const int* __restrict__ perm,
+__global__ void __launch_bounds__(256, RT == 1 ? 6 : 1) k_near_stream(int N, int R, int nun, const int* __restrict__ perm,
                                                      const int2* __restrict__ work,
                                                      const int* __restrict__ leaf_start, const int* __restrict__ near_ptr,
                                                      const int* __restrict__ near_src, const int64_t* __restrict__ near_blk,
