@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256) k_interp_pb1(int nthc, int nphc, int nthp
 }
 
 template <typename T, int PT>
-__global__ void __launch_bounds__(256) k_anterp_cb1(int nthc, int nphc, int nthp, int nphp,
+__global__ void __launch_bounds__(256, 8) k_anterp_cb1(int nthc, int nphc, int nthp, int nphp,
                                                     const int* __restrict__ parent, const int* __restrict__ octant,
                                                     const tap<T>* __restrict__ tth_pad, const tap<T>* __restrict__ tph_pad,
                                                     const cpx<T>* __restrict__ shift, const cpx<T>* __restrict__ Vp,
