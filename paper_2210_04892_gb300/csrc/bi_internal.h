@@ -120,6 +120,8 @@ struct bi_handle_s {
     int near_ncol_max = 0;
     int near_nwork = 0;                 // work items of the streaming near kernel (box, first row)
     int* d_near_work = nullptr;
+    int* d_near_col0 = nullptr;         // per near entry: first column in the test box's segment
+    int* d_near_ncol = nullptr;         // per leaf box: segment width (near columns)
     int num_sms = 152;              // widest near segment of a leaf box (columns)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 

@@ -381,6 +381,7 @@ __global__ void __launch_bounds__(256, RT == 1 ? 6 : 1) k_near_stream(int N, int
                                                      const int2* __restrict__ work,
                                                      const int* __restrict__ leaf_start, const int* __restrict__ near_ptr,
                                                      const int* __restrict__ near_src, const int64_t* __restrict__ near_blk,
+                                                     const int* __restrict__ near_col0, const int* __restrict__ near_ncol,
                                                      const cpx<T>* __restrict__ blocks, const int* __restrict__ gptr,
                                                      const int* __restrict__ gseg, const T* __restrict__ gval,
                                                      const cpx<T>* __restrict__ x, cpx<T>* __restrict__ yt,
@@ -393,17 +394,18 @@ __global__ void __launch_bounds__(256, RT == 1 ? 6 : 1) k_near_stream(int N, int
     const int m0 = leaf_start[b], mb = leaf_start[b + 1] - m0;
     const int q0 = near_ptr[b], q1 = near_ptr[b + 1];
     const int64_t seg = near_blk[q0];
-    const int ncol = (int)((near_blk[q1] - seg) / mb);
+    const int ncol = near_ncol[b];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const int row_end = min(mb, row0 + 2 * nwarp);
     for (int r0 = 0; r0 < R; r0 += RT) {
         const int rn = min(RT, R - r0);
         __syncthreads();
-        for (int q = q0; q < q1; ++q) {
+        // x of the near columns: one near box per warp, lanes over its RWGs
+        for (int q = q0 + warp; q < q1; q += nwarp) {
             const int s = near_src[q];
             const int n0 = leaf_start[s], nbs = leaf_start[s + 1] - n0;
-            const int c0 = (int)((near_blk[q] - seg) / mb);
-            for (int i = threadIdx.x; i < nbs; i += blockDim.x) {
+            const int c0 = near_col0[q];
+            for (int i = lane; i < nbs; i += 32) {
                 const int u = perm[n0 + i];
 #pragma unroll
                 for (int X = 0; X < NX; ++X)
@@ -1168,7 +1170,8 @@ void launch_near_stream(bi_handle_s* h, const cpx<T>* x, cpx<T>* yt, cpx<T>* yus
     if (smem > 48 * 1024) CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<h->near_nwork, 256, smem, s>>>(h->N, R, h->nun, h->d_perm, (const int2*)h->d_near_work, h->d_leaf_start,
                                           h->d_near_ptr, h->d_near_src,
-                                                 h->d_near_blk, (const cpx<T>*)h->d_near, h->d_gram_ptr, h->d_gram_seg,
+                                                 h->d_near_blk, h->d_near_col0, h->d_near_ncol, (const cpx<T>*)h->d_near,
+                                                 h->d_gram_ptr, h->d_gram_seg,
                                                  (const T*)h->d_gram_val, x, yt, yuser);
     CU(cudaGetLastError());
 }

@@ -933,6 +933,17 @@ void bi_device_geometry(bi_handle_s* h, const double* V, const int* Tm) {
             }
         h->near_nwork = (int)(work.size() / 2);
         h->d_near_work = h->upload(work);
+        // column offset of every near entry inside its test box's segment, and the segment
+        // width of every box (int32: the product kernels need no 64-bit division)
+        std::vector<int> col0(h->near_src.size()), ncol(LF.nbox);
+        for (int b = 0; b < LF.nbox; ++b) {
+            const int mb = h->leaf_start[b + 1] - h->leaf_start[b];
+            const int64_t seg = h->near_blk[h->near_ptr[b]];
+            for (int q = h->near_ptr[b]; q < h->near_ptr[b + 1]; ++q) col0[q] = (int)((h->near_blk[q] - seg) / mb);
+            ncol[b] = (int)((h->near_blk[h->near_ptr[b + 1]] - seg) / mb);
+        }
+        h->d_near_col0 = h->upload(col0);
+        h->d_near_ncol = h->upload(ncol);
     }
     std::vector<double> cen = LF.center;
     h->d_leaf_center = h->upload(cen);
