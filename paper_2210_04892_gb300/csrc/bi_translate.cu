@@ -19,10 +19,9 @@
 
 namespace {
 
-constexpr int kWarps = 4;
 constexpr unsigned short kNone = 0xFFFF;
 
-template <typename T>
+template <typename T, int kWarps>
 __global__ void __launch_bounds__(32 * kWarps) k_translate_pc(int K, const int* __restrict__ cptr,
                                                               const int* __restrict__ tptr, const int* __restrict__ src,
                                                               const uint4* __restrict__ codes,
@@ -38,6 +37,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_translate_pc(int K, const int* 
     cpx<T> a0[8], a1[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) a0[j] = a1[j] = czero<T>();
+    // unrolled so that several sources' loads are in flight at once
+#pragma unroll 4
     for (int q = tptr[p] + warp; q < tptr[p + 1]; q += kWarps) {
         const int s = src[q];
         const uint4 cw = codes[q];
@@ -83,7 +84,12 @@ template <typename T>
 void launch_t(bi_handle_s* h, int l, cudaStream_t s) {
     level_t& L = h->lev[l];
     dim3 g(L.tp_np, (L.K + 31) / 32);
-    k_translate_pc<T><<<g, 32 * kWarps, 0, s>>>(L.K, L.d_tp_cptr, L.d_tp_ptr, L.d_tp_src, (const uint4*)L.d_tp_code,
+    // levels with few (parent, chunk) CTAs split each parent's sources over more warps
+    if ((int64_t)g.x * g.y < 4 * h->num_sms)
+        k_translate_pc<T, 8><<<g, 256, 0, s>>>(L.K, L.d_tp_cptr, L.d_tp_ptr, L.d_tp_src, (const uint4*)L.d_tp_code,
+                                               (const cpx<T>*)L.d_T, (const cpx<T>*)L.d_U, (cpx<T>*)L.d_V);
+    else
+        k_translate_pc<T, 4><<<g, 128, 0, s>>>(L.K, L.d_tp_cptr, L.d_tp_ptr, L.d_tp_src, (const uint4*)L.d_tp_code,
                                                (const cpx<T>*)L.d_T, (const cpx<T>*)L.d_U, (cpx<T>*)L.d_V);
     CU(cudaGetLastError());
 }
