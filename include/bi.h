@@ -73,6 +73,11 @@ typedef struct {
     int gmres_restart;      /* GMRES(m) restart length (default 100) */
     int gmres_maxit;        /* total GMRES iterations per right-hand side (default 1000) */
     void* stream;           /* cudaStream_t for all work of this handle; NULL = legacy default stream */
+    int precond;            /* bi_solve preconditioner: 0 none (default); 1 sparse approximate inverse
+                               from the near field only (Sec. III.B), a right preconditioner that is
+                               block-diagonal over leaf boxes, M_b = argmin ||A(N,T) M_b - I(N,T)||_F
+                               with T the box's unknowns and N those of its near boxes; built at
+                               bi_setup, used by bi_solve and the server, never by bi_matvec */
 } bi_params;
 
 typedef struct {
@@ -91,6 +96,7 @@ typedef struct {
     double setup_near_regular_ms;   /* near-field fill: separated triangle pairs (FP32) */
     double setup_near_special_ms;   /* near-field fill: singular / near-singular pairs (FP64) */
     int64_t near_special_entries;   /* triangle pairs of the near field integrated in FP64 (singular / near-singular) */
+    double setup_sai_ms;            /* set-up time of the preconditioner (0 without) */
 } bi_info_t;
 
 /* Fill *p with the defaults listed above. */

@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
     _fields_ = [("digits", ctypes.c_int), ("leaf_box", ctypes.c_double), ("levels", ctypes.c_int),
                 ("interp_order", ctypes.c_int), ("precision", ctypes.c_int), ("op_mode", ctypes.c_int),
                 ("max_rhs", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("precond", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -51,7 +51,7 @@ class Info(ctypes.Structure):
                 ("K", ctypes.c_int * 32), ("near_pairs", ctypes.c_int64), ("interactions", ctypes.c_int64 * 32),
                 ("device_bytes", ctypes.c_int64), ("root_size", ctypes.c_double), ("setup_ms", ctypes.c_double),
                 ("setup_near_regular_ms", ctypes.c_double), ("setup_near_special_ms", ctypes.c_double),
-                ("near_special_entries", ctypes.c_int64)]
+                ("near_special_entries", ctypes.c_int64), ("setup_sai_ms", ctypes.c_double)]
 
 
 class ServerParams(ctypes.Structure):
@@ -124,7 +124,7 @@ class Operator:
     precision "fp32" (complex64 vectors) or "fp64" (complex128)."""
 
     def __init__(self, verts, tris, k0, digits=3, precision="fp32", op_mode=0, leaf_box=0.25, levels=0,
-                 interp_order=10, max_rhs=1, gmres_restart=100, gmres_maxit=1000, stream=None):
+                 interp_order=10, max_rhs=1, gmres_restart=100, gmres_maxit=1000, stream=None, precond=0):
         import torch
         L = load()
         p = default_params()
@@ -137,6 +137,7 @@ class Operator:
         p.max_rhs = int(max_rhs)
         p.gmres_restart = int(gmres_restart)
         p.gmres_maxit = int(gmres_maxit)
+        p.precond = int(precond)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -168,7 +169,8 @@ class Operator:
                     boxes=list(I.boxes[:nl]), L=list(I.L[:nl]), K=list(I.K[:nl]), near_pairs=I.near_pairs,
                     interactions=list(I.interactions[:nl]), device_bytes=I.device_bytes, root_size=I.root_size,
                     setup_ms=I.setup_ms, setup_near_regular_ms=I.setup_near_regular_ms,
-                    setup_near_special_ms=I.setup_near_special_ms, near_special_entries=I.near_special_entries)
+                    setup_near_special_ms=I.setup_near_special_ms, near_special_entries=I.near_special_entries,
+                    setup_sai_ms=I.setup_sai_ms)
 
     def edges(self) -> np.ndarray:
         e = np.zeros((self.n_rwg, 2), np.int32)
@@ -307,9 +309,10 @@ class Server:
         self._meta = {}
 
     def submit(self, verts, tris, k0, khat, phat, tol=1e-3, digits=3, precision="fp32", op_mode=1, leaf_box=0.25,
-               levels=0, interp_order=10, gmres_restart=100, gmres_maxit=1000):
+               levels=0, interp_order=10, gmres_restart=100, gmres_maxit=1000, precond=0):
         L = load()
         p = default_params()
+        p.precond = int(precond)
         p.digits, p.leaf_box, p.levels, p.interp_order = int(digits), float(leaf_box), int(levels), int(interp_order)
         p.precision = 0 if precision == "fp64" else 1
         p.op_mode = int(op_mode)

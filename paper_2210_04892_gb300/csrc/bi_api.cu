@@ -69,7 +69,8 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
     bi_params& P = h->prm;
     if (P.digits < 1 || P.digits > 8 || !(P.leaf_box > 0) || P.interp_order < 2 || P.interp_order > 32 ||
         (P.precision != 0 && P.precision != 1) || (P.op_mode != 0 && P.op_mode != 1) || P.max_rhs < 1 ||
-        P.max_rhs > 4096 || P.gmres_restart < 1 || P.gmres_maxit < 1 || P.levels < 0 || P.levels > 21) {
+        P.max_rhs > 4096 || P.gmres_restart < 1 || P.gmres_maxit < 1 || P.levels < 0 || P.levels > 21 ||
+        (P.precond != 0 && P.precond != 1)) {
         g_setup_error = "bi_setup: parameter out of range";
         delete h;
         return BI_ERR_ARG;
@@ -116,6 +117,7 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
         bi_fill_translations(h);
         bi_build_translate_lists(h);
         bi_alloc_work(h);
+        bi_build_sai(h);
         CU(cudaStreamSynchronize(h->stream));
     } catch (const bi_error& e) {
         g_setup_error = e.msg;

@@ -117,6 +117,8 @@ struct bi_handle_s {
     bool use_fast = true;               // fused kernels (false: two-pass reference kernels)
     bool use_leaf_bulk = true;          // bulk-copy pipelines for leaf aggregation and receive
     int* d_status = nullptr;            // device status word (0: healthy; see bi_tma.cuh)
+    void* d_sai = nullptr;              // near-field SAI blocks, one dense [n_b][n_b] per leaf box (precond 1)
+    int64_t* sai_off = nullptr;         // [nbox + 1] offsets of the blocks (complex entries)
     int near_ncol_max = 0;
     int near_nwork = 0;                 // work items of the streaming near kernel (box, first row)
     int* d_near_work = nullptr;
@@ -219,6 +221,8 @@ bool bi_interp_level(bi_handle_s* h, int l, int E, cudaStream_t s);
 bool bi_anterp_level(bi_handle_s* h, int l, int E, cudaStream_t s);
 void bi_upload_taps(bi_handle_s* h);
 bool bi_translate_level(bi_handle_s* h, int l, int E, cudaStream_t s);
+void bi_build_sai(bi_handle_s* h);
+void bi_sai_apply(bi_handle_s* h, const void* x, void* y, int R, cudaStream_t s);
 void bi_build_translate_lists(bi_handle_s* h);
 bool bi_leaf_receive_bulk(bi_handle_s* h, void* y, int R, cudaStream_t s);
 int bi_take_device_status(bi_handle_s* h);

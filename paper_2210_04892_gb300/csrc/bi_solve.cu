@@ -280,6 +280,7 @@ struct gmres_ctx_impl {
     double *cs = nullptr, *nrm = nullptr, *res = nullptr;
     int *act = nullptr, *nk = nullptr;
     void *xin = nullptr, *yout = nullptr;
+    void* zbuf = nullptr;               // M v in the handle precision (right preconditioner)
     double* h_res = nullptr;  // pinned
     cudaEvent_t ev = nullptr;
     std::vector<double> bnorm, last_true;
@@ -303,11 +304,17 @@ struct gmres_ctx_impl {
     static int64_t estimate_bytes(int64_t nun, int R, int m) {
         return (int64_t)sizeof(z2) * nun * R * (m + 5) + (int64_t)R * (m + 2) * (m + 4) * 32 + 2 * nun * R * 16;
     }
+    // out = A M in (M the right preconditioner when the handle has one, else the identity)
     void matvec64(const z2* in, z2* out) {
         const int th = 256;
         if (h->prec == 0) k_cvt_to<double><<<nb(nv, th), th, 0, s>>>(nv, in, (double*)xin);
         else k_cvt_to<float><<<nb(nv, th), th, 0, s>>>(nv, in, (float*)xin);
-        bi_matvec_launch(h, xin, yout, R, s);
+        if (h->d_sai) {
+            bi_sai_apply(h, xin, zbuf, R, s);
+            bi_matvec_launch(h, zbuf, yout, R, s);
+        } else {
+            bi_matvec_launch(h, xin, yout, R, s);
+        }
         if (h->prec == 0) k_cvt_from<double><<<nb(nv, th), th, 0, s>>>(nv, (const double*)yout, out);
         else k_cvt_from<float><<<nb(nv, th), th, 0, s>>>(nv, (const float*)yout, out);
     }
@@ -338,6 +345,7 @@ struct gmres_ctx_impl {
         nk = (int*)A(sizeof(int) * R);
         xin = xin_ ? xin_ : A(h->csize * nv);
         yout = yout_ ? yout_ : A(h->csize * nv);
+        if (h->d_sai) zbuf = A(h->csize * nv);
         CU(cudaMallocHost(&h_res, sizeof(double) * 2 * R));
         CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         const int th = 256;
@@ -446,8 +454,11 @@ struct gmres_ctx_impl {
         k_norms<<<R, 256, 0, s>>>(nun, w, nrm);
         std::vector<double> rr(R);
         CU(cudaMemcpyAsync(rr.data(), nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
-        if (h->prec == 0) k_cvt_to<double><<<nb(nv, th), th, 0, s>>>(nv, x64, (double*)xout);
-        else k_cvt_to<float><<<nb(nv, th), th, 0, s>>>(nv, x64, (float*)xout);
+        // x = M u (the iterate lives in the preconditioned variable)
+        void* xdst = h->d_sai ? zbuf : xout;
+        if (h->prec == 0) k_cvt_to<double><<<nb(nv, th), th, 0, s>>>(nv, x64, (double*)xdst);
+        else k_cvt_to<float><<<nb(nv, th), th, 0, s>>>(nv, x64, (float*)xdst);
+        if (h->d_sai) bi_sai_apply(h, zbuf, xout, R, s);
         CU(cudaStreamSynchronize(s));
         int status = bi_take_device_status(h);
         for (int r = 0; r < R; ++r) {

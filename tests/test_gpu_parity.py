@@ -193,6 +193,49 @@ def test_pec_solve_matches_dense_solution(bi, sphere_c1, Z_c1, precision, tol):
     op.close()
 
 
+@pytest.mark.parametrize("precision,mode,tol", [("fp64", 1, 1e-6), ("fp64", 0, 1e-6), ("fp32", 1, 5e-4),
+                                                ("fp32", 0, 5e-4)])
+def test_sai_preconditioned_solve(bi, sphere_c1, Z_c1, precision, mode, tol):
+    """Near-field SAI right preconditioner (Sec. III.B): the preconditioned solve reaches the
+    same tolerance in fewer GMRES iterations and returns the solution of the unpreconditioned
+    system (dense LU of the oracle's matrix, within the MLFMA accuracy)."""
+    v, t = sphere_c1
+    out = {}
+    for pc in (0, 1):
+        op = bi.Operator(v, t, K0, precision=precision, op_mode=mode, max_rhs=2, precond=pc)
+        b = op.rhs_planewave([[0, 0, 1.0], [1.0, 0, 0]], [[1.0, 0, 0], [0, 0, 1.0]])
+        x, its, relres = op.solve(b, tol=tol)
+        op.status()
+        out[pc] = (x.cpu().numpy().astype(np.complex128), its.copy(), relres.copy(), b.cpu().numpy())
+        if pc == 1:
+            assert op.info()["setup_sai_ms"] > 0
+        op.close()
+    x1, its1, rel1, bb = out[1]
+    x0, its0, rel0, _ = out[0]
+    assert np.all(rel1 <= tol * 1.001), rel1
+    assert np.all(its1 < its0), (its0, its1)
+    for r in range(2):
+        xr = np.linalg.solve(Z_c1[mode], bb[r].astype(np.complex128))
+        assert rel(x1[r], xr) < 2e-3
+        assert rel(x1[r], x0[r]) < 50 * tol + 1e-9
+
+
+def test_sai_preconditioned_server_request(bi):
+    """A served request with the SAI preconditioner gives the direct preconditioned solve."""
+    v, t = icosphere(8, 0.5)
+    srv = bi.Server(max_active=2)
+    rid = srv.submit(v, t, K0, [0, 0, 1.0], [1.0, 0, 0], tol=1e-3, op_mode=1, precond=1)
+    r = srv.wait(rid)
+    srv.close()
+    assert r["status"] == bi.BI_OK
+    assert np.all(r["relres"] <= 1e-3 * 1.001)
+    op = bi.Operator(v, t, K0, op_mode=1, max_rhs=1, precond=1)
+    b = op.rhs_planewave([0, 0, 1.0], [1.0, 0, 0])
+    x, its, relres = op.solve(b, tol=1e-3)
+    assert rel(r["x"][0], x.cpu().numpy()[0]) < 1e-2
+    op.close()
+
+
 def test_cblock_solve_converges(bi, sphere_c1):
     v, t = sphere_c1
     op = bi.Operator(v, t, K0, precision="fp32", op_mode=0, max_rhs=1)
