@@ -38,12 +38,14 @@ __device__ __forceinline__ int fdiv(int o, int d, float inv) {
     return q;
 }
 
-template <typename T>
-__device__ __forceinline__ cpx<T> ldg_c(const cpx<T>* p) {
-    cpx<T> v;
-    v.x = __ldg(&p->x);
-    v.y = __ldg(&p->y);
-    return v;
+// one complex value through the read-only path as a single vector load
+__device__ __forceinline__ cpx<float> ldg_c(const cpx<float>* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ cpx<double> ldg_c(const cpx<double>* p) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    return {v.x, v.y};
 }
 
 template <typename T>
@@ -314,6 +316,172 @@ __global__ void __launch_bounds__(256, 8) k_anterp_cb1(int nthc, int nphc, int n
     }
 }
 
+// ---------------------------------------------------------------- many right-hand sides (E >= 32)
+// Two passes through the per-child intermediate tmp[child][ip][jc][e].  One CTA per (box, row),
+// rows fastest so that the CTAs of one box run together and share its patterns in L2; the
+// row's taps are uniform over the CTA; threads = 32 lanes over e x 8 over columns.
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_interp_theta_w(int nthc, int nphc, int nthp, int E, const tap<T>* __restrict__ th_tap,
+                                                        const cpx<T>* __restrict__ Uc, cpx<T>* __restrict__ tmp) {
+    const int cb = blockIdx.x / nthp, ip = blockIdx.x - cb * nthp;
+    const int half = nphc / 2, Kc = nthc * nphc;
+    int code[P];
+    T w[P];
+#pragma unroll
+    for (int t = 0; t < P; ++t) {
+        const tap<T> q = th_tap[ip * P + t];
+        code[t] = q.c;
+        w[t] = q.w;
+    }
+    const cpx<T>* u = Uc + (int64_t)cb * Kc * E;
+    cpx<T>* out = tmp + (((int64_t)cb * nthp + ip) * nphc) * E;
+    for (int jc = threadIdx.y; jc < nphc; jc += blockDim.y) {
+        const int jf = jc + half < nphc ? jc + half : jc + half - nphc;
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+            cpx<T> a = czero<T>();
+#pragma unroll
+            for (int t = 0; t < P; ++t) {
+                const cpx<T> v = ldg_c(u + ((int64_t)(code[t] >> 1) * nphc + ((code[t] & 1) ? jf : jc)) * E + e);
+                a.x = fma(w[t], v.x, a.x);
+                a.y = fma(w[t], v.y, a.y);
+            }
+            out[(int64_t)jc * E + e] = a;
+        }
+    }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_interp_phi_w(int nthp, int nphp, int nphc, int E, const tap<T>* __restrict__ ph_tap,
+                                                      const int* __restrict__ child_ptr, const int* __restrict__ octant,
+                                                      const cpx<T>* __restrict__ shift, const cpx<T>* __restrict__ tmp,
+                                                      cpx<T>* __restrict__ Up) {
+    const int pb = blockIdx.x / nthp, ip = blockIdx.x - pb * nthp;
+    const int Kp = nthp * nphp;
+    const int c0 = child_ptr[pb], nc = child_ptr[pb + 1] - c0;
+    for (int jp = threadIdx.y; jp < nphp; jp += blockDim.y) {
+        int src[P];
+        T w[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const tap<T> tq = ph_tap[jp * P + q];
+            src[q] = tq.c;
+            w[q] = tq.w;
+        }
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+            cpx<T> acc = czero<T>();
+            for (int c = 0; c < nc; ++c) {
+                const cpx<T>* row = tmp + (((int64_t)(c0 + c) * nthp + ip) * nphc) * E + e;
+                cpx<T> a = czero<T>();
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const cpx<T> v = ldg_c(row + (int64_t)src[q] * E);
+                    a.x = fma(w[q], v.x, a.x);
+                    a.y = fma(w[q], v.y, a.y);
+                }
+                cfma(acc, ldg_c(shift + (int64_t)octant[c0 + c] * Kp + ip * nphp + jp), a);
+            }
+            Up[((int64_t)pb * Kp + ip * nphp + jp) * E + e] = acc;
+        }
+    }
+}
+
+// tmp[cb][ip][jc][e] = sum over parent columns jp of w conj(shift(ip, jp)) V_p[ip][jp][e]
+template <typename T, int PT>
+__global__ void __launch_bounds__(256) k_anterp_phi_w(int nthp, int nphp, int nphc, int E, const tap<T>* __restrict__ tph_pad,
+                                                      const int* __restrict__ parent, const int* __restrict__ octant,
+                                                      const cpx<T>* __restrict__ shift, const cpx<T>* __restrict__ Vp,
+                                                      cpx<T>* __restrict__ tmp) {
+    const int cb = blockIdx.x / nthp, ip = blockIdx.x - cb * nthp;
+    const int Kp = nthp * nphp;
+    const int pb = parent[cb];
+    const cpx<T>* sh = shift + (int64_t)octant[cb] * Kp + ip * nphp;
+    const cpx<T>* vp = Vp + ((int64_t)pb * Kp + ip * nphp) * E;
+    cpx<T>* out = tmp + (((int64_t)cb * nthp + ip) * nphc) * E;
+    for (int jc = threadIdx.y; jc < nphc; jc += blockDim.y) {
+        int dst[PT];
+        T w[PT];
+        cpx<T> sc[PT];
+#pragma unroll
+        for (int q = 0; q < PT; ++q) {
+            const tap<T> tq = tph_pad[jc * PT + q];
+            dst[q] = tq.c;
+            const cpx<T> z = ldg_c(sh + tq.c);
+            sc[q] = {tq.w * z.x, -tq.w * z.y};   // w conj(shift)
+        }
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+            cpx<T> a = czero<T>();
+#pragma unroll
+            for (int q = 0; q < PT; ++q) cfma(a, sc[q], ldg_c(vp + (int64_t)dst[q] * E + e));
+            out[(int64_t)jc * E + e] = a;
+        }
+    }
+}
+
+// V_c[ic][jc][e] += sum over parent rows ip of w tmp[cb][ip][jc or jc + half][e]
+template <typename T, int PT>
+__global__ void __launch_bounds__(256) k_anterp_theta_w(int nthc, int nphc, int nthp, int E, const tap<T>* __restrict__ tth_pad,
+                                                        const cpx<T>* __restrict__ tmp, cpx<T>* __restrict__ Vc) {
+    const int cb = blockIdx.x / nthc, ic = blockIdx.x - cb * nthc;
+    const int half = nphc / 2, Kc = nthc * nphc;
+    int code[PT];
+    T w[PT];
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+        const tap<T> tq = tth_pad[ic * PT + q];
+        code[q] = tq.c;
+        w[q] = tq.w;
+    }
+    const cpx<T>* t0 = tmp + (int64_t)cb * nthp * nphc * E;
+    cpx<T>* vc = Vc + ((int64_t)cb * Kc + ic * nphc) * E;
+    for (int jc = threadIdx.y; jc < nphc; jc += blockDim.y) {
+        const int jf = jc + half < nphc ? jc + half : jc + half - nphc;
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+            cpx<T> a = czero<T>();
+#pragma unroll
+            for (int q = 0; q < PT; ++q) {
+                const cpx<T> v = ldg_c(t0 + ((int64_t)(code[q] >> 1) * nphc + ((code[q] & 1) ? jf : jc)) * E + e);
+                a.x = fma(w[q], v.x, a.x);
+                a.y = fma(w[q], v.y, a.y);
+            }
+            vc[(int64_t)jc * E + e] = cadd(vc[(int64_t)jc * E + e], a);
+        }
+    }
+}
+
+template <typename T>
+bool interp_wide(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    level_t& Pl = h->lev[l];
+    level_t& C = h->lev[l + 1];
+    interp_t& I = h->itp[l];
+    if (!I.d_tmp) return false;
+    const dim3 blk(32, 8);
+    k_interp_theta_w<T, 10><<<(unsigned)((int64_t)C.nbox * Pl.nth), blk, 0, s>>>(C.nth, C.nph, Pl.nth, E, (const tap<T>*)I.d_th_tap,
+                                                                               (const cpx<T>*)C.d_U, (cpx<T>*)I.d_tmp);
+    CU(cudaGetLastError());
+    k_interp_phi_w<T, 10><<<(unsigned)((int64_t)Pl.nbox * Pl.nth), blk, 0, s>>>(Pl.nth, Pl.nph, C.nph, E, (const tap<T>*)I.d_ph_tap,
+                                                                             Pl.d_child_ptr, C.d_octant, (const cpx<T>*)Pl.d_shift,
+                                                                             (const cpx<T>*)I.d_tmp, (cpx<T>*)Pl.d_U);
+    CU(cudaGetLastError());
+    return true;
+}
+
+template <typename T, int PT>
+bool anterp_wide(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    level_t& Pl = h->lev[l];
+    level_t& C = h->lev[l + 1];
+    interp_t& I = h->itp[l];
+    if (!I.d_tmp) return false;
+    const dim3 blk(32, 8);
+    k_anterp_phi_w<T, PT><<<(unsigned)((int64_t)C.nbox * Pl.nth), blk, 0, s>>>(Pl.nth, Pl.nph, C.nph, E, (const tap<T>*)I.d_tph_pad,
+                                                                             C.d_parent, C.d_octant, (const cpx<T>*)Pl.d_shift,
+                                                                             (const cpx<T>*)Pl.d_V, (cpx<T>*)I.d_tmp);
+    CU(cudaGetLastError());
+    k_anterp_theta_w<T, PT><<<(unsigned)((int64_t)C.nbox * C.nth), blk, 0, s>>>(C.nth, C.nph, Pl.nth, E, (const tap<T>*)I.d_tth_pad,
+                                                                               (const cpx<T>*)I.d_tmp, (cpx<T>*)C.d_V);
+    CU(cudaGetLastError());
+    return true;
+}
+
 template <typename T>
 void upload_taps_t(bi_handle_s* h) {
     for (int l = 2; l + 1 <= h->leaf; ++l) {
@@ -421,10 +589,17 @@ void bi_upload_taps(bi_handle_s* h) {
 bool bi_interp_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
     const interp_t& I = h->itp[l];
     if (I.p_th != 10 || I.p_ph != 10 || !I.d_th_tap) return false;
+    if (E >= 32) return h->prec == 0 ? interp_wide<double>(h, l, E, s) : interp_wide<float>(h, l, E, s);
     return h->prec == 0 ? interp_t_p<double, 10>(h, l, E, s) : interp_t_p<float, 10>(h, l, E, s);
 }
 
 bool bi_anterp_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
-    if (!h->itp[l].d_tth_pad) return false;
+    const interp_t& I = h->itp[l];
+    if (!I.d_tth_pad) return false;
+    if (E >= 32) {
+        if (I.pt_th == 16) return h->prec == 0 ? anterp_wide<double, 16>(h, l, E, s) : anterp_wide<float, 16>(h, l, E, s);
+        if (I.pt_th == 24) return h->prec == 0 ? anterp_wide<double, 24>(h, l, E, s) : anterp_wide<float, 24>(h, l, E, s);
+        return false;
+    }
     return h->prec == 0 ? anterp_t<double>(h, l, E, s) : anterp_t<float>(h, l, E, s);
 }

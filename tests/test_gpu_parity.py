@@ -262,7 +262,7 @@ def test_c2_sampled_rows(bi):
     op.close()
 
 
-@pytest.mark.parametrize("mode,nrhs", [(0, 1), (0, 3), (1, 5)])
+@pytest.mark.parametrize("mode,nrhs", [(0, 1), (0, 3), (1, 5), (0, 16), (1, 20)])
 def test_fused_kernels_match_two_pass_kernels(bi, mode, nrhs, monkeypatch):
     """The fused/streaming kernels and the two-pass reference kernels give the same product
     (FP64; 4 levels so the interpolation and anterpolation kernels run)."""
