@@ -73,11 +73,14 @@ __global__ void __launch_bounds__(256) k_interp_pb(int nthc, int nphc, int nthp,
     const int c0 = child_ptr[p], nc = child_ptr[p + 1] - c0;
     const int W = nphc * E, Wp = nphp * E, Kc = nthc * nphc, Kp = nthp * nphp, half = nphc / 2;
     tap<T>* tt = reinterpret_cast<tap<T>*>(smem_raw);  // [RB][P]
-    tap<T>* pt = tt + RB * P;                          // [nphp][P]
+    tap<T>* pt = tt + RB * P;                          // [P][nphp]
     int* oc = reinterpret_cast<int*>(pt + nphp * P);   // [8]
     cpx<T>* s2 = reinterpret_cast<cpx<T>*>(oc + 8);    // [nc][nr][W]
     for (int i = threadIdx.x; i < nr * P; i += blockDim.x) tt[i] = th_tap[ip0 * P + i];
-    for (int i = threadIdx.x; i < nphp * P; i += blockDim.x) pt[i] = ph_tap[i];
+    for (int i = threadIdx.x; i < nphp * P; i += blockDim.x) {
+        const int jp = i / P, q = i - jp * P;
+        pt[q * nphp + jp] = ph_tap[i];
+    }
     if (threadIdx.x < nc) oc[threadIdx.x] = octant[c0 + threadIdx.x];
     __syncthreads();
     const float invE = 1.0f / E, invW = 1.0f / W, invRW = 1.0f / (nr * W), invWp = 1.0f / Wp;
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(256) k_interp_pb(int nthc, int nphc, int nthp,
             cpx<T> a = czero<T>();
 #pragma unroll
             for (int q = 0; q < P; ++q) {
-                const tap<T> tq = pt[jp * P + q];
+                const tap<T> tq = pt[q * nphp + jp];
                 const cpx<T> v = row[tq.c * E];
                 a.x = fma(tq.w, v.x, a.x);
                 a.y = fma(tq.w, v.y, a.y);
@@ -134,11 +137,14 @@ __global__ void __launch_bounds__(256) k_anterp_cb(int nthc, int nphc, int nthp,
     const int pb = parent[c], oct = octant[c];
     const int W = nphc * E, Wp = nphp * E, Kc = nthc * nphc, Kp = nthp * nphp, half = nphc / 2;
     tap<T>* tt = reinterpret_cast<tap<T>*>(smem_raw);       // [nthc][PT]
-    tap<T>* pt = tt + nthc * PT;                             // [nphc][PP]
+    tap<T>* pt = tt + nthc * PT;                             // [PP][nphc]
     cpx<T>* S = reinterpret_cast<cpx<T>*>(pt + nphc * PP);  // [Kp][E] conj(shift) V_p
     cpx<T>* t1 = S + (int64_t)Kp * E;                        // [nthp][W] transposed phi pass
     for (int i = threadIdx.x; i < nthc * PT; i += blockDim.x) tt[i] = tth_pad[i];
-    for (int i = threadIdx.x; i < nphc * PP; i += blockDim.x) pt[i] = tph_pad[i];
+    for (int i = threadIdx.x; i < nphc * PP; i += blockDim.x) {
+        const int jc = i / PP, q = i - jc * PP;
+        pt[q * nphc + jc] = tph_pad[i];
+    }
     const cpx<T>* sh = shift + (int64_t)oct * Kp;
     const cpx<T>* vp = Vp + (int64_t)pb * Kp * E;
     const float invE = 1.0f / E, invW = 1.0f / W;
@@ -153,7 +159,7 @@ __global__ void __launch_bounds__(256) k_anterp_cb(int nthc, int nphc, int nthp,
         cpx<T> a = czero<T>();
 #pragma unroll
         for (int q = 0; q < PP; ++q) {
-            const tap<T> tq = pt[jc * PP + q];
+            const tap<T> tq = pt[q * nphc + jc];
             const cpx<T> v = row[tq.c * E];
             a.x = fma(tq.w, v.x, a.x);
             a.y = fma(tq.w, v.y, a.y);
@@ -184,7 +190,7 @@ __global__ void __launch_bounds__(256) k_anterp_cb(int nthc, int nphc, int nthp,
 
 // ---------------------------------------------------------------- one right-hand side (E = 2)
 template <typename T, int P>
-__global__ void __launch_bounds__(256) k_interp_pb1(int nthc, int nphc, int nthp, int nphp, int RB,
+__global__ void __launch_bounds__(256, 4) k_interp_pb1(int nthc, int nphc, int nthp, int nphp, int RB,
                                                     const int* __restrict__ child_ptr, const int* __restrict__ octant,
                                                     const tap<T>* __restrict__ th_tap, const tap<T>* __restrict__ ph_tap,
                                                     const cpx<T>* __restrict__ shift, const cpx<T>* __restrict__ Uc,
@@ -194,11 +200,14 @@ __global__ void __launch_bounds__(256) k_interp_pb1(int nthc, int nphc, int nthp
     const int c0 = child_ptr[p], nc = child_ptr[p + 1] - c0;
     const int Kc = nthc * nphc, Kp = nthp * nphp, half = nphc / 2;
     tap<T>* tt = reinterpret_cast<tap<T>*>(smem_raw);  // [RB][P]
-    tap<T>* pt = tt + RB * P;                          // [nphp][P]
+    tap<T>* pt = tt + RB * P;                          // [P][nphp]: lanes (columns) read consecutive taps
     int* oc = reinterpret_cast<int*>(pt + nphp * P);   // [8]
     cpx<T>* s2 = reinterpret_cast<cpx<T>*>(oc + 8);    // [nc][nr][nphc][2]
     for (int i = threadIdx.x; i < nr * P; i += blockDim.x) tt[i] = th_tap[ip0 * P + i];
-    for (int i = threadIdx.x; i < nphp * P; i += blockDim.x) pt[i] = ph_tap[i];
+    for (int i = threadIdx.x; i < nphp * P; i += blockDim.x) {
+        const int jp = i / P, q = i - jp * P;
+        pt[q * nphp + jp] = ph_tap[i];
+    }
     if (threadIdx.x < nc) oc[threadIdx.x] = octant[c0 + threadIdx.x];
     __syncthreads();
     // theta pass: one (child, row, column) per thread, both components
@@ -231,7 +240,7 @@ __global__ void __launch_bounds__(256) k_interp_pb1(int nthc, int nphc, int nthp
         T w[P];
 #pragma unroll
         for (int q = 0; q < P; ++q) {
-            const tap<T> tq = pt[jp * P + q];
+            const tap<T> tq = pt[q * nphp + jp];
             src[q] = tq.c;
             w[q] = tq.w;
         }
@@ -266,11 +275,14 @@ __global__ void __launch_bounds__(256, 8) k_anterp_cb1(int nthc, int nphc, int n
     const int pb = parent[c], oct = octant[c];
     const int Kc = nthc * nphc, Kp = nthp * nphp, half = nphc / 2;
     tap<T>* tt = reinterpret_cast<tap<T>*>(smem_raw);       // [nthc][PT]
-    tap<T>* pt = tt + nthc * PT;                             // [nphc][PT]
+    tap<T>* pt = tt + nthc * PT;                             // [PT][nphc]: lanes (columns) read consecutive taps
     cpx<T>* S = reinterpret_cast<cpx<T>*>(pt + nphc * PT);  // [Kp][2] conj(shift) V_p
     cpx<T>* t1 = S + (int64_t)Kp * 2;                        // [nthp][nphc][2]
     for (int i = threadIdx.x; i < nthc * PT; i += blockDim.x) tt[i] = tth_pad[i];
-    for (int i = threadIdx.x; i < nphc * PT; i += blockDim.x) pt[i] = tph_pad[i];
+    for (int i = threadIdx.x; i < nphc * PT; i += blockDim.x) {
+        const int jc = i / PT, q = i - jc * PT;
+        pt[q * nphc + jc] = tph_pad[i];
+    }
     const cpx<T>* sh = shift + (int64_t)oct * Kp;
     const cpx<T>* vp = Vp + (int64_t)pb * Kp * 2;
     for (int i = threadIdx.x; i < Kp; i += blockDim.x) {
@@ -288,7 +300,7 @@ __global__ void __launch_bounds__(256, 8) k_anterp_cb1(int nthc, int nphc, int n
         cpx<T> a = czero<T>(), b = czero<T>();
 #pragma unroll
         for (int q = 0; q < PT; ++q) {
-            const tap<T> tq = pt[jc * PT + q];
+            const tap<T> tq = pt[q * nphc + jc];
             cpx<T> va, vb;
             lds_pair(row + 2 * tq.c, va, vb);
             fma_pair(tq.w, va, vb, a, b);
