@@ -132,6 +132,15 @@ __device__ __forceinline__ void load_pair(const cpx<double>* p, cpx<double>& A, 
     A = {a.x, a.y};
     B = {b.x, b.y};
 }
+// One complex value through the read-only path as a single vector load.
+__device__ __forceinline__ cpx<float> ldg_cpx(const cpx<float>* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ cpx<double> ldg_cpx(const cpx<double>* p) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    return {v.x, v.y};
+}
 // Two adjacent complex values from 16-byte aligned shared memory (one vector load for floats).
 __device__ __forceinline__ void lds_pair(const cpx<float>* p, cpx<float>& A, cpx<float>& B) {
     const float4 v = *reinterpret_cast<const float4*>(p);

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) k_aggregate_bulk(int N, int K, int nph, i
 
 // CTA = one leaf box; warp task = (RWG of the stage, RHS r); lanes over stored directions.
 template <typename T, int MODE, int R1>
-__global__ void __launch_bounds__(128) k_receive_bulk(int N, int K, int nph, int R_, int nun, int G, int S,
+__global__ void __launch_bounds__(256) k_receive_bulk(int N, int K, int nph, int R_, int nun, int G, int S,
                                                       const int* __restrict__ perm, const int* __restrict__ leaf_start,
                                                       const int* __restrict__ order, const cpx<T>* __restrict__ F,
                                                       const cpx<T>* __restrict__ RX, const cpx<T>* __restrict__ V, T cc,
@@ -256,15 +256,17 @@ bool receive_bulk(bi_handle_s* h, void* yv, int R, cudaStream_t s) {
     const level_t& L = h->lev[h->leaf];
     const int Kh = L.K / 2, E = 2 * R;
     const size_t rowb = (size_t)Kh * 2 * sizeof(cpx<T>);
-    const int G = (int)std::max<size_t>(1, std::min<size_t>(h->max_leaf_count, kStageBytes / (2 * rowb)));
-    const size_t smem = kBarBytes + (size_t)L.K * E * sizeof(cpx<T>) + (size_t)kStages * G * 2 * rowb + (size_t)Kh * sizeof(int);
+    // 8 warps, one RWG each per stage; two stages
+    const int S = 2;
+    const int G = (int)std::max<size_t>(1, std::min<size_t>(h->max_leaf_count, (2 * kStageBytes) / (2 * rowb)));
+    const size_t smem = kBarBytes + (size_t)L.K * E * sizeof(cpx<T>) + (size_t)S * G * 2 * rowb + (size_t)Kh * sizeof(int);
     if (smem > 200 * 1024) return false;
     const double pi = 3.14159265358979323846;
     const T cc = (T)(h->k * h->k / (32.0 * pi * pi));
     auto kern = h->prm.op_mode == 0 ? (R == 1 ? k_receive_bulk<T, 0, 1> : k_receive_bulk<T, 0, 0>)
                                     : (R == 1 ? k_receive_bulk<T, 1, 1> : k_receive_bulk<T, 1, 0>);
     CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<L.nbox, 128, smem, s>>>(h->N, L.K, L.nph, R, h->nun, G, kStages, h->d_perm, h->d_leaf_start, h->d_leaf_order,
+    kern<<<L.nbox, 256, smem, s>>>(h->N, L.K, L.nph, R, h->nun, G, S, h->d_perm, h->d_leaf_start, h->d_leaf_order,
                                    (const cpx<T>*)h->d_F, (const cpx<T>*)h->d_RX, (const cpx<T>*)L.d_V, cc,
                                    (const cpx<T>*)h->d_yt, (cpx<T>*)yv, h->d_status);
     CU(cudaGetLastError());

@@ -49,9 +49,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_translate_pc(int K, const int* 
         for (int j = 0; j < 8; ++j) {
             const unsigned code = (cc[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
             if (code != kNone) {
-                cpx<T> t;
-                t.x = __ldg(&Top[(int64_t)code * K + kk].x);
-                t.y = __ldg(&Top[(int64_t)code * K + kk].y);
+                const cpx<T> t = ldg_cpx(Top + (int64_t)code * K + kk);
                 cfma(a0[j], t, u0);
                 cfma(a1[j], t, u1);
             }
