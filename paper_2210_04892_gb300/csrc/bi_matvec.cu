@@ -1322,8 +1322,11 @@ bool launch_receive_tile(bi_handle_s* h, const cpx<T>* x, cpx<T>* y, int R, cuda
     return launch_receive_tile_opt<T, 8>(h, y, R, s);
 }
 
-// The product with fused kernels: near (side stream) || aggregate -> interpolate -> translate
-// -> anterpolate -> receive (+ near result, + permutation to user order).
+// The product: near (side stream) || aggregate -> interpolate -> translate -> anterpolate ->
+// receive (+ near result, + permutation to user order).  Each step takes the first kernel
+// family that applies: the bulk-copy leaf kernels (bi_leaf.cu), the level passes of
+// bi_interp.cu and bi_translate.cu, then the per-child, tiled and two-pass kernels of this
+// file (large RHS counts, shared memory that does not fit, or non-default tap counts).
 template <typename T>
 void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s, cudaStream_t side, cudaEvent_t* ev) {
     if (ev) side = s;
