@@ -144,6 +144,27 @@ int bi_rhs_planewave(bi_handle h, const double* khat, const double* phat, int nr
  * column missed tol (x holds the last iterate). */
 int bi_solve(bi_handle h, const void* rhs, void* x, int nrhs, double tol, int* iters, double* relres);
 
+/* Coupling with an interior discretisation (Eq. 52; Sec. II.E steps 2(a)-(e)).  Once set,
+ * bi_solve solves the reduced system (C - D^{X Lambda} Q^{-1} D^{Lambda X}) x = rhs and
+ * bi_matvec_coupled applies that operator; bi_matvec keeps applying C alone.
+ *   n_int: interior (hybrid) unknowns.
+ *   D^{Lambda X}: CSR, n_int rows, columns in [0, n_unknowns): dlx_ptr [n_int + 1],
+ *     dlx_col [nnz], dlx_val [nnz] complex of the handle's precision (device pointers).
+ *   D^{X Lambda}: CSR, n_unknowns rows, columns in [0, n_int): dxl_ptr, dxl_col, dxl_val.
+ *   qsolve(user, in, out, nrhs, stream): out = Q^{-1} in for nrhs columns (device,
+ *     column-major [nrhs][n_int], handle precision), its work ordered on `stream` (the
+ *     handle's cudaStream_t) or finished before it returns; the paper uses the LU factors of
+ *     the sparse Q from a direct solver, which the caller owns.
+ * The caller keeps every array alive while the coupling is set; qsolve == NULL clears it.
+ * The handle allocates two n_int x max_rhs work vectors.  BI_ERR_ARG on null arrays or
+ * n_int < 1. */
+typedef void (*bi_qsolve_fn)(void* user, const void* in, void* out, int nrhs, void* stream);
+int bi_set_coupling(bi_handle h, int64_t n_int, const int* dlx_ptr, const int* dlx_col, const void* dlx_val,
+                    const int* dxl_ptr, const int* dxl_col, const void* dxl_val, bi_qsolve_fn qsolve, void* user);
+/* y = (C - D^{X Lambda} Q^{-1} D^{Lambda X}) x, the product of steps 2(a)-(e); same
+ * arguments and stream behaviour as bi_matvec.  BI_ERR_ARG when no coupling is set. */
+int bi_matvec_coupled(bi_handle h, const void* x, void* y, int nrhs);
+
 /* Far field of the currents x (Eq. 22a in the far zone, time factor exp(-jkr)/r removed):
  *   F(rhat) = -jk/(4 pi) [ (I - rhat rhat) N_J - rhat x N_M ],  N_X = sum_n x_X,n int f_n exp(+jk rhat.r') ds',
  * so that sigma(rhat) = 4 pi |F(rhat)|^2 for a unit incident field (RCS of Sec. III, Eq. 5-25).

@@ -27,9 +27,21 @@ _NAMES = {0: "BI_OK", -1: "BI_ERR_ARG", -2: "BI_ERR_MESH", -3: "BI_ERR_OOM", -4:
 
 # entry points declared in include/bi.h
 EXPORTS = ["bi_default_params", "bi_setup", "bi_num_unknowns", "bi_rwg_edges", "bi_get_info", "bi_matvec",
-           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_profile_stages", "bi_stage_name", "bi_last_error", "bi_device_status",
+           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_profile_stages", "bi_stage_name", "bi_last_error", "bi_device_status", "bi_set_coupling", "bi_matvec_coupled",
            "bi_destroy", "bi_server_default_params", "bi_server_create", "bi_submit", "bi_poll", "bi_result",
            "bi_release", "bi_server_last_error", "bi_server_destroy"]
+
+
+# qsolve(user, in, out, nrhs, stream) of bi_set_coupling
+QSOLVE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p)
+
+
+class _DeviceView:
+    """A raw device buffer seen by torch (argument marshalling for the qsolve callback)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False), "version": 3,
+                                         "strides": None}
 
 
 class BIError(RuntimeError):
@@ -89,6 +101,8 @@ def load(path: str = LIB_PATH):
     L.bi_last_error.argtypes = [vp]
     L.bi_last_error.restype = ctypes.c_char_p
     L.bi_device_status.argtypes = [vp]
+    L.bi_set_coupling.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, QSOLVE, vp]
+    L.bi_matvec_coupled.argtypes = [vp, vp, vp, i]
     L.bi_destroy.argtypes = [vp]
     L.bi_destroy.restype = None
     L.bi_server_default_params.argtypes = [ctypes.POINTER(ServerParams)]
@@ -242,6 +256,42 @@ class Operator:
         _check(load().bi_profile_stages(self.h, x.data_ptr(), y.data_ptr(), x.shape[0], int(reps), ms.ctypes.data),
                self.h)
         return {load().bi_stage_name(i).decode(): float(ms[i]) for i in range(8)}
+
+    def set_coupling(self, n_int, dlx, dxl, qsolve):
+        """Couple to an interior discretisation (Eq. 52).  dlx = (ptr, col, val) of
+        D^{Lambda X} (n_int rows), dxl = (ptr, col, val) of D^{X Lambda} (n_unknowns rows):
+        torch CUDA tensors (int32, int32, complex of the handle precision).  qsolve(inp, out,
+        stream) writes Q^{-1} inp into out (torch views [nrhs, n_int] on the device), queueing
+        its work on the given torch stream.  qsolve=None clears the coupling."""
+        import torch
+        L = load()
+        if qsolve is None:
+            _check(L.bi_set_coupling(self.h, 0, None, None, None, None, None, None, QSOLVE(), None), self.h)
+            self._cpl = None
+            return
+        ts = "<c16" if self.precision == "fp64" else "<c8"
+        n_int = int(n_int)
+
+        def _cb(user, pin, pout, nrhs, stream):
+            st = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+            with torch.cuda.stream(st):
+                a = torch.as_tensor(_DeviceView(pin, (nrhs, n_int), ts), device="cuda")
+                b = torch.as_tensor(_DeviceView(pout, (nrhs, n_int), ts), device="cuda")
+                qsolve(a, b, st)
+
+        cb = QSOLVE(_cb)
+        arrs = [t.contiguous() for t in (*dlx, *dxl)]
+        _check(L.bi_set_coupling(self.h, n_int, *[t.data_ptr() for t in arrs], cb, None), self.h)
+        self._cpl = (cb, arrs)   # keep the callback and the arrays alive while set
+
+    def matvec_coupled(self, x, out=None):
+        """y = (C - D^{X Lambda} Q^{-1} D^{Lambda X}) x (Eq. 52's operator); queued on the stream."""
+        import torch
+        x = self._vec(x)
+        if out is None:
+            out = torch.empty_like(x)
+        _check(load().bi_matvec_coupled(self.h, x.data_ptr(), out.data_ptr(), x.shape[0]), self.h)
+        return out
 
     def status(self):
         """Synchronise and raise BIError if a product kernel gave up a bounded device wait."""

@@ -215,6 +215,36 @@ extern "C" int bi_matvec(bi_handle h, const void* x, void* y, int nrhs) {
     });
 }
 
+extern "C" int bi_set_coupling(bi_handle h, int64_t n_int, const int* dlx_ptr, const int* dlx_col, const void* dlx_val,
+                               const int* dxl_ptr, const int* dxl_col, const void* dxl_val, bi_qsolve_fn qsolve,
+                               void* user) {
+    if (!h) return BI_ERR_ARG;
+    if (qsolve && (n_int < 1 || !dlx_ptr || !dlx_col || !dlx_val || !dxl_ptr || !dxl_col || !dxl_val)) {
+        h->err = "bi_set_coupling: n_int < 1 or a null CSR array";
+        return BI_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        bi_coupling_set(h, n_int, dlx_ptr, dlx_col, dlx_val, dxl_ptr, dxl_col, dxl_val, qsolve, user);
+        return (int)BI_OK;
+    });
+}
+
+extern "C" int bi_matvec_coupled(bi_handle h, const void* x, void* y, int nrhs) {
+    if (!h) return BI_ERR_ARG;
+    if (!h->cpl.qsolve) {
+        h->err = "bi_matvec_coupled: no coupling set (bi_set_coupling)";
+        return BI_ERR_ARG;
+    }
+    if (!x || !y || nrhs < 1 || nrhs > h->max_rhs) {
+        h->err = "bi_matvec_coupled: null vector or nrhs outside [1, max_rhs]";
+        return BI_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        bi_operator_launch(h, x, y, nrhs, h->stream);
+        return (int)BI_OK;
+    });
+}
+
 extern "C" int bi_matvec_host(bi_handle h, const void* x, void* y, int nrhs) {
     if (!h) return BI_ERR_ARG;
     if (!x || !y || nrhs < 1 || nrhs > h->max_rhs) {

@@ -118,6 +118,14 @@ struct bi_handle_s {
     bool use_leaf_bulk = true;          // bulk-copy pipelines for leaf aggregation and receive
     int* d_status = nullptr;            // device status word (0: healthy; see bi_tma.cuh)
     void* d_sai = nullptr;              // near-field SAI blocks, one dense [n_b][n_b] per leaf box (precond 1)
+    struct coupling_t {                 // Eq. 52 coupling (caller-owned CSR arrays and Q^{-1} solver)
+        int64_t n_int = 0;
+        const int *lx_ptr = nullptr, *lx_col = nullptr, *xl_ptr = nullptr, *xl_col = nullptr;
+        const void *lx_val = nullptr, *xl_val = nullptr;
+        bi_qsolve_fn qsolve = nullptr;
+        void* user = nullptr;
+        void *t1 = nullptr, *t2 = nullptr;   // work: D^{Lambda X} x, Q^{-1} of it
+    } cpl;
     int64_t* sai_off = nullptr;         // [nbox + 1] offsets of the blocks (complex entries)
     int near_ncol_max = 0;
     int near_nwork = 0;                 // work items of the streaming near kernel (box, first row)
@@ -222,6 +230,9 @@ bool bi_anterp_level(bi_handle_s* h, int l, int E, cudaStream_t s);
 void bi_upload_taps(bi_handle_s* h);
 bool bi_translate_level(bi_handle_s* h, int l, int E, cudaStream_t s);
 void bi_build_sai(bi_handle_s* h);
+void bi_operator_launch(bi_handle_s* h, const void* x, void* y, int R, cudaStream_t s);
+void bi_coupling_set(bi_handle_s* h, int64_t n_int, const int* lx_ptr, const int* lx_col, const void* lx_val,
+                     const int* xl_ptr, const int* xl_col, const void* xl_val, bi_qsolve_fn qsolve, void* user);
 void bi_sai_apply(bi_handle_s* h, const void* x, void* y, int R, cudaStream_t s);
 void bi_build_translate_lists(bi_handle_s* h);
 bool bi_leaf_receive_bulk(bi_handle_s* h, void* y, int R, cudaStream_t s);

@@ -309,11 +309,12 @@ struct gmres_ctx_impl {
         const int th = 256;
         if (h->prec == 0) k_cvt_to<double><<<nb(nv, th), th, 0, s>>>(nv, in, (double*)xin);
         else k_cvt_to<float><<<nb(nv, th), th, 0, s>>>(nv, in, (float*)xin);
+        // the operator of Eq. 52 when a coupling is set, else C
         if (h->d_sai) {
             bi_sai_apply(h, xin, zbuf, R, s);
-            bi_matvec_launch(h, zbuf, yout, R, s);
+            bi_operator_launch(h, zbuf, yout, R, s);
         } else {
-            bi_matvec_launch(h, xin, yout, R, s);
+            bi_operator_launch(h, xin, yout, R, s);
         }
         if (h->prec == 0) k_cvt_from<double><<<nb(nv, th), th, 0, s>>>(nv, (const double*)yout, out);
         else k_cvt_from<float><<<nb(nv, th), th, 0, s>>>(nv, (const float*)yout, out);
