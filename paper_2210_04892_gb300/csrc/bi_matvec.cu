@@ -696,118 +696,6 @@ __global__ void __launch_bounds__(256) k_receive_tile(int N, int K, int nph, int
     }
 }
 
-// ------------------------------------------------------------------ fused interpolation (one CTA per parent)
-// U_p = sum_children shift * Interp_phi(Interp_theta(U_c)); child pattern and theta-pass in shared memory,
-// parent outputs accumulated in registers (OPT outputs per thread).
-template <typename T, int OPT>
-__global__ void __launch_bounds__(256) k_interp_fused(int nthc, int nphc, int nthp, int nphp, int E, int pth, int pph,
-                                                      const int* __restrict__ th_src, const int* __restrict__ th_flip,
-                                                      const T* __restrict__ th_w, const int* __restrict__ ph_src,
-                                                      const T* __restrict__ ph_w, const int* __restrict__ child_ptr,
-                                                      const int* __restrict__ octant, const cpx<T>* __restrict__ shift,
-                                                      const cpx<T>* __restrict__ Uc, cpx<T>* __restrict__ Up) {
-    extern __shared__ unsigned char smem_raw[];
-    const int Kc = nthc * nphc, Kp = nthp * nphp;
-    cpx<T>* s1 = reinterpret_cast<cpx<T>*>(smem_raw);   // child [Kc][E]
-    cpx<T>* s2 = s1 + (size_t)Kc * E;                   // theta pass [nthp][nphc][E]
-    const int pb = blockIdx.x;
-    const int half = nphc / 2;
-    const int nout = Kp * E;
-    cpx<T> acc[OPT];
-#pragma unroll
-    for (int i = 0; i < OPT; ++i) acc[i] = czero<T>();
-    for (int cb = child_ptr[pb]; cb < child_ptr[pb + 1]; ++cb) {
-        __syncthreads();
-        const cpx<T>* u = Uc + (int64_t)cb * Kc * E;
-        for (int i = threadIdx.x; i < Kc * E; i += blockDim.x) s1[i] = u[i];
-        __syncthreads();
-        for (int i = threadIdx.x; i < nthp * nphc * E; i += blockDim.x) {
-            const int e = i % E, jc = (i / E) % nphc, ip = i / (E * nphc);
-            cpx<T> a = czero<T>();
-            for (int t = 0; t < pth; ++t) {
-                const int src = th_src[ip * pth + t], f = th_flip[ip * pth + t];
-                const T w = f ? -th_w[ip * pth + t] : th_w[ip * pth + t];
-                const cpx<T> v = s1[((size_t)src * nphc + (f ? (jc + half) % nphc : jc)) * E + e];
-                a.x = fma(w, v.x, a.x);
-                a.y = fma(w, v.y, a.y);
-            }
-            s2[i] = a;
-        }
-        __syncthreads();
-        const cpx<T>* sh = shift + (int64_t)octant[cb] * Kp;
-#pragma unroll
-        for (int o = 0; o < OPT; ++o) {
-            const int i = threadIdx.x + o * blockDim.x;
-            if (i < nout) {
-                const int e = i % E, kk = i / E, ip = kk / nphp, jp = kk % nphp;
-                cpx<T> a = czero<T>();
-                for (int q = 0; q < pph; ++q) {
-                    const T w = ph_w[jp * pph + q];
-                    const cpx<T> v = s2[((size_t)ip * nphc + ph_src[jp * pph + q]) * E + e];
-                    a.x = fma(w, v.x, a.x);
-                    a.y = fma(w, v.y, a.y);
-                }
-                cfma(acc[o], sh[kk], a);
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 0; o < OPT; ++o) {
-        const int i = threadIdx.x + o * blockDim.x;
-        if (i < nout) Up[(int64_t)pb * nout + i] = acc[o];
-    }
-}
-
-// ------------------------------------------------------------------ fused anterpolation (one CTA per parent)
-// V_c += Anterp_theta(Anterp_phi(conj(shift) * V_p)) for every child of the parent.
-template <typename T>
-__global__ void __launch_bounds__(256) k_anterp_fused(int nthc, int nphc, int nthp, int nphp, int E,
-                                                      const int* __restrict__ tph_ptr, const int* __restrict__ tph_dst,
-                                                      const T* __restrict__ tph_w, const int* __restrict__ tth_ptr,
-                                                      const int* __restrict__ tth_dst, const int* __restrict__ tth_flip,
-                                                      const T* __restrict__ tth_w, const int* __restrict__ child_ptr,
-                                                      const int* __restrict__ octant, const cpx<T>* __restrict__ shift,
-                                                      const cpx<T>* __restrict__ Vp, cpx<T>* __restrict__ Vc) {
-    extern __shared__ unsigned char smem_raw[];
-    const int Kc = nthc * nphc, Kp = nthp * nphp;
-    cpx<T>* s0 = reinterpret_cast<cpx<T>*>(smem_raw);   // parent [Kp][E]
-    cpx<T>* s2 = s0 + (size_t)Kp * E;                   // [nthp][nphc][E]
-    const int pb = blockIdx.x;
-    const int half = nphc / 2;
-    const cpx<T>* vp = Vp + (int64_t)pb * Kp * E;
-    for (int i = threadIdx.x; i < Kp * E; i += blockDim.x) s0[i] = vp[i];
-    for (int cb = child_ptr[pb]; cb < child_ptr[pb + 1]; ++cb) {
-        __syncthreads();
-        const cpx<T>* sh = shift + (int64_t)octant[cb] * Kp;
-        for (int i = threadIdx.x; i < nthp * nphc * E; i += blockDim.x) {
-            const int e = i % E, jc = (i / E) % nphc, ip = i / (E * nphc);
-            cpx<T> a = czero<T>();
-            for (int q = tph_ptr[jc]; q < tph_ptr[jc + 1]; ++q) {
-                const int kk = ip * nphp + tph_dst[q];
-                const cpx<T> v = cmulc(sh[kk], s0[(size_t)kk * E + e]);
-                const T w = tph_w[q];
-                a.x = fma(w, v.x, a.x);
-                a.y = fma(w, v.y, a.y);
-            }
-            s2[i] = a;
-        }
-        __syncthreads();
-        cpx<T>* vc = Vc + (int64_t)cb * Kc * E;
-        for (int i = threadIdx.x; i < Kc * E; i += blockDim.x) {
-            const int e = i % E, kk = i / E, ic = kk / nphc, jc = kk % nphc;
-            cpx<T> a = czero<T>();
-            for (int q = tth_ptr[ic]; q < tth_ptr[ic + 1]; ++q) {
-                const int f = tth_flip[q];
-                const T w = f ? -tth_w[q] : tth_w[q];
-                const cpx<T> v = s2[((size_t)tth_dst[q] * nphc + (f ? (jc + half) % nphc : jc)) * E + e];
-                a.x = fma(w, v.x, a.x);
-                a.y = fma(w, v.y, a.y);
-            }
-            vc[i] = cadd(vc[i], a);
-        }
-    }
-}
-
 // ------------------------------------------------------------------ per-child interpolation / anterpolation
 // One CTA per child box; the child's pattern, the pass intermediate and the interpolation
 // tables live in shared memory, so every tap is a shared-memory read.
@@ -1196,44 +1084,6 @@ void launch_near_any(bi_handle_s* h, const cpx<T>* x, cpx<T>* yt, cpx<T>* yuser,
     else launch_near_stream<T, MODE, 8>(h, x, yt, yuser, R, s);
 }
 
-template <typename T, int OPT>
-bool try_interp_fused(bi_handle_s* h, int l, int E, cudaStream_t s) {
-    level_t& P = h->lev[l];
-    level_t& C = h->lev[l + 1];
-    interp_t& I = h->itp[l];
-    if ((int64_t)P.K * E > (int64_t)256 * OPT) return false;
-    size_t smem = ((size_t)C.K * E + (size_t)P.nth * C.nph * E) * sizeof(cpx<T>);
-    if (smem > 160 * 1024) return false;
-    auto kern = k_interp_fused<T, OPT>;
-    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<P.nbox, 256, smem, s>>>(C.nth, C.nph, P.nth, P.nph, E, I.p_th, I.p_ph, I.d_th_src, I.d_th_flip,
-                                   (const T*)I.d_th_w, I.d_ph_src, (const T*)I.d_ph_w, P.d_child_ptr, C.d_octant,
-                                   (const cpx<T>*)P.d_shift, (const cpx<T>*)C.d_U, (cpx<T>*)P.d_U);
-    CU(cudaGetLastError());
-    return true;
-}
-
-template <typename T>
-bool interp_fused(bi_handle_s* h, int l, int E, cudaStream_t s) {
-    return try_interp_fused<T, 1>(h, l, E, s) || try_interp_fused<T, 2>(h, l, E, s) || try_interp_fused<T, 4>(h, l, E, s) ||
-           try_interp_fused<T, 8>(h, l, E, s) || try_interp_fused<T, 16>(h, l, E, s);
-}
-
-template <typename T>
-bool anterp_fused(bi_handle_s* h, int l, int E, cudaStream_t s) {
-    level_t& P = h->lev[l];
-    level_t& C = h->lev[l + 1];
-    interp_t& I = h->itp[l];
-    size_t smem = ((size_t)P.K * E + (size_t)P.nth * C.nph * E) * sizeof(cpx<T>);
-    if (smem > 160 * 1024) return false;
-    auto kern = k_anterp_fused<T>;
-    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<P.nbox, 256, smem, s>>>(C.nth, C.nph, P.nth, P.nph, E, I.d_tph_ptr, I.d_tph_dst, (const T*)I.d_tph_w,
-                                   I.d_tth_ptr, I.d_tth_dst, I.d_tth_flip, (const T*)I.d_tth_w, P.d_child_ptr, C.d_octant,
-                                   (const cpx<T>*)P.d_shift, (const cpx<T>*)P.d_V, (cpx<T>*)C.d_V);
-    CU(cudaGetLastError());
-    return true;
-}
 
 
 template <typename T>
