@@ -1,6 +1,6 @@
 """Compile the CPU oracle (plain C, FP64, OpenMP) into oracle/_bi_oracle.so.
 
-Test infrastructure: builds the checker, not the product.
+Test infrastructure: builds the oracle library that the tests compare against, not the product.
 """
 import os
 import subprocess
