@@ -249,6 +249,33 @@ const char* bi_server_last_error(bi_server s);
 /* Stop the threads and free every request and buffer. */
 void bi_server_destroy(bi_server s);
 
+/* Host-only plan (inspection of the set-up, no counterpart in the paper): the RWG numbering,
+ * octree, near and interaction lists, parent-centred translation lists, angular sampling and
+ * interpolation tables that bi_setup builds, computed on the host with no device and no CUDA
+ * call.  Same mesh and parameter rules as bi_setup; BI_ERR_MESH / BI_ERR_ARG as there.
+ * bi_plan_get copies one array to `out` (`bytes` long; NULL out only reports the element
+ * count in *count).  Element type int32 unless marked (double):
+ *    0 leaf_start [nbox_leaf + 1]   1 near_ptr [nbox_leaf + 1]   2 near_src
+ *    3 coords [nbox][3] of `level`  4 parent [nbox] of `level` >= 1
+ *    5 child_ptr [nbox + 1] of `level` (children at level + 1)
+ *    6 il_ptr, 7 il_src, 8 il_off (offset code (ox+3)*49 + (oy+3)*7 + (oz+3), ox = receiver - source)
+ *      of translation `level` >= 2
+ *    9 parent-centred list pointers [nbox(level-1) + 1], 10 its sources, 11 its codes [entries][8]
+ *      (65535: the child slot has no interaction with that source)
+ *   12 perm [N] (tree position -> RWG index)
+ *   13 edges [N][2] (vertex ids of the edge of each RWG), 14 T+ [N], 15 T- [N] (its triangles)
+ *   20 theta nodes (double), 21 theta weights in cos(theta) (double) of `level` >= 2
+ *   22 th_src, 23 th_flip, 24 th_w (double): theta taps [nth(level)][p] from level + 1 to level
+ *   25 ph_src, 26 ph_w (double): phi taps [nph(level)][p]
+ *   27 tth_ptr, 28 tth_dst, 29 tth_flip, 30 tth_w (double): transposed theta lists per child row
+ *   31 tph_ptr, 32 tph_dst, 33 tph_w (double): transposed phi lists per child column */
+typedef struct bi_plan_s* bi_plan;
+int bi_plan_create(const double* verts, int nv, const int* tris, int nt, double k0, const bi_params* opt, bi_plan* out);
+int bi_plan_info(bi_plan p, bi_info_t* info);
+int bi_plan_get(bi_plan p, int what, int level, void* out, int64_t bytes, int64_t* count);
+const char* bi_plan_last_error(void);
+void bi_plan_destroy(bi_plan p);
+
 /* Text of the last error on h (or of the last failed bi_setup when h is NULL). */
 const char* bi_last_error(bi_handle h);
 

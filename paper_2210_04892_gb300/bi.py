@@ -27,7 +27,8 @@ _NAMES = {0: "BI_OK", -1: "BI_ERR_ARG", -2: "BI_ERR_MESH", -3: "BI_ERR_OOM", -4:
 
 # entry points declared in include/bi.h
 EXPORTS = ["bi_default_params", "bi_setup", "bi_num_unknowns", "bi_rwg_edges", "bi_get_info", "bi_matvec",
-           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_profile_stages", "bi_stage_name", "bi_last_error", "bi_device_status", "bi_set_coupling", "bi_matvec_coupled",
+           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_profile_stages", "bi_stage_name", "bi_last_error", "bi_device_status", "bi_set_coupling", "bi_matvec_coupled", "bi_plan_create", "bi_plan_info", "bi_plan_get",
+           "bi_plan_last_error", "bi_plan_destroy",
            "bi_destroy", "bi_server_default_params", "bi_server_create", "bi_submit", "bi_poll", "bi_result",
            "bi_release", "bi_server_last_error", "bi_server_destroy"]
 
@@ -103,6 +104,13 @@ def load(path: str = LIB_PATH):
     L.bi_device_status.argtypes = [vp]
     L.bi_set_coupling.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, QSOLVE, vp]
     L.bi_matvec_coupled.argtypes = [vp, vp, vp, i]
+    L.bi_plan_create.argtypes = [vp, i, vp, i, d, ctypes.POINTER(Params), ctypes.POINTER(vp)]
+    L.bi_plan_info.argtypes = [vp, ctypes.POINTER(Info)]
+    L.bi_plan_get.argtypes = [vp, i, i, vp, i64, ctypes.POINTER(i64)]
+    L.bi_plan_last_error.argtypes = []
+    L.bi_plan_last_error.restype = ctypes.c_char_p
+    L.bi_plan_destroy.argtypes = [vp]
+    L.bi_plan_destroy.restype = None
     L.bi_destroy.argtypes = [vp]
     L.bi_destroy.restype = None
     L.bi_server_default_params.argtypes = [ctypes.POINTER(ServerParams)]
@@ -417,6 +425,55 @@ class Server:
     def close(self):
         if getattr(self, "h", None):
             load().bi_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_PLAN_DOUBLE = {20, 21, 24, 26, 30, 33}
+
+
+class Plan:
+    """Host-only plan of the set-up (bi_plan_*): lists and tables as numpy arrays, no GPU."""
+
+    def __init__(self, verts, tris, k0, digits=3, op_mode=0, leaf_box=0.25, levels=0, interp_order=10):
+        L = load()
+        p = default_params()
+        p.digits, p.leaf_box, p.levels, p.interp_order = int(digits), float(leaf_box), int(levels), int(interp_order)
+        p.op_mode = int(op_mode)
+        v = np.ascontiguousarray(verts, np.float64)
+        t = np.ascontiguousarray(tris, np.int32)
+        h = ctypes.c_void_p()
+        rc = L.bi_plan_create(v.ctypes.data, len(v), t.ctypes.data, len(t), float(k0), ctypes.byref(p), ctypes.byref(h))
+        if rc != BI_OK:
+            raise BIError(rc, L.bi_plan_last_error().decode())
+        self.h = h
+
+    def info(self) -> dict:
+        I = Info()
+        _check(load().bi_plan_info(self.h, ctypes.byref(I)), None)
+        nl = I.levels
+        return dict(n_rwg=I.n_rwg, n_unknowns=I.n_unknowns, levels=nl, leaf_level=I.leaf_level,
+                    boxes=list(I.boxes[:nl]), L=list(I.L[:nl]), K=list(I.K[:nl]), near_pairs=I.near_pairs,
+                    interactions=list(I.interactions[:nl]), root_size=I.root_size)
+
+    def get(self, what, level=0):
+        L = load()
+        n = ctypes.c_int64()
+        rc = L.bi_plan_get(self.h, int(what), int(level), None, 0, ctypes.byref(n))
+        if rc != BI_OK:
+            raise BIError(rc, "bi_plan_get(%d, %d)" % (what, level))
+        out = np.zeros(n.value, np.float64 if what in _PLAN_DOUBLE else np.int32)
+        _check(L.bi_plan_get(self.h, int(what), int(level), out.ctypes.data, out.nbytes, ctypes.byref(n)), None)
+        return out
+
+    def close(self):
+        if self.h:
+            load().bi_plan_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbi_gb300.so")
-SOURCES = ["bi_setup_host.cu", "bi_setup_device.cu", "bi_matvec.cu", "bi_leaf.cu", "bi_interp.cu", "bi_translate.cu", "bi_sai.cu", "bi_coupling.cu", "bi_solve.cu", "bi_farfield.cu", "bi_server.cu", "bi_api.cu"]
+SOURCES = ["bi_setup_host.cu", "bi_setup_device.cu", "bi_matvec.cu", "bi_leaf.cu", "bi_interp.cu", "bi_translate.cu", "bi_sai.cu", "bi_coupling.cu", "bi_plan.cu", "bi_solve.cu", "bi_farfield.cu", "bi_server.cu", "bi_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -62,6 +62,8 @@ struct level_t {
     // parent-centred interaction lists (translation level l, parents at l - 1): per parent its
     // children range, and per source box the offset codes to each child (0xFFFF: near or none)
     int tp_np = 0;
+    std::vector<int> tp_ptr, tp_src;    // host copies of the lists below
+    std::vector<unsigned short> tp_code;
     int* d_tp_cptr = nullptr;           // [np + 1] children of each parent (level-l indices)
     int* d_tp_ptr = nullptr;            // [np + 1] source entries of each parent
     int* d_tp_src = nullptr;            // [entries] source box
@@ -235,6 +237,7 @@ void bi_coupling_set(bi_handle_s* h, int64_t n_int, const int* lx_ptr, const int
                      const int* xl_ptr, const int* xl_col, const void* xl_val, bi_qsolve_fn qsolve, void* user);
 void bi_sai_apply(bi_handle_s* h, const void* x, void* y, int R, cudaStream_t s);
 void bi_build_translate_lists(bi_handle_s* h);
+void bi_plan_translate_lists(bi_handle_s* h);   // host part of bi_build_translate_lists
 bool bi_leaf_receive_bulk(bi_handle_s* h, void* y, int R, cudaStream_t s);
 int bi_take_device_status(bi_handle_s* h);
 size_t bi_farfield_scratch_bytes(const bi_handle_s* h, int nrhs, int ndir);

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "bi_cpx.cuh"
@@ -98,7 +99,7 @@ inline uint64_t ckey(int x, int y, int z) {
 
 }  // namespace
 
-void bi_build_translate_lists(bi_handle_s* h) {
+void bi_plan_translate_lists(bi_handle_s* h) {
     for (int l = 2; l <= h->leaf; ++l) {
         level_t& C = h->lev[l];
         const level_t& P = h->lev[l - 1];
@@ -140,13 +141,24 @@ void bi_build_translate_lists(bi_handle_s* h) {
                     }
             tptr[p + 1] = (int)src.size();
         }
-        std::vector<int> cptr(P.child_ptr.begin(), P.child_ptr.end());
         C.tp_np = P.nbox;
+        C.tp_ptr = std::move(tptr);
+        C.tp_src = std::move(src);
+        C.tp_code = std::move(code);
+    }
+}
+
+void bi_build_translate_lists(bi_handle_s* h) {
+    bi_plan_translate_lists(h);
+    for (int l = 2; l <= h->leaf; ++l) {
+        level_t& C = h->lev[l];
+        const level_t& P = h->lev[l - 1];
+        std::vector<int> cptr(P.child_ptr.begin(), P.child_ptr.end());
         C.d_tp_cptr = h->upload(cptr);
-        C.d_tp_ptr = h->upload(tptr);
-        if (!src.empty()) {
-            C.d_tp_src = h->upload(src);
-            C.d_tp_code = h->upload(code);
+        C.d_tp_ptr = h->upload(C.tp_ptr);
+        if (!C.tp_src.empty()) {
+            C.d_tp_src = h->upload(C.tp_src);
+            C.d_tp_code = h->upload(C.tp_code);
         } else {
             C.d_tp_src = (int*)h->alloc(sizeof(int));
             C.d_tp_code = h->alloc(16);

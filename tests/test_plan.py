@@ -1,0 +1,338 @@
+"""Host-only checks of the set-up of the multilevel product (bi_plan_*): RWG numbering, octree,
+near and interaction lists of the MLFMA (Sec. II.D), parent-centred translation lists, angular
+sampling and Lagrange interpolation between levels.  The plan runs the same host code as
+bi_setup without a device, so these run on any machine; every expected value below follows
+from geometry or from the mathematics of the quadrature and the interpolation, not from the
+library."""
+import numpy as np
+import pytest
+
+from paper_2210_04892_gb300 import inputs
+
+K0 = 2 * np.pi          # wavelength 1
+NONE = 0xFFFF
+
+
+@pytest.fixture(scope="module")
+def bi():
+    from paper_2210_04892_gb300 import bi as mod
+    try:
+        mod.load()
+    except (ImportError, OSError) as e:  # pragma: no cover - library not built here
+        pytest.skip(f"library not loadable: {e}")
+    return mod
+
+
+@pytest.fixture(scope="module")
+def sphere():
+    # sphere of radius 2 wavelengths: 5 levels with 0.25-wavelength leaves (far field on 2..4)
+    v, t = inputs.icosphere(20, radius=2.0)
+    return v, t
+
+
+@pytest.fixture(scope="module")
+def plan(bi, sphere):
+    v, t = sphere
+    p = bi.Plan(v, t, K0, digits=3)
+    yield p
+    p.close()
+
+
+def ancestors(plan, info):
+    """anc[l][leaf box] = its ancestor at level l."""
+    lf = info["leaf_level"]
+    anc = {lf: np.arange(info["boxes"][lf])}
+    for l in range(lf, 0, -1):
+        anc[l - 1] = plan.get(4, l)[anc[l]]
+    return anc
+
+
+def test_rwg_numbering_is_the_interior_edges(plan, sphere):
+    v, t = sphere
+    info = plan.info()
+    edges = plan.get(13).reshape(-1, 2)
+    tp, tm = plan.get(14), plan.get(15)
+    assert info["n_rwg"] == len(edges) == 3 * len(t) // 2     # closed surface: every edge shared
+    assert info["n_unknowns"] == 2 * info["n_rwg"]             # J and M per RWG (Eq. 42)
+    # each RWG's edge belongs to both of its triangles, traversed a -> b in T+ and b -> a in T-
+    for n in range(0, len(edges), 97):
+        a, b = edges[n]
+        for tri, fwd in ((t[tp[n]], True), (t[tm[n]], False)):
+            cyc = list(tri) + [tri[0]]
+            pairs = {(cyc[k], cyc[k + 1]) for k in range(3)}
+            assert ((a, b) in pairs) == fwd and ((b, a) in pairs) == (not fwd)
+    assert len({(int(a), int(b)) for a, b in edges}) == len(edges)
+
+
+def test_octree_boxes_hold_their_rwgs(plan, sphere):
+    v, _ = sphere
+    info = plan.info()
+    lf = info["leaf_level"]
+    assert info["levels"] == 5 and lf == 4
+    perm = plan.get(12)
+    assert np.array_equal(np.sort(perm), np.arange(info["n_rwg"]))
+    start = plan.get(0)
+    assert start[0] == 0 and start[-1] == info["n_rwg"] and np.all(np.diff(start) > 0)
+    coords = plan.get(3, lf).reshape(-1, 3)
+    edges = plan.get(13).reshape(-1, 2)
+    mid = 0.5 * (v[edges[:, 0]] + v[edges[:, 1]])
+    a = info["root_size"] / 2**lf
+    assert a == pytest.approx(0.25)
+    lo = 0.5 * (mid.min(0) + mid.max(0)) - 0.5 * info["root_size"]
+    for b in range(len(coords)):
+        m = mid[perm[start[b]:start[b + 1]]]
+        cell = np.clip(np.floor((m - lo) / a).astype(int), 0, 2**lf - 1)
+        assert np.all(cell == coords[b])
+    # parents hold their children contiguously, each child's cell inside its parent's
+    for l in range(1, lf + 1):
+        par = plan.get(4, l)
+        cp = plan.get(5, l - 1)
+        assert np.all(np.diff(par) >= 0)
+        assert np.array_equal(np.repeat(np.arange(len(cp) - 1), np.diff(cp)), par)
+        assert np.all(np.diff(cp) <= 8) and np.all(np.diff(cp) >= 1)
+        c = plan.get(3, l).reshape(-1, 3)
+        pc = plan.get(3, l - 1).reshape(-1, 3)
+        assert np.array_equal(c >> 1, pc[par])
+
+
+def test_near_and_interactions_cover_every_pair_once(plan):
+    """Sec. II.D: a pair of leaf boxes is handled exactly once, either by the near-field blocks
+    (touching boxes) or by one translation between ancestors that are not neighbours but whose
+    parents are."""
+    info = plan.info()
+    lf = info["leaf_level"]
+    nb = info["boxes"][lf]
+    anc = ancestors(plan, info)
+    cover = np.zeros((nb, nb), np.int32)
+    nptr, nsrc = plan.get(1), plan.get(2)
+    for b in range(nb):
+        cover[b, nsrc[nptr[b]:nptr[b + 1]]] += 1
+    coords_lf = plan.get(3, lf).reshape(-1, 3)
+    for b in range(nb):
+        s = nsrc[nptr[b]:nptr[b + 1]]
+        assert np.all(np.abs(coords_lf[s] - coords_lf[b]).max(1) <= 1)
+    total = 0
+    for l in range(2, lf + 1):
+        ptr, src = plan.get(6, l), plan.get(7, l)
+        total += len(src)
+        assert info["interactions"][l] == len(src)
+        members = [np.flatnonzero(anc[l] == c) for c in range(info["boxes"][l])]
+        for c in range(info["boxes"][l]):
+            rows = members[c]
+            for s in src[ptr[c]:ptr[c + 1]]:
+                cover[np.ix_(rows, members[s])] += 1
+    assert total > 0
+    assert np.all(cover == 1), np.unique(cover, return_counts=True)
+
+
+def test_interaction_offsets_match_box_coordinates(plan):
+    info = plan.info()
+    for l in range(2, info["leaf_level"] + 1):
+        c = plan.get(3, l).reshape(-1, 3)
+        par = plan.get(4, l)
+        pc = plan.get(3, l - 1).reshape(-1, 3)
+        ptr, src, off = plan.get(6, l), plan.get(7, l), plan.get(8, l)
+        recv = np.repeat(np.arange(len(ptr) - 1), np.diff(ptr))
+        o = c[recv] - c[src]
+        assert np.array_equal(off, (o[:, 0] + 3) * 49 + (o[:, 1] + 3) * 7 + (o[:, 2] + 3))
+        cheb = np.abs(o).max(1)
+        assert np.all(cheb >= 2) and np.all(cheb <= 3)
+        assert np.all(np.abs(pc[par[recv]] - pc[par[src]]).max(1) <= 1)
+
+
+def test_parent_centred_lists_equal_the_interaction_lists(plan):
+    info = plan.info()
+    for l in range(2, info["leaf_level"] + 1):
+        cp = plan.get(5, l - 1)
+        ptr, src, off = plan.get(6, l), plan.get(7, l), plan.get(8, l)
+        tptr, tsrc = plan.get(9, l), plan.get(10, l)
+        tcode = plan.get(11, l).reshape(-1, 8)
+        assert len(tptr) == len(cp) and len(tsrc) == len(tcode)
+        n_live = 0
+        for p in range(len(cp) - 1):
+            for j in range(8):
+                if cp[p] + j >= cp[p + 1]:
+                    assert np.all(tcode[tptr[p]:tptr[p + 1], j] == NONE)
+                    continue
+                b = cp[p] + j
+                got = {(int(s), int(k)) for s, k in zip(tsrc[tptr[p]:tptr[p + 1]], tcode[tptr[p]:tptr[p + 1], j])
+                       if k != NONE}
+                want = {(int(s), int(k)) for s, k in zip(src[ptr[b]:ptr[b + 1]], off[ptr[b]:ptr[b + 1]])}
+                assert got == want, (l, p, j)
+                n_live += len(got)
+        assert n_live == len(src)
+        # no source entry without a live slot, and no source twice for one parent
+        assert np.all((tcode != NONE).any(1))
+        for p in range(len(cp) - 1):
+            s = tsrc[tptr[p]:tptr[p + 1]]
+            assert len(np.unique(s)) == len(s)
+
+
+def test_theta_sampling_is_gauss_legendre(plan):
+    info = plan.info()
+    for l in range(2, info["leaf_level"] + 1):
+        th, w = plan.get(20, l), plan.get(21, l)
+        L = info["L"][l]
+        assert len(th) == L + 1 and info["K"][l] == (L + 1) * 2 * (L + 1)
+        assert np.all(np.diff(th) > 0) and th[0] > 0 and th[-1] < np.pi
+        x = np.cos(th)
+        assert np.allclose(x, -x[::-1], atol=1e-14) and np.allclose(w, w[::-1], rtol=1e-12)
+        # exact for polynomials of degree 2n - 1 in cos(theta)
+        for k in range(2 * len(x)):
+            exact = 2.0 / (k + 1) if k % 2 == 0 else 0.0
+            assert abs(np.dot(w, x**k) - exact) < 1e-12, (l, k)
+        # the bandwidth covers at least the box diagonal k*sqrt(3)*a (excess-bandwidth rule)
+        a = info["root_size"] / 2**l
+        assert L >= K0 * np.sqrt(3) * a
+    Ls = [info["L"][l] for l in range(2, info["leaf_level"] + 1)]
+    assert all(p > c for p, c in zip(Ls, Ls[1:]))
+
+
+def interp_matrices(plan, l, nth_c, nph_c, nth_p, nph_p):
+    """Dense theta and phi interpolation of the transverse components from level l + 1 to l,
+    as the tap lists define them (a theta tap with the flip bit reads the column half a turn
+    away and negates both components)."""
+    src, flip, w = plan.get(22, l), plan.get(23, l), plan.get(24, l)
+    p_th = len(src) // nth_p
+    Kc = nth_c * nph_c
+    A = np.zeros((nth_p * nph_c, Kc))
+    for ip in range(nth_p):
+        for t in range(p_th):
+            e = ip * p_th + t
+            for jc in range(nph_c):
+                jj = (jc + nph_c // 2) % nph_c if flip[e] else jc
+                A[ip * nph_c + jc, src[e] * nph_c + jj] += -w[e] if flip[e] else w[e]
+    ps, pw = plan.get(25, l), plan.get(26, l)
+    p_ph = len(ps) // nph_p
+    B = np.zeros((nph_p, nph_c))
+    for jp in range(nph_p):
+        for q in range(p_ph):
+            B[jp, ps[jp * p_ph + q]] += pw[jp * p_ph + q]
+    return A, B, p_th, p_ph
+
+
+def transverse_field(theta, phi, k0, sources):
+    """Theta and phi components of sum_i (I - k k) p_i exp(j k0 k . r_i) on a (theta, phi) grid:
+    the radiation pattern of a few point dipoles, a smooth transverse field on the sphere."""
+    T, P = np.meshgrid(theta, phi, indexing="ij")
+    kh = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], -1)
+    th = np.stack([np.cos(T) * np.cos(P), np.cos(T) * np.sin(P), -np.sin(T)], -1)
+    ph = np.stack([-np.sin(P), np.cos(P), np.zeros_like(P)], -1)
+    F = np.zeros(T.shape + (3,), complex)
+    for r, pvec in sources:
+        F += np.exp(1j * k0 * kh @ r)[..., None] * pvec
+    return np.sum(F * th, -1), np.sum(F * ph, -1)
+
+
+def test_interpolation_weights_and_transposes(plan):
+    info = plan.info()
+    for l in range(2, info["leaf_level"]):
+        nth_c, nph_c = info["L"][l + 1] + 1, 2 * (info["L"][l + 1] + 1)
+        nth_p, nph_p = info["L"][l] + 1, 2 * (info["L"][l] + 1)
+        src, flip, w = plan.get(22, l), plan.get(23, l), plan.get(24, l)
+        ps, pw = plan.get(25, l), plan.get(26, l)
+        p_th, p_ph = len(src) // nth_p, len(ps) // nph_p
+        assert p_th == min(10, nth_c) and p_ph == min(10, nph_c)
+        # Lagrange weights reproduce constants
+        assert np.allclose(w.reshape(nth_p, p_th).sum(1), 1.0, atol=1e-12)
+        assert np.allclose(pw.reshape(nph_p, p_ph).sum(1), 1.0, atol=1e-12)
+        assert np.all((src >= 0) & (src < nth_c)) and np.all((ps >= 0) & (ps < nph_c))
+        # the transposed lists are exactly the transposes of the forward lists
+        fwd = {}
+        for ip in range(nth_p):
+            for t in range(p_th):
+                e = ip * p_th + t
+                key = (int(src[e]), ip, int(flip[e]))
+                fwd[key] = fwd.get(key, 0.0) + w[e]
+        tptr, tdst, tflip, tw = plan.get(27, l), plan.get(28, l), plan.get(29, l), plan.get(30, l)
+        assert len(tptr) == nth_c + 1 and tptr[-1] == len(src)
+        back = {}
+        for ic in range(nth_c):
+            for q in range(tptr[ic], tptr[ic + 1]):
+                key = (ic, int(tdst[q]), int(tflip[q]))
+                back[key] = back.get(key, 0.0) + tw[q]
+        assert fwd.keys() == back.keys()
+        assert all(abs(fwd[k] - back[k]) < 1e-15 for k in fwd)
+        fph, bph = np.zeros((nph_p, nph_c)), np.zeros((nph_p, nph_c))
+        for jp in range(nph_p):
+            for q in range(p_ph):
+                fph[jp, ps[jp * p_ph + q]] += pw[jp * p_ph + q]
+        pptr, pdst, pwt = plan.get(31, l), plan.get(32, l), plan.get(33, l)
+        assert len(pptr) == nph_c + 1
+        for jc in range(nph_c):
+            for q in range(pptr[jc], pptr[jc + 1]):
+                bph[pdst[q], jc] += pwt[q]
+        assert np.allclose(fph, bph, rtol=0, atol=1e-15)
+
+
+def interp_error(plan, info, l, sources, drop_reflection_sign=False):
+    """Largest error, relative to the field's peak, of interpolating the dipole pattern from
+    the level-(l + 1) grid to the level-l grid through the plan's tap lists."""
+    Lc, Lp = info["L"][l + 1], info["L"][l]
+    nth_c, nph_c, nth_p, nph_p = Lc + 1, 2 * (Lc + 1), Lp + 1, 2 * (Lp + 1)
+    th_c, th_p = plan.get(20, l + 1), plan.get(20, l)
+    ph_c = 2 * np.pi * np.arange(nph_c) / nph_c
+    ph_p = 2 * np.pi * np.arange(nph_p) / nph_p
+    A, B, _, _ = interp_matrices(plan, l, nth_c, nph_c, nth_p, nph_p)
+    if drop_reflection_sign:
+        A = np.abs(A)
+    ref = transverse_field(th_p, ph_p, K0, sources)
+    scale = max(np.abs(r).max() for r in ref)
+    err = 0.0
+    for comp, r in zip(transverse_field(th_c, ph_c, K0, sources), ref):
+        out = (A @ comp.reshape(-1)).reshape(nth_p, nph_c) @ B.T
+        err = max(err, np.abs(out - r).max() / scale)
+    return err
+
+
+def dipoles_in_box(rng, a, count=6):
+    out = []
+    for _ in range(count):
+        d = rng.normal(size=3)
+        out.append((0.5 * a * rng.uniform(-1, 1, 3), d / np.linalg.norm(d)))
+    return out
+
+
+def test_interpolation_of_a_transverse_field_across_the_poles(plan):
+    """Interpolating the pattern of dipoles inside a child box to the parent's denser grid
+    (theta pass with pole reflection, then phi) reproduces the field sampled directly.  The
+    reflection sign matters: dropping it leaves O(1) errors near the poles."""
+    info = plan.info()
+    rng = np.random.default_rng(inputs.SEED_BASE + 77)
+    for l in range(2, info["leaf_level"]):
+        src = dipoles_in_box(rng, info["root_size"] / 2 ** (l + 1))
+        # order-10 local Lagrange on the excess-bandwidth grids: a few 1e-6 measured
+        assert interp_error(plan, info, l, src) < 5e-5, l
+        assert interp_error(plan, info, l, src, drop_reflection_sign=True) > 1e-2, l
+
+
+def test_interpolation_error_falls_with_the_order(bi, sphere):
+    v, t = sphere
+    rng = np.random.default_rng(inputs.SEED_BASE + 78)
+    errs = []
+    for order in (4, 6, 10):
+        p = bi.Plan(v, t, K0, digits=3, interp_order=order)
+        info = p.info()
+        src = dipoles_in_box(np.random.default_rng(inputs.SEED_BASE + 78), info["root_size"] / 2**3)
+        errs.append(interp_error(p, info, 2, src))
+        p.close()
+    assert errs[0] > errs[1] > errs[2], errs
+    assert errs[0] / errs[2] > 30, errs
+
+
+def test_plan_rejects_open_and_bad_meshes(bi):
+    v, t = inputs.icosphere(4)
+    with pytest.raises(bi.BIError):
+        bi.Plan(v, t[:-1], K0)                    # one triangle removed: open surface
+    bad = t.copy()
+    bad[0] = bad[0][::-1]
+    with pytest.raises(bi.BIError):
+        bi.Plan(v, bad, K0)                       # inconsistent orientation
+    with pytest.raises(bi.BIError):
+        bi.Plan(v, t, -1.0)
+    p = bi.Plan(v, t, K0)
+    with pytest.raises(bi.BIError):
+        p.get(99)
+    with pytest.raises(bi.BIError):
+        p.get(6, 1)                               # no interaction list above level 2
+    p.close()
