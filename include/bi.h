@@ -268,7 +268,9 @@ void bi_server_destroy(bi_server s);
  *   22 th_src, 23 th_flip, 24 th_w (double): theta taps [nth(level)][p] from level + 1 to level
  *   25 ph_src, 26 ph_w (double): phi taps [nph(level)][p]
  *   27 tth_ptr, 28 tth_dst, 29 tth_flip, 30 tth_w (double): transposed theta lists per child row
- *   31 tph_ptr, 32 tph_dst, 33 tph_w (double): transposed phi lists per child column */
+ *   31 tph_ptr, 32 tph_dst, 33 tph_w (double): transposed phi lists per child column
+ *   40 distance index [343] of each offset code of translation `level` (-1: touching offset)
+ *   41 spherical Hankel values (double) [distances][L + 1][2]: h_n^(2)(k|X|) as (re, im) */
 typedef struct bi_plan_s* bi_plan;
 int bi_plan_create(const double* verts, int nv, const int* tris, int nt, double k0, const bi_params* opt, bi_plan* out);
 int bi_plan_info(bi_plan p, bi_info_t* info);

@@ -434,7 +434,7 @@ class Server:
             pass
 
 
-_PLAN_DOUBLE = {20, 21, 24, 26, 30, 33}
+_PLAN_DOUBLE = {20, 21, 24, 26, 30, 33, 41}
 
 
 class Plan:

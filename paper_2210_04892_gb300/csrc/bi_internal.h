@@ -221,6 +221,10 @@ void bi_device_geometry(bi_handle_s* h, const double* V, const int* T);
 void bi_fill_near(bi_handle_s* h);
 void bi_fill_patterns(bi_handle_s* h);
 void bi_fill_translations(bi_handle_s* h);
+// Host part of the translation operators of level l: for each of the 343 offset codes the index
+// of its distance |X| (-1 for touching offsets), and per distance h_n^(2)(k|X|), n = 0..L, as
+// interleaved (re, im) pairs.
+void bi_translation_series(const bi_handle_s* h, int l, std::vector<int>& dist_idx, std::vector<double>& hk);
 void bi_alloc_work(bi_handle_s* h);
 void bi_matvec_launch(bi_handle_s* h, const void* x, void* y, int nrhs, cudaStream_t s);
 void bi_rhs_launch(bi_handle_s* h, const double* khat, const double* phat, int nrhs, void* b);

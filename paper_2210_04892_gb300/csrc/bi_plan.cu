@@ -122,6 +122,14 @@ extern "C" int bi_plan_get(bi_plan p, int what, int level, void* out, int64_t by
         case 31: return itp_ok ? put(h.itp[level].tph_ptr, out, bytes, count) : BI_ERR_ARG;
         case 32: return itp_ok ? put(h.itp[level].tph_dst, out, bytes, count) : BI_ERR_ARG;
         case 33: return itp_ok ? put(h.itp[level].tph_w, out, bytes, count) : BI_ERR_ARG;
+        case 40:
+        case 41: {
+            if (!far_ok) return BI_ERR_ARG;
+            std::vector<int> di;
+            std::vector<double> hk;
+            bi_translation_series(&h, level, di, hk);
+            return what == 40 ? put(di, out, bytes, count) : put(hk, out, bytes, count);
+        }
         default: return BI_ERR_ARG;
     }
 }

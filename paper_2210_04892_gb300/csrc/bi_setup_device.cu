@@ -876,6 +876,32 @@ void hankel2(int L, double x, std::vector<double>& out) {
 
 }  // namespace
 
+void bi_translation_series(const bi_handle_s* h, int l, std::vector<int>& dist_idx, std::vector<double>& hk) {
+    const level_t& L = h->lev[l];
+    // distinct offset lengths |X|^2 = a^2 (ox^2 + oy^2 + oz^2)
+    dist_idx.assign(343, -1);
+    std::vector<int> sq_of;
+    for (int o = 0; o < 343; ++o) {
+        int ox = o / 49 - 3, oy = (o / 7) % 7 - 3, oz = o % 7 - 3;
+        if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
+        int sq = ox * ox + oy * oy + oz * oz;
+        auto it = std::find(sq_of.begin(), sq_of.end(), sq);
+        if (it == sq_of.end()) {
+            dist_idx[o] = (int)sq_of.size();
+            sq_of.push_back(sq);
+        } else {
+            dist_idx[o] = (int)(it - sq_of.begin());
+        }
+    }
+    hk.clear();
+    hk.reserve(sq_of.size() * 2 * (L.L + 1));
+    for (int sq : sq_of) {
+        std::vector<double> one;
+        hankel2(L.L, h->k * L.a * std::sqrt((double)sq), one);
+        hk.insert(hk.end(), one.begin(), one.end());
+    }
+}
+
 // ---------------------------------------------------------------------------------
 void bi_device_geometry(bi_handle_s* h, const double* V, const int* Tm) {
     const int nt = h->nt, N = h->N;
@@ -1209,27 +1235,9 @@ void bi_fill_patterns(bi_handle_s* h) {
 void bi_fill_translations(bi_handle_s* h) {
     for (int l = 2; l <= h->leaf; ++l) {
         level_t& L = h->lev[l];
-        // distinct offset lengths |X|^2 = a^2 (ox^2 + oy^2 + oz^2)
-        std::vector<int> dist_idx(343, -1), sq_of;
-        for (int o = 0; o < 343; ++o) {
-            int ox = o / 49 - 3, oy = (o / 7) % 7 - 3, oz = o % 7 - 3;
-            if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
-            int sq = ox * ox + oy * oy + oz * oz;
-            auto it = std::find(sq_of.begin(), sq_of.end(), sq);
-            if (it == sq_of.end()) {
-                dist_idx[o] = (int)sq_of.size();
-                sq_of.push_back(sq);
-            } else {
-                dist_idx[o] = (int)(it - sq_of.begin());
-            }
-        }
+        std::vector<int> dist_idx;
         std::vector<double> hk;
-        hk.reserve(sq_of.size() * 2 * (L.L + 1));
-        for (int sq : sq_of) {
-            std::vector<double> one;
-            hankel2(L.L, h->k * L.a * std::sqrt((double)sq), one);
-            hk.insert(hk.end(), one.begin(), one.end());
-        }
+        bi_translation_series(h, l, dist_idx, hk);
         double* d_theta = h->upload(L.theta);
         double* d_wth = h->upload(L.wtheta);
         int* d_di = h->upload(dist_idx);

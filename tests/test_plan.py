@@ -336,3 +336,39 @@ def test_plan_rejects_open_and_bad_meshes(bi):
     with pytest.raises(bi.BIError):
         p.get(6, 1)                               # no interaction list above level 2
     p.close()
+
+
+@pytest.mark.parametrize("digits,leaf_box", [(3, 0.25), (6, 0.125)])
+def test_translation_hankel_table(bi, sphere, digits, leaf_box):
+    """Spherical Hankel functions h_n^(2)(k|X|) = j_n - i y_n behind the translation operators
+    of every level, for every far offset, against scipy.  j_n comes from Miller's downward
+    recurrence, so beyond the turning point (n > x) it must keep its relative accuracy too;
+    near its zeros only the absolute error is meaningful."""
+    special = pytest.importorskip("scipy.special")
+    v, t = sphere
+    p = bi.Plan(v, t, K0, digits=digits, leaf_box=leaf_box)
+    info = p.info()
+    for l in range(2, info["leaf_level"] + 1):
+        L = info["L"][l]
+        di = p.get(40, l)
+        hk = p.get(41, l).reshape(-1, L + 1, 2)
+        a = info["root_size"] / 2**l
+        sq = set()
+        for o in range(343):
+            off = np.array([o // 49 - 3, (o // 7) % 7 - 3, o % 7 - 3])
+            if np.abs(off).max() <= 1:
+                assert di[o] == -1
+                continue
+            sq.add(int(off @ off))
+            x = K0 * a * np.linalg.norm(off)
+            n = np.arange(L + 1)
+            j, y = special.spherical_jn(n, x), special.spherical_yn(n, x)
+            g = hk[di[o]]
+            assert np.abs(g[:, 0] - j).max() < 1e-13, (l, o)
+            h = j - 1j * y
+            assert np.all(np.abs(g[:, 0] + 1j * g[:, 1] - h) <= 1e-13 * np.abs(h)), (l, o)
+            deep = n > x + 2
+            if deep.any():
+                assert np.all(np.abs(g[deep, 0] - j[deep]) <= 1e-12 * np.abs(j[deep])), (l, o)
+        assert di.max() + 1 == len(sq) == 15      # distinct |X|^2 among the 316 far offsets
+    p.close()
