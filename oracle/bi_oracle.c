@@ -9,7 +9,8 @@
  *   - RWG basis functions on pairs of triangles (Sec. II.C, Eq. exp4-5, Rao-Wilton-
  *     Glisson 1982): f = (l / 2A+)(r - p+) on T+, (l / 2A-)(p- - r) on T-.
  *   - Free-space Green's function G = exp(-j k R) / (4 pi R), time convention
- *     exp(j w t) (Sec. II.A).
+ *     exp(j w t) (Sec. II.A).  k may be complex (a lossy medium such as the coating of
+ *     Sec. III.D, Im k < 0): every kernel piece below is analytic in k.
  *   - Operators L and K of Sec. II.C (Eq. 22 and the definitions below it),
  *     K-bar = principal value of K.
  *   - Galerkin primitives (inner product without conjugation, Eq. 10):
@@ -349,18 +350,20 @@ void or_static_tri(const double* P, const double* r, double* I1, double* Ir, dou
 }
 
 /* ----------------------------------------------------------- kernel pieces */
-/* G - 1/(4 pi R) + k^2 R/(8 pi)  (smooth: -jk/(4 pi) + j k^3 R^2/(24 pi) + ...) */
-static inline cx g_rem(double k, double R) {
-    double x = k * R;
-    if (x < 1e-2) return (-I * k + I * k * x * x / 6.0 + k * x * x * x / 24.0 - I * k * x * x * x * x / 120.0) / (4.0 * PI);
+/* G - 1/(4 pi R) + k^2 R/(8 pi)  (smooth: -jk/(4 pi) + j k^3 R^2/(24 pi) + ...).  Every kernel
+   piece is analytic in k, so a complex wavenumber (lossy medium, Im k < 0 with exp(j w t))
+   goes through the same expressions. */
+static inline cx g_rem(cx k, double R) {
+    cx x = k * R;
+    if (cabs(x) < 1e-2) return (-I * k + I * k * x * x / 6.0 + k * x * x * x / 24.0 - I * k * x * x * x * x / 120.0) / (4.0 * PI);
     return (cexp(-I * x) - 1.0 + 0.5 * x * x) / (4.0 * PI * R);
 }
 /* gt(R) with grad_r G = (r' - r) gt(R): gt = (1 + jkR) exp(-jkR) / (4 pi R^3) */
-static inline cx gt_full(double k, double R) { return (1.0 + I * k * R) * cexp(-I * k * R) / (4.0 * PI * R * R * R); }
+static inline cx gt_full(cx k, double R) { return (1.0 + I * k * R) * cexp(-I * k * R) / (4.0 * PI * R * R * R); }
 /* gt - (1/R^3 + k^2/(2R))/(4 pi) */
-static inline cx gt_rem(double k, double R) {
-    double x = k * R;
-    if (x < 2e-2) {
+static inline cx gt_rem(cx k, double R) {
+    cx x = k * R;
+    if (cabs(x) < 2e-2) {
         /* series of (1+jx)e^{-jx} = 1 + x^2/2 - j x^3/3 - x^4/8 + j x^5/30 + ... */
         cx s = -I * x * x * x / 3.0 - x * x * x * x / 8.0 + I * x * x * x * x * x / 30.0 + x * x * x * x * x * x / 144.0;
         return s / (4.0 * PI * R * R * R);
@@ -372,7 +375,7 @@ static inline cx gt_rem(double k, double R) {
  *   Sg = int_S G ds',  Sr = int_S (r' - r) G ds',  Kv = int_S grad_r G ds'. */
 typedef struct { cx Sg; cv3 Sr; cv3 Kv; } inner_t;
 
-static void inner_plain(const tri_t* S, const trirule* R, double k, const double* r, inner_t* o) {
+static void inner_plain(const tri_t* S, const trirule* R, cx k, const double* r, inner_t* o) {
     o->Sg = 0;
     for (int d = 0; d < 3; ++d) { o->Sr.x[d] = 0; o->Kv.x[d] = 0; }
     for (int q = 0; q < R->n; ++q) {
@@ -391,7 +394,7 @@ static void inner_plain(const tri_t* S, const trirule* R, double k, const double
     }
 }
 
-static void inner_sing(const tri_t* S, const trirule* R, double k, const double* r, inner_t* o) {
+static void inner_sing(const tri_t* S, const trirule* R, cx k, const double* r, inner_t* o) {
     double I1, Ir[3], Ig[3], IR, IrR[3];
     double P[9];
     for (int a = 0; a < 3; ++a)
@@ -463,7 +466,7 @@ static void quality_set(int level, quality_t* q) {
 typedef struct { int perm[3]; } rot_t;
 
 static void accumulate_outer(const tri_t* Tm, const tri_t* Tn, const double* r, double W, const inner_t* in,
-                             double k, int far_surface_nl, blocks_t* B) {
+                             cx k, int far_surface_nl, blocks_t* B) {
     cx jk = I * k;
     for (int i = 0; i < 3; ++i) {
         double gi[3];
@@ -506,7 +509,7 @@ static void accumulate_outer(const tri_t* Tm, const tri_t* Tn, const double* r, 
  *   -(j/k) int_Tm g_i . (n x grad Phi) ds = (j/k) int_Tm (n x g_i) . grad Phi ds
  *   = (j/k) sum_edges int_e Phi (n x g_i) . nu dl = -(j/k) sum_e int_e Phi g_i . tau dl,
  * with Phi = 2 int_Tn G ds' and tau the counter-clockwise edge tangent. */
-static void nl_boundary(const tri_t* Tm, const tri_t* Tn, const trirule* Rin, int nline, double k, blocks_t* B) {
+static void nl_boundary(const tri_t* Tm, const tri_t* Tn, const trirule* Rin, int nline, cx k, blocks_t* B) {
     double x[64], w[64];
     gauss01(nline, x, w);
     /* Phi has logarithmic derivative singularities at the vertices of the source triangle;
@@ -569,7 +572,7 @@ static int tri_relation(const tri_t* A, const tri_t* B, int* sa, int* sb) {
     return ns;
 }
 
-static void pair_blocks(const tri_t* Tm, const tri_t* Tn, const rules_t* R, double k, blocks_t* B) {
+static void pair_blocks(const tri_t* Tm, const tri_t* Tn, const rules_t* R, cx k, blocks_t* B) {
     memset(B, 0, sizeof(*B));
     int sa[3], sb[3];
     int ns = tri_relation(Tm, Tn, sa, sb);
@@ -653,8 +656,11 @@ static void pair_blocks(const tri_t* Tm, const tri_t* Tn, const rules_t* R, doub
     }
 }
 
-/* exposed for tests: raw blocks of one triangle pair (row-major [4][3][3] complex) */
-void or_pair_blocks(const double* Pm, const double* Pn, const int* idm, const int* idn, double k, int level, double* out) {
+/* exposed for tests: raw blocks of one triangle pair (row-major [4][3][3] complex) at the
+   wavenumber k_re + j k_im */
+void or_pair_blocks(const double* Pm, const double* Pn, const int* idm, const int* idn, double k_re, double k_im,
+                    int level, double* out) {
+    const cx k = k_re + I * k_im;
     tri_t Tm, Tn;
     make_tri(Pm, (int[]){0, 1, 2}, &Tm);
     make_tri(Pn, (int[]){0, 1, 2}, &Tn);
@@ -757,10 +763,12 @@ static void gram_raw(const tri_t* T, double Gr[3][3], double Xr[3][3]) {
  * rows == NULL (nrows ignored) means all rows.  Z is row-major [nrows][ncols],
  * complex128.  'part' selects: 0 everything, 1 P only (as -P in the JJ slot),
  * 2 Q only (as -Q in the JM slot) -- parts are used by tests.
+ * The wavenumber is k_re + j k_im (k_im <= 0 for a lossy medium).
  * Returns 0, or the negative mesh error of or_rwg.
  */
-int or_fill_rows(int nv, const double* V, int nt, const int* T, double k, int mode, int level,
+int or_fill_rows(int nv, const double* V, int nt, const int* T, double k_re, double k_im, int mode, int level,
                  int nrows, const int* rows, double* Zout) {
+    const cx k = k_re + I * k_im;
     mesh_t M;
     int rc = mesh_build(nv, V, nt, T, &M);
     if (rc) return rc;
@@ -886,8 +894,11 @@ int or_gram(int nv, const double* V, int nt, const int* T, double* Gout, double*
 }
 
 /* Raw operator matrices <f_m, L f_n>, <f_m, n x L f_n>, <f_m, Kbar f_n>, <f_m, n x Kbar f_n>
-   (dense N x N each, complex128); used by tests to check invariants. */
-int or_operators(int nv, const double* V, int nt, const int* T, double k, int level, double* Lo, double* NLo, double* Ko, double* NKo) {
+   (dense N x N each, complex128) at the wavenumber k_re + j k_im: the invariants' tests, and
+   the operators of each region of a multi-region surface formulation. */
+int or_operators(int nv, const double* V, int nt, const int* T, double k_re, double k_im, int level, double* Lo,
+                 double* NLo, double* Ko, double* NKo) {
+    const cx k = k_re + I * k_im;
     mesh_t M;
     int rc = mesh_build(nv, V, nt, T, &M);
     if (rc) return rc;
@@ -922,14 +933,16 @@ int or_operators(int nv, const double* V, int nt, const int* T, double k, int le
 /* ------------------------------------------------ excitation and far field */
 /* Plane wave of Sec. III with normalised fields: E = p exp(-jk khat.r), H = (khat x p) exp(-jk khat.r).
  * b^J_m = <f_m, E/2 + n x H/2> (Eq. 49),  b^M_m = <f_m, H/2 - n x E/2> (Eq. 50).
- * Output b: complex128 [nrhs][nun] (nun = 2N for mode 0: J block then M block; N for mode 1). */
+ * Mode 2: the tested fields themselves, <f_m, E> then <f_m, H> (the excitation of a two-region
+ * surface formulation, where the tangential traces of E and H are matched).
+ * Output b: complex128 [nrhs][nun] (nun = 2N for modes 0 and 2: J block then M block; N for mode 1). */
 int or_rhs_planewave(int nv, const double* V, int nt, const int* T, double k, int mode, int nrhs,
                      const double* khat, const double* phat, double* bout) {
     mesh_t M;
     int rc = mesh_build(nv, V, nt, T, &M);
     if (rc) return rc;
     int N = M.ne;
-    int nun = mode == 0 ? 2 * N : N;
+    int nun = mode == 1 ? N : 2 * N;
     cx* b = (cx*)bout;
     memset(b, 0, sizeof(cx) * (size_t)nun * nrhs);
     trirule Rq;
@@ -954,6 +967,11 @@ int or_rhs_planewave(int nv, const double* V, int nt, const int* T, double k, in
                     double gi[3];
                     v_sub(r, Tt->p[i], gi);
                     double c = M.t_cf[3 * t + i];
+                    if (mode == 2) {
+                        b[(size_t)s * nun + m] += v_dot(gi, ph) * ph_ * c * w;
+                        b[(size_t)s * nun + N + m] += v_dot(gi, hp) * ph_ * c * w;
+                        continue;
+                    }
                     cx bj = 0.5 * (v_dot(gi, ph) + v_dot(gi, nH)) * ph_ * c * w;
                     b[(size_t)s * nun + m] += bj;
                     if (mode == 0) {

@@ -363,3 +363,145 @@ def test_addition_theorem_plane_wave_expansion():
     assert e3 < 5e-3, e3
     assert e5 < 5e-4 and e5 < e3 / 5, e5
     assert _expansion_error(3, sign=+1.0) > 0.1
+
+
+# ------------------------------------------- complex wavenumbers and two-region formulations
+K_LOSSY = K0 * np.sqrt(2.0 - 0.5j)      # coating permittivity of Sec. III.D, exp(j w t): Im k < 0
+
+
+def _pair_geometries():
+    """Test triangle and source triangles sharing the triangle, an edge or a vertex with it,
+    or lying close by (vertex ids decide the relation)."""
+    Pm = np.array([[0, 0, 0], [0.08, 0, 0], [0.02, 0.07, 0.01]], float)
+    out = {"same": (Pm, [0, 1, 2])}
+    out["edge"] = (np.array([Pm[1], Pm[0], [0.05, -0.06, 0.03]]), [1, 0, 3])
+    out["vertex"] = (np.array([Pm[2], [-0.03, 0.1, 0.0], [-0.06, 0.04, 0.04]]), [2, 4, 5])
+    out["near"] = (np.array([[0, 0, 0], [0.07, 0.01, 0.02], [0.01, 0.08, -0.01]]) + [0.0, 0.05, 0.08], [6, 7, 8])
+    return Pm, out
+
+
+def test_pair_blocks_vs_brute_force_lossy():
+    """The separated-pair check (singular subtraction and the boundary form of the grad-Phi
+    term, as for a close pair) at the complex wavenumber of a lossy coating."""
+    Pm = np.array([[0, 0, 0], [0.08, 0, 0], [0.02, 0.07, 0.01]], float)
+    Pn = np.array([[0, 0, 0], [0.07, 0.01, 0.02], [0.01, 0.08, -0.01]], float) + np.array([0.0, 0.05, 0.08])
+    ours = oracle.pair_blocks(Pm, Pn, [0, 1, 2], [3, 4, 5], K_LOSSY, 1)
+    ref = _brute_blocks(Pm, Pn, K_LOSSY)
+    for q in range(4):
+        err = np.abs(ours[q] - ref[q]).max() / np.abs(ref[q]).max()
+        assert err < 2e-6, (q, err)
+
+
+@pytest.mark.parametrize("rel", ["same", "edge", "vertex", "near"])
+def test_pair_blocks_are_analytic_in_k(rel):
+    """Every entry is an analytic function of k (the kernels contain k only through exp(-jkR),
+    powers of k and their series), so the Cauchy-Riemann relation d/d(Im k) = j d/d(Re k)
+    holds on the singular paths too.  A stray modulus, conjugate or real part of k anywhere
+    in the singular subtraction or the boundary term breaks it."""
+    Pm, geo = _pair_geometries()
+    Pn, idn = geo[rel]
+    h = 1e-4 * abs(K_LOSSY)
+
+    def f(k):
+        return oracle.pair_blocks(Pm, Pn, [0, 1, 2], idn, k, 0)
+
+    d_re = (f(K_LOSSY + h) - f(K_LOSSY - h)) / (2 * h)
+    d_im = (f(K_LOSSY + 1j * h) - f(K_LOSSY - 1j * h)) / (2 * h)
+    for q in range(4):
+        scale = np.abs(d_re[q]).max()
+        if scale == 0:
+            assert np.abs(d_im[q]).max() == 0
+            continue
+        assert np.abs(d_im[q] - 1j * d_re[q]).max() / scale < 1e-6, (rel, q)
+
+
+def test_operators_symmetric_at_complex_k():
+    v, t = icosphere(3, 0.4)
+    L, _, K, _ = oracle.operators(v, t, K_LOSSY, 0)
+    assert np.linalg.norm(L - L.T) / np.linalg.norm(L) < 1e-7
+    assert np.linalg.norm(K - K.T) / np.linalg.norm(K) < 1e-5
+
+
+def test_mie_dielectric_and_coated_limits():
+    """The dielectric and coated series reduce to the PEC series and to each other where
+    they must, follow the Rayleigh law, conserve energy without loss and absorb with it."""
+    th = np.deg2rad(np.arange(0, 181))
+    pec = mie.rcs_pec(K0, 0.3, th)
+    assert mie.rcs_dielectric(K0, 0.4, 1.0, th).max() < 1e-25 * pec.max()          # no contrast
+    assert np.abs(mie.rcs_coated_pec(K0, 0.3, 0.4, 1.0, th) / pec - 1).max() < 1e-12  # air coat
+    assert np.abs(mie.rcs_coated_pec(K0, 0.4, 0.4, 4.0, th) / mie.rcs_pec(K0, 0.4, th) - 1).max() < 1e-12
+    hom = mie.rcs_dielectric(K0, 0.4, 2 - 0.5j, th)
+    assert np.abs(mie.rcs_coated_pec(K0, 1e-4, 0.4, 2 - 0.5j, th) / hom - 1).max() < 1e-6  # vanishing core
+    # a good conductor tends to PEC as 1/|m| (surface impedance)
+    e1 = np.abs(mie.rcs_dielectric(K0, 0.4, 1e5 * (1 - 1j), th) / mie.rcs_pec(K0, 0.4, th) - 1).max()
+    e2 = np.abs(mie.rcs_dielectric(K0, 0.4, 1e7 * (1 - 1j), th) / mie.rcs_pec(K0, 0.4, th) - 1).max()
+    assert e2 < 0.02 and 7 < e1 / e2 < 13
+    # Rayleigh: sigma_back = 4 pi k^4 a^6 |(eps - 1)/(eps + 2)|^2
+    a, eps = 0.01, 4 - 1j
+    sb = mie.rcs_dielectric(1.0, a, eps, np.array([np.pi]))[0]
+    assert abs(sb / (4 * np.pi * a ** 6 * abs((eps - 1) / (eps + 2)) ** 2) - 1) < 1e-4
+    # energy: no absorption without loss, absorption with Im eps < 0 (exp(j w t))
+    for x, e in ((2.5, 4.0), (10.0, 2.25)):
+        qe, qs, qa = mie.efficiencies_from(x, mie.coeffs_dielectric(x, e))
+        assert abs(qa) < 1e-10 * qe
+    qe, qs, qa = mie.efficiencies_from(K0 * 0.4, mie.coeffs_coated_pec(K0 * 0.3, K0 * 0.4, 8.0))
+    assert abs(qa) < 1e-10 * qe
+    for coeffs in (mie.coeffs_dielectric(K0 * 0.4, 2 - 0.5j), mie.coeffs_coated_pec(K0 * 0.3, K0 * 0.4, 2 - 0.5j)):
+        qe, qs, qa = mie.efficiencies_from(K0 * 0.4, coeffs)
+        assert qa > 0.1 * qe
+
+
+def _sphere_rcs_check(s, sm):
+    mask = 10 * np.log10(sm) >= 10 * np.log10(sm.max()) - 20
+    return np.abs(10 * np.log10(s / sm))[mask].max(), oracle.rcs_error(s, sm)
+
+
+def test_two_region_invisible_sphere():
+    """With eps_r = 1 the body is free space: the PMCHWT solution radiates nothing."""
+    v, t = icosphere(4, 0.4)
+    Z = oracle.two_region(v, t, K0, 1.0)
+    b = oracle.two_region_rhs(v, t, K0, [0, 0, 1.0], [1.0, 0, 0])[0]
+    x = np.linalg.solve(Z, b)
+    th = np.deg2rad(np.arange(0, 181, 5))
+    dirs = np.stack([np.sin(th), 0 * th, np.cos(th)], 1)
+    s = oracle.rcs(v, t, K0, 0, x, dirs)
+    assert s.max() < 1e-4 * mie.rcs_pec(K0, 0.4, th).max()
+
+
+@pytest.mark.slow
+def test_two_region_dielectric_sphere_rcs_vs_mie():
+    """PMCHWT with the interior operators at k1 = k0 sqrt(eps_r): homogeneous spheres of radius
+    0.4 lambda, lossy (2 - 0.5j) and lossless (4), against the Mie series; the error of
+    Eq. 5-25 falls with the mesh size."""
+    th = np.deg2rad(np.arange(0, 181))
+    dirs = np.stack([np.sin(th), 0 * th, np.cos(th)], 1)
+    errs = {}
+    for nu, eps in ((5, 2 - 0.5j), (7, 2 - 0.5j), (6, 4.0)):
+        v, t = icosphere(nu, 0.4)
+        x = np.linalg.solve(oracle.two_region(v, t, K0, eps),
+                            oracle.two_region_rhs(v, t, K0, [0, 0, 1.0], [1.0, 0, 0])[0])
+        db, err = _sphere_rcs_check(oracle.rcs(v, t, K0, 0, x, dirs), mie.rcs_dielectric(K0, 0.4, eps, th))
+        assert db < 0.5 and err < 0.05, (nu, eps, db, err)
+        errs[(nu, eps)] = err
+    assert errs[(7, 2 - 0.5j)] < 0.8 * errs[(5, 2 - 0.5j)]
+
+
+@pytest.mark.slow
+def test_coated_pec_sphere_rcs_vs_mie():
+    """The object of Sec. III.A: PEC sphere of radius 0.3 lambda under a 0.1 lambda coat, in a
+    surface-only form (PMCHWT on the coat's outer surface, zero tangential E on the core),
+    against the coated-sphere Mie series; lossy coat (2 - 0.5j) at two mesh sizes and the
+    paper's eps_r = 8."""
+    th = np.deg2rad(np.arange(0, 181))
+    dirs = np.stack([np.sin(th), 0 * th, np.cos(th)], 1)
+    errs = {}
+    for (nu1, nu2), eps in (((6, 5), 2 - 0.5j), ((7, 6), 2 - 0.5j), ((7, 6), 8.0)):
+        v1, t1 = icosphere(nu1, 0.4)
+        v2, t2 = icosphere(nu2, 0.3)
+        Z, rhs, n1, n2 = oracle.coated_pec(v1, t1, v2, t2, K0, eps)
+        x = np.linalg.solve(Z, rhs([0, 0, 1.0], [1.0, 0, 0])[0])
+        s = oracle.rcs(v1, t1, K0, 0, x[:2 * n1], dirs)
+        db, err = _sphere_rcs_check(s, mie.rcs_coated_pec(K0, 0.3, 0.4, eps, th))
+        assert db < 0.5 and err < 0.05, (nu1, eps, db, err)
+        errs[(nu1, eps)] = err
+    assert errs[(7, 2 - 0.5j)] < 0.85 * errs[(6, 2 - 0.5j)]
