@@ -272,10 +272,17 @@ void bi_server_destroy(bi_server s);
  *   40 distance index [343] of each offset code of translation `level` (-1: touching offset)
  *   41 spherical Hankel values (double) [distances][L + 1][2]: h_n^(2)(k|X|) as (re, im) */
 typedef struct bi_plan_s* bi_plan;
+/* verts, tris, opt as for bi_setup (opt may be NULL; stream and precision are ignored).
+ * *out is NULL on failure. */
 int bi_plan_create(const double* verts, int nv, const int* tris, int nt, double k0, const bi_params* opt, bi_plan* out);
+/* Sizes of the plan (host struct; device and timing fields are 0). */
 int bi_plan_info(bi_plan p, bi_info_t* info);
+/* BI_ERR_ARG for an unknown `what`, a level that has no such array, or `bytes` smaller than
+ * the array (nothing is copied then; *count still holds the element count). */
 int bi_plan_get(bi_plan p, int what, int level, void* out, int64_t bytes, int64_t* count);
+/* Text of the last failed bi_plan_create of the calling thread. */
 const char* bi_plan_last_error(void);
+/* Free the plan (host memory only).  NULL is ignored. */
 void bi_plan_destroy(bi_plan p);
 
 /* Text of the last error on h (or of the last failed bi_setup when h is NULL). */
