@@ -38,6 +38,27 @@ def plan(bi, sphere):
     p.close()
 
 
+GEOMETRIES = {
+    # 5 levels, one closed component
+    "sphere_r2": lambda: inputs.icosphere(20, radius=2.0),
+    # two disjoint closed components (cube with a cylinder inside), flat faces, ragged octree
+    "cube_cylinder": lambda: inputs.cube_with_cylinder(size=2.0, h_face=1 / 6, h_edge=1 / 8, cyl_radius=0.4,
+                                                       cyl_height=1.2, h_cyl=1 / 8),
+    # elongated: many partly filled parents
+    "ellipsoid": lambda: tuple(a * 3.0 if i == 0 else a for i, a in enumerate(inputs.ellipsoid(12))),
+    # smaller than two leaf boxes: no far field, everything is near
+    "tiny_sphere": lambda: inputs.icosphere(3, radius=0.1),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(GEOMETRIES))
+def geo_plan(bi, request):
+    v, t = GEOMETRIES[request.param]()
+    p = bi.Plan(v, t, K0, digits=3)
+    yield request.param, v, t, p
+    p.close()
+
+
 def ancestors(plan, info):
     """anc[l][leaf box] = its ancestor at level l."""
     lf = info["leaf_level"]
@@ -64,11 +85,15 @@ def test_rwg_numbering_is_the_interior_edges(plan, sphere):
     assert len({(int(a), int(b)) for a, b in edges}) == len(edges)
 
 
-def test_octree_boxes_hold_their_rwgs(plan, sphere):
-    v, _ = sphere
+def test_sphere_level_count(plan):
+    info = plan.info()
+    assert info["levels"] == 5 and info["leaf_level"] == 4
+
+
+def test_octree_boxes_hold_their_rwgs(geo_plan):
+    _, v, _, plan = geo_plan
     info = plan.info()
     lf = info["leaf_level"]
-    assert info["levels"] == 5 and lf == 4
     perm = plan.get(12)
     assert np.array_equal(np.sort(perm), np.arange(info["n_rwg"]))
     start = plan.get(0)
@@ -95,10 +120,11 @@ def test_octree_boxes_hold_their_rwgs(plan, sphere):
         assert np.array_equal(c >> 1, pc[par])
 
 
-def test_near_and_interactions_cover_every_pair_once(plan):
+def test_near_and_interactions_cover_every_pair_once(geo_plan):
     """Sec. II.D: a pair of leaf boxes is handled exactly once, either by the near-field blocks
     (touching boxes) or by one translation between ancestors that are not neighbours but whose
     parents are."""
+    name, _, _, plan = geo_plan
     info = plan.info()
     lf = info["leaf_level"]
     nb = info["boxes"][lf]
@@ -121,11 +147,12 @@ def test_near_and_interactions_cover_every_pair_once(plan):
             rows = members[c]
             for s in src[ptr[c]:ptr[c + 1]]:
                 cover[np.ix_(rows, members[s])] += 1
-    assert total > 0
+    assert (total > 0) == (lf >= 2), (name, lf)
     assert np.all(cover == 1), np.unique(cover, return_counts=True)
 
 
-def test_interaction_offsets_match_box_coordinates(plan):
+def test_interaction_offsets_match_box_coordinates(geo_plan):
+    plan = geo_plan[3]
     info = plan.info()
     for l in range(2, info["leaf_level"] + 1):
         c = plan.get(3, l).reshape(-1, 3)
@@ -140,7 +167,8 @@ def test_interaction_offsets_match_box_coordinates(plan):
         assert np.all(np.abs(pc[par[recv]] - pc[par[src]]).max(1) <= 1)
 
 
-def test_parent_centred_lists_equal_the_interaction_lists(plan):
+def test_parent_centred_lists_equal_the_interaction_lists(geo_plan):
+    plan = geo_plan[3]
     info = plan.info()
     for l in range(2, info["leaf_level"] + 1):
         cp = plan.get(5, l - 1)
