@@ -1,0 +1,75 @@
+"""Host logic of bench.py checked without a GPU: its algorithmic-byte model and launch count
+for the bench workload (sizes from the host-only plan, the same set-up code as the GPU
+handle), against the committed ncu summaries that its roofline line reads."""
+import os
+import re
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+@pytest.fixture(scope="module")
+def bench_info():
+    import bench
+    from paper_2210_04892_gb300 import bi
+    try:
+        bi.load()
+    except (ImportError, OSError) as e:  # pragma: no cover - library not built here
+        pytest.skip(f"library not loadable: {e}")
+    v, t, _ = bench.workload_mesh()
+    p = bi.Plan(v, t, bench.K0, digits=3)
+    info = p.info()
+    p.close()
+    return bench, info
+
+
+def test_workload_sizes(bench_info):
+    bench, info = bench_info
+    assert info["n_unknowns"] == 61440 and info["levels"] == 5
+    assert str(info["n_unknowns"]) in bench.WORKLOAD.replace(",", "")
+
+
+def test_measured_traffic_matches_the_byte_model(bench_info):
+    """Every HBM-bound kernel of the roofline has a committed per-launch DRAM figure that fits
+    the algorithmic bytes of its stage: at most 5% above (the kernels re-read nothing), and
+    below only by the leaf outgoing/incoming patterns, which may stay in L2 between
+    kernels.  That also ties the summary to this workload."""
+    bench, info = bench_info
+    traffic = bench.measured_traffic()
+    model = bench.stage_bytes(info, 1)
+    lf = info["leaf_level"]
+    leaf_patterns = info["boxes"][lf] * info["K"][lf] * 2 * 8
+    assert set(traffic) == {"near", "receive", "aggregate"}
+    for stage, (kernel, nbytes) in traffic.items():
+        assert kernel.startswith("k_")
+        assert model[stage] - leaf_patterns - 0.01 * model[stage] <= nbytes <= 1.05 * model[stage], \
+            (stage, nbytes, model[stage])
+
+
+def test_launch_count_matches_the_launch_summary(bench_info):
+    """Kernels per single-RHS product on the 5-level tree: near, aggregation, one translation
+    per level 2..4, interpolation and anterpolation per level pair, receive."""
+    bench, info = bench_info
+    n = bench.launches_per_step(info)
+    assert n == 1 + 1 + 3 + 2 + 2 + 1
+    text = open(os.path.join(ROOT, "profiles", "launches_matvec_sphere_r2_61440.md")).read()
+    assert re.search(r"\(%d product kernels each" % n, text)
+    rows = re.findall(r"^\| (k_\w+)<[^|]*\| (\d+) \| [\d.]+ \| [\d.]+ \| [\d.]+% \|$", text, re.M)
+    launches = sum(int(c) for _, c in rows)
+    products = max(int(c) for _, c in rows if _ == "k_near_stream")
+    assert abs(launches / products - n) < 0.1 * n
+
+
+def test_peaks_are_the_measured_file_when_present(bench_info):
+    bench, _ = bench_info
+    peak, kind = bench.peaks()
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        import json
+        assert kind == "measured" and peak == float(json.load(open(path))["hbm_gbs"])
+    else:
+        assert kind == "fallback" and peak == 6800.0
