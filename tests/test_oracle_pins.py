@@ -326,7 +326,8 @@ def _hankel2(l, x):
 def _expansion_error(digits, a=0.25, k=K0, sign=-1.0, seed=7):
     from scipy import special
     dmax = np.sqrt(3) * a
-    L = int(math.ceil(k * dmax + 1.8 * digits ** (2 / 3) * (k * dmax) ** (1 / 3)))
+    kd = float(np.real(k)) * dmax                 # the rule takes Re k for a lossy medium
+    L = int(math.ceil(kd + 1.8 * digits ** (2 / 3) * kd ** (1 / 3)))
     x, wx = np.polynomial.legendre.leggauss(L + 1)
     nphi = 2 * (L + 1)
     th = np.arccos(x)
@@ -505,3 +506,17 @@ def test_coated_pec_sphere_rcs_vs_mie():
         assert db < 0.5 and err < 0.05, (nu1, eps, db, err)
         errs[(nu1, eps)] = err
     assert errs[(7, 2 - 0.5j)] < 0.85 * errs[(6, 2 - 0.5j)]
+
+
+def test_addition_theorem_at_lossy_wavenumber():
+    """The plane-wave expansion behind the translations, at the coating's complex wavenumber
+    k1 = k0 sqrt(2 - 0.5j): the same formulas ((-j)^l h_l^(2), exp(-jk khat.d)) continue
+    analytically, and the excess-bandwidth rule with Re k keeps the 3-digit worst-pair error of
+    0.25-wavelength boxes (free-space wavelengths) at the level of the real-k case (measured
+    1.8e-3 against 3.1e-3).  The wrong phase sign fails, as at real k."""
+    e3 = _expansion_error(3, k=K_LOSSY)
+    assert e3 < 5e-3, e3
+    assert _expansion_error(3, k=K_LOSSY, sign=+1.0) > 0.1
+    # the coat's own wavelength is shorter: boxes of a quarter of it behave like free-space ones
+    a1 = 0.25 * K0 / abs(K_LOSSY)
+    assert _expansion_error(4, a=a1, k=K_LOSSY) < 2e-3
