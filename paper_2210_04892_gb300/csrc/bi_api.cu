@@ -53,6 +53,13 @@ static void release(bi_handle_s* h) {
     }
 }
 
+bool bi_params_valid(const bi_params& P) {
+    return P.digits >= 1 && P.digits <= 8 && P.leaf_box > 0 && P.interp_order >= 2 && P.interp_order <= 32 &&
+           (P.precision == 0 || P.precision == 1) && (P.op_mode == 0 || P.op_mode == 1) && P.max_rhs >= 1 &&
+           P.max_rhs <= 4096 && P.gmres_restart >= 1 && P.gmres_maxit >= 1 && P.levels >= 0 && P.levels <= 21 &&
+           (P.precond == 0 || P.precond == 1);
+}
+
 extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, double k0, int digits, const bi_params* opt,
                         bi_handle* out) {
     if (!out) return BI_ERR_ARG;
@@ -67,10 +74,7 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
     else bi_default_params(&h->prm);
     if (digits > 0) h->prm.digits = digits;
     bi_params& P = h->prm;
-    if (P.digits < 1 || P.digits > 8 || !(P.leaf_box > 0) || P.interp_order < 2 || P.interp_order > 32 ||
-        (P.precision != 0 && P.precision != 1) || (P.op_mode != 0 && P.op_mode != 1) || P.max_rhs < 1 ||
-        P.max_rhs > 4096 || P.gmres_restart < 1 || P.gmres_maxit < 1 || P.levels < 0 || P.levels > 21 ||
-        (P.precond != 0 && P.precond != 1)) {
+    if (!bi_params_valid(P)) {
         g_setup_error = "bi_setup: parameter out of range";
         delete h;
         return BI_ERR_ARG;

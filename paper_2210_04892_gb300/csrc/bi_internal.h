@@ -242,6 +242,7 @@ void bi_coupling_set(bi_handle_s* h, int64_t n_int, const int* lx_ptr, const int
 void bi_sai_apply(bi_handle_s* h, const void* x, void* y, int R, cudaStream_t s);
 void bi_build_translate_lists(bi_handle_s* h);
 void bi_plan_translate_lists(bi_handle_s* h);   // host part of bi_build_translate_lists
+bool bi_params_valid(const bi_params& P);       // the parameter ranges bi_setup accepts
 bool bi_leaf_receive_bulk(bi_handle_s* h, void* y, int R, cudaStream_t s);
 int bi_take_device_status(bi_handle_s* h);
 size_t bi_farfield_scratch_bytes(const bi_handle_s* h, int nrhs, int ndir);

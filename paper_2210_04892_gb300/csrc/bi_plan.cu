@@ -40,6 +40,11 @@ extern "C" int bi_plan_create(const double* verts, int nv, const int* tris, int 
     bi_handle_s* h = &p->h;
     if (opt) h->prm = *opt;
     else bi_default_params(&h->prm);
+    if (!bi_params_valid(h->prm)) {
+        g_plan_error = "bi_plan_create: parameter out of range";
+        delete p;
+        return BI_ERR_ARG;
+    }
     h->k = k0;
     h->nX = h->prm.op_mode == 0 ? 2 : 1;
     try {

@@ -358,6 +358,10 @@ def test_plan_rejects_open_and_bad_meshes(bi):
         bi.Plan(v, bad, K0)                       # inconsistent orientation
     with pytest.raises(bi.BIError):
         bi.Plan(v, t, -1.0)
+    for bad in (dict(digits=0), dict(digits=-2), dict(leaf_box=0.0), dict(leaf_box=float("nan")),
+                dict(interp_order=1), dict(levels=22), dict(op_mode=2)):
+        with pytest.raises(bi.BIError):
+            bi.Plan(v, t, K0, **bad)              # the parameter ranges of bi_setup
     p = bi.Plan(v, t, K0)
     with pytest.raises(bi.BIError):
         p.get(99)
