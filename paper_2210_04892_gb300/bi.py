@@ -279,6 +279,13 @@ class Operator:
             return
         ts = "<c16" if self.precision == "fp64" else "<c8"
         n_int = int(n_int)
+        for name, (ptr, col, val), rows in (("dlx", dlx, n_int), ("dxl", dxl, self.n_unknowns)):
+            if not (ptr.is_cuda and col.is_cuda and val.is_cuda):
+                raise TypeError("%s: CSR arrays must be CUDA tensors" % name)
+            if ptr.dtype != torch.int32 or col.dtype != torch.int32 or val.dtype != self.cdtype:
+                raise TypeError("%s: CSR arrays must be (int32, int32, %s)" % (name, self.cdtype))
+            if ptr.numel() != rows + 1 or col.numel() != val.numel():
+                raise ValueError("%s: ptr must have %d entries and col, val the same length" % (name, rows + 1))
 
         def _cb(user, pin, pout, nrhs, stream):
             st = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
