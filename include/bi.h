@@ -285,7 +285,7 @@ const char* bi_plan_last_error(void);
 /* Free the plan (host memory only).  NULL is ignored. */
 void bi_plan_destroy(bi_plan p);
 
-/* Text of the last error on h (or of the last failed bi_setup when h is NULL). */
+/* Text of the last error on h (or, when h is NULL, of the calling thread's last failed bi_setup). */
 const char* bi_last_error(bi_handle h);
 
 /* Device status of h (implementation health, no counterpart in the paper): synchronises

@@ -8,6 +8,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <exception>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -156,6 +157,9 @@ static void setup_worker(bi_server_s* S) {
             S->cv.notify_all();
         } catch (const bi_error& e) {
             fail_request(S, r, e.code, e.msg);
+        } catch (const std::exception& e) {
+            // host allocation failure: fail this request, keep the worker alive
+            fail_request(S, r, BI_ERR_OOM, std::string("setup: ") + e.what());
         }
     }
 }
@@ -193,6 +197,10 @@ static void serve_loop(bi_server_s* S) {
                 }
             } catch (const bi_error& e) {
                 fail_request(S, r, e.code, e.msg);
+                S->running.erase(S->running.begin() + i);
+                continue;
+            } catch (const std::exception& e) {
+                fail_request(S, r, BI_ERR_OOM, std::string("solve: ") + e.what());
                 S->running.erase(S->running.begin() + i);
                 continue;
             }
