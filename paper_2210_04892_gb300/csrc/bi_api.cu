@@ -1,6 +1,7 @@
 // C-ABI entry points (include/bi.h): argument checks, handle lifecycle, error text.
 #include <chrono>
 #include <cstring>
+#include <exception>
 #include <string>
 
 #include "bi_internal.h"
@@ -178,6 +179,10 @@ static int guarded(bi_handle h, F&& f) {
     } catch (const bi_error& e) {
         h->err = e.msg;
         return e.code;
+    } catch (const std::exception& e) {
+        // a host allocation failed: report it rather than let it cross the C ABI
+        h->err = std::string("host: ") + e.what();
+        return BI_ERR_OOM;
     }
 }
 

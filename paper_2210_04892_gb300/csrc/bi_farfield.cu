@@ -189,5 +189,8 @@ extern "C" int bi_farfield_noalloc(bi_handle h, const void* x, int nrhs, const d
     } catch (const bi_error& e) {
         h->err = e.msg;
         return e.code;
+    } catch (const std::exception& e) {
+        h->err = std::string("host: ") + e.what();
+        return BI_ERR_OOM;
     }
 }

@@ -4,6 +4,7 @@
 // a machine without a GPU.
 #include <cstring>
 #include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -36,7 +37,8 @@ extern "C" int bi_plan_create(const double* verts, int nv, const int* tris, int 
         g_plan_error = "bi_plan_create: null mesh, fewer than 4 triangles, or k0 <= 0";
         return BI_ERR_ARG;
     }
-    bi_plan_s* p = new bi_plan_s();
+    bi_plan_s* p = new (std::nothrow) bi_plan_s();
+    if (!p) return BI_ERR_OOM;
     bi_handle_s* h = &p->h;
     if (opt) h->prm = *opt;
     else bi_default_params(&h->prm);
@@ -86,8 +88,18 @@ extern "C" int bi_plan_info(bi_plan p, bi_info_t* info) {
     return BI_OK;
 }
 
+static int plan_get(const bi_plan_s* p, int what, int level, void* out, int64_t bytes, int64_t* count);
+
 extern "C" int bi_plan_get(bi_plan p, int what, int level, void* out, int64_t bytes, int64_t* count) {
     if (!p) return BI_ERR_ARG;
+    try {
+        return plan_get(p, what, level, out, bytes, count);
+    } catch (const std::exception&) {
+        return BI_ERR_OOM;              // a converted copy (codes 11, 40, 41) did not fit
+    }
+}
+
+static int plan_get(const bi_plan_s* p, int what, int level, void* out, int64_t bytes, int64_t* count) {
     const bi_handle_s& h = p->h;
     const bool lev_ok = level >= 0 && level < h.nlev;
     const bool far_ok = lev_ok && level >= 2 && level <= h.leaf;

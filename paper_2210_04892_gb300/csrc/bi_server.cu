@@ -11,7 +11,9 @@
 #include <exception>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
+#include <new>
 #include <thread>
 #include <unordered_map>
 
@@ -221,7 +223,8 @@ extern "C" void bi_server_default_params(bi_server_params* p) {
 extern "C" int bi_server_create(const bi_server_params* prm, bi_server* out) {
     if (!out) return BI_ERR_ARG;
     *out = nullptr;
-    bi_server_s* S = new bi_server_s();
+    bi_server_s* S = new (std::nothrow) bi_server_s();
+    if (!S) return BI_ERR_OOM;
     if (prm) S->prm = *prm;
     else bi_server_default_params(&S->prm);
     if (S->prm.max_active < 1 || S->prm.queue_capacity < 1 || S->prm.mem_budget_bytes < 0) {
@@ -240,8 +243,21 @@ extern "C" int bi_server_create(const bi_server_params* prm, bi_server* out) {
         }
         S->prm.mem_budget_bytes = (int64_t)(fr * 0.8);
     }
-    S->setup_thread = std::thread(setup_worker, S);
-    S->serve_thread = std::thread(serve_loop, S);
+    try {
+        S->setup_thread = std::thread(setup_worker, S);
+        S->serve_thread = std::thread(serve_loop, S);
+    } catch (const std::exception&) {
+        // a thread could not be started: stop the one that may have started, then give up
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->stop = true;
+        }
+        S->cv.notify_all();
+        if (S->setup_thread.joinable()) S->setup_thread.join();
+        if (S->serve_thread.joinable()) S->serve_thread.join();
+        delete S;
+        return BI_ERR_OOM;
+    }
     *out = S;
     return BI_OK;
 }
@@ -251,32 +267,41 @@ extern "C" int bi_submit(bi_server S, const double* verts, int nv, const int* tr
                          int64_t* req) {
     if (!S || !verts || !tris || nv < 3 || nt < 4 || !(k0 > 0) || nrhs < 1 || !khat || !phat || !(tol > 0) || !req)
         return BI_ERR_ARG;
-    request* r = new request();
-    r->verts.assign(verts, verts + 3 * (size_t)nv);
-    r->tris.assign(tris, tris + 3 * (size_t)nt);
+    std::unique_ptr<request> r;
+    try {
+        r.reset(new request());
+        r->verts.assign(verts, verts + 3 * (size_t)nv);
+        r->tris.assign(tris, tris + 3 * (size_t)nt);
+        r->khat.assign(khat, khat + 3 * (size_t)nrhs);
+        r->phat.assign(phat, phat + 3 * (size_t)nrhs);
+    } catch (const std::exception&) {
+        return BI_ERR_OOM;              // the copies of the inputs did not fit in host memory
+    }
     r->k0 = k0;
     if (opt) r->prm = *opt;
     else bi_default_params(&r->prm);
     r->nrhs = nrhs;
-    r->khat.assign(khat, khat + 3 * (size_t)nrhs);
-    r->phat.assign(phat, phat + 3 * (size_t)nrhs);
     r->tol = tol;
     r->t_submit = clk::now();
-    r->est_bytes = estimate_request_bytes(r);
+    r->est_bytes = estimate_request_bytes(r.get());
     std::lock_guard<std::mutex> lk(S->mu);
-    if ((int)S->queue.size() >= S->prm.queue_capacity) {
-        delete r;
-        return BI_ERR_BUSY;
-    }
+    if ((int)S->queue.size() >= S->prm.queue_capacity) return BI_ERR_BUSY;
     if (r->est_bytes > S->prm.mem_budget_bytes) {
         S->err = "bi_submit: request needs more device memory than the whole budget";
-        delete r;
         return BI_ERR_OOM;
     }
-    r->id = S->next_id++;
-    S->all[r->id] = r;
-    S->queue.push_back(r);
-    *req = r->id;
+    const int64_t id = S->next_id;
+    try {
+        S->all[id] = r.get();
+        S->queue.push_back(r.get());
+    } catch (const std::exception&) {
+        S->all.erase(id);
+        return BI_ERR_OOM;
+    }
+    S->next_id += 1;
+    r->id = id;
+    *req = id;
+    r.release();                        // owned by S->all from here on
     S->cv.notify_all();
     return BI_OK;
 }
