@@ -57,3 +57,38 @@ def test_setup_rejects_bad_arguments_without_gpu_work():
     assert L.bi_setup(v4.ctypes.data, 4, t4.ctypes.data, 4, 1.0, 3, ctypes.byref(p), ctypes.byref(h)) == bi.BI_ERR_ARG
     assert b"out of range" in L.bi_last_error(None)
     assert L.bi_matvec(None, None, None, 1) == bi.BI_ERR_ARG
+
+
+def test_every_entry_point_rejects_null_handles():
+    """The error contract of the header: a NULL handle, server or plan (or a NULL output)
+    gives BI_ERR_ARG, never a crash; the void entry points accept NULL.  No device call is
+    made, so this runs without a GPU."""
+    from paper_2210_04892_gb300 import bi
+    L = bi.load()
+    E = bi.BI_ERR_ARG
+    assert L.bi_num_unknowns(None, None, None) == E
+    assert L.bi_rwg_edges(None, None) == E
+    assert L.bi_get_info(None, None) == E
+    assert L.bi_matvec(None, None, None, 1) == E
+    assert L.bi_matvec_host(None, None, None, 1) == E
+    assert L.bi_rhs_planewave(None, None, None, 1, None) == E
+    assert L.bi_solve(None, None, None, 1, 1e-3, None, None) == E
+    assert L.bi_set_coupling(None, 1, None, None, None, None, None, None, bi.QSOLVE(), None) == E
+    assert L.bi_matvec_coupled(None, None, None, 1) == E
+    assert L.bi_farfield(None, None, 1, None, 1, None) == E
+    assert L.bi_farfield_noalloc(None, None, 1, None, 1, None) == E
+    assert L.bi_debug_copy(None, 0, 0, None, 0) == E
+    assert L.bi_profile_stages(None, None, None, 1, 1, None) == E
+    assert L.bi_device_status(None) == E
+    L.bi_destroy(None)
+    assert L.bi_server_create(None, None) == E
+    assert L.bi_submit(None, None, 0, None, 0, 1.0, None, 1, None, None, 1e-3, None) == E
+    assert L.bi_poll(None, 0, None, None) == E
+    assert L.bi_result(None, 0, None, 0, None, None, None, None) == E
+    assert L.bi_release(None, 0) == E
+    assert L.bi_server_last_error(None) == b""
+    L.bi_server_destroy(None)
+    assert L.bi_plan_info(None, None) == E
+    assert L.bi_plan_get(None, 0, 0, None, 0, None) == E
+    L.bi_plan_destroy(None)
+    assert L.bi_stage_name(0) == b"gather" and L.bi_stage_name(-1) == b"" and L.bi_stage_name(8) == b""
