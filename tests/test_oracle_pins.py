@@ -520,3 +520,80 @@ def test_addition_theorem_at_lossy_wavenumber():
     # the coat's own wavelength is shorter: boxes of a quarter of it behave like free-space ones
     a1 = 0.25 * K0 / abs(K_LOSSY)
     assert _expansion_error(4, a=a1, k=K_LOSSY) < 2e-3
+
+
+def _rwg_patterns(v, t, k, khat, center, sign):
+    """Per RWG n of mesh (v, t): int f_n exp(sign j k khat.(r - center)) dS and the same for
+    n x f_n, on every direction (numpy, subdivided Gauss rule per triangle; independent of
+    the C oracle except for the RWG numbering)."""
+    r = oracle.rwg(v, t)
+    e, tp, tm, lp, lm = r["edges"], r["tplus"], r["tminus"], r["lplus"], r["lminus"]
+    N = len(e)
+    P = np.zeros((N, len(khat), 3), complex)
+    PX = np.zeros_like(P)
+    for n in range(N):
+        length = np.linalg.norm(v[e[n, 1]] - v[e[n, 0]])
+        for tri, loc, s in ((tp[n], lp[n], 1.0), (tm[n], lm[n], -1.0)):
+            T = v[t[tri]]
+            area = np.linalg.norm(np.cross(T[1] - T[0], T[2] - T[0])) / 2
+            nrm = np.cross(T[1] - T[0], T[2] - T[0]) / (2 * area)
+            x, w = _brute_rule(T, s=1, n=6)
+            f = s * (length / (2 * area)) * (x - T[loc])            # RWG on this triangle
+            ph = np.exp(sign * 1j * k * ((x - center) @ khat.T))    # [q, dir]
+            P[n] += np.einsum("q,qd,qc->dc", w, ph, f)
+            PX[n] += np.einsum("q,qd,qc->dc", w, ph, np.cross(nrm, f))
+    return P, PX
+
+
+@pytest.mark.parametrize("k", [K0, K_LOSSY], ids=["real_k", "lossy_k"])
+def test_far_field_factorisation_of_the_four_operators(k):
+    """The far-field forms on which the multilevel product rests, checked on two small spheres
+    three box sizes apart against the oracle's dense cross blocks:
+        <L>   = -jk c R.F_t,     <n x L>    =  jk c RX.F_t,
+        <Kbar> = -jk c R.(khat x F),  <n x Kbar> = jk c RX.(khat x F),
+    with c = (-jk/16 pi^2) sum_khat w T_L, F = int f exp(+jk khat.(r' - c_s)),
+    R = int f exp(-jk khat.(r - c_b)), RX the same for n x f.  At a complex k, R is not
+    conj(F) and must be integrated as such."""
+    from scipy import special
+    a = 0.2
+    cb, cs = np.array([0.0, 0.0, 0.0]), np.array([3 * a, 0.0, 0.0])
+    vb, tb = icosphere(2, 0.04, center=cb)
+    vs, ts = icosphere(2, 0.04, center=cs)
+    v = np.concatenate([vb, vs])
+    t = np.concatenate([tb, ts + len(vb)])
+    L, NL, K, NK = oracle.operators(v, t, k, 1)
+    nb = len(oracle.rwg(vb, tb)["edges"])
+    blocks = [A[:nb, nb:] for A in (L, NL, K, NK)]
+    # directions and the translation operator for the box offset X = c_b - c_s
+    kr = float(np.real(k)) * np.sqrt(3) * a
+    Lmax = int(math.ceil(kr + 1.8 * 6 ** (2 / 3) * kr ** (1 / 3)))
+    x, wx = np.polynomial.legendre.leggauss(Lmax + 1)
+    nphi = 2 * (Lmax + 1)
+    TH, PH = np.meshgrid(np.arccos(x), 2 * np.pi * np.arange(nphi) / nphi, indexing="ij")
+    W = (wx[:, None] * np.ones(nphi)[None, :] * 2 * np.pi / nphi).ravel()
+    kh = np.stack([np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)], -1).reshape(-1, 3)
+    X = cb - cs
+    Xn = np.linalg.norm(X)
+    cosg = kh @ (X / Xn)
+    T = sum((-1j) ** l * (2 * l + 1) * (special.spherical_jn(l, k * Xn) - 1j * special.spherical_yn(l, k * Xn))
+            * special.eval_legendre(l, cosg) for l in range(Lmax + 1))
+    c = (-1j * k / (16 * np.pi ** 2)) * W * T                        # per direction
+    R, RX = _rwg_patterns(vb, tb, k, kh, cb, -1.0)
+    F, _ = _rwg_patterns(vs, ts, k, kh, cs, +1.0)
+    Ft = F - kh[None] * np.einsum("ndc,dc->nd", F, kh)[..., None]
+    kxF = np.cross(kh[None], F)
+    far = [-1j * k * np.einsum("d,mdc,ndc->mn", c, R, Ft),
+           1j * k * np.einsum("d,mdc,ndc->mn", c, RX, Ft),
+           -1j * k * np.einsum("d,mdc,ndc->mn", c, R, kxF),
+           1j * k * np.einsum("d,mdc,ndc->mn", c, RX, kxF)]
+    for q, (dense, ff) in enumerate(zip(blocks, far)):
+        err = np.abs(dense - ff).max() / np.abs(dense).max()
+        assert err < 1e-6, (q, err)
+    # R = conj(F) (and so the antipodal packing of the stored patterns) holds at real k only
+    Fb, _ = _rwg_patterns(vb, tb, k, kh, cb, +1.0)
+    via_conj = -1j * k * np.einsum("d,mdc,ndc->mn", c, np.conj(Fb), Ft)
+    err_conj = np.abs(blocks[0] - via_conj).max() / np.abs(blocks[0]).max()
+    if np.imag(k) == 0:
+        assert err_conj < 1e-6
+    else:
+        assert err_conj > 1e-2
