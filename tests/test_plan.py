@@ -404,3 +404,83 @@ def test_translation_hankel_table(bi, sphere, digits, leaf_box):
                 assert np.all(np.abs(g[deep, 0] - j[deep]) <= 1e-12 * np.abs(j[deep])), (l, o)
         assert di.max() + 1 == len(sq) == 15      # distinct |X|^2 among the 316 far offsets
     p.close()
+
+
+def _rwg_pattern_subset(v, t, rwg, idx, k, khat, center):
+    """int f_n exp(+jk khat.(r - center)) dS for the RWG indices idx (numpy: a 6 x 6 conical
+    Gauss rule on each of the four midpoint sub-triangles of every triangle)."""
+    e, tp, tm, lp, lm = rwg["edges"], rwg["tplus"], rwg["tminus"], rwg["lplus"], rwg["lminus"]
+    g, gw = np.polynomial.legendre.leggauss(6)
+    g, gw = (g + 1) / 2, gw / 2
+    U, V = np.meshgrid(g, g, indexing="ij")
+    b1, b2 = U.ravel(), ((1 - U) * V).ravel()
+    ww = (np.outer(gw, gw) * (1 - U)).ravel() * 2
+    P = np.zeros((len(idx), len(khat), 3), complex)
+    for j, n in enumerate(idx):
+        length = np.linalg.norm(v[e[n, 1]] - v[e[n, 0]])
+        for tri, loc, s in ((tp[n], lp[n], 1.0), (tm[n], lm[n], -1.0)):
+            T = v[t[tri]]
+            area = np.linalg.norm(np.cross(T[1] - T[0], T[2] - T[0])) / 2
+            m01, m12, m20 = (T[0] + T[1]) / 2, (T[1] + T[2]) / 2, (T[2] + T[0]) / 2
+            for S in ((T[0], m01, m20), (m01, T[1], m12), (m20, m12, T[2]), (m01, m12, m20)):
+                x = S[0] + b1[:, None] * (S[1] - S[0]) + b2[:, None] * (S[2] - S[0])
+                f = s * (length / (2 * area)) * (x - T[loc])
+                ph = np.exp(1j * k * ((x - center) @ khat.T))
+                P[j] += np.einsum("q,qd,qc->dc", ww * area / 4, ph, f)
+    return P
+
+
+def _directions(theta, nph):
+    TH, PH = np.meshgrid(theta, 2 * np.pi * np.arange(nph) / nph, indexing="ij")
+    kh = np.stack([np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)], -1).reshape(-1, 3)
+    th = np.stack([np.cos(TH) * np.cos(PH), np.cos(TH) * np.sin(PH), -np.sin(TH)], -1).reshape(-1, 3)
+    ph = np.stack([-np.sin(PH), np.cos(PH), 0 * PH], -1).reshape(-1, 3)
+    return kh, th, ph
+
+
+@pytest.mark.parametrize("k", [K0, K0 * np.sqrt(2.0 - 0.5j)], ids=["real_k", "lossy_k"])
+def test_aggregation_step_reproduces_the_parent_pattern(bi, k):
+    """One upward step of the multilevel product, with the plan's tables: each child box's
+    outgoing pattern (RWG radiation patterns about the child centre, random coefficients) is
+    interpolated to the parent grid and multiplied by exp(+jk khat.(c_child - c_parent)); the
+    sum over the children equals the pattern computed directly about the parent centre, in
+    both transverse components.  The opposite shift sign fails.  At the coating's complex k
+    the sampling comes from Re k."""
+    import oracle
+    v, t = inputs.icosphere(16, 1.0)
+    p = bi.Plan(v, t, float(np.real(k)), digits=3)
+    info = p.info()
+    lf = info["leaf_level"]
+    l = lf - 1
+    a = info["root_size"] / 2 ** l
+    edges, perm, start = p.get(13).reshape(-1, 2), p.get(12), p.get(0)
+    mid = 0.5 * (v[edges[:, 0]] + v[edges[:, 1]])
+    lo = 0.5 * (mid.min(0) + mid.max(0)) - 0.5 * info["root_size"]
+    cp, cc, pc = p.get(5, l), p.get(3, lf).reshape(-1, 3), p.get(3, l).reshape(-1, 3)
+    q = int(np.argmax(np.diff(cp)))                     # the parent with the most children
+    c_par = lo + (pc[q] + 0.5) * a
+    nth_c, nph_c = info["L"][lf] + 1, 2 * (info["L"][lf] + 1)
+    nth_p, nph_p = info["L"][l] + 1, 2 * (info["L"][l] + 1)
+    khc, thc, phc = _directions(p.get(20, lf), nph_c)
+    khp, thp, php = _directions(p.get(20, l), nph_p)
+    A, B, _, _ = interp_matrices(p, l, nth_c, nph_c, nth_p, nph_p)
+    rwg = oracle.rwg(v, t)
+    rng = np.random.default_rng(inputs.SEED_BASE + 79)
+    direct = np.zeros((len(khp), 3), complex)
+    up = {+1: [0, 0], -1: [0, 0]}
+    for b in range(cp[q], cp[q + 1]):
+        c_ch = lo + (cc[b] + 0.5) * (a / 2)
+        rows = perm[start[b]:start[b + 1]]
+        x = rng.normal(size=len(rows)) + 1j * rng.normal(size=len(rows))
+        Fc = np.einsum("n,ndc->dc", x, _rwg_pattern_subset(v, t, rwg, rows, k, khc, c_ch))
+        direct += np.einsum("n,ndc->dc", x, _rwg_pattern_subset(v, t, rwg, rows, k, khp, c_par))
+        for sgn in (+1, -1):
+            sh = np.exp(sgn * 1j * k * (khp @ (c_ch - c_par)))
+            for i, comp in enumerate((thc, phc)):
+                g = (A @ np.einsum("dc,dc->d", Fc, comp)).reshape(nth_p, nph_c) @ B.T
+                up[sgn][i] = up[sgn][i] + g.reshape(-1) * sh
+    ref = [np.einsum("dc,dc->d", direct, thp), np.einsum("dc,dc->d", direct, php)]
+    scale = max(np.abs(r).max() for r in ref)
+    err = {s: max(np.abs(up[s][i] - ref[i]).max() for i in range(2)) / scale for s in (+1, -1)}
+    assert err[+1] < 1e-4, err
+    assert err[-1] > 0.1, err
