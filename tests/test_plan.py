@@ -484,3 +484,123 @@ def test_aggregation_step_reproduces_the_parent_pattern(bi, k):
     err = {s: max(np.abs(up[s][i] - ref[i]).max() for i in range(2)) / scale for s in (+1, -1)}
     assert err[+1] < 1e-4, err
     assert err[-1] > 0.1, err
+
+
+def _multilevel_L_product(bi, k, nu, radius, leaf, digits):
+    """The multilevel product of the Galerkin operator <f, L f> in numpy, built only from the
+    plan's tables (sampling from Re k, interpolation taps, interaction lists, box tree):
+    leaf patterns F and R (integrated separately: at complex k, R is not conj F), upward
+    interpolation and shift, diagonal translations T_L (weights and -jk/16 pi^2 folded in),
+    downward shift and exact-transpose anterpolation, receive -jk sum R.V.  Near pairs come
+    from the oracle's dense matrix.  Returns (levels, relative error of the whole product,
+    relative error of its far part) against the oracle's dense product."""
+    import oracle
+    from scipy import special
+    v, t = inputs.icosphere(nu, radius)
+    p = bi.Plan(v, t, float(np.real(k)), digits=digits, leaf_box=leaf)
+    info = p.info()
+    lf = info["leaf_level"]
+    rwg = oracle.rwg(v, t)
+    edges, perm, start = p.get(13).reshape(-1, 2), p.get(12), p.get(0)
+    mid = 0.5 * (v[edges[:, 0]] + v[edges[:, 1]])
+    lo = 0.5 * (mid.min(0) + mid.max(0)) - 0.5 * info["root_size"]
+    size = {l: info["root_size"] / 2 ** l for l in range(lf + 1)}
+    cen = {l: lo + (p.get(3, l).reshape(-1, 3) + 0.5) * size[l] for l in range(2, lf + 1)}
+    grids = {}
+    for l in range(2, lf + 1):
+        nth, nph = info["L"][l] + 1, 2 * (info["L"][l] + 1)
+        grids[l] = (nth, nph) + _directions(p.get(20, l), nph) + (p.get(21, l),)
+    # leaf patterns F (about the leaf centre, +jk) and R (-jk), theta/phi components
+    nth, nph, kh, th, ph, _ = grids[lf]
+    N = len(rwg["edges"])
+    nb = info["boxes"][lf]
+    F = np.zeros((2, N, nth * nph), complex)          # theta, phi components
+    R = np.zeros_like(F)
+    for b in range(nb):
+        rows = perm[start[b]:start[b + 1]]
+        Fp = _rwg_pattern_subset(v, t, rwg, rows, k, kh, cen[lf][b])
+        Rp = _rwg_pattern_subset(v, t, rwg, rows, -k, kh, cen[lf][b])   # exp(-jk khat.(r - c))
+        for i, comp in enumerate((th, ph)):
+            F[i, rows] = np.einsum("ndc,dc->nd", Fp, comp)
+            R[i, rows] = np.einsum("ndc,dc->nd", Rp, comp)
+    rng = np.random.default_rng(inputs.SEED_BASE + 80)
+    x = rng.normal(size=N) + 1j * rng.normal(size=N)
+    # outgoing leaf patterns
+    U = {lf: np.zeros((nb, 2, nth * nph), complex)}
+    for b in range(nb):
+        rows = perm[start[b]:start[b + 1]]
+        for i in range(2):
+            U[lf][b, i] = x[rows] @ F[i, rows]
+    interp = {}
+    for l in range(lf - 1, 1, -1):
+        nthc, nphc = grids[l + 1][:2]
+        nthp, nphp, khp = grids[l][:3]
+        A, B, _, _ = interp_matrices(p, l, nthc, nphc, nthp, nphp)
+        interp[l] = (A, B)
+        cp = p.get(5, l)
+        U[l] = np.zeros((info["boxes"][l], 2, nthp * nphp), complex)
+        for q in range(info["boxes"][l]):
+            for c in range(cp[q], cp[q + 1]):
+                sh = np.exp(1j * k * (khp @ (cen[l + 1][c] - cen[l][q])))
+                for i in range(2):
+                    g = (A @ U[l + 1][c, i]).reshape(nthp, nphc) @ B.T
+                    U[l][q, i] += g.reshape(-1) * sh
+    # translations (weights and -jk/16pi^2 folded into T)
+    V = {l: np.zeros_like(U[l]) for l in U}
+    for l in range(2, lf + 1):
+        nthl, nphl, khl, _, _, wl = grids[l]
+        W = (wl[:, None] * np.ones(nphl)[None, :] * 2 * np.pi / nphl).ravel()
+        Lt = info["L"][l]
+        ptr, src, off = p.get(6, l), p.get(7, l), p.get(8, l)
+        cache = {}
+        for b in range(info["boxes"][l]):
+            for e in range(ptr[b], ptr[b + 1]):
+                o = int(off[e])
+                if o not in cache:
+                    X = np.array([o // 49 - 3, (o // 7) % 7 - 3, o % 7 - 3]) * size[l]
+                    Xn = np.linalg.norm(X)
+                    cg = khl @ (X / Xn)
+                    h2 = [special.spherical_jn(n, k * Xn) - 1j * special.spherical_yn(n, k * Xn) for n in range(Lt + 1)]
+                    T = sum((-1j) ** n * (2 * n + 1) * h2[n] * special.eval_legendre(n, cg) for n in range(Lt + 1))
+                    cache[o] = (-1j * k / (16 * np.pi ** 2)) * W * T
+                V[l][b] += cache[o][None] * U[l][src[e]]
+    # downward: shift, anterpolate (exact transpose)
+    for l in range(2, lf):
+        A, B = interp[l]
+        nthp, nphp, khp = grids[l][:3]
+        cp = p.get(5, l)
+        for q in range(info["boxes"][l]):
+            for c in range(cp[q], cp[q + 1]):
+                sh = np.exp(-1j * k * (khp @ (cen[l + 1][c] - cen[l][q])))
+                for i in range(2):
+                    vv = (V[l][q, i] * sh).reshape(nthp, nphp) @ B
+                    V[l + 1][c, i] += A.T @ vv.reshape(-1)
+    # receive
+    yfar = np.zeros(N, complex)
+    for b in range(nb):
+        rows = perm[start[b]:start[b + 1]]
+        yfar[rows] = -1j * k * (R[0, rows] @ V[lf][b, 0] + R[1, rows] @ V[lf][b, 1])
+    # near pairs from the dense matrix, reference = dense product
+    Ld, _, _, _ = oracle.operators(v, t, k, 0)
+    nptr, nsrc = p.get(1), p.get(2)
+    ynear = np.zeros(N, complex)
+    for b in range(nb):
+        rb = perm[start[b]:start[b + 1]]
+        cols = np.concatenate([perm[start[s]:start[s + 1]] for s in nsrc[nptr[b]:nptr[b + 1]]])
+        ynear[rb] += Ld[np.ix_(rb, cols)] @ x[cols]
+    ref = Ld @ x
+    err_all = np.linalg.norm(ynear + yfar - ref) / np.linalg.norm(ref)
+    err_far = np.linalg.norm(yfar - (ref - ynear)) / np.linalg.norm(ref - ynear)
+    return info["levels"], err_all, err_far
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("k", [K0, K0 * np.sqrt(2.0 - 0.5j)], ids=["real_k", "lossy_k"])
+def test_multilevel_product_model_matches_the_dense_operator(bi, k):
+    """The whole multilevel chain on the 1280-triangle sphere of radius 0.5 lambda, with leaf
+    boxes of a quarter wavelength (of Re k) and 3 digits, reproduces the dense <f, L f> x of
+    the oracle within the 1e-3 bar, at real k (measured 1.2e-4; the GPU product gives 1.3e-4
+    on this mesh) and at the coating's complex k (1.5e-4)."""
+    levels, e_all, e_far = _multilevel_L_product(bi, k, 8, 0.5, 0.25, 3)
+    assert levels >= 3
+    assert e_all < 5e-4, (e_all, e_far)
