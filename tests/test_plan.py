@@ -1,9 +1,11 @@
 """Host-only checks of the set-up of the multilevel product (bi_plan_*): RWG numbering, octree,
 near and interaction lists of the MLFMA (Sec. II.D), parent-centred translation lists, angular
-sampling and Lagrange interpolation between levels.  The plan runs the same host code as
-bi_setup without a device, so these run on any machine; every expected value below follows
-from geometry or from the mathematics of the quadrature and the interpolation, not from the
-library."""
+sampling, Lagrange interpolation between levels and the translation Hankel table.  The plan
+runs the same host code as bi_setup without a device, so these run on any machine.  Every
+expected value below follows from geometry, from the mathematics of the quadrature, the
+interpolation and the special functions, or from the oracle's dense operator (the last two
+tests, which run one aggregation step and the whole multilevel chain in numpy on the plan's
+tables); none comes from the library."""
 import numpy as np
 import pytest
 
