@@ -3,9 +3,9 @@ near and interaction lists of the MLFMA (Sec. II.D), parent-centred translation 
 sampling, Lagrange interpolation between levels and the translation Hankel table.  The plan
 runs the same host code as bi_setup without a device, so these run on any machine.  Every
 expected value below follows from geometry, from the mathematics of the quadrature, the
-interpolation and the special functions, or from the oracle's dense operator (the last two
-tests, which run one aggregation step and the whole multilevel chain in numpy on the plan's
-tables); none comes from the library."""
+interpolation and the special functions, from radiation patterns integrated directly (the
+aggregation step), or from the oracle's dense operator (the whole multilevel chain, run in
+numpy on the plan's tables); none comes from the library."""
 import numpy as np
 import pytest
 
