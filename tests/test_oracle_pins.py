@@ -597,3 +597,99 @@ def test_far_field_factorisation_of_the_four_operators(k):
         assert err_conj < 1e-6
     else:
         assert err_conj > 1e-2
+
+
+# ------------------------------------------------- plane-wave right-hand sides (Eqs. 49-50)
+def _rwg_independent(v, t):
+    """RWG functions built here from the mesh alone: edges sorted by (min, max) vertex; T+ is
+    the triangle that runs along the edge from its smaller to its larger vertex (as listed)."""
+    owners = {}
+    for ti, tri in enumerate(t):
+        for i in range(3):
+            a, b = int(tri[i]), int(tri[(i + 1) % 3])
+            owners.setdefault((min(a, b), max(a, b)), []).append((ti, a < b, int(tri[(i + 2) % 3])))
+    out = []
+    for e in sorted(owners):
+        (t0, fwd0, p0), (t1, fwd1, p1) = owners[e]
+        plus, minus = ((t0, p0), (t1, p1)) if fwd0 else ((t1, p1), (t0, p0))
+        out.append((e, plus, minus))
+    return out
+
+
+def _rhs_by_quadrature(v, t, k, khat, phat, rule):
+    """b^J = <f, E/2 + n x H/2>, b^M = <f, H/2 - n x E/2> (Eqs. 49-50) for E = p exp(-jk khat.r),
+    H = (khat x p) exp(-jk khat.r), integrated with rule(triangle vertices) -> (points, weights)."""
+    khat, phat = np.asarray(khat, float), np.asarray(phat, float)
+    hp = np.cross(khat, phat)
+    funcs = _rwg_independent(v, t)
+    N = len(funcs)
+    b = np.zeros(2 * N, complex)
+    for m, (e, plus, minus) in enumerate(funcs):
+        l = np.linalg.norm(v[e[1]] - v[e[0]])
+        for sgn, (ti, pv) in ((1.0, plus), (-1.0, minus)):
+            P = v[t[ti]]
+            nn = np.cross(P[1] - P[0], P[2] - P[0])
+            A = np.linalg.norm(nn) / 2
+            nn /= 2 * A
+            x, w = rule(P)
+            f = sgn * (l / (2 * A)) * (x - v[pv])
+            ph = np.exp(-1j * k * (x @ khat))
+            tj = phat + np.cross(nn, hp)          # E + n x H (both times the phase)
+            tm = hp - np.cross(nn, phat)          # H - n x E
+            b[m] += 0.5 * np.sum(w * ph * (f @ tj))
+            b[N + m] += 0.5 * np.sum(w * ph * (f @ tm))
+    return b
+
+
+def _centroid_rule(P):
+    """At k = 0 the integrand is linear in r: the centroid rule is exact."""
+    A = np.linalg.norm(np.cross(P[1] - P[0], P[2] - P[0])) / 2
+    return P.mean(0)[None, :], np.array([A])
+
+
+KH_RHS = np.array([0.36, -0.48, 0.8])
+PH_RHS = np.cross(KH_RHS, [0.0, 0.0, 1.0]) / np.linalg.norm(np.cross(KH_RHS, [0.0, 0.0, 1.0]))
+
+
+def test_rwg_numbering_of_the_pins_matches_the_oracle():
+    v, t = icosphere(1, 0.3)
+    E = oracle.rwg(v, t)
+    mine = _rwg_independent(v, t)
+    assert [tuple(e) for e in E["edges"]] == [f[0] for f in mine]
+    assert list(E["tplus"]) == [f[1][0] for f in mine]
+    assert list(E["tminus"]) == [f[2][0] for f in mine]
+
+
+def test_planewave_rhs_closed_form_at_zero_frequency():
+    """At k = 0, int_T f = +-(l/2)(centroid - p): b^J and b^M of Eqs. 49-50 are sums of dot
+    products with the constant fields.  A flipped n x E (or n x H) term fails by O(1)."""
+    v, t = icosphere(1, 0.3)
+    b = oracle.rhs_planewave(v, t, 0.0, 0, KH_RHS, PH_RHS)[0]
+    ref = _rhs_by_quadrature(v, t, 0.0, KH_RHS, PH_RHS, _centroid_rule)
+    N = len(ref) // 2
+    assert np.abs(b - ref).max() < 1e-14 * np.abs(ref).max()
+    # the pin separates the signs of Eq. 50: H/2 + n x E/2 is far from the oracle's row
+    hp = np.cross(KH_RHS, PH_RHS)
+    funcs = _rwg_independent(v, t)
+    flip = np.zeros(N, complex)
+    for m, (e, plus, minus) in enumerate(funcs):
+        l = np.linalg.norm(v[e[1]] - v[e[0]])
+        for sgn, (ti, pv) in ((1.0, plus), (-1.0, minus)):
+            P = v[t[ti]]
+            nn = np.cross(P[1] - P[0], P[2] - P[0])
+            nn /= np.linalg.norm(nn)
+            flip[m] += 0.5 * sgn * (l / 2) * np.dot(P.mean(0) - v[pv], hp + np.cross(nn, PH_RHS))
+    assert np.linalg.norm(flip - b[N:]) > 0.3 * np.linalg.norm(b[N:])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_planewave_rhs_vs_brute_force(mode):
+    """At k = 2 pi on a 0.3-wavelength sphere, against a subdivided Gauss product rule.  Mode 1
+    (the PEC combined-field row) is the J half of mode 0."""
+    v, t = icosphere(2, 0.3)
+    b = oracle.rhs_planewave(v, t, K0, mode, KH_RHS, PH_RHS)[0]
+    ref = _rhs_by_quadrature(v, t, K0, KH_RHS, PH_RHS, lambda P: _brute_rule(P, s=1, n=8))
+    N = len(ref) // 2
+    if mode == 1:
+        ref = ref[:N]
+    assert np.linalg.norm(b - ref) / np.linalg.norm(ref) < 1e-6
