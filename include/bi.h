@@ -174,20 +174,22 @@ int bi_matvec_coupled(bi_handle h, const void* x, void* y, int nrhs);
  * when a later call needs more) and keeps until bi_destroy.  Queued on the handle's stream. */
 int bi_farfield(bi_handle h, const void* x, int nrhs, const double* dirs, int ndir, void* F);
 
-/* Allocation-free far field, for callers that must not allocate device memory during the
- * call: code that runs while a CUDA stream is being captured into a graph, real-time loops
- * with a fixed memory budget, or hosts whose allocator is owned by someone else.  (The paper
- * has no counterpart: it is a deployment variant of bi_farfield.)
+/* Allocation-free far field, for callers that cannot allocate device memory while they
+ * run: real-time loops with a fixed memory budget set up in advance, or hosts whose device
+ * allocator belongs to another runtime or framework that forbids outside cudaMalloc calls.
+ * (The paper has no counterpart: it is a deployment variant of bi_farfield.)
  * Computes exactly what bi_farfield computes, with the same arguments, but its partial sums
  * go to a fixed array of BI_FARFIELD_NOALLOC_MAX_BYTES bytes compiled into the library: every
  * GPU that loads the library holds that array until the process exits.  Scratch needed:
  * ceil(N / 256) * nrhs * ndir * 96 bytes; larger requests return BI_ERR_ARG (split the
- * directions over several calls).  The call allocates nothing; its first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device current, so
- * make that first call before any stream capture.  All calls on a device share the array:
- * calls whose work overlaps on the GPU (different streams, or different handles on one
- * device) race on it -- order them on one stream or synchronise between them.  The handle
- * itself must already exist (bi_setup allocates). */
+ * directions over several calls).  The call allocates nothing.  The handle's device (the one
+ * current at bi_setup) must be current: otherwise BI_ERR_ARG.  The first call on each handle
+ * looks up the array's device address (cudaGetSymbolAddress) and keeps it in the handle; make
+ * that first call before any stream capture.  All calls on a device share the array, which
+ * keeps the last call's partial sums (each call writes every slot it reads): calls whose work
+ * overlaps on the GPU (different streams, or different handles on one device) race on it --
+ * order them on one stream or synchronise between them.  The handle itself must already
+ * exist (bi_setup allocates). */
 #define BI_FARFIELD_NOALLOC_MAX_BYTES (8u << 20)
 int bi_farfield_noalloc(bi_handle h, const void* x, int nrhs, const double* dirs, int ndir, void* F);
 
@@ -287,6 +289,15 @@ void bi_plan_destroy(bi_plan p);
 
 /* Text of the last error on h (or, when h is NULL, of the calling thread's last failed bi_setup). */
 const char* bi_last_error(bi_handle h);
+
+/* Diagnostics (no counterpart in the paper): limit, in SM clock cycles, of the consumer waits of
+ * the bulk-copy leaf kernels (aggregation and receive of one and few right-hand sides); cycles <= 0
+ * restores the default of 2^31 (about one second).  A wait that runs out makes its CTA drain its
+ * copies in flight (always with the default limit, so no copy lands after the CTA has left),
+ * record BI_ERR_TIMEOUT in the handle's device status word and leave its outputs unwritten.  With
+ * a limit of a few cycles a normal product gives up on its first copies: that is how the
+ * give-up path is tested without a copy that never lands.  Synchronises the handle's stream. */
+int bi_debug_set_wait_limit(bi_handle h, long long cycles);
 
 /* Device status of h (implementation health, no counterpart in the paper): synchronises
  * the handle's stream, then returns BI_ERR_TIMEOUT if a product kernel gave up a bounded

@@ -27,7 +27,7 @@ _NAMES = {0: "BI_OK", -1: "BI_ERR_ARG", -2: "BI_ERR_MESH", -3: "BI_ERR_OOM", -4:
 
 # entry points declared in include/bi.h
 EXPORTS = ["bi_default_params", "bi_setup", "bi_num_unknowns", "bi_rwg_edges", "bi_get_info", "bi_matvec",
-           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_profile_stages", "bi_stage_name", "bi_last_error", "bi_device_status", "bi_set_coupling", "bi_matvec_coupled", "bi_plan_create", "bi_plan_info", "bi_plan_get",
+           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_debug_set_wait_limit", "bi_profile_stages", "bi_stage_name", "bi_last_error", "bi_device_status", "bi_set_coupling", "bi_matvec_coupled", "bi_plan_create", "bi_plan_info", "bi_plan_get",
            "bi_plan_last_error", "bi_plan_destroy",
            "bi_destroy", "bi_server_default_params", "bi_server_create", "bi_submit", "bi_poll", "bi_result",
            "bi_release", "bi_server_last_error", "bi_server_destroy"]
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
     L.bi_farfield.argtypes = [vp, vp, i, vp, i, vp]
     L.bi_farfield_noalloc.argtypes = [vp, vp, i, vp, i, vp]
     L.bi_debug_copy.argtypes = [vp, i, i, vp, i64]
+    L.bi_debug_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
     L.bi_profile_stages.argtypes = [vp, vp, vp, i, i, vp]
     L.bi_stage_name.argtypes = [i]
     L.bi_stage_name.restype = ctypes.c_char_p
@@ -311,6 +312,10 @@ class Operator:
     def status(self):
         """Synchronise and raise BIError if a product kernel gave up a bounded device wait."""
         _check(load().bi_device_status(self.h), self.h)
+
+    def set_wait_limit(self, cycles):
+        """Diagnostics: limit of the bulk-copy waits in SM cycles (<= 0: the default)."""
+        _check(load().bi_debug_set_wait_limit(self.h, int(cycles)), self.h)
 
     def debug_buffer(self, what, level=0):
         """Copy of an internal device buffer (diagnostics; see bi_debug_copy in bi.h)."""

@@ -1,4 +1,6 @@
 // C-ABI entry points (include/bi.h): argument checks, handle lifecycle, error text.
+#include <map>
+#include <mutex>
 #include <chrono>
 #include <cstring>
 #include <exception>
@@ -19,6 +21,19 @@ void* bi_handle_s::alloc(size_t bytes) {
     owned.push_back({p, bytes});
     info.device_bytes += (int64_t)bytes;
     return p;
+}
+
+void bi_raise_smem_limit(const void* func, size_t bytes) {
+    if (bytes <= 48 * 1024) return;
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> limit;
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = limit[{dev, func}];
+    if (bytes <= cur) return;
+    CU(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
 }
 
 extern "C" void bi_default_params(bi_params* p) {
@@ -114,6 +129,7 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
         {
             int dev = 0;
             CU(cudaGetDevice(&dev));
+            h->device = dev;
             CU(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
         }
         bi_device_geometry(h, verts, tris);
@@ -356,6 +372,18 @@ extern "C" int bi_profile_stages(bi_handle h, const void* x, void* y, int nrhs, 
 }
 
 extern "C" const char* bi_stage_name(int i) { return bi_stage_name_impl(i); }
+
+extern "C" int bi_debug_set_wait_limit(bi_handle h, long long cycles) {
+    if (!h) return BI_ERR_ARG;
+    return guarded(h, [&] {
+        CU(cudaStreamSynchronize(h->stream));
+        h->wait_cycles = cycles > 0 ? cycles : (1ll << 31);
+        // the captured products carry the old limit as a kernel argument
+        for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+        h->graphs.clear();
+        return (int)BI_OK;
+    });
+}
 
 extern "C" int bi_farfield(bi_handle h, const void* x, int nrhs, const double* dirs, int ndir, void* F) {
     if (!h) return BI_ERR_ARG;

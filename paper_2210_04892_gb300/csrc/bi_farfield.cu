@@ -144,14 +144,7 @@ void bi_farfield_launch(bi_handle_s* h, const void* x, int nrhs, const double* d
 // array compiled into the library instead of handle-owned scratch, so the call itself
 // never allocates device memory.  Every GPU that loads the library holds this array until
 // the process exits; all calls on one device share it.
-#include <mutex>
-
 static __device__ __align__(256) double g_ff_noalloc_scratch[BI_FARFIELD_NOALLOC_MAX_BYTES / sizeof(double)];
-
-namespace {
-std::mutex g_ff_noalloc_mu;
-double* g_ff_noalloc_ptr[256] = {};  // device address of the array, per device ordinal
-}  // namespace
 
 extern "C" int bi_farfield_noalloc(bi_handle h, const void* x, int nrhs, const double* dirs, int ndir, void* F) {
     if (!h) return BI_ERR_ARG;
@@ -169,22 +162,24 @@ extern "C" int bi_farfield_noalloc(bi_handle h, const void* x, int nrhs, const d
     try {
         int dev = 0;
         CU(cudaGetDevice(&dev));
-        if (dev < 0 || dev >= 256) throw bi_error{BI_ERR_CUDA, "bi_farfield_noalloc: device ordinal out of range"};
-        double* part = nullptr;
-        {
-            // host code cannot use the array's name as an address: look the address up once
-            // per device, with that device current
-            std::lock_guard<std::mutex> lock(g_ff_noalloc_mu);
-            if (!g_ff_noalloc_ptr[dev]) {
-                void* p = nullptr;
-                CU(cudaGetSymbolAddress(&p, g_ff_noalloc_scratch));
-                g_ff_noalloc_ptr[dev] = (double*)p;
-            }
-            part = g_ff_noalloc_ptr[dev];
+        if (dev != h->device) {
+            // the array's address is per device: on another device it would name memory the
+            // handle's stream cannot use
+            h->err = "bi_farfield_noalloc: the current device (" + std::to_string(dev) +
+                     ") is not the handle's device (" + std::to_string(h->device) + "); make it current first";
+            return BI_ERR_ARG;
+        }
+        if (!h->ff_noalloc_part) {
+            // Host code cannot use the array's name as an address: look the address up on the
+            // handle's first call, with its device current.  The handle's lifetime is bounded by
+            // its device context, so the cached address cannot outlive the context it belongs to.
+            void* p = nullptr;
+            CU(cudaGetSymbolAddress(&p, g_ff_noalloc_scratch));
+            h->ff_noalloc_part = (double*)p;
         }
         // every partial-sum slot used by this call is written by the first pass before the
         // second pass reads it, so nothing needs clearing
-        bi_farfield_launch(h, x, nrhs, dirs, ndir, F, part, h->stream);
+        bi_farfield_launch(h, x, nrhs, dirs, ndir, F, h->ff_noalloc_part, h->stream);
         return BI_OK;
     } catch (const bi_error& e) {
         h->err = e.msg;

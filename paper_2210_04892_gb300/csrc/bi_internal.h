@@ -26,6 +26,16 @@ struct bi_error {
                            std::string(#call) + ": " + cudaGetErrorString(e_)};                        \
     } while (0)
 
+// Raise (never lower) a kernel's dynamic shared-memory limit on the current device.  The
+// limit belongs to the function, not to one launch: products captured into graphs earlier (by
+// this or another handle) keep their larger sizes, so a later, smaller request must not
+// lower it.  Sizes up to the 48 KB default need no call.
+void bi_raise_smem_limit(const void* func, size_t bytes);
+template <typename F>
+inline void bi_raise_smem(F* func, size_t bytes) {
+    bi_raise_smem_limit(reinterpret_cast<const void*>(func), bytes);
+}
+
 // Device pointer with a host-side size, freed by the handle.
 struct dbuf {
     void* p = nullptr;
@@ -119,6 +129,7 @@ struct bi_handle_s {
     bool use_fast = true;               // fused kernels (false: two-pass reference kernels)
     bool use_leaf_bulk = true;          // bulk-copy pipelines for leaf aggregation and receive
     int* d_status = nullptr;            // device status word (0: healthy; see bi_tma.cuh)
+    long long wait_cycles = 1ll << 31;  // limit of the bulk-copy waits of the leaf kernels (SM clocks)
     void* d_sai = nullptr;              // near-field SAI blocks, one dense [n_b][n_b] per leaf box (precond 1)
     struct coupling_t {                 // Eq. 52 coupling (caller-owned CSR arrays and Q^{-1} solver)
         int64_t n_int = 0;
@@ -134,7 +145,9 @@ struct bi_handle_s {
     int* d_near_work = nullptr;
     int* d_near_col0 = nullptr;         // per near entry: first column in the test box's segment
     int* d_near_ncol = nullptr;         // per leaf box: segment width (near columns)
-    int num_sms = 152;              // widest near segment of a leaf box (columns)
+    int num_sms = 152;
+    int device = -1;                    // CUDA device current at bi_setup (the handle's buffers live there)
+    double* ff_noalloc_part = nullptr;  // device address of the allocation-free far-field array on that device
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // host mesh / RWG in user order

@@ -24,8 +24,9 @@ namespace {
 
 constexpr int kBarBytes = 128;  // shared-memory header: up to 16 mbarriers
 
-// Thread 0, after a wait gave up: wait (bounded) for the copies still in flight so that no
-// copy lands after the CTA has left, then record the failure.
+// Thread 0, after a wait gave up: wait (bounded, with the default limit of about one second
+// whatever limit the consumers used) for the copies still in flight so that no copy lands
+// after the CTA has left, then record the failure.
 __device__ void give_up(uint64_t* bar, int first_chunk, int nch, int S, int* status) {
     if (threadIdx.x != 0) return;
     for (int c = first_chunk; c < min(first_chunk + S, nch); ++c) mbar_wait_bounded(&bar[c % S], (c / S) & 1);
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__(256) k_aggregate_bulk(int N, int K, int nph, i
                                                         const int* __restrict__ perm, const int* __restrict__ leaf_start,
                                                         const int* __restrict__ order, const cpx<T>* __restrict__ F,
                                                         const cpx<T>* __restrict__ x, cpx<T>* __restrict__ U,
-                                                        int* __restrict__ status) {
+                                                        int* __restrict__ status, long long wait) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int Kh = K / 2, E = 2 * R;
     const int b = order[blockIdx.x];
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(256) k_aggregate_bulk(int N, int K, int nph, i
     for (int j = 0; j < SL; ++j) ut[j] = up[j] = vt[j] = vp[j] = czero<T>();
     for (int c = 0; c < nch; ++c) {
         const int st = c % S;
-        const bool ok = mbar_wait_bounded(&bar[st], (c / S) & 1);
+        const bool ok = mbar_wait_bounded(&bar[st], (c / S) & 1, wait);
         if (!__syncthreads_and(ok)) {
             give_up(bar, c, nch, S, status);
             return;
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(256) k_receive_bulk(int N, int K, int nph, int
                                                       const int* __restrict__ order, const cpx<T>* __restrict__ F,
                                                       const cpx<T>* __restrict__ RX, const cpx<T>* __restrict__ V, T cc,
                                                       const cpx<T>* __restrict__ yt, cpx<T>* __restrict__ y,
-                                                      int* __restrict__ status) {
+                                                      int* __restrict__ status, long long wait) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int R = R1 ? 1 : R_;   // R1: one right-hand side, (V_theta, V_phi) adjacent
     const int Kh = K / 2, E = 2 * R;
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(256) k_receive_bulk(int N, int K, int nph, int
         }
     }
     __syncthreads();
-    if (!__syncthreads_and(mbar_wait_bounded(&bar[S], 0))) {
+    if (!__syncthreads_and(mbar_wait_bounded(&bar[S], 0, wait))) {
         if (threadIdx.x == 0) mbar_wait_bounded(&bar[S], 0);
         give_up(bar, 0, nch, S, status);
         return;
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(256) k_receive_bulk(int N, int K, int nph, int
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     for (int c = 0; c < nch; ++c) {
         const int st = c % S;
-        const bool ok = mbar_wait_bounded(&bar[st], (c / S) & 1);
+        const bool ok = mbar_wait_bounded(&bar[st], (c / S) & 1, wait);
         if (!__syncthreads_and(ok)) {
             give_up(bar, c, nch, S, status);
             return;
@@ -218,9 +219,10 @@ template <typename T, int MODE, int SL>
 void launch_aggregate(bi_handle_s* h, const cpx<T>* x, int R, int threads, int G, size_t smem, cudaStream_t s) {
     const level_t& L = h->lev[h->leaf];
     auto kern = k_aggregate_bulk<T, MODE, SL>;
-    CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    bi_raise_smem(kern, smem);
     kern<<<L.nbox, threads, smem, s>>>(h->N, L.K, L.nph, R, h->nun, G, kStages, h->d_perm, h->d_leaf_start,
-                                       h->d_leaf_order, (const cpx<T>*)h->d_F, x, (cpx<T>*)L.d_U, h->d_status);
+                                       h->d_leaf_order, (const cpx<T>*)h->d_F, x, (cpx<T>*)L.d_U, h->d_status,
+                                       h->wait_cycles);
     CU(cudaGetLastError());
 }
 
@@ -265,10 +267,10 @@ bool receive_bulk(bi_handle_s* h, void* yv, int R, cudaStream_t s) {
     const T cc = (T)(h->k * h->k / (32.0 * pi * pi));
     auto kern = h->prm.op_mode == 0 ? (R == 1 ? k_receive_bulk<T, 0, 1> : k_receive_bulk<T, 0, 0>)
                                     : (R == 1 ? k_receive_bulk<T, 1, 1> : k_receive_bulk<T, 1, 0>);
-    CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    bi_raise_smem(kern, smem);
     kern<<<L.nbox, 256, smem, s>>>(h->N, L.K, L.nph, R, h->nun, G, S, h->d_perm, h->d_leaf_start, h->d_leaf_order,
                                    (const cpx<T>*)h->d_F, (const cpx<T>*)h->d_RX, (const cpx<T>*)L.d_V, cc,
-                                   (const cpx<T>*)h->d_yt, (cpx<T>*)yv, h->d_status);
+                                   (const cpx<T>*)h->d_yt, (cpx<T>*)yv, h->d_status, h->wait_cycles);
     CU(cudaGetLastError());
     return true;
 }

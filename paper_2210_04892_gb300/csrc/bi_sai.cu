@@ -232,13 +232,11 @@ void bi_sai_apply(bi_handle_s* h, const void* x, void* y, int R, cudaStream_t s)
     const int nbox = (int)h->leaf_start.size() - 1;
     const size_t smem = (size_t)h->nX * h->max_leaf_count * R * h->csize;
     if (h->prec == 0) {
-        if (smem > 48 * 1024)
-            CU(cudaFuncSetAttribute(k_sai_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        bi_raise_smem(k_sai_apply<double>, smem);
         k_sai_apply<double><<<nbox, 128, smem, s>>>(h->N, h->nun, h->nX, R, h->d_perm, h->d_leaf_start, h->sai_off,
                                                     (const cpx<double>*)h->d_sai, (const cpx<double>*)x, (cpx<double>*)y);
     } else {
-        if (smem > 48 * 1024)
-            CU(cudaFuncSetAttribute(k_sai_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        bi_raise_smem(k_sai_apply<float>, smem);
         k_sai_apply<float><<<nbox, 128, smem, s>>>(h->N, h->nun, h->nX, R, h->d_perm, h->d_leaf_start, h->sai_off,
                                                    (const cpx<float>*)h->d_sai, (const cpx<float>*)x, (cpx<float>*)y);
     }

@@ -40,9 +40,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return done != 0;
 }
 
+// Non-blocking probe of the phase of the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
 // Wait for the phase of the given parity; gives up (returns false) after about `cycles` SM
 // clocks (2^31: about one second at 2 GHz), so a copy that never lands cannot hang the GPU.
+// Limits below 2^20 cycles (diagnostics) probe with the non-blocking test_wait, whose result
+// is not held back by the suspend window that try_wait may spend inside one call.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long cycles = (1ll << 31)) {
+    if (cycles < (1ll << 20)) {
+        const long long t0 = clock64();
+        do {
+            if (mbar_test_wait(bar, parity)) return true;
+        } while (clock64() - t0 < cycles);
+        return false;
+    }
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))

@@ -73,9 +73,16 @@ def test_same_result_alone_and_in_the_mix(bi):
     mix.close()
     for r in res:
         assert r["status"] == bi.BI_OK
+    # Each request builds its own operator.  The near-field set-up adds the up-to-four
+    # triangle-pair contributions of an entry with atomics, so two set-ups of one surface may
+    # differ in the last bit of an entry; the products themselves are deterministic (no
+    # atomics).  With the same GMRES iteration count the solutions agree to that rounding as
+    # GMRES amplifies it (measured 2.2e-5 in FP32); in any case both meet the stated tolerance.
     for r in (res[1], res[4]):
-        assert rel(r["x"], a["x"]) < 10 * TOL
+        assert rel(r["x"], a["x"]) < TOL
         assert np.all(r["relres"] <= TOL * 1.001)
+        if np.array_equal(r["iters"], a["iters"]):
+            assert rel(r["x"], a["x"]) < 1e-4
 
 
 def test_admission_limits(bi):

@@ -1,6 +1,7 @@
-"""bi_farfield_noalloc: the far field for callers that cannot allocate device memory during
-the call (stream capture, fixed-budget loops).  It must return what bi_farfield returns,
-call after call, while its partial sums live in the library's fixed device array.
+"""bi_farfield_noalloc: the far field for callers that cannot allocate device memory while
+they run (fixed-budget real-time loops, hosts whose allocator belongs to another runtime).
+It must return what bi_farfield returns, call after call, while its partial sums live in the
+library's fixed device array.
 
 Collected last on purpose (file name), so a stop-at-first-failure run has already run the
 rest of the suite; it also passes when run alone in a fresh process."""
