@@ -188,6 +188,165 @@ __global__ void __launch_bounds__(256) k_anterp_cb(int nthc, int nphc, int nthp,
     }
 }
 
+// ---------------------------------------------------------------- several right-hand sides, chunked
+// CTA = (parent p, block of nr parent rows, chunk of EC entries of the E-vector); threads work
+// on pairs of adjacent entries (16-byte loads and stores).  The theta pass of every child for
+// the block's rows goes to shared memory, then each thread sums one parent (sample, pair) over
+// the children.  Chunking E keeps the shared memory per CTA bounded at every level.
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_interp_pbE(int nthc, int nphc, int nthp, int nphp, int E, int RB, int EC,
+                                                    int nrb, const int* __restrict__ child_ptr,
+                                                    const int* __restrict__ octant, const tap<T>* __restrict__ th_tap,
+                                                    const tap<T>* __restrict__ ph_tap, const cpx<T>* __restrict__ shift,
+                                                    const cpx<T>* __restrict__ Uc, cpx<T>* __restrict__ Up) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nec = E / EC;
+    const int ec = blockIdx.x % nec;
+    const int rb = (blockIdx.x / nec) % nrb;
+    const int p = blockIdx.x / (nec * nrb);
+    const int ip0 = rb * RB, nr = min(RB, nthp - ip0), e0 = ec * EC, PC = EC / 2;
+    const int c0 = child_ptr[p], nc = child_ptr[p + 1] - c0;
+    const int Kc = nthc * nphc, Kp = nthp * nphp, half = nphc / 2;
+    tap<T>* tt = reinterpret_cast<tap<T>*>(smem_raw);  // [RB][P]
+    tap<T>* pt = tt + RB * P;                          // [P][nphp]
+    int* oc = reinterpret_cast<int*>(pt + nphp * P);   // [8]
+    cpx<T>* s2 = reinterpret_cast<cpx<T>*>(smem_raw + (((size_t)(RB + nphp) * P * sizeof(tap<T>) + 8 * sizeof(int) + 15) / 16) * 16);
+    // s2: [nc][nr][nphc][EC]
+    for (int i = threadIdx.x; i < nr * P; i += blockDim.x) tt[i] = th_tap[ip0 * P + i];
+    for (int i = threadIdx.x; i < nphp * P; i += blockDim.x) {
+        const int jp = i / P, q = i - jp * P;
+        pt[q * nphp + jp] = ph_tap[i];
+    }
+    if (threadIdx.x < nc) oc[threadIdx.x] = octant[c0 + threadIdx.x];
+    __syncthreads();
+    const int64_t E64 = E;
+    const float invPC = 1.0f / PC, invCP = 1.0f / (nphc * PC), invRCP = 1.0f / (nr * nphc * PC);
+    for (int o = threadIdx.x; o < nc * nr * nphc * PC; o += blockDim.x) {
+        const int c = fdiv(o, nr * nphc * PC, invRCP);
+        int rem = o - c * nr * nphc * PC;
+        const int ipl = fdiv(rem, nphc * PC, invCP);
+        rem -= ipl * nphc * PC;
+        const int jc = fdiv(rem, PC, invPC), pr = rem - jc * PC;
+        const int jf = jc + half < nphc ? jc + half : jc + half - nphc;
+        const cpx<T>* u = Uc + (int64_t)(c0 + c) * Kc * E64 + e0 + 2 * pr;
+        cpx<T> a = czero<T>(), b = czero<T>();
+#pragma unroll
+        for (int t = 0; t < P; ++t) {
+            const tap<T> q = tt[ipl * P + t];
+            cpx<T> va, vb;
+            load_pair(u + ((int64_t)(q.c >> 1) * nphc + ((q.c & 1) ? jf : jc)) * E64, va, vb);
+            fma_pair(q.w, va, vb, a, b);
+        }
+        sts_pair(s2 + 2 * (int64_t)o, a, b);
+    }
+    __syncthreads();
+    const float invPP = 1.0f / (nphp * PC);
+    for (int o = threadIdx.x; o < nr * nphp * PC; o += blockDim.x) {
+        const int ipl = fdiv(o, nphp * PC, invPP);
+        const int rem = o - ipl * nphp * PC;
+        const int jp = fdiv(rem, PC, invPC), pr = rem - jp * PC;
+        const int ip = ip0 + ipl;
+        int src[P];
+        T w[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const tap<T> tq = pt[q * nphp + jp];
+            src[q] = tq.c;
+            w[q] = tq.w;
+        }
+        cpx<T> A = czero<T>(), B = czero<T>();
+        for (int c = 0; c < nc; ++c) {
+            const cpx<T>* row = s2 + ((((int64_t)c * nr + ipl) * nphc) * PC + pr) * 2;
+            cpx<T> a = czero<T>(), b = czero<T>();
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                cpx<T> va, vb;
+                lds_pair(row + (int64_t)src[q] * EC, va, vb);
+                fma_pair(w[q], va, vb, a, b);
+            }
+            const cpx<T> sh = ldg_c(shift + (int64_t)oc[c] * Kp + ip * nphp + jp);
+            cfma(A, sh, a);
+            cfma(B, sh, b);
+        }
+        cpx<T>* out = Up + ((int64_t)p * Kp + ip * nphp + jp) * E64 + e0 + 2 * pr;
+        sts_pair(out, A, B);
+    }
+}
+
+// CTA = (child c, chunk of EC entries of the E-vector): the shifted parent field for the chunk,
+// the transposed phi pass for every parent row, then the transposed theta pass added into the
+// child's incoming field, all on pairs of adjacent entries.
+template <typename T, int PT>
+__global__ void __launch_bounds__(256) k_anterp_cbE(int nthc, int nphc, int nthp, int nphp, int E, int EC,
+                                                    const int* __restrict__ parent, const int* __restrict__ octant,
+                                                    const tap<T>* __restrict__ tth_pad, const tap<T>* __restrict__ tph_pad,
+                                                    const cpx<T>* __restrict__ shift, const cpx<T>* __restrict__ Vp,
+                                                    cpx<T>* __restrict__ Vc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nec = E / EC;
+    const int c = blockIdx.x / nec, ec = blockIdx.x - c * nec;
+    const int e0 = ec * EC, PC = EC / 2;
+    const int pb = parent[c], oct = octant[c];
+    const int Kc = nthc * nphc, Kp = nthp * nphp, half = nphc / 2;
+    const int64_t E64 = E;
+    tap<T>* tt = reinterpret_cast<tap<T>*>(smem_raw);       // [nthc][PT]
+    tap<T>* pt = tt + nthc * PT;                             // [PT][nphc]
+    cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw + (((size_t)(nthc + nphc) * PT * sizeof(tap<T>) + 15) / 16) * 16);
+    cpx<T>* t1 = S + (int64_t)Kp * EC;                       // [nthp][nphc][EC]
+    for (int i = threadIdx.x; i < nthc * PT; i += blockDim.x) tt[i] = tth_pad[i];
+    for (int i = threadIdx.x; i < nphc * PT; i += blockDim.x) {
+        const int jc = i / PT, q = i - jc * PT;
+        pt[q * nphc + jc] = tph_pad[i];
+    }
+    const cpx<T>* sh = shift + (int64_t)oct * Kp;
+    const cpx<T>* vp = Vp + (int64_t)pb * Kp * E64 + e0;
+    const float invPC = 1.0f / PC;
+    for (int o = threadIdx.x; o < Kp * PC; o += blockDim.x) {
+        const int i = fdiv(o, PC, invPC), pr = o - i * PC;
+        cpx<T> a, b;
+        load_pair(vp + (int64_t)i * E64 + 2 * pr, a, b);
+        const cpx<T> z = ldg_c(sh + i);
+        sts_pair(S + 2 * (int64_t)o, cmulc(z, a), cmulc(z, b));
+    }
+    __syncthreads();
+    const float invCP = 1.0f / (nphc * PC);
+    for (int o = threadIdx.x; o < nthp * nphc * PC; o += blockDim.x) {
+        const int ip = fdiv(o, nphc * PC, invCP);
+        const int rem = o - ip * nphc * PC;
+        const int jc = fdiv(rem, PC, invPC), pr = rem - jc * PC;
+        const cpx<T>* row = S + ((int64_t)ip * nphp * PC + pr) * 2;
+        cpx<T> a = czero<T>(), b = czero<T>();
+#pragma unroll
+        for (int q = 0; q < PT; ++q) {
+            const tap<T> tq = pt[q * nphc + jc];
+            cpx<T> va, vb;
+            lds_pair(row + (int64_t)tq.c * EC, va, vb);
+            fma_pair(tq.w, va, vb, a, b);
+        }
+        sts_pair(t1 + 2 * (int64_t)o, a, b);
+    }
+    __syncthreads();
+    cpx<T>* vc = Vc + (int64_t)c * Kc * E64 + e0;
+    for (int o = threadIdx.x; o < Kc * PC; o += blockDim.x) {
+        const int ic = fdiv(o, nphc * PC, invCP);
+        const int rem = o - ic * nphc * PC;
+        const int jc = fdiv(rem, PC, invPC), pr = rem - jc * PC;
+        const int jf = jc + half < nphc ? jc + half : jc + half - nphc;
+        cpx<T> a = czero<T>(), b = czero<T>();
+#pragma unroll
+        for (int q = 0; q < PT; ++q) {
+            const tap<T> tq = tt[ic * PT + q];
+            cpx<T> va, vb;
+            lds_pair(t1 + ((((int64_t)(tq.c >> 1) * nphc + ((tq.c & 1) ? jf : jc)) * PC) + pr) * 2, va, vb);
+            fma_pair(tq.w, va, vb, a, b);
+        }
+        cpx<T>* g = vc + ((int64_t)ic * nphc + jc) * E64 + 2 * pr;
+        cpx<T> ga, gb;
+        load_pair(g, ga, gb);
+        sts_pair(g, cadd(ga, a), cadd(gb, b));
+    }
+}
+
 // ---------------------------------------------------------------- one right-hand side (E = 2)
 template <typename T, int P>
 __global__ void __launch_bounds__(256, 4) k_interp_pb1(int nthc, int nphc, int nthp, int nphp, int RB,
@@ -541,7 +700,7 @@ bool interp_t_p(bi_handle_s* h, int l, int E, cudaStream_t s) {
     dim3 g(Pl.nbox, (Pl.nth + RB - 1) / RB);
     if (E == 2) {
         auto k1 = k_interp_pb1<T, P>;
-        if (smem > 48 * 1024) CU(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        bi_raise_smem(k1, smem);
         k1<<<g, 256, smem, s>>>(C.nth, C.nph, Pl.nth, Pl.nph, RB, Pl.d_child_ptr, C.d_octant, (const tap<T>*)I.d_th_tap,
                                 (const tap<T>*)I.d_ph_tap, (const cpx<T>*)Pl.d_shift, (const cpx<T>*)C.d_U,
                                 (cpx<T>*)Pl.d_U);
@@ -549,10 +708,47 @@ bool interp_t_p(bi_handle_s* h, int l, int E, cudaStream_t s) {
         return true;
     }
     auto kern = k_interp_pb<T, P>;
-    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    bi_raise_smem(kern, smem);
     kern<<<g, 256, smem, s>>>(C.nth, C.nph, Pl.nth, Pl.nph, E, RB, Pl.d_child_ptr, C.d_octant, (const tap<T>*)I.d_th_tap,
                               (const tap<T>*)I.d_ph_tap, (const cpx<T>*)Pl.d_shift, (const cpx<T>*)C.d_U,
                               (cpx<T>*)Pl.d_U);
+    CU(cudaGetLastError());
+    return true;
+}
+
+// Several right-hand sides: the chunked kernel.  EC (entries per chunk) is the largest of 16,
+// 8, 4, 2 that divides E and leaves room for at least one parent row of 8 children in about
+// 64 KB of shared memory; rows per CTA fill the rest.
+template <typename T, int P>
+bool interp_chunked(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    level_t& Pl = h->lev[l];
+    level_t& C = h->lev[l + 1];
+    interp_t& I = h->itp[l];
+    const size_t budget = 64 * 1024;
+    int EC = 0;
+    for (int ec : {16, 8, 4, 2})
+        if (E % ec == 0 && (size_t)8 * C.nph * ec * sizeof(cpx<T>) <= budget / 2) {
+            EC = ec;
+            break;
+        }
+    if (!EC) return false;
+    const size_t per_row = (size_t)8 * C.nph * EC * sizeof(cpx<T>);
+    int RB = (int)std::max<size_t>(1, budget / per_row);
+    RB = std::min(RB, Pl.nth);
+    auto smem_of = [&](int rb) {
+        return (((size_t)(rb + Pl.nph) * P * sizeof(tap<T>) + 8 * sizeof(int) + 15) / 16) * 16 + (size_t)rb * per_row;
+    };
+    while (RB > 1 && smem_of(RB) > budget + 16 * 1024) --RB;
+    const size_t smem = smem_of(RB);
+    if (smem > 160 * 1024) return false;
+    const int nrb = (Pl.nth + RB - 1) / RB, nec = E / EC;
+    const int64_t blocks = (int64_t)Pl.nbox * nrb * nec;
+    if (blocks > 0x7fffffffLL) return false;
+    auto kern = k_interp_pbE<T, P>;
+    bi_raise_smem(kern, smem);
+    kern<<<(unsigned)blocks, 256, smem, s>>>(C.nth, C.nph, Pl.nth, Pl.nph, E, RB, EC, nrb, Pl.d_child_ptr, C.d_octant,
+                                             (const tap<T>*)I.d_th_tap, (const tap<T>*)I.d_ph_tap,
+                                             (const cpx<T>*)Pl.d_shift, (const cpx<T>*)C.d_U, (cpx<T>*)Pl.d_U);
     CU(cudaGetLastError());
     return true;
 }
@@ -567,7 +763,7 @@ bool anterp_t_p(bi_handle_s* h, int l, int E, cudaStream_t s) {
     if (smem > 160 * 1024) return false;
     if (E == 2) {
         auto k1 = k_anterp_cb1<T, PT>;
-        if (smem > 48 * 1024) CU(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        bi_raise_smem(k1, smem);
         k1<<<C.nbox, 256, smem, s>>>(C.nth, C.nph, Pl.nth, Pl.nph, C.d_parent, C.d_octant, (const tap<T>*)I.d_tth_pad,
                                      (const tap<T>*)I.d_tph_pad, (const cpx<T>*)Pl.d_shift, (const cpx<T>*)Pl.d_V,
                                      (cpx<T>*)C.d_V);
@@ -575,10 +771,41 @@ bool anterp_t_p(bi_handle_s* h, int l, int E, cudaStream_t s) {
         return true;
     }
     auto kern = k_anterp_cb<T, PT, PP>;
-    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    bi_raise_smem(kern, smem);
     kern<<<C.nbox, 256, smem, s>>>(C.nth, C.nph, Pl.nth, Pl.nph, E, C.d_parent, C.d_octant, (const tap<T>*)I.d_tth_pad,
                                    (const tap<T>*)I.d_tph_pad, (const cpx<T>*)Pl.d_shift, (const cpx<T>*)Pl.d_V,
                                    (cpx<T>*)C.d_V);
+    CU(cudaGetLastError());
+    return true;
+}
+
+// Several right-hand sides: one CTA per (child, chunk of EC entries), EC the largest of 16, 8,
+// 4, 2 dividing E whose shared memory (shifted parent field and transposed phi pass of the
+// chunk) stays within about 80 KB; false when even EC = 2 does not fit (coarse levels).
+template <typename T, int PT>
+bool anterp_chunked(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    level_t& Pl = h->lev[l];
+    level_t& C = h->lev[l + 1];
+    interp_t& I = h->itp[l];
+    const size_t taps = (((size_t)(C.nth + C.nph) * PT * sizeof(tap<T>) + 15) / 16) * 16;
+    int EC = 0;
+    size_t smem = 0;
+    for (int ec : {16, 8, 4, 2}) {
+        const size_t sm = taps + ((size_t)Pl.K + (size_t)Pl.nth * C.nph) * ec * sizeof(cpx<T>);
+        if (E % ec == 0 && sm <= 80 * 1024) {
+            EC = ec;
+            smem = sm;
+            break;
+        }
+    }
+    if (!EC) return false;
+    const int64_t blocks = (int64_t)C.nbox * (E / EC);
+    if (blocks > 0x7fffffffLL) return false;
+    auto kern = k_anterp_cbE<T, PT>;
+    bi_raise_smem(kern, smem);
+    kern<<<(unsigned)blocks, 256, smem, s>>>(C.nth, C.nph, Pl.nth, Pl.nph, E, EC, C.d_parent, C.d_octant,
+                                             (const tap<T>*)I.d_tth_pad, (const tap<T>*)I.d_tph_pad,
+                                             (const cpx<T>*)Pl.d_shift, (const cpx<T>*)Pl.d_V, (cpx<T>*)C.d_V);
     CU(cudaGetLastError());
     return true;
 }
@@ -601,6 +828,8 @@ void bi_upload_taps(bi_handle_s* h) {
 bool bi_interp_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
     const interp_t& I = h->itp[l];
     if (I.p_th != 10 || I.p_ph != 10 || !I.d_th_tap) return false;
+    if (E > 2 && (h->prec == 0 ? interp_chunked<double, 10>(h, l, E, s) : interp_chunked<float, 10>(h, l, E, s)))
+        return true;
     if (E >= 32) return h->prec == 0 ? interp_wide<double>(h, l, E, s) : interp_wide<float>(h, l, E, s);
     return h->prec == 0 ? interp_t_p<double, 10>(h, l, E, s) : interp_t_p<float, 10>(h, l, E, s);
 }
@@ -608,6 +837,12 @@ bool bi_interp_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
 bool bi_anterp_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
     const interp_t& I = h->itp[l];
     if (!I.d_tth_pad) return false;
+    if (E > 2 && I.pt_th == I.pt_ph) {
+        if (I.pt_th == 16 && (h->prec == 0 ? anterp_chunked<double, 16>(h, l, E, s) : anterp_chunked<float, 16>(h, l, E, s)))
+            return true;
+        if (I.pt_th == 24 && (h->prec == 0 ? anterp_chunked<double, 24>(h, l, E, s) : anterp_chunked<float, 24>(h, l, E, s)))
+            return true;
+    }
     if (E >= 32) {
         if (I.pt_th == 16) return h->prec == 0 ? anterp_wide<double, 16>(h, l, E, s) : anterp_wide<float, 16>(h, l, E, s);
         if (I.pt_th == 24) return h->prec == 0 ? anterp_wide<double, 24>(h, l, E, s) : anterp_wide<float, 24>(h, l, E, s);

@@ -499,6 +499,105 @@ __global__ void __launch_bounds__(256, RT == 1 ? 6 : 1) k_near_stream(int N, int
     }
 }
 
+// ------------------------------------------------------------------ near field, several RHS
+// Same work items and near-block segments as k_near_stream, for R >= 2: x comes from the
+// tree-ordered copy xt [N][NX][R] (gathered once per product), so the x of one near box is one
+// contiguous chunk and its staging is coalesced; each warp owns one row at a time (RT RHS of J
+// and M in registers), lanes stride the row's columns with 16-byte block loads.
+template <typename T, int MODE, int RT>
+__global__ void __launch_bounds__(256, RT >= 8 ? 2 : 3) k_near_multi(int N, int R, int nun, const int* __restrict__ perm,
+                                                      const int2* __restrict__ work,
+                                                      const int* __restrict__ leaf_start, const int* __restrict__ near_ptr,
+                                                      const int* __restrict__ near_src, const int64_t* __restrict__ near_blk,
+                                                      const int* __restrict__ near_col0, const int* __restrict__ near_ncol,
+                                                      const cpx<T>* __restrict__ blocks, const int* __restrict__ gptr,
+                                                      const int* __restrict__ gseg, const T* __restrict__ gval,
+                                                      const cpx<T>* __restrict__ xt, cpx<T>* __restrict__ yt,
+                                                      cpx<T>* __restrict__ yuser) {
+    constexpr int NX = MODE == 0 ? 2 : 1;
+    extern __shared__ unsigned char smem_raw[];
+    cpx<T>* xs = reinterpret_cast<cpx<T>*>(smem_raw);  // [NX][RT][ncol]
+    const int b = work[blockIdx.x].x, row0 = work[blockIdx.x].y;
+    const int m0 = leaf_start[b], mb = leaf_start[b + 1] - m0;
+    const int q0 = near_ptr[b], q1 = near_ptr[b + 1];
+    const int64_t seg = near_blk[q0];
+    const int ncol = near_ncol[b];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const int row_end = min(mb, row0 + 16);   // a work item holds up to 16 rows of its box
+    for (int r0 = 0; r0 < R; r0 += RT) {
+        const int rn = min(RT, R - r0);
+        __syncthreads();
+        // x of the near columns: one near box per warp; its tree-ordered x is contiguous
+        for (int q = q0 + warp; q < q1; q += nwarp) {
+            const int s = near_src[q];
+            const int n0 = leaf_start[s], nbs = leaf_start[s + 1] - n0;
+            const int c0 = near_col0[q];
+            const cpx<T>* xb = xt + (int64_t)n0 * NX * R + r0;
+            for (int i = lane; i < nbs * NX * RT; i += 32) {
+                const int rr = i % RT, X = (i / RT) % NX, n = i / (RT * NX);
+                xs[((size_t)X * RT + rr) * ncol + c0 + n] = rr < rn ? xb[((int64_t)n * NX + X) * R + rr] : czero<T>();
+            }
+        }
+        __syncthreads();
+        const int stride = (MODE == 0 ? 2 : 1);
+        for (int ml = row0 + warp; ml < row_end; ml += nwarp) {
+            cpx<T> aJ[RT], aM[RT];
+#pragma unroll
+            for (int rr = 0; rr < RT; ++rr) { aJ[rr] = czero<T>(); aM[rr] = czero<T>(); }
+            const cpx<T>* row = blocks + stride * (seg + (int64_t)ml * ncol);
+#pragma unroll 2
+            for (int c = lane; c < ncol; c += 32) {
+                if (MODE == 0) {
+                    cpx<T> A, B;
+                    load_pair(row + 2 * c, A, B);
+#pragma unroll
+                    for (int rr = 0; rr < RT; ++rr) {
+                        const cpx<T> xJ = xs[(size_t)rr * ncol + c], xM = xs[(size_t)(RT + rr) * ncol + c];
+                        cfma(aJ[rr], A, xJ);
+                        cfma(aJ[rr], B, xM);
+                        cfma(aM[rr], B, xJ);
+                        cfma(aM[rr], A, cpx<T>{-xM.x, -xM.y});
+                    }
+                } else {
+                    const cpx<T> A = ldg_cpx(row + c);
+#pragma unroll
+                    for (int rr = 0; rr < RT; ++rr) cfma(aJ[rr], A, xs[(size_t)rr * ncol + c]);
+                }
+            }
+            const int m = m0 + ml;
+            if (MODE == 0) {
+                const int g0 = gptr[m], gn = gptr[m + 1] - g0;
+                for (int qq = lane; qq < gn; qq += 32) {
+                    const int c = gseg[g0 + qq];
+                    const T gg = gval[2 * (g0 + qq)], xx = gval[2 * (g0 + qq) + 1];
+#pragma unroll
+                    for (int rr = 0; rr < RT; ++rr) {
+                        const cpx<T> xJ = xs[(size_t)rr * ncol + c], xM = xs[(size_t)(RT + rr) * ncol + c];
+                        aM[rr].x += T(0.5) * (xx * xJ.x - gg * xM.x);
+                        aM[rr].y += T(0.5) * (xx * xJ.y - gg * xM.y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int rr = 0; rr < RT; ++rr) {
+                const cpx<T> sJ = warp_sum(aJ[rr]);
+                const cpx<T> sM = MODE == 0 ? warp_sum(aM[rr]) : czero<T>();
+                if (lane == rr && rr < rn) {
+                    const int r = r0 + rr;
+                    const cpx<T> vJ = {-sJ.x, -sJ.y};
+                    if (yuser) {
+                        yuser[(int64_t)r * nun + perm[m]] = vJ;
+                        if (MODE == 0) yuser[(int64_t)r * nun + N + perm[m]] = sM;
+                    } else {
+                        yt[((int64_t)m * NX + 0) * R + r] = vJ;
+                        if (MODE == 0) yt[((int64_t)m * NX + 1) * R + r] = sM;
+                    }
+                }
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ leaf aggregation (fused gather)
 // thread per (stored direction kk, RHS r): both components from one 16-byte pattern load give
 // U at kk and at its antipode.
@@ -1055,12 +1154,25 @@ void launch_near_stream(bi_handle_s* h, const cpx<T>* x, cpx<T>* yt, cpx<T>* yus
     const int NX = MODE == 0 ? 2 : 1;
     size_t smem = (size_t)h->near_ncol_max * NX * RT * sizeof(cpx<T>);
     auto kern = k_near_stream<T, MODE, RT>;
-    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    bi_raise_smem(kern, smem);
     kern<<<h->near_nwork, 256, smem, s>>>(h->N, R, h->nun, h->d_perm, (const int2*)h->d_near_work, h->d_leaf_start,
                                           h->d_near_ptr, h->d_near_src,
                                                  h->d_near_blk, h->d_near_col0, h->d_near_ncol, (const cpx<T>*)h->d_near,
                                                  h->d_gram_ptr, h->d_gram_seg,
                                                  (const T*)h->d_gram_val, x, yt, yuser);
+    CU(cudaGetLastError());
+}
+
+template <typename T, int MODE, int RT>
+void launch_near_multi(bi_handle_s* h, cpx<T>* yt, cpx<T>* yuser, int R, cudaStream_t s) {
+    const int NX = MODE == 0 ? 2 : 1;
+    size_t smem = (size_t)h->near_ncol_max * NX * RT * sizeof(cpx<T>);
+    auto kern = k_near_multi<T, MODE, RT>;
+    bi_raise_smem(kern, smem);
+    kern<<<h->near_nwork, 256, smem, s>>>(h->N, R, h->nun, h->d_perm, (const int2*)h->d_near_work, h->d_leaf_start,
+                                          h->d_near_ptr, h->d_near_src, h->d_near_blk, h->d_near_col0, h->d_near_ncol,
+                                          (const cpx<T>*)h->d_near, h->d_gram_ptr, h->d_gram_seg, (const T*)h->d_gram_val,
+                                          (const cpx<T>*)h->d_xt, yt, yuser);
     CU(cudaGetLastError());
 }
 
@@ -1078,10 +1190,17 @@ void launch_near_any(bi_handle_s* h, const cpx<T>* x, cpx<T>* yt, cpx<T>* yuser,
         CU(cudaGetLastError());
         return;
     }
-    if (R == 1) launch_near_stream<T, MODE, 1>(h, x, yt, yuser, R, s);
-    else if (R == 2) launch_near_stream<T, MODE, 2>(h, x, yt, yuser, R, s);
-    else if (R <= 4 || (size_t)h->near_ncol_max * 2 * 8 * sizeof(cpx<T>) > 160 * 1024) launch_near_stream<T, MODE, 4>(h, x, yt, yuser, R, s);
-    else launch_near_stream<T, MODE, 8>(h, x, yt, yuser, R, s);
+    if (R == 1) {
+        launch_near_stream<T, MODE, 1>(h, x, yt, yuser, R, s);
+        return;
+    }
+    // several right-hand sides: x gathered once into tree order, then staged per work item
+    const int64_t nvec = (int64_t)h->N * h->nX * R;
+    k_gather_x<T><<<nblk(nvec, 256), 256, 0, s>>>(h->N, h->nX, R, h->nun, h->d_perm, x, (cpx<T>*)h->d_xt);
+    CU(cudaGetLastError());
+    if (R == 2) launch_near_multi<T, MODE, 2>(h, yt, yuser, R, s);
+    else if (R <= 4 || (size_t)h->near_ncol_max * 2 * 8 * sizeof(cpx<T>) > 160 * 1024) launch_near_multi<T, MODE, 4>(h, yt, yuser, R, s);
+    else launch_near_multi<T, MODE, 8>(h, yt, yuser, R, s);
 }
 
 
@@ -1110,7 +1229,7 @@ bool interp_child(bi_handle_s* h, int l, int E, cudaStream_t s) {
     interp_t& I = h->itp[l];
     size_t smem = interp_child_smem<T>(h, l, E);
     if (smem > 180 * 1024) return false;
-    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(k_interp_child<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    bi_raise_smem(k_interp_child<T>, smem);
     CU(cudaMemsetAsync(P.d_U, 0, (size_t)P.nbox * P.K * E * sizeof(cpx<T>), s));
     k_interp_child<T><<<C.nbox, 256, smem, s>>>(C.nth, C.nph, P.nth, P.nph, E, I.p_th, I.p_ph, I.d_th_src, I.d_th_flip,
                                                 (const T*)I.d_th_w, I.d_ph_src, (const T*)I.d_ph_w, C.d_parent, C.d_octant,
@@ -1127,7 +1246,7 @@ bool anterp_child(bi_handle_s* h, int l, int E, cudaStream_t s) {
     interp_t& I = h->itp[l];
     size_t smem = anterp_child_smem<T>(h, l, E);
     if (smem > 180 * 1024) return false;
-    if (smem > 48 * 1024) CU(cudaFuncSetAttribute(k_anterp_child<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    bi_raise_smem(k_anterp_child<T>, smem);
     k_anterp_child<T><<<C.nbox, 256, smem, s>>>(C.nth, C.nph, P.nth, P.nph, E, (int)I.tph_dst.size(), (int)I.tth_dst.size(),
                                                 I.d_tph_ptr, I.d_tph_dst, (const T*)I.d_tph_w, I.d_tth_ptr, I.d_tth_dst,
                                                 I.d_tth_flip, (const T*)I.d_tth_w, C.d_parent, C.d_octant,
@@ -1149,14 +1268,14 @@ bool launch_receive_tile_opt(bi_handle_s* h, cpx<T>* y, int R, cudaStream_t s) {
     const T c = (T)(h->k * h->k / (32.0 * pi * pi));
     if (h->prm.op_mode == 0) {
         if (smem > 48 * 1024)
-            CU(cudaFuncSetAttribute(k_receive_tile<T, 0, OPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            bi_raise_smem(k_receive_tile<T, 0, OPT>, smem);
         k_receive_tile<T, 0, OPT><<<dim3(L.nbox, (R + RC - 1) / RC), 256, smem, s>>>(h->N, L.K, L.nph, R, RC, h->nun, h->d_perm,
                                                                                    h->d_leaf_start,
                                                             (const cpx<T>*)h->d_F, (const cpx<T>*)h->d_RX,
                                                             (const cpx<T>*)L.d_V, c, (const cpx<T>*)h->d_yt, y);
     } else {
         if (smem > 48 * 1024)
-            CU(cudaFuncSetAttribute(k_receive_tile<T, 1, OPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            bi_raise_smem(k_receive_tile<T, 1, OPT>, smem);
         k_receive_tile<T, 1, OPT><<<dim3(L.nbox, (R + RC - 1) / RC), 256, smem, s>>>(h->N, L.K, L.nph, R, RC, h->nun, h->d_perm,
                                                                                    h->d_leaf_start,
                                                             (const cpx<T>*)h->d_F, (const cpx<T>*)h->d_RX,
@@ -1209,8 +1328,8 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
         dim3 g(L.nbox, nblk(L.K / 2, 32));
         size_t smem = ((size_t)h->max_leaf_count * 32 * 2 + (size_t)h->max_leaf_count * 2 * R) * sizeof(C);
         if (smem > 48 * 1024) {
-            CU(cudaFuncSetAttribute(k_aggregate_tile<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            CU(cudaFuncSetAttribute(k_aggregate_tile<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            bi_raise_smem(k_aggregate_tile<T, 0>, smem);
+            bi_raise_smem(k_aggregate_tile<T, 1>, smem);
         }
         if (h->prm.op_mode == 0)
             k_aggregate_tile<T, 0><<<g, 256, smem, s>>>(N, L.K, L.nph, R, nun, h->d_perm, h->d_leaf_start, (const C*)h->d_F, x,
@@ -1224,8 +1343,8 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
         dim3 g(L.nbox, nblk((int64_t)(L.K / 2) * R, 64));
         size_t smem = (size_t)h->max_leaf_count * 2 * R * sizeof(C);
         if (smem > 48 * 1024) {
-            CU(cudaFuncSetAttribute(k_aggregate2<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            CU(cudaFuncSetAttribute(k_aggregate2<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            bi_raise_smem(k_aggregate2<T, 0>, smem);
+            bi_raise_smem(k_aggregate2<T, 1>, smem);
         }
         if (h->prm.op_mode == 0)
             k_aggregate2<T, 0><<<g, th, smem, s>>>(N, L.K, L.nph, R, nun, h->d_perm, h->d_leaf_start, (const C*)h->d_F, x, (C*)L.d_U);

@@ -9,6 +9,12 @@
 // record of eight codes per (parent, source)).  The CTA's warps split the sources and meet
 // in shared memory; every child's V is written once, without atomics.  One right-hand side
 // (E = 2): each lane carries both components of its direction.
+//
+// Several right-hand sides (E = 2R > 2): thread = (direction k, pair of adjacent entries of
+// the E-vector of k), so a CTA reads a contiguous tile of D directions x E entries of each
+// source and the R threads of a direction share every operator value (one broadcast load).
+// CTAs run parents fastest: the CTAs resident at one time work on one direction tile of
+// neighbouring parents, whose sources and the tile of the 343 operators stay in L2/L1.
 #include <algorithm>
 #include <cstdlib>
 #include <unordered_map>
@@ -77,6 +83,71 @@ __global__ void __launch_bounds__(32 * kWarps) k_translate_pc(int K, const int* 
         out[0] = s0;
         out[1] = s1;
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_pair(cpx<T>* p, cpx<T> a, cpx<T> b) {
+    p[0] = a;
+    p[1] = b;
+}
+__device__ __forceinline__ void store_pair(cpx<float>* p, cpx<float> a, cpx<float> b) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_translate_pcE(int K, int R, int D, int np, const int* __restrict__ cptr,
+                                                       const int* __restrict__ tptr, const int* __restrict__ src,
+                                                       const uint4* __restrict__ codes, const cpx<T>* __restrict__ Top,
+                                                       const cpx<T>* __restrict__ U, cpx<T>* __restrict__ V) {
+    const int p = (int)(blockIdx.x % (unsigned)np);
+    const int chunk = (int)(blockIdx.x / (unsigned)np);
+    const int d = threadIdx.x / R, j = threadIdx.x - d * R;
+    const int k = chunk * D + d;
+    if (d >= D || k >= K) return;   // no barrier below
+    const int64_t E = 2 * R;
+    const int c0 = cptr[p], nc = cptr[p + 1] - c0;
+    cpx<T> a0[8], a1[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a0[i] = a1[i] = czero<T>();
+    const cpx<T>* ub = U + (int64_t)k * E + 2 * j;
+    const cpx<T>* tk = Top + k;
+    const int64_t box = (int64_t)K * E;
+#pragma unroll 4
+    for (int q = tptr[p]; q < tptr[p + 1]; ++q) {
+        const int s = src[q];
+        const uint4 cw = codes[q];
+        const unsigned cc[4] = {cw.x, cw.y, cw.z, cw.w};
+        cpx<T> u0, u1;
+        load_pair(ub + (int64_t)s * box, u0, u1);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const unsigned code = (cc[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
+            if (code != kNone) {
+                const cpx<T> t = ldg_cpx(tk + (int64_t)code * K);
+                cfma(a0[i], t, u0);
+                cfma(a1[i], t, u1);
+            }
+        }
+    }
+    cpx<T>* vb = V + (int64_t)c0 * box + (int64_t)k * E + 2 * j;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        if (i < nc) store_pair(vb + i * box, a0[i], a1[i]);
+}
+
+template <typename T>
+void launch_tE(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    level_t& L = h->lev[l];
+    const int R = E / 2;
+    const int D = std::max(1, 256 / R);
+    const int threads = std::min(1024, (D * R + 31) / 32 * 32);
+    const int64_t nchunk = (L.K + D - 1) / D;
+    const int64_t blocks = nchunk * L.tp_np;
+    if (blocks > 0x7fffffffLL) throw bi_error{BI_ERR_ARG, "translation grid too large"};
+    k_translate_pcE<T><<<(unsigned)blocks, threads, 0, s>>>(L.K, R, D, L.tp_np, L.d_tp_cptr, L.d_tp_ptr, L.d_tp_src,
+                                                             (const uint4*)L.d_tp_code, (const cpx<T>*)L.d_T,
+                                                             (const cpx<T>*)L.d_U, (cpx<T>*)L.d_V);
+    CU(cudaGetLastError());
 }
 
 template <typename T>
@@ -167,8 +238,15 @@ void bi_build_translate_lists(bi_handle_s* h) {
 }
 
 bool bi_translate_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
-    if (E != 2 || !h->lev[l].d_tp_ptr) return false;
-    if (h->prec == 0) launch_t<double>(h, l, s);
-    else launch_t<float>(h, l, s);
+    if (!h->lev[l].d_tp_ptr || h->lev[l].tp_np == 0) return false;
+    if (E == 2) {
+        if (h->prec == 0) launch_t<double>(h, l, s);
+        else launch_t<float>(h, l, s);
+    } else if (E <= 512) {
+        if (h->prec == 0) launch_tE<double>(h, l, E, s);
+        else launch_tE<float>(h, l, E, s);
+    } else {
+        return false;
+    }
     return true;
 }
