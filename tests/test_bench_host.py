@@ -1,6 +1,7 @@
-"""Host logic of bench.py checked without a GPU: its algorithmic-byte model and launch count
-for the bench workload (sizes from the host-only plan, the same set-up code as the GPU
-handle), against the committed ncu summaries that its roofline line reads."""
+"""Host logic of bench.py checked without a GPU: the headline workload's sizes, and the
+algorithmic-byte model and launch count of the one-RHS section (sizes from the host-only
+plan, the same set-up code as the GPU handle) against the committed ncu summaries that its
+roofline line reads."""
 import os
 import re
 import sys
@@ -11,25 +12,56 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 
-@pytest.fixture(scope="module")
-def bench_info():
+def _plan_info(name):
     import bench
     from paper_2210_04892_gb300 import bi
     try:
         bi.load()
     except (ImportError, OSError) as e:  # pragma: no cover - library not built here
         pytest.skip(f"library not loadable: {e}")
-    v, t, _ = bench.workload_mesh()
+    v, t, _ = bench.workload_mesh(name)
     p = bi.Plan(v, t, bench.K0, digits=3)
     info = p.info()
     p.close()
     return bench, info
 
 
-def test_workload_sizes(bench_info):
+@pytest.fixture(scope="module")
+def bench_info():
+    import bench
+    return _plan_info(bench.SECONDARY["name"])
+
+
+@pytest.mark.slow
+def test_headline_workload_sizes():
+    import bench
+    bench, info = _plan_info(bench.HEADLINE["name"])
+    assert info["n_unknowns"] == 3484860 and info["levels"] == 9
+    assert str(info["n_unknowns"]) in bench.WORKLOAD.replace(",", "")
+    assert bench.HEADLINE["nrhs"] == 8
+
+
+def test_secondary_workload_sizes(bench_info):
     bench, info = bench_info
     assert info["n_unknowns"] == 61440 and info["levels"] == 5
-    assert str(info["n_unknowns"]) in bench.WORKLOAD.replace(",", "")
+    assert str(info["n_unknowns"]) in bench.SECONDARY["desc"].replace(",", "")
+
+
+def test_stage_roofline_picks_the_slower_bound(bench_info):
+    """A stage is ALU-bound when its flops at the FP32 peak take longer than its bytes at the
+    HBM peak; the fraction is that ideal time over the measured one."""
+    bench, info = bench_info
+    sb, sf = bench.stage_bytes(info, 64), bench.stage_flops(info, 64)
+    stages = {k: 1.0 for k in sb}
+    sr = bench.stage_roofline(info, 64, stages, 6000.0)
+    for k in sb:
+        t_hbm = sb[k] / 6e12
+        t_alu = sf[k] / (bench.ALU_FP32_TFLOPS * 1e12)
+        assert sr[k]["bound"] == ("alu" if t_alu > t_hbm else "hbm")
+        assert abs(sr[k]["frac"] - max(t_hbm, t_alu) / 1e-3) < 1e-12
+    # one right-hand side: the near product is bandwidth-bound (2 flop/B), 64 make it ALU-bound
+    assert bench.stage_roofline(info, 1, stages, 6000.0)["near"]["bound"] == "hbm"
+    assert sr["near"]["bound"] == "alu"
 
 
 def test_measured_traffic_matches_the_byte_model(bench_info):

@@ -1,0 +1,168 @@
+"""Per-stage precision study of the multilevel product (the mixed-precision question of the
+batched form): the far part of <f, L f> x on a 4-level sphere (radius 1 wavelength, 5120
+triangles, leaf boxes of a quarter wavelength, 3 digits), computed by the numpy model of the
+whole chain (the plan's tables; FP64 reference), with the operands of ONE stage rounded to a
+narrower format and accumulated exactly:
+
+  aggregate  leaf radiation patterns F and the vector x
+  interp     outgoing child patterns and the Lagrange matrices of the upward step
+  translate  outgoing patterns and the translation operators T_L
+  anterp     shifted incoming parent patterns and the Lagrange matrices of the downward step
+  receive    leaf incoming patterns and the receive patterns R
+
+Formats: FP32; TF32 (10-bit mantissa); FP16 with one scale per box pattern (10-bit mantissa,
+range kept by the scale); BF16 (7-bit mantissa).  The error is relative to the FP64 far part.
+The conclusions asserted here fix the product's precision policy: FP32 everywhere keeps the
+error near 1e-6, while BF16 operands on the upward side of the translations (aggregation,
+interpolation, the outgoing patterns of the translations) exceed the 1e-3 bar, because the
+diagonal translation of quarter-wavelength boxes amplifies relative errors of the outgoing
+patterns by orders of magnitude.
+
+  python tests/test_precision_study.py      prints the table (a few minutes)
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+sys.path.insert(0, os.path.dirname(HERE))
+
+K0 = 2 * np.pi
+STAGES = ("aggregate", "interp", "translate", "anterp", "receive")
+FORMATS = ("fp32", "tf32", "fp16_scaled", "bf16")
+
+
+def _round_mantissa(a, bits):
+    """Round float32 values to `bits` explicit mantissa bits (round to nearest even)."""
+    f = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    drop = 23 - bits
+    lsb = (f >> drop) & 1
+    r = ((f + (1 << (drop - 1)) - 1 + lsb) >> drop) << drop
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def rnd(x, fmt):
+    """x (real or complex array) rounded to fmt and returned in float64/complex128."""
+    x = np.asarray(x)
+    if np.iscomplexobj(x):
+        return rnd(x.real, fmt) + 1j * rnd(x.imag, fmt)
+    if fmt == "fp64":
+        return x.astype(np.float64)
+    if fmt == "fp32":
+        return x.astype(np.float32).astype(np.float64)
+    if fmt == "tf32":
+        return _round_mantissa(x, 10)
+    if fmt == "bf16":
+        return _round_mantissa(x, 7)
+    if fmt == "fp16_scaled":
+        s = float(np.abs(x).max()) or 1.0
+        return (x / s).astype(np.float16).astype(np.float64) * s
+    raise ValueError(fmt)
+
+
+def _far_product(m, x, fmt, stage):
+    """Far part of <f, L f> x with one stage's operands rounded to fmt (the model's propagate
+    restated with rounding hooks)."""
+    q = (lambda a: rnd(a, fmt)) if fmt != "fp64" else (lambda a: a)
+    p, info, lf, k, cen, grids = m.p, m.info, m.lf, m.k, m.cen, m.grids
+    F = m.F
+    xa = x
+    if stage == "aggregate":
+        F = np.stack([np.stack([q(F[i, r]) for r in range(F.shape[1])]) for i in range(2)])
+        xa = q(x)
+    U_leaf = np.zeros((m.nb, 2, F.shape[2]), complex)
+    for b in range(m.nb):
+        r = m.rows(b)
+        U_leaf[b, 0] = xa[r] @ F[0, r]
+        U_leaf[b, 1] = xa[r] @ F[1, r]
+    U = {lf: U_leaf}
+    for l in range(lf - 1, 1, -1):
+        A, B = m.interp[l]
+        if stage == "interp":
+            A, B = q(A), q(B)
+        nphc = grids[l + 1][1]
+        nthp, nphp, khp = grids[l][:3]
+        cp = p.get(5, l)
+        U[l] = np.zeros((info["boxes"][l], 2, nthp * nphp), complex)
+        for b in range(info["boxes"][l]):
+            for c in range(cp[b], cp[b + 1]):
+                sh = np.exp(1j * k * (khp @ (cen[l + 1][c] - cen[l][b])))
+                for i in range(2):
+                    uc = q(U[l + 1][c, i]) if stage == "interp" else U[l + 1][c, i]
+                    U[l][b, i] += ((A @ uc).reshape(nthp, nphc) @ B.T).reshape(-1) * sh
+    V = {l: np.zeros_like(U[l]) for l in U}
+    for l in range(2, lf + 1):
+        ptr, src, off = p.get(6, l), p.get(7, l), p.get(8, l)
+        Uq = [[q(U[l][s, i]) for i in range(2)] for s in range(info["boxes"][l])] if stage == "translate" else None
+        for b in range(info["boxes"][l]):
+            for e in range(ptr[b], ptr[b + 1]):
+                T = m._translation(l, int(off[e]))
+                if stage == "translate":
+                    T = q(T)
+                    V[l][b] += T[None] * np.stack(Uq[src[e]])
+                else:
+                    V[l][b] += T[None] * U[l][src[e]]
+    for l in range(2, lf):
+        A, B = m.interp[l]
+        if stage == "anterp":
+            A, B = q(A), q(B)
+        nthp, nphp, khp = grids[l][:3]
+        cp = p.get(5, l)
+        for b in range(info["boxes"][l]):
+            for c in range(cp[b], cp[b + 1]):
+                sh = np.exp(-1j * k * (khp @ (cen[l + 1][c] - cen[l][b])))
+                for i in range(2):
+                    s = V[l][b, i] * sh
+                    if stage == "anterp":
+                        s = q(s)
+                    V[l + 1][c, i] += A.T @ (s.reshape(nthp, nphp) @ B).reshape(-1)
+    Vl = V[lf]
+    R = m.R
+    if stage == "receive":
+        Vl = np.stack([np.stack([q(Vl[b, i]) for i in range(2)]) for b in range(m.nb)])
+        R = np.stack([np.stack([q(R[i, r]) for r in range(R.shape[1])]) for i in range(2)])
+    y = np.zeros(m.N, complex)
+    for b in range(m.nb):
+        r = m.rows(b)
+        y[r] = -1j * k * (R[0, r] @ Vl[b, 0] + R[1, r] @ Vl[b, 1])
+    return y
+
+
+def precision_table(nu=16, radius=1.0, formats=FORMATS, stages=STAGES):
+    from paper_2210_04892_gb300 import bi, inputs
+    import test_plan
+    bi.load()
+    v, t = inputs.icosphere(nu, radius)
+    m = test_plan._MultilevelModel(bi, v, t, K0, 0.25, 3)
+    rng = np.random.default_rng(inputs.SEED_BASE + 82)
+    x = rng.normal(size=m.N) + 1j * rng.normal(size=m.N)
+    ref = _far_product(m, x, "fp64", None)
+    out = {}
+    for st in stages:
+        for fmt in formats:
+            y = _far_product(m, x, fmt, st)
+            out[(st, fmt)] = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+    return m.info, out
+
+
+@pytest.mark.slow
+def test_precision_policy_of_the_product():
+    info, e = precision_table(formats=("fp32", "bf16"), stages=("interp", "translate", "anterp"))
+    assert info["levels"] == 4
+    for st in ("interp", "translate", "anterp"):
+        assert e[(st, "fp32")] < 1e-5, (st, e)
+    # BF16 operands before the translations break the 1e-3 bar of the product
+    assert e[("interp", "bf16")] > 1e-3, e
+    assert e[("translate", "bf16")] > 1e-3, e
+
+
+if __name__ == "__main__":
+    info, e = precision_table()
+    print("levels %d, N %d, K per level %s" % (info["levels"], info["n_rwg"], info["K"][:info["levels"]]))
+    print("| stage | " + " | ".join(FORMATS) + " |")
+    print("|---|" + "---:|" * len(FORMATS))
+    for st in STAGES:
+        print("| %s | " % st + " | ".join("%.1e" % e[(st, f)] for f in FORMATS) + " |")
