@@ -12,11 +12,21 @@ narrower format and accumulated exactly:
 
 Formats: FP32; TF32 (10-bit mantissa); FP16 with one scale per box pattern (10-bit mantissa,
 range kept by the scale); BF16 (7-bit mantissa).  The error is relative to the FP64 far part.
-The conclusions asserted here fix the product's precision policy: FP32 everywhere keeps the
-error near 1e-6, while BF16 operands on the upward side of the translations (aggregation,
-interpolation, the outgoing patterns of the translations) exceed the 1e-3 bar, because the
-diagonal translation of quarter-wavelength boxes amplifies relative errors of the outgoing
-patterns by orders of magnitude.
+Measured (far part, 7680 RWG, 4 levels):
+
+  | stage     | fp32    | tf32    | fp16_scaled | bf16    |
+  | aggregate | 1.9e-05 | 1.5e-01 | 1.3e-01     | 1.2e+00 |
+  | interp    | 1.0e-05 | 4.3e-02 | 3.1e-02     | 3.4e-01 |
+  | translate | 2.9e-05 | 2.7e-01 | 3.6e-01     | 2.1e+00 |
+  | anterp    | 1.1e-05 | 5.5e-02 | 4.5e-02     | 4.3e-01 |
+  | receive   | 2.6e-05 | 2.1e-01 | 1.9e-01     | 1.6e+00 |
+
+Every stage amplifies its operands' relative rounding by about 400: the far-field sum over the
+directions cancels heavily for quarter-wavelength boxes (the translation operators' high-order
+terms), on the incoming side as much as on the outgoing side.  FP32 keeps every stage 30x or
+more inside the 1e-3 bar; TF32, scaled FP16 and BF16 operands break it at every stage, so the
+product computes in FP32 throughout (tensor-core inputs of those formats would need a split
+representation to reach FP32 accuracy).
 
   python tests/test_precision_study.py      prints the table (a few minutes)
 """
@@ -153,10 +163,9 @@ def test_precision_policy_of_the_product():
     info, e = precision_table(formats=("fp32", "bf16"), stages=("interp", "translate", "anterp"))
     assert info["levels"] == 4
     for st in ("interp", "translate", "anterp"):
-        assert e[(st, "fp32")] < 1e-5, (st, e)
-    # BF16 operands before the translations break the 1e-3 bar of the product
-    assert e[("interp", "bf16")] > 1e-3, e
-    assert e[("translate", "bf16")] > 1e-3, e
+        assert e[(st, "fp32")] < 1e-4, (st, e)
+        # BF16 operands break the 1e-3 bar of the product at every level pass
+        assert e[(st, "bf16")] > 1e-2, (st, e)
 
 
 if __name__ == "__main__":
