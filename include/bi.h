@@ -78,6 +78,14 @@ typedef struct {
                                block-diagonal over leaf boxes, M_b = argmin ||A(N,T) M_b - I(N,T)||_F
                                with T the box's unknowns and N those of its near boxes; built at
                                bi_setup, used by bi_solve and the server, never by bi_matvec */
+    double k_im;            /* imaginary part of the wavenumber, k = k0 + j k_im (default 0).  A lossy
+                               medium (with exp(j w t), -k0 <= k_im < 0; Sec. III.D's coating) takes
+                               the same integrals and expansions continued to complex k: sampling and
+                               box sizes follow Re k, the leaf patterns are stored for every direction
+                               (R_n is no longer conj F_n), the translation operators use spherical
+                               Hankel functions of complex argument, and the near field is integrated
+                               in FP64 throughout.  bi_rhs_planewave, bi_farfield(_noalloc) and the
+                               server take free-space handles only (BI_ERR_ARG otherwise). */
 } bi_params;
 
 typedef struct {

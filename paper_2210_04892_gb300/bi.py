@@ -55,7 +55,7 @@ class Params(ctypes.Structure):
     _fields_ = [("digits", ctypes.c_int), ("leaf_box", ctypes.c_double), ("levels", ctypes.c_int),
                 ("interp_order", ctypes.c_int), ("precision", ctypes.c_int), ("op_mode", ctypes.c_int),
                 ("max_rhs", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("precond", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("precond", ctypes.c_int), ("k_im", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -144,7 +144,8 @@ class Operator:
     """The boundary-integral operator C (Eqs. 43-46) of one closed surface, on the GPU.
 
     op_mode 0: C block (2N unknowns, J then M); op_mode 1: PEC combined field (N).
-    precision "fp32" (complex64 vectors) or "fp64" (complex128)."""
+    precision "fp32" (complex64 vectors) or "fp64" (complex128).  k0 may be complex
+    (k0.real > 0 >= k0.imag: a lossy medium); its imaginary part goes to bi_params.k_im."""
 
     def __init__(self, verts, tris, k0, digits=3, precision="fp32", op_mode=0, leaf_box=0.25, levels=0,
                  interp_order=10, max_rhs=1, gmres_restart=100, gmres_maxit=1000, stream=None, precond=0):
@@ -161,6 +162,8 @@ class Operator:
         p.gmres_restart = int(gmres_restart)
         p.gmres_maxit = int(gmres_maxit)
         p.precond = int(precond)
+        k0 = complex(k0)
+        p.k_im = k0.imag
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -169,7 +172,7 @@ class Operator:
         t = np.ascontiguousarray(tris, np.int32)
         self._v, self._t = v, t
         h = ctypes.c_void_p()
-        rc = L.bi_setup(v.ctypes.data, len(v), t.ctypes.data, len(t), float(k0), int(digits), ctypes.byref(p),
+        rc = L.bi_setup(v.ctypes.data, len(v), t.ctypes.data, len(t), k0.real, int(digits), ctypes.byref(p),
                         ctypes.byref(h))
         _check(rc, None)
         self.h = h
@@ -181,7 +184,7 @@ class Operator:
         L.bi_num_unknowns(h, ctypes.byref(n), ctypes.byref(nu))
         self.n_rwg, self.n_unknowns = n.value, nu.value
         self.max_rhs = int(max_rhs)
-        self.k0 = float(k0)
+        self.k0 = k0.real if k0.imag == 0 else k0
 
     # ---------------------------------------------------------------- queries
     def info(self) -> dict:
@@ -457,10 +460,12 @@ class Plan:
         p = default_params()
         p.digits, p.leaf_box, p.levels, p.interp_order = int(digits), float(leaf_box), int(levels), int(interp_order)
         p.op_mode = int(op_mode)
+        k0 = complex(k0)
+        p.k_im = k0.imag
         v = np.ascontiguousarray(verts, np.float64)
         t = np.ascontiguousarray(tris, np.int32)
         h = ctypes.c_void_p()
-        rc = L.bi_plan_create(v.ctypes.data, len(v), t.ctypes.data, len(t), float(k0), ctypes.byref(p), ctypes.byref(h))
+        rc = L.bi_plan_create(v.ctypes.data, len(v), t.ctypes.data, len(t), k0.real, ctypes.byref(p), ctypes.byref(h))
         if rc != BI_OK:
             raise BIError(rc, L.bi_plan_last_error().decode())
         self.h = h

@@ -73,7 +73,7 @@ bool bi_params_valid(const bi_params& P) {
     return P.digits >= 1 && P.digits <= 8 && P.leaf_box > 0 && P.interp_order >= 2 && P.interp_order <= 32 &&
            (P.precision == 0 || P.precision == 1) && (P.op_mode == 0 || P.op_mode == 1) && P.max_rhs >= 1 &&
            P.max_rhs <= 4096 && P.gmres_restart >= 1 && P.gmres_maxit >= 1 && P.levels >= 0 && P.levels <= 21 &&
-           (P.precond == 0 || P.precond == 1);
+           (P.precond == 0 || P.precond == 1) && P.k_im <= 0.0;
 }
 
 extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, double k0, int digits, const bi_params* opt,
@@ -95,7 +95,13 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
         delete h;
         return BI_ERR_ARG;
     }
+    if (P.k_im < -k0) {
+        g_setup_error = "bi_setup: k_im outside [-k0, 0]";
+        delete h;
+        return BI_ERR_ARG;
+    }
     h->k = k0;
+    h->ki = P.k_im;
     h->prec = P.precision;
     h->csize = P.precision == 0 ? 16 : 8;
     h->nX = P.op_mode == 0 ? 2 : 1;
@@ -104,9 +110,11 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
     const char* env = std::getenv("BI_NO_GRAPHS");
     h->use_graphs = !(env && env[0] == '1');
     const char* env2 = std::getenv("BI_TWO_PASS");
-    h->use_fast = !(env2 && env2[0] == '1');
+    h->use_fast = !(env2 && env2[0] == '1') || h->ki != 0.0;   // the reference kernels assume a real k
     const char* env3 = std::getenv("BI_LEAF_BULK");
     h->use_leaf_bulk = !(env3 && env3[0] == '0');
+    const char* env4 = std::getenv("BI_ANTERP_ROWS");
+    h->force_anterp_rows = env4 && env4[0] == '1';
     try {
         bi_build_rwg(h, verts, nv, tris, nt);
         h->nun = h->nX * h->N;
@@ -287,6 +295,10 @@ extern "C" int bi_matvec_host(bi_handle h, const void* x, void* y, int nrhs) {
 }
 
 extern "C" int bi_rhs_planewave(bi_handle h, const double* khat, const double* phat, int nrhs, void* b) {
+    if (h && h->ki != 0.0) {
+        h->err = "bi_rhs_planewave: the handle's medium is lossy (k_im != 0); plane waves are built for free space";
+        return BI_ERR_ARG;
+    }
     if (!h) return BI_ERR_ARG;
     if (!khat || !phat || !b || nrhs < 1) {
         h->err = "bi_rhs_planewave: null argument or nrhs < 1";
@@ -386,6 +398,10 @@ extern "C" int bi_debug_set_wait_limit(bi_handle h, long long cycles) {
 }
 
 extern "C" int bi_farfield(bi_handle h, const void* x, int nrhs, const double* dirs, int ndir, void* F) {
+    if (h && h->ki != 0.0) {
+        h->err = "bi_farfield: the handle's medium is lossy (k_im != 0); a far field exists in free space only";
+        return BI_ERR_ARG;
+    }
     if (!h) return BI_ERR_ARG;
     if (!x || !dirs || !F || nrhs < 1 || ndir < 1 || nrhs > 65535 || ndir > 65535) {
         h->err = "bi_farfield: null argument or nrhs/ndir outside [1, 65535]";

@@ -152,6 +152,10 @@ extern "C" int bi_farfield_noalloc(bi_handle h, const void* x, int nrhs, const d
         h->err = "bi_farfield_noalloc: null argument or nrhs/ndir outside [1, 65535]";
         return BI_ERR_ARG;
     }
+    if (h->ki != 0.0) {
+        h->err = "bi_farfield_noalloc: the handle's medium is lossy (k_im != 0); a far field exists in free space only";
+        return BI_ERR_ARG;
+    }
     const size_t need = bi_farfield_scratch_bytes(h, nrhs, ndir);
     if (need > (size_t)BI_FARFIELD_NOALLOC_MAX_BYTES) {
         h->err = "bi_farfield_noalloc: needs " + std::to_string(need) + " B of scratch, more than the fixed " +

@@ -66,6 +66,8 @@ struct level_t {
     int* d_octant = nullptr;            // octant of each box inside its parent
     int* d_child_order = nullptr;       // boxes ordered by (slot in parent, parent): siblings far apart in a grid
     void* d_shift = nullptr;            // [8][K] exp(+jk khat.(c_child - c_parent)) for parent level
+    void* d_shift_dn = nullptr;         // [8][K] conj(exp(-jk khat.(c_child - c_parent))), read conjugated by the
+                                        // downward pass; the same table as d_shift when k is real
     void* d_U = nullptr;                // outgoing patterns [nbox][K][E]
     void* d_V = nullptr;                // incoming patterns [nbox][K][E]
     int64_t n_inter = 0;
@@ -111,7 +113,8 @@ struct interp_t {
 
 struct bi_handle_s {
     bi_params prm{};
-    double k = 0;
+    double k = 0;     // Re k: sets the sampling and the box sizes in wavelengths
+    double ki = 0;    // Im k (<= 0: a lossy medium; 0: free space)
     int N = 0, nt = 0, nv = 0;
     int nun = 0;      // unknowns
     int nX = 2;       // currents per RWG (2 for op_mode 0, 1 for op_mode 1)
@@ -128,6 +131,7 @@ struct bi_handle_s {
     bool use_graphs = true;
     bool use_fast = true;               // fused kernels (false: two-pass reference kernels)
     bool use_leaf_bulk = true;          // bulk-copy pipelines for leaf aggregation and receive
+    bool force_anterp_rows = false;     // row-blocked anterpolation on every level (test switch)
     int* d_status = nullptr;            // device status word (0: healthy; see bi_tma.cuh)
     long long wait_cycles = 1ll << 31;  // limit of the bulk-copy waits of the leaf kernels (SM clocks)
     void* d_sai = nullptr;              // near-field SAI blocks, one dense [n_b][n_b] per leaf box (precond 1)

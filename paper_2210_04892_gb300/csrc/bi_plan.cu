@@ -47,7 +47,13 @@ extern "C" int bi_plan_create(const double* verts, int nv, const int* tris, int 
         delete p;
         return BI_ERR_ARG;
     }
+    if (h->prm.k_im < -k0) {
+        g_plan_error = "bi_plan_create: k_im outside [-k0, 0]";
+        delete p;
+        return BI_ERR_ARG;
+    }
     h->k = k0;
+    h->ki = h->prm.k_im;
     h->nX = h->prm.op_mode == 0 ? 2 : 1;
     try {
         bi_build_rwg(h, verts, nv, tris, nt);

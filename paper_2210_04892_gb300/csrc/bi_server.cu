@@ -267,6 +267,11 @@ extern "C" int bi_submit(bi_server S, const double* verts, int nv, const int* tr
                          int64_t* req) {
     if (!S || !verts || !tris || nv < 3 || nt < 4 || !(k0 > 0) || nrhs < 1 || !khat || !phat || !(tol > 0) || !req)
         return BI_ERR_ARG;
+    if (opt && opt->k_im != 0.0) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->err = "bi_submit: plane-wave requests are for free space (k_im = 0)";
+        return BI_ERR_ARG;
+    }
     std::unique_ptr<request> r;
     try {
         r.reset(new request());

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <complex>
 #include <cstdlib>
 #include <vector>
 
@@ -98,6 +99,22 @@ __device__ __forceinline__ zd zexpj(double ph) {  // exp(j ph)
     sincos(ph, &s, &c);
     return zd{c, s};
 }
+__device__ __forceinline__ zd zsub(zd a, zd b) { return zd{a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ zd zinv(zd a) {
+    const double d = 1.0 / (a.x * a.x + a.y * a.y);
+    return zd{a.x * d, -a.y * d};
+}
+
+// Wavenumber arithmetic.  KT = double: a real wavenumber (the exterior free space, the paths
+// used before complex wavenumbers existed, compiled unchanged); KT = zd: a complex wavenumber
+// k = k' + j k'' of a lossy medium (k'' <= 0 with exp(j w t)), where every kernel is the
+// analytic continuation of the real-k one.
+template <typename KT>
+constexpr bool kReal = sizeof(KT) == sizeof(double);
+__device__ __forceinline__ zd kz(double k) { return zd{k, 0.0}; }
+__device__ __forceinline__ zd kz(zd k) { return k; }
+// exp(-j k R) for real R
+__device__ __forceinline__ zd zexp_mjk(zd k, double R) { return zscale(zexpj(-k.x * R), exp(k.y * R)); }
 
 // Closed-form integrals over triangle S seen from r (in the plane: principal values):
 //   I1 = int 1/R, IR = int R, Irho = int (rho'-rho)/R, IrhoR = int (rho'-rho) R, Ig = int grad_r(1/R)
@@ -167,7 +184,8 @@ struct inner_res {
     zd Kv[3];
 };
 
-__device__ void inner_regular(const dtri& S, double k, const double* r, inner_res& o) {
+template <typename KT>
+__device__ void inner_regular(const dtri& S, KT k, const double* r, inner_res& o) {
     o.Sg = zmk(0, 0);
     for (int d = 0; d < 3; ++d) { o.Sr[d] = zmk(0, 0); o.Kv[d] = zmk(0, 0); }
     const double i4pi = 1.0 / (4.0 * kPiD);
@@ -178,10 +196,17 @@ __device__ void inner_regular(const dtri& S, double k, const double* r, inner_re
         for (int c = 0; c < 3; ++c) d[c] = b0 * S.p[0][c] + b1 * S.p[1][c] + b2 * S.p[2][c] - r[c];
         double R = sqrt(dot3(d, d));
         double ww = w * S.area;
-        zd e = zexpj(-k * R);
+        zd e, jkr;   // exp(-jkR), 1 + jkR
+        if constexpr (kReal<KT>) {
+            e = zexpj(-k * R);
+            jkr = zmk(1.0, k * R);
+        } else {
+            e = zexp_mjk(k, R);
+            jkr = zmk(1.0 - k.y * R, k.x * R);
+        }
         zd G = zscale(e, i4pi / R * ww);
         // (1 + jkR) e / (4 pi R^3)
-        zd gt = zscale(zmul(zmk(1.0, k * R), e), i4pi / (R * R * R) * ww);
+        zd gt = zscale(zmul(jkr, e), i4pi / (R * R * R) * ww);
         o.Sg = zadd(o.Sg, G);
         for (int c = 0; c < 3; ++c) {
             o.Sr[c] = zadd(o.Sr[c], zscale(G, d[c]));
@@ -190,11 +215,11 @@ __device__ void inner_regular(const dtri& S, double k, const double* r, inner_re
     }
 }
 
-__device__ void inner_singular(const dtri& S, double k, const double* r, inner_res& o, bool need_kv) {
+template <typename KT>
+__device__ void inner_singular(const dtri& S, KT k, const double* r, inner_res& o, bool need_kv) {
     statics st;
     static_parts(S, r, st);
     const double i4pi = 1.0 / (4.0 * kPiD);
-    const double k2 = k * k;
     // int (r'-r)/R = Irho - h n I1 ;  int (r'-r) R = IrhoR - h n IR
     double rr1[3], rrR[3];
     for (int c = 0; c < 3; ++c) {
@@ -202,10 +227,20 @@ __device__ void inner_singular(const dtri& S, double k, const double* r, inner_r
         rrR[c] = st.IrhoR[c] - st.h * S.n[c] * st.IR;
     }
     // static parts of G = 1/(4 pi R) - k^2 R/(8 pi) + smooth, grad G = (r'-r)[1/R^3 + k^2/(2R)]/(4 pi) + smooth
-    o.Sg = zmk((st.I1 - 0.5 * k2 * st.IR) * i4pi, 0.0);
-    for (int c = 0; c < 3; ++c) {
-        o.Sr[c] = zmk((rr1[c] - 0.5 * k2 * rrR[c]) * i4pi, 0.0);
-        o.Kv[c] = need_kv ? zmk((st.Ig[c] + 0.5 * k2 * rr1[c]) * i4pi, 0.0) : zmk(0, 0);
+    if constexpr (kReal<KT>) {
+        const double k2 = k * k;
+        o.Sg = zmk((st.I1 - 0.5 * k2 * st.IR) * i4pi, 0.0);
+        for (int c = 0; c < 3; ++c) {
+            o.Sr[c] = zmk((rr1[c] - 0.5 * k2 * rrR[c]) * i4pi, 0.0);
+            o.Kv[c] = need_kv ? zmk((st.Ig[c] + 0.5 * k2 * rr1[c]) * i4pi, 0.0) : zmk(0, 0);
+        }
+    } else {
+        const zd h2 = zscale(zmul(k, k), 0.5 * i4pi);   // k^2 / (8 pi)
+        o.Sg = zsub(zmk(st.I1 * i4pi, 0.0), zscale(h2, st.IR));
+        for (int c = 0; c < 3; ++c) {
+            o.Sr[c] = zsub(zmk(rr1[c] * i4pi, 0.0), zscale(h2, rrR[c]));
+            o.Kv[c] = need_kv ? zadd(zmk(st.Ig[c] * i4pi, 0.0), zscale(h2, rr1[c])) : zmk(0, 0);
+        }
     }
     for (int q = 0; q < 7; ++q) {
         double b0, b1, b2, w;
@@ -213,20 +248,46 @@ __device__ void inner_singular(const dtri& S, double k, const double* r, inner_r
         double d[3];
         for (int c = 0; c < 3; ++c) d[c] = b0 * S.p[0][c] + b1 * S.p[1][c] + b2 * S.p[2][c] - r[c];
         double R = sqrt(dot3(d, d));
-        double x = k * R;
         double ww = w * S.area * i4pi;
         zd gr, gtr;
-        if (x < 1e-2) {
-            // series of the remainders
-            gr = zmk(k * x * x * x / 24.0, -k + k * x * x / 6.0 - k * x * x * x * x / 120.0);
-            gtr = (R > 0) ? zmk((-x * x * x * x / 8.0 + x * x * x * x * x * x / 144.0) / (R * R * R),
-                                (-x * x * x / 3.0 + x * x * x * x * x / 30.0) / (R * R * R))
-                          : zmk(0, -k * k * k / 3.0);
+        if constexpr (kReal<KT>) {
+            double x = k * R;
+            if (x < 1e-2) {
+                // series of the remainders
+                gr = zmk(k * x * x * x / 24.0, -k + k * x * x / 6.0 - k * x * x * x * x / 120.0);
+                gtr = (R > 0) ? zmk((-x * x * x * x / 8.0 + x * x * x * x * x * x / 144.0) / (R * R * R),
+                                    (-x * x * x / 3.0 + x * x * x * x * x / 30.0) / (R * R * R))
+                              : zmk(0, -k * k * k / 3.0);
+            } else {
+                zd e = zexpj(-x);
+                gr = zscale(zmk(e.x - 1.0 + 0.5 * x * x, e.y), 1.0 / R);
+                zd t = zmul(zmk(1.0, x), e);
+                gtr = zscale(zmk(t.x - 1.0 - 0.5 * x * x, t.y), 1.0 / (R * R * R));
+            }
         } else {
-            zd e = zexpj(-x);
-            gr = zscale(zmk(e.x - 1.0 + 0.5 * x * x, e.y), 1.0 / R);
-            zd t = zmul(zmk(1.0, x), e);
-            gtr = zscale(zmk(t.x - 1.0 - 0.5 * x * x, t.y), 1.0 / (R * R * R));
+            // the same remainders at complex x = kR:
+            //   (exp(-jx) - 1 + x^2/2) / R,   ((1 + jx) exp(-jx) - 1 - x^2/2) / R^3
+            const zd x = zscale(k, R);
+            const zd x2 = zmul(x, x), x3 = zmul(x2, x), x4 = zmul(x2, x2);
+            if (sqrt(x.x * x.x + x.y * x.y) < 1e-2) {
+                // k (x^3/24 + j(-1 + x^2/6 - x^4/120)),  (-j x^3/3 - x^4/8 + j x^5/30 + x^6/144) / R^3
+                const zd a = zmk(-1.0 + x2.x / 6.0 - x4.x / 120.0, x2.y / 6.0 - x4.y / 120.0);
+                gr = zmul(k, zadd(zscale(x3, 1.0 / 24.0), zmk(-a.y, a.x)));
+                if (R > 0) {
+                    const zd x5 = zmul(x4, x), x6 = zmul(x3, x3);
+                    const zd im = zadd(zscale(x3, -1.0 / 3.0), zscale(x5, 1.0 / 30.0));   // times j
+                    const zd re = zadd(zscale(x4, -1.0 / 8.0), zscale(x6, 1.0 / 144.0));
+                    gtr = zscale(zadd(re, zmk(-im.y, im.x)), 1.0 / (R * R * R));
+                } else {
+                    const zd k3 = zmul(zmul(k, k), k);
+                    gtr = zmk(k3.y / 3.0, -k3.x / 3.0);   // -j k^3 / 3
+                }
+            } else {
+                const zd e = zexp_mjk(k, R);
+                gr = zscale(zadd(zsub(e, zmk(1.0, 0.0)), zscale(x2, 0.5)), 1.0 / R);
+                const zd t = zmul(zmk(1.0 - x.y, x.x), e);   // (1 + jx) e
+                gtr = zscale(zsub(zsub(t, zmk(1.0, 0.0)), zscale(x2, 0.5)), 1.0 / (R * R * R));
+            }
         }
         gr = zscale(gr, ww);
         gtr = zscale(gtr, ww);
@@ -243,8 +304,9 @@ struct raw4 {
     zd L, NL, K, NK;
 };
 
+template <typename KT>
 __device__ void outer_point(const dtri& Tm, const dtri& Tn, int i, int j, const double* r, double W, const inner_res& in,
-                            double k, bool surface_nl, raw4& acc) {
+                            KT k, bool surface_nl, raw4& acc) {
     double gi[3], gj[3], ngi[3], ngj[3];
     for (int c = 0; c < 3; ++c) { gi[c] = r[c] - Tm.p[i][c]; gj[c] = r[c] - Tn.p[j][c]; }
     cross3(Tm.n, gi, ngi);
@@ -258,13 +320,22 @@ __device__ void outer_point(const dtri& Tm, const dtri& Tn, int i, int j, const 
     }
     double gg = dot3(gi, gj), gngj = dot3(gi, ngj);
     // L: -jk [ g_i.Sr + (g_i.g_j) Sg - (4/k^2) Sg ]
-    zd tL = zadd(giSr, zscale(in.Sg, gg - 4.0 / (k * k)));
-    acc.L = zadd(acc.L, zscale(zmul(zmk(0, -k), tL), W));
     // NL surface part: -jk [ -(n x g_i).Sr + (g_i.(n x g_j)) Sg ] (+ (2j/k)(n x g_i).Kv when separated)
     zd tN = zadd(zscale(ngiSr, -1.0), zscale(in.Sg, gngj));
-    zd nl = zmul(zmk(0, -k), tN);
-    if (surface_nl) nl = zadd(nl, zmul(zmk(0, 2.0 / k), ngiKv));
-    acc.NL = zadd(acc.NL, zscale(nl, W));
+    if constexpr (kReal<KT>) {
+        zd tL = zadd(giSr, zscale(in.Sg, gg - 4.0 / (k * k)));
+        acc.L = zadd(acc.L, zscale(zmul(zmk(0, -k), tL), W));
+        zd nl = zmul(zmk(0, -k), tN);
+        if (surface_nl) nl = zadd(nl, zmul(zmk(0, 2.0 / k), ngiKv));
+        acc.NL = zadd(acc.NL, zscale(nl, W));
+    } else {
+        const zd ik = zinv(k), mjk = zmk(k.y, -k.x);
+        zd tL = zadd(zadd(giSr, zscale(in.Sg, gg)), zscale(zmul(in.Sg, zmul(ik, ik)), -4.0));
+        acc.L = zadd(acc.L, zscale(zmul(mjk, tL), W));
+        zd nl = zmul(mjk, tN);
+        if (surface_nl) nl = zadd(nl, zmul(zmk(-2.0 * ik.y, 2.0 * ik.x), ngiKv));
+        acc.NL = zadd(acc.NL, zscale(nl, W));
+    }
     // K: g_i.(Kv x g_j) = Kv.(g_j x g_i) ; NK: g_i.(n x (Kv x g_j)) = (Kv.g_i)(n.g_j) - (g_i.g_j)(n.Kv)
     double gjxgi[3];
     cross3(gj, gi, gjxgi);
@@ -280,7 +351,8 @@ __device__ void outer_point(const dtri& Tm, const dtri& Tn, int i, int j, const 
 }
 
 // grad-Phi part of NL on the edges of the test triangle: -(j/k) sum_e int_e Phi (g_i . tau) dl, Phi = 2 int G
-__device__ void nl_edges(const dtri& Tm, const dtri& Tn, int i, double k, raw4& acc) {
+template <typename KT>
+__device__ void nl_edges(const dtri& Tm, const dtri& Tn, int i, KT k, raw4& acc) {
     for (int e = 0; e < 3; ++e) {
         const double* A = Tm.p[e];
         const double* B = Tm.p[(e + 1) % 3];
@@ -295,12 +367,18 @@ __device__ void nl_edges(const dtri& Tm, const dtri& Tn, int i, double k, raw4& 
             double gt = (r[0] - Tm.p[i][0]) * t[0] + (r[1] - Tm.p[i][1]) * t[1] + (r[2] - Tm.p[i][2]) * t[2];
             double wl = c_rules.line_w[q] * len * gt;
             // -(j/k) * 2 Sg * wl
-            acc.NL = zadd(acc.NL, zmul(zmk(0, -2.0 * wl / k), in.Sg));
+            if constexpr (kReal<KT>) {
+                acc.NL = zadd(acc.NL, zmul(zmk(0, -2.0 * wl / k), in.Sg));
+            } else {
+                const zd ik = zinv(k);
+                acc.NL = zadd(acc.NL, zmul(zmk(2.0 * wl * ik.y, -2.0 * wl * ik.x), in.Sg));
+            }
         }
     }
 }
 
-__device__ raw4 tri_pair(const dtri& Tm, int i, const dtri& Tn, int j, double k) {
+template <typename KT>
+__device__ raw4 tri_pair(const dtri& Tm, int i, const dtri& Tn, int j, KT k) {
     raw4 acc{zmk(0, 0), zmk(0, 0), zmk(0, 0), zmk(0, 0)};
     int sa[3], ns = 0;
     for (int a = 0; a < 3; ++a)
@@ -657,13 +735,13 @@ __global__ void __launch_bounds__(128) k_near_special(unsigned long long nlist, 
 
 // One CTA per near block (test leaf box b, source box s); threads loop over the block's
 // entries, column-major (source column outer, test row inner).
-template <typename T>
+template <typename T, typename KT>
 __global__ void k_near_fill(int nblk, const int* __restrict__ blk_box, const int* __restrict__ near_ptr,
                             const int* __restrict__ near_src,
                             const int64_t* __restrict__ near_blk, const int* __restrict__ leaf_start,
                             const int* __restrict__ rwg_t, const int* __restrict__ rwg_l, const double* __restrict__ rwg_len,
                             const double* __restrict__ tri, const double* __restrict__ nrm, const double* __restrict__ area,
-                            const int* __restrict__ vid, double k, int mode, T* __restrict__ out) {
+                            const int* __restrict__ vid, KT k, int mode, T* __restrict__ out) {
     int q = blockIdx.x;
     if (q >= nblk) return;
     int b = blk_box[q], s = near_src[q];
@@ -735,12 +813,14 @@ __global__ void k_near_fill(int nblk, const int* __restrict__ blk_box, const int
 // the antipode -khat is the conjugate vector, and theta-hat(-khat) = theta-hat(khat),
 // phi-hat(-khat) = -phi-hat(khat): only the first K/2 directions (theta-major: one of each
 // antipodal pair) are stored, [N][K/2][2].
+// With a complex wavenumber (ki != 0) the identities behind the packing fail (R_n is no longer
+// conj F_n): every direction is stored, Kh = K, and exp(+-jk khat.(r - c)) carries the decay.
 template <typename T>
 __global__ void k_patterns(int N, int K, int nph, const double* __restrict__ theta, const int* __restrict__ leaf_of,
                            const double* __restrict__ centers, const int* __restrict__ rwg_t, const int* __restrict__ rwg_l,
                            const double* __restrict__ rwg_len, const double* __restrict__ tri, const double* __restrict__ nrm,
-                           const double* __restrict__ area, double k, T* __restrict__ F, T* __restrict__ RX) {
-    const int Kh = K / 2;
+                           const double* __restrict__ area, double k, double ki, T* __restrict__ F, T* __restrict__ RX) {
+    const int Kh = ki != 0.0 ? K : K / 2;
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)N * Kh) return;
     int n = (int)(idx / Kh), kk = (int)(idx % Kh);
@@ -767,9 +847,13 @@ __global__ void k_patterns(int N, int K, int nph, const double* __restrict__ the
             }
             double nf[3];
             cross3(nn, f, nf);
-            double arg = k * (kh[0] * (r[0] - c[0]) + kh[1] * (r[1] - c[1]) + kh[2] * (r[2] - c[2]));
-            zd e = zexpj(arg);
+            const double a = kh[0] * (r[0] - c[0]) + kh[1] * (r[1] - c[1]) + kh[2] * (r[2] - c[2]);
+            zd e = zexpj(k * a);
             zd ec = zmk(e.x, -e.y);
+            if (ki != 0.0) {   // exp(+jka) = exp(jk'a) exp(-k''a), exp(-jka) = exp(-jk'a) exp(k''a)
+                e = zscale(e, exp(-ki * a));
+                ec = zscale(ec, exp(ki * a));
+            }
             Ft = zadd(Ft, zscale(e, dot3(f, tv)));
             Fp = zadd(Fp, zscale(e, dot3(f, pv)));
             Rt = zadd(Rt, zscale(ec, dot3(nf, tv)));
@@ -826,7 +910,8 @@ __global__ void k_translations(int K, int nph, int L, const double* __restrict__
 
 // exp(+jk khat.(c_child - c_parent)) for the 8 child octants of a parent level
 template <typename T>
-__global__ void k_shifts(int K, int nph, const double* __restrict__ theta, double half_child, double k, T* __restrict__ out) {
+__global__ void k_shifts(int K, int nph, const double* __restrict__ theta, double half_child, double k, double ki,
+                         T* __restrict__ out) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 8 * K) return;
     int o = idx / K, kk = idx % K;
@@ -836,7 +921,9 @@ __global__ void k_shifts(int K, int nph, const double* __restrict__ theta, doubl
     sincos(th, &st, &ct);
     sincos(ph, &sp, &cp);
     double d[3] = {((o & 1) ? 1.0 : -1.0) * half_child, ((o & 2) ? 1.0 : -1.0) * half_child, ((o & 4) ? 1.0 : -1.0) * half_child};
-    zd e = zexpj(k * (st * cp * d[0] + st * sp * d[1] + ct * d[2]));
+    const double a = st * cp * d[0] + st * sp * d[1] + ct * d[2];
+    zd e = zexpj(k * a);
+    if (ki != 0.0) e = zscale(e, exp(-ki * a));
     out[2 * idx] = (T)e.x;
     out[2 * idx + 1] = (T)e.y;
 }
@@ -874,6 +961,34 @@ void hankel2(int L, double x, std::vector<double>& out) {
     }
 }
 
+// h_l^(2)(z) for complex z (a lossy medium's k |X|): y_l by upward recurrence, j_l by Miller's
+// downward recurrence normalised with the closed form of the larger of j_0, j_1 (neither
+// vanishes off the real axis, and no sum that cancels is formed).
+void hankel2c(int L, std::complex<double> z, std::vector<double>& out) {
+    typedef std::complex<double> C;
+    out.assign(2 * (L + 1), 0.0);
+    const C sz = std::sin(z), cz = std::cos(z);
+    std::vector<C> y(L + 2);
+    y[0] = -cz / z;
+    if (L >= 1) y[1] = -cz / (z * z) - sz / z;
+    for (int l = 1; l < L; ++l) y[l + 1] = (2.0 * l + 1.0) / z * y[l] - y[l - 1];
+    const int start = L + 40 + (int)(1.2 * std::abs(z));
+    std::vector<C> f(start + 2, C(0.0));
+    f[start] = 1.0;
+    for (int l = start; l >= 1; --l) {
+        f[l - 1] = (2.0 * l + 1.0) / z * f[l] - f[l + 1];
+        if (std::abs(f[l - 1]) > 1e100)
+            for (int m = l - 1; m <= start; ++m) f[m] *= 1e-100;
+    }
+    const C j0 = sz / z, j1 = sz / (z * z) - cz / z;
+    const C s = std::abs(j0) >= std::abs(j1) ? j0 / f[0] : j1 / f[1];
+    for (int l = 0; l <= L; ++l) {
+        const C h = f[l] * s - C(0.0, 1.0) * y[l];
+        out[2 * l] = h.real();
+        out[2 * l + 1] = h.imag();
+    }
+}
+
 }  // namespace
 
 void bi_translation_series(const bi_handle_s* h, int l, std::vector<int>& dist_idx, std::vector<double>& hk) {
@@ -897,7 +1012,9 @@ void bi_translation_series(const bi_handle_s* h, int l, std::vector<int>& dist_i
     hk.reserve(sq_of.size() * 2 * (L.L + 1));
     for (int sq : sq_of) {
         std::vector<double> one;
-        hankel2(L.L, h->k * L.a * std::sqrt((double)sq), one);
+        const double X = L.a * std::sqrt((double)sq);
+        if (h->ki != 0.0) hankel2c(L.L, std::complex<double>(h->k * X, h->ki * X), one);
+        else hankel2(L.L, h->k * X, one);
         hk.insert(hk.end(), one.begin(), one.end());
     }
 }
@@ -1058,7 +1175,7 @@ void bi_fill_near(bi_handle_s* h) {
     size_t per = (h->prm.op_mode == 0 ? 2 : 1) * h->csize;
     h->d_near = h->alloc(per * (size_t)std::max<int64_t>(h->near_nnz, 1));
     const char* env_fill = std::getenv("BI_NEAR_FILL_SINGLE_PASS");
-    const bool two_pass = !(env_fill && env_fill[0] == '1');
+    const bool two_pass = !(env_fill && env_fill[0] == '1') && h->ki == 0.0;
     if (nblk > 0 && two_pass) {
         // per-class lists of singular / near-singular triangle pairs, counted first and sized exactly
         unsigned long long* d_count = nullptr;
@@ -1116,14 +1233,28 @@ void bi_fill_near(bi_handle_s* h) {
         h->info.setup_near_regular_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
         h->info.setup_near_special_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
         h->info.near_special_entries = (int64_t)total;
+    } else if (nblk > 0 && h->ki != 0.0) {
+        // complex wavenumber: every triangle pair in FP64 (singularity extraction for close pairs)
+        const zd kc{h->k, h->ki};
+        if (h->prec == 0)
+            k_near_fill<double, zd><<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_ptr, h->d_near_src, h->d_near_blk,
+                                                                  h->d_leaf_start, h->d_rwg_t, h->d_rwg_l, h->d_rwg_len,
+                                                                  h->d_tri, h->d_tri_n, h->d_tri_area, h->d_tri_vid, kc,
+                                                                  h->prm.op_mode, (double*)h->d_near);
+        else
+            k_near_fill<float, zd><<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_ptr, h->d_near_src, h->d_near_blk,
+                                                                 h->d_leaf_start, h->d_rwg_t, h->d_rwg_l, h->d_rwg_len,
+                                                                 h->d_tri, h->d_tri_n, h->d_tri_area, h->d_tri_vid, kc,
+                                                                 h->prm.op_mode, (float*)h->d_near);
+        CU(cudaGetLastError());
     } else if (nblk > 0) {
         if (h->prec == 0)
-            k_near_fill<double><<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_ptr, h->d_near_src, h->d_near_blk, h->d_leaf_start,
+            k_near_fill<double, double><<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_ptr, h->d_near_src, h->d_near_blk, h->d_leaf_start,
                                                               h->d_rwg_t, h->d_rwg_l, h->d_rwg_len, h->d_tri, h->d_tri_n,
                                                               h->d_tri_area, h->d_tri_vid, h->k, h->prm.op_mode,
                                                               (double*)h->d_near);
         else
-            k_near_fill<float><<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_ptr, h->d_near_src, h->d_near_blk, h->d_leaf_start,
+            k_near_fill<float, double><<<nblk, 128, 0, h->stream>>>(nblk, d_blk_box, h->d_near_ptr, h->d_near_src, h->d_near_blk, h->d_leaf_start,
                                                              h->d_rwg_t, h->d_rwg_l, h->d_rwg_len, h->d_tri, h->d_tri_n,
                                                              h->d_tri_area, h->d_tri_vid, h->k, h->prm.op_mode,
                                                              (float*)h->d_near);
@@ -1215,20 +1346,21 @@ void bi_fill_patterns(bi_handle_s* h) {
     if (h->leaf < 2) return;
     const level_t& LF = h->lev[h->leaf];
     double* d_theta = h->upload(LF.theta);
-    size_t nel = (size_t)h->N * (LF.K / 2) * 2;
+    const int Ks = h->ki != 0.0 ? LF.K : LF.K / 2;   // stored directions (all of them at complex k)
+    size_t nel = (size_t)h->N * Ks * 2;
     h->d_F = h->alloc(nel * h->csize);
     h->d_RX = h->alloc(nel * h->csize);
-    int64_t tot = (int64_t)h->N * (LF.K / 2);
+    int64_t tot = (int64_t)h->N * Ks;
     int th = 256;
     int64_t nb = (tot + th - 1) / th;
     if (h->prec == 0)
         k_patterns<double><<<(unsigned)nb, th, 0, h->stream>>>(h->N, LF.K, LF.nph, d_theta, h->d_leaf_of, h->d_leaf_center,
                                                                 h->d_rwg_t, h->d_rwg_l, h->d_rwg_len, h->d_tri, h->d_tri_n,
-                                                                h->d_tri_area, h->k, (double*)h->d_F, (double*)h->d_RX);
+                                                                h->d_tri_area, h->k, h->ki, (double*)h->d_F, (double*)h->d_RX);
     else
         k_patterns<float><<<(unsigned)nb, th, 0, h->stream>>>(h->N, LF.K, LF.nph, d_theta, h->d_leaf_of, h->d_leaf_center,
                                                                h->d_rwg_t, h->d_rwg_l, h->d_rwg_len, h->d_tri, h->d_tri_n,
-                                                               h->d_tri_area, h->k, (float*)h->d_F, (float*)h->d_RX);
+                                                               h->d_tri_area, h->k, h->ki, (float*)h->d_F, (float*)h->d_RX);
     CU(cudaGetLastError());
 }
 
@@ -1259,10 +1391,23 @@ void bi_fill_translations(bi_handle_s* h) {
             unsigned nb2 = (unsigned)((8 * L.K + 255) / 256);
             double half_child = 0.5 * h->lev[l + 1].a;
             if (h->prec == 0)
-                k_shifts<double><<<nb2, 256, 0, h->stream>>>(L.K, L.nph, d_theta, half_child, h->k, (double*)L.d_shift);
+                k_shifts<double><<<nb2, 256, 0, h->stream>>>(L.K, L.nph, d_theta, half_child, h->k, h->ki, (double*)L.d_shift);
             else
-                k_shifts<float><<<nb2, 256, 0, h->stream>>>(L.K, L.nph, d_theta, half_child, h->k, (float*)L.d_shift);
+                k_shifts<float><<<nb2, 256, 0, h->stream>>>(L.K, L.nph, d_theta, half_child, h->k, h->ki, (float*)L.d_shift);
             CU(cudaGetLastError());
+            L.d_shift_dn = L.d_shift;
+            if (h->ki != 0.0) {
+                // downward factor exp(-jk khat.d) = exp(-jk'a) exp(k''a), stored conjugated
+                // (exp(+jk'a) exp(k''a)) because the downward kernels conjugate what they read
+                L.d_shift_dn = h->alloc((size_t)8 * L.K * h->csize);
+                if (h->prec == 0)
+                    k_shifts<double><<<nb2, 256, 0, h->stream>>>(L.K, L.nph, d_theta, half_child, h->k, -h->ki,
+                                                                 (double*)L.d_shift_dn);
+                else
+                    k_shifts<float><<<nb2, 256, 0, h->stream>>>(L.K, L.nph, d_theta, half_child, h->k, -h->ki,
+                                                                (float*)L.d_shift_dn);
+                CU(cudaGetLastError());
+            }
             L.d_child_ptr = h->upload(L.child_ptr);
         }
         // octant of each box of this level inside its parent

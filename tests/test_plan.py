@@ -408,6 +408,40 @@ def test_translation_hankel_table(bi, sphere, digits, leaf_box):
     p.close()
 
 
+def test_translation_hankel_table_at_complex_k(bi, sphere):
+    """The same table for a lossy medium (the coating's k1 = k0 sqrt(2 - 0.5j)): h_n^(2) of the
+    complex argument k1 |X| on every level against scipy.  Here y_n runs upward and j_n
+    downward, normalised with the closed form of the larger of j_0, j_1 (neither vanishes off
+    the real axis).  At low orders and large |Im z| (8 on the coarsest level) h_n is the small
+    difference of j_n and j y_n, each about e^|Im z| / |z|: the error is bounded against
+    |j_n| + |y_n|, and relative to h_n wherever no such cancellation occurs."""
+    special = pytest.importorskip("scipy.special")
+    v, t = sphere
+    k1 = K0 * np.sqrt(2.0 - 0.5j)
+    p = bi.Plan(v, t, k1, digits=3)
+    info = p.info()
+    assert info["levels"] >= 5
+    for l in range(2, info["leaf_level"] + 1):
+        L = info["L"][l]
+        di = p.get(40, l)
+        hk = p.get(41, l).reshape(-1, L + 1, 2)
+        a = info["root_size"] / 2**l
+        for o in range(343):
+            off = np.array([o // 49 - 3, (o // 7) % 7 - 3, o % 7 - 3])
+            if np.abs(off).max() <= 1:
+                continue
+            z = k1 * a * np.linalg.norm(off)
+            n = np.arange(L + 1)
+            j, y = special.spherical_jn(n, z), special.spherical_yn(n, z)
+            h = j - 1j * y
+            g = hk[di[o]]
+            err = np.abs(g[:, 0] + 1j * g[:, 1] - h)
+            assert np.all(err <= 1e-12 * (np.abs(j) + np.abs(y))), (l, o)
+            if abs(z.imag) < 2:
+                assert np.all(err <= 1e-11 * np.abs(h)), (l, o)
+    p.close()
+
+
 def _rwg_pattern_subset(v, t, rwg, idx, k, khat, center):
     """int f_n exp(+jk khat.(r - center)) dS for the RWG indices idx (numpy: a 6 x 6 conical
     Gauss rule on each of the four midpoint sub-triangles of every triangle)."""
