@@ -347,6 +347,79 @@ __global__ void __launch_bounds__(256) k_anterp_cbE(int nthc, int nphc, int nthp
     }
 }
 
+// Coarse levels, where one child's shifted parent field does not fit: CTA = (child c, block of
+// nr child rows, chunk of EC entries).  Interpolation in phi commutes with the half turn that the
+// pole taps apply (both grids are uniform with an even count), so the transpose can take theta
+// first, on the parent's columns, then phi:
+//   t[ic][jp]  = sum over the transposed theta taps (ip, w, flip) of w conj(shift) V_p[ip][jp or jp + nphp/2]
+//   V_c[ic][jc] += sum over the transposed phi taps (jp, w) of w t[ic][jp]
+// The shifted parent field is read from L2 per tap; only t is kept in shared memory.
+template <typename T, int PT>
+__global__ void __launch_bounds__(256) k_anterp_rbE(int nthc, int nphc, int nthp, int nphp, int E, int RB, int EC, int nrb,
+                                                    const int* __restrict__ parent, const int* __restrict__ octant,
+                                                    const tap<T>* __restrict__ tth_pad, const tap<T>* __restrict__ tph_pad,
+                                                    const cpx<T>* __restrict__ shift, const cpx<T>* __restrict__ Vp,
+                                                    cpx<T>* __restrict__ Vc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nec = E / EC;
+    const int ec = blockIdx.x % nec;
+    const int rb = (blockIdx.x / nec) % nrb;
+    const int c = blockIdx.x / (nec * nrb);
+    const int ic0 = rb * RB, nr = min(RB, nthc - ic0), e0 = ec * EC, PC = EC / 2;
+    const int pb = parent[c], oct = octant[c];
+    const int Kc = nthc * nphc, Kp = nthp * nphp, hp = nphp / 2;
+    const int64_t E64 = E;
+    tap<T>* tt = reinterpret_cast<tap<T>*>(smem_raw);       // [RB][PT]
+    tap<T>* pt = tt + RB * PT;                               // [PT][nphc]
+    cpx<T>* tS = reinterpret_cast<cpx<T>*>(smem_raw + (((size_t)(RB + nphc) * PT * sizeof(tap<T>) + 15) / 16) * 16);
+    for (int i = threadIdx.x; i < nr * PT; i += blockDim.x) tt[i] = tth_pad[ic0 * PT + i];
+    for (int i = threadIdx.x; i < nphc * PT; i += blockDim.x) {
+        const int jc = i / PT, q = i - jc * PT;
+        pt[q * nphc + jc] = tph_pad[i];
+    }
+    __syncthreads();
+    const cpx<T>* sh = shift + (int64_t)oct * Kp;
+    const cpx<T>* vp = Vp + (int64_t)pb * Kp * E64 + e0;
+    const float invPC = 1.0f / PC, invPP = 1.0f / (nphp * PC), invCP = 1.0f / (nphc * PC);
+    for (int o = threadIdx.x; o < nr * nphp * PC; o += blockDim.x) {
+        const int icl = fdiv(o, nphp * PC, invPP);
+        const int rem = o - icl * nphp * PC;
+        const int jp = fdiv(rem, PC, invPC), pr = rem - jp * PC;
+        const int jpf = jp + hp < nphp ? jp + hp : jp + hp - nphp;
+        cpx<T> a = czero<T>(), b = czero<T>();
+        for (int q = 0; q < PT; ++q) {
+            const tap<T> tq = tt[icl * PT + q];
+            if (tq.w == T(0)) continue;
+            const int i = (tq.c >> 1) * nphp + ((tq.c & 1) ? jpf : jp);
+            cpx<T> va, vb;
+            load_pair(vp + (int64_t)i * E64 + 2 * pr, va, vb);
+            const cpx<T> z = ldg_c(sh + i);
+            fma_pair(tq.w, cmulc(z, va), cmulc(z, vb), a, b);
+        }
+        sts_pair(tS + 2 * (int64_t)o, a, b);
+    }
+    __syncthreads();
+    cpx<T>* vc = Vc + ((int64_t)c * Kc + (int64_t)ic0 * nphc) * E64 + e0;
+    for (int o = threadIdx.x; o < nr * nphc * PC; o += blockDim.x) {
+        const int icl = fdiv(o, nphc * PC, invCP);
+        const int rem = o - icl * nphc * PC;
+        const int jc = fdiv(rem, PC, invPC), pr = rem - jc * PC;
+        const cpx<T>* row = tS + ((int64_t)icl * nphp * PC + pr) * 2;
+        cpx<T> a = czero<T>(), b = czero<T>();
+#pragma unroll
+        for (int q = 0; q < PT; ++q) {
+            const tap<T> tq = pt[q * nphc + jc];
+            cpx<T> va, vb;
+            lds_pair(row + (int64_t)tq.c * EC, va, vb);
+            fma_pair(tq.w, va, vb, a, b);
+        }
+        cpx<T>* g = vc + ((int64_t)icl * nphc + jc) * E64 + 2 * pr;
+        cpx<T> ga, gb;
+        load_pair(g, ga, gb);
+        sts_pair(g, cadd(ga, a), cadd(gb, b));
+    }
+}
+
 // ---------------------------------------------------------------- one right-hand side (E = 2)
 template <typename T, int P>
 __global__ void __launch_bounds__(256, 4) k_interp_pb1(int nthc, int nphc, int nthp, int nphp, int RB,
@@ -644,7 +717,7 @@ bool anterp_wide(bi_handle_s* h, int l, int E, cudaStream_t s) {
     if (!I.d_tmp) return false;
     const dim3 blk(32, 8);
     k_anterp_phi_w<T, PT><<<(unsigned)((int64_t)C.nbox * Pl.nth), blk, 0, s>>>(Pl.nth, Pl.nph, C.nph, E, (const tap<T>*)I.d_tph_pad,
-                                                                             C.d_parent, C.d_octant, (const cpx<T>*)Pl.d_shift,
+                                                                             C.d_parent, C.d_octant, (const cpx<T>*)Pl.d_shift_dn,
                                                                              (const cpx<T>*)Pl.d_V, (cpx<T>*)I.d_tmp);
     CU(cudaGetLastError());
     k_anterp_theta_w<T, PT><<<(unsigned)((int64_t)C.nbox * C.nth), blk, 0, s>>>(C.nth, C.nph, Pl.nth, E, (const tap<T>*)I.d_tth_pad,
@@ -765,7 +838,7 @@ bool anterp_t_p(bi_handle_s* h, int l, int E, cudaStream_t s) {
         auto k1 = k_anterp_cb1<T, PT>;
         bi_raise_smem(k1, smem);
         k1<<<C.nbox, 256, smem, s>>>(C.nth, C.nph, Pl.nth, Pl.nph, C.d_parent, C.d_octant, (const tap<T>*)I.d_tth_pad,
-                                     (const tap<T>*)I.d_tph_pad, (const cpx<T>*)Pl.d_shift, (const cpx<T>*)Pl.d_V,
+                                     (const tap<T>*)I.d_tph_pad, (const cpx<T>*)Pl.d_shift_dn, (const cpx<T>*)Pl.d_V,
                                      (cpx<T>*)C.d_V);
         CU(cudaGetLastError());
         return true;
@@ -773,7 +846,7 @@ bool anterp_t_p(bi_handle_s* h, int l, int E, cudaStream_t s) {
     auto kern = k_anterp_cb<T, PT, PP>;
     bi_raise_smem(kern, smem);
     kern<<<C.nbox, 256, smem, s>>>(C.nth, C.nph, Pl.nth, Pl.nph, E, C.d_parent, C.d_octant, (const tap<T>*)I.d_tth_pad,
-                                   (const tap<T>*)I.d_tph_pad, (const cpx<T>*)Pl.d_shift, (const cpx<T>*)Pl.d_V,
+                                   (const tap<T>*)I.d_tph_pad, (const cpx<T>*)Pl.d_shift_dn, (const cpx<T>*)Pl.d_V,
                                    (cpx<T>*)C.d_V);
     CU(cudaGetLastError());
     return true;
@@ -805,7 +878,39 @@ bool anterp_chunked(bi_handle_s* h, int l, int E, cudaStream_t s) {
     bi_raise_smem(kern, smem);
     kern<<<(unsigned)blocks, 256, smem, s>>>(C.nth, C.nph, Pl.nth, Pl.nph, E, EC, C.d_parent, C.d_octant,
                                              (const tap<T>*)I.d_tth_pad, (const tap<T>*)I.d_tph_pad,
-                                             (const cpx<T>*)Pl.d_shift, (const cpx<T>*)Pl.d_V, (cpx<T>*)C.d_V);
+                                             (const cpx<T>*)Pl.d_shift_dn, (const cpx<T>*)Pl.d_V, (cpx<T>*)C.d_V);
+    CU(cudaGetLastError());
+    return true;
+}
+
+// Coarse levels: the row-blocked kernel, EC the largest of 16, 8, 4, 2 dividing E with at least
+// one child row's parent-column field (nphp x EC) in about 48 KB; rows fill up to that.
+template <typename T, int PT>
+bool anterp_rows(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    level_t& Pl = h->lev[l];
+    level_t& C = h->lev[l + 1];
+    interp_t& I = h->itp[l];
+    const size_t budget = 48 * 1024;
+    int EC = 0;
+    for (int ec : {16, 8, 4, 2})
+        if (E % ec == 0 && (size_t)Pl.nph * ec * sizeof(cpx<T>) * 2 <= budget) {
+            EC = ec;
+            break;
+        }
+    if (!EC) return false;
+    const size_t per_row = (size_t)Pl.nph * EC * sizeof(cpx<T>);
+    int RB = (int)std::max<size_t>(1, budget / per_row);
+    RB = std::min(RB, C.nth);
+    const size_t smem = (((size_t)(RB + C.nph) * PT * sizeof(tap<T>) + 15) / 16) * 16 + (size_t)RB * per_row;
+    if (smem > 160 * 1024) return false;
+    const int nrb = (C.nth + RB - 1) / RB, nec = E / EC;
+    const int64_t blocks = (int64_t)C.nbox * nrb * nec;
+    if (blocks > 0x7fffffffLL) return false;
+    auto kern = k_anterp_rbE<T, PT>;
+    bi_raise_smem(kern, smem);
+    kern<<<(unsigned)blocks, 256, smem, s>>>(C.nth, C.nph, Pl.nth, Pl.nph, E, RB, EC, nrb, C.d_parent, C.d_octant,
+                                             (const tap<T>*)I.d_tth_pad, (const tap<T>*)I.d_tph_pad,
+                                             (const cpx<T>*)Pl.d_shift_dn, (const cpx<T>*)Pl.d_V, (cpx<T>*)C.d_V);
     CU(cudaGetLastError());
     return true;
 }
@@ -838,9 +943,14 @@ bool bi_anterp_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
     const interp_t& I = h->itp[l];
     if (!I.d_tth_pad) return false;
     if (E > 2 && I.pt_th == I.pt_ph) {
-        if (I.pt_th == 16 && (h->prec == 0 ? anterp_chunked<double, 16>(h, l, E, s) : anterp_chunked<float, 16>(h, l, E, s)))
+        const bool whole = !h->force_anterp_rows;
+        if (whole && I.pt_th == 16 && (h->prec == 0 ? anterp_chunked<double, 16>(h, l, E, s) : anterp_chunked<float, 16>(h, l, E, s)))
             return true;
-        if (I.pt_th == 24 && (h->prec == 0 ? anterp_chunked<double, 24>(h, l, E, s) : anterp_chunked<float, 24>(h, l, E, s)))
+        if (whole && I.pt_th == 24 && (h->prec == 0 ? anterp_chunked<double, 24>(h, l, E, s) : anterp_chunked<float, 24>(h, l, E, s)))
+            return true;
+        if (I.pt_th == 16 && (h->prec == 0 ? anterp_rows<double, 16>(h, l, E, s) : anterp_rows<float, 16>(h, l, E, s)))
+            return true;
+        if (I.pt_th == 24 && (h->prec == 0 ? anterp_rows<double, 24>(h, l, E, s) : anterp_rows<float, 24>(h, l, E, s)))
             return true;
     }
     if (E >= 32) {

@@ -739,6 +739,10 @@ __global__ void __launch_bounds__(256) k_receive_tile(int N, int K, int nph, int
     const int Kh = K / 2;
     cpx<T>* fs = reinterpret_cast<cpx<T>*>(smem_raw);       // [nb][KT][4]: Ft Fp Xt Xp (stored directions)
     cpx<T>* vs = fs + (size_t)nb * KT * 4;                    // [KT][4][RC]: V at kk (t, p), at its antipode (t, p)
+    // When the box has fewer (RWG, RHS) outputs than threads, G groups of threads split the
+    // directions of each tile (group g takes kl = g, g + G, ...) and meet in shared memory.
+    const int no = nb * rc;
+    const int G = no > 0 ? max(1, min(8, (int)blockDim.x / no)) : 1;
     cpx<T> aJ[OPT], aM[OPT];
 #pragma unroll
     for (int o = 0; o < OPT; ++o) { aJ[o] = czero<T>(); aM[o] = czero<T>(); }
@@ -767,6 +771,20 @@ __global__ void __launch_bounds__(256) k_receive_tile(int N, int K, int nph, int
         }
         __syncthreads();
         const int kn = min(KT, Kh - k0);
+        if (G > 1) {
+            const int g = threadIdx.x / no, it = threadIdx.x - g * no;
+            if (g < G) {
+                const int n = it / rc, r = it % rc;
+                for (int kl = g; kl < kn; kl += G) {
+                    const cpx<T>* f = fs + (n * KT + kl) * 4;
+                    const cpx<T>* v = vs + kl * 4 * RC + r;
+                    recv_terms<T, MODE>(f[0], f[1], f[2], f[3], v[0], v[RC], aJ[0], aM[0]);
+                    recv_terms<T, MODE>(cconj(f[0]), cnegconj(f[1]), cconj(f[2]), cnegconj(f[3]), v[2 * RC], v[3 * RC],
+                                        aJ[0], aM[0]);
+                }
+            }
+            continue;
+        }
 #pragma unroll
         for (int o = 0; o < OPT; ++o) {
             const int it = threadIdx.x + o * blockDim.x;
@@ -780,6 +798,32 @@ __global__ void __launch_bounds__(256) k_receive_tile(int N, int K, int nph, int
                                     aM[o]);
             }
         }
+    }
+    if (G > 1) {
+        // the groups' partial sums meet in the (now free) pattern stage: [G][no][2]
+        __syncthreads();
+        cpx<T>* red = fs;
+        const int g = threadIdx.x / no, it = threadIdx.x - g * no;
+        if (g < G) {
+            red[(g * no + it) * 2] = aJ[0];
+            red[(g * no + it) * 2 + 1] = aM[0];
+        }
+        __syncthreads();
+        if (threadIdx.x < no) {
+            cpx<T> sJ = czero<T>(), sM = czero<T>();
+            for (int gg = 0; gg < G; ++gg) {
+                sJ = cadd(sJ, red[(gg * no + threadIdx.x) * 2]);
+                sM = cadd(sM, red[(gg * no + threadIdx.x) * 2 + 1]);
+            }
+            const int n = threadIdx.x / rc, r = r0 + threadIdx.x % rc, m = n0 + n, u = perm[m];
+            if (MODE == 0) {
+                y[(int64_t)r * nun + u] = cadd(yt[((int64_t)m * 2 + 0) * R + r], cscale(sJ, -c));
+                y[(int64_t)r * nun + N + u] = cadd(yt[((int64_t)m * 2 + 1) * R + r], cscale(sM, c));
+            } else {
+                y[(int64_t)r * nun + u] = cadd(yt[(int64_t)m * R + r], cscale(sJ, -c));
+            }
+        }
+        return;
     }
 #pragma unroll
     for (int o = 0; o < OPT; ++o) {
@@ -998,7 +1042,107 @@ __global__ void __launch_bounds__(256) k_receive2(int N, int K, int nph, int R, 
     }
 }
 
+// ------------------------------------------------------------------ complex wavenumber (lossy medium)
+// The leaf patterns are stored for every direction ([N][K][2]): at complex k the receive
+// pattern R_m(khat) = int f_m exp(-jk khat.(r - c)) is not conj F_m, but it is F_m at the
+// antipode -khat (theta-hat the same there, phi-hat reversed): R = (F_theta, -F_phi)(-khat).
+// Aggregation: U_b(k) = sum_n ( -x_J,n F_n(k) + x_M,n khat x F_n(k) ), thread per (direction, entry).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_aggregate_full(int N, int K, int R, int nun, const int* __restrict__ perm,
+                                                        const int* __restrict__ leaf_start, const cpx<T>* __restrict__ F,
+                                                        const cpx<T>* __restrict__ x, cpx<T>* __restrict__ U) {
+    const int b = blockIdx.x;
+    const int E = 2 * R;
+    const int64_t idx = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)K * E) return;
+    const int kk = (int)(idx / E), e = (int)(idx % E);
+    const int c = e / R, r = e % R;
+    cpx<T> acc = czero<T>();
+    for (int n = leaf_start[b]; n < leaf_start[b + 1]; ++n) {
+        const cpx<T> Ft = F[((int64_t)n * K + kk) * 2], Fp = F[((int64_t)n * K + kk) * 2 + 1];
+        const int u = perm[n];
+        const cpx<T> xJ = x[(int64_t)r * nun + u];
+        if (MODE == 0) {
+            const cpx<T> xM = x[(int64_t)r * nun + N + u];
+            acc = c == 0 ? csub(acc, cadd(cmul(xJ, Ft), cmul(xM, Fp))) : cadd(acc, csub(cmul(xM, Ft), cmul(xJ, Fp)));
+        } else {
+            acc = csub(acc, cmul(xJ, c == 0 ? Ft : Fp));
+        }
+    }
+    U[((int64_t)b * K) * E + idx] = acc;
+}
+
+// Receive: y_J = yt_J - cc sum_k [ R.V - RX.(khat x V) ],  y_M = yt_M + cc sum_k [ -R.(khat x V) - RX.V ]
+// with the complex constant cc = k^2 / (32 pi^2); one warp per (tree RWG m, RHS r).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_receive_full(int N, int K, int nph, int R, int nun, const int* __restrict__ perm,
+                                                      const int* __restrict__ leaf_of, const cpx<T>* __restrict__ F,
+                                                      const cpx<T>* __restrict__ RX, const cpx<T>* __restrict__ V,
+                                                      cpx<T> cc, const cpx<T>* __restrict__ yt, cpx<T>* __restrict__ y) {
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= N * R) return;
+    const int m = warp / R, r = warp % R;
+    const int b = leaf_of[m];
+    const int E = 2 * R;
+    cpx<T> sJ = czero<T>(), sM = czero<T>();
+    for (int kk = lane; kk < K; kk += 32) {
+        const int ka = antipode(kk, K, nph);
+        const cpx<T> Rt = F[((int64_t)m * K + ka) * 2];
+        const cpx<T> Fa = F[((int64_t)m * K + ka) * 2 + 1];
+        const cpx<T> Rp = {-Fa.x, -Fa.y};
+        const cpx<T> Xt = RX[((int64_t)m * K + kk) * 2], Xp = RX[((int64_t)m * K + kk) * 2 + 1];
+        const cpx<T> Vt = V[((int64_t)b * K + kk) * E + r], Vp = V[((int64_t)b * K + kk) * E + R + r];
+        sJ = cadd(sJ, cadd(csub(cadd(cmul(Rt, Vt), cmul(Rp, Vp)), cmul(Xp, Vt)), cmul(Xt, Vp)));
+        if (MODE == 0) sM = cadd(sM, csub(csub(cmul(Rt, Vp), cmul(Rp, Vt)), cadd(cmul(Xt, Vt), cmul(Xp, Vp))));
+    }
+    sJ = warp_sum(sJ);
+    if (MODE == 0) sM = warp_sum(sM);
+    if (lane == 0) {
+        const int u = perm[m];
+        const cpx<T> nc = {-cc.x, -cc.y};
+        if (MODE == 0) {
+            y[(int64_t)r * nun + u] = cadd(yt[((int64_t)m * 2 + 0) * R + r], cmul(nc, sJ));
+            y[(int64_t)r * nun + N + u] = cadd(yt[((int64_t)m * 2 + 1) * R + r], cmul(cc, sM));
+        } else {
+            y[(int64_t)r * nun + u] = cadd(yt[(int64_t)m * R + r], cmul(nc, sJ));
+        }
+    }
+}
+
 inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) / th); }
+
+// complex wavenumber: aggregation and receive on the full pattern layout (any R)
+template <typename T>
+void launch_aggregate_full(bi_handle_s* h, const cpx<T>* x, int R, cudaStream_t s) {
+    level_t& L = h->lev[h->leaf];
+    dim3 g(L.nbox, nblk((int64_t)L.K * 2 * R, 256));
+    if (h->prm.op_mode == 0)
+        k_aggregate_full<T, 0><<<g, 256, 0, s>>>(h->N, L.K, R, h->nun, h->d_perm, h->d_leaf_start, (const cpx<T>*)h->d_F, x,
+                                                 (cpx<T>*)L.d_U);
+    else
+        k_aggregate_full<T, 1><<<g, 256, 0, s>>>(h->N, L.K, R, h->nun, h->d_perm, h->d_leaf_start, (const cpx<T>*)h->d_F, x,
+                                                 (cpx<T>*)L.d_U);
+    CU(cudaGetLastError());
+}
+template <typename T>
+void launch_receive_full(bi_handle_s* h, cpx<T>* y, int R, cudaStream_t s) {
+    level_t& L = h->lev[h->leaf];
+    const double pi = 3.14159265358979323846;
+    // k^2 / (32 pi^2) at complex k
+    const double kr = h->k, ki = h->ki;
+    const cpx<T> cc = {(T)((kr * kr - ki * ki) / (32.0 * pi * pi)), (T)(2.0 * kr * ki / (32.0 * pi * pi))};
+    const int64_t nthreads = (int64_t)h->N * R * 32;
+    if (h->prm.op_mode == 0)
+        k_receive_full<T, 0><<<nblk(nthreads, 256), 256, 0, s>>>(h->N, L.K, L.nph, R, h->nun, h->d_perm, h->d_leaf_of,
+                                                                 (const cpx<T>*)h->d_F, (const cpx<T>*)h->d_RX,
+                                                                 (const cpx<T>*)L.d_V, cc, (const cpx<T>*)h->d_yt, y);
+    else
+        k_receive_full<T, 1><<<nblk(nthreads, 256), 256, 0, s>>>(h->N, L.K, L.nph, R, h->nun, h->d_perm, h->d_leaf_of,
+                                                                 (const cpx<T>*)h->d_F, (const cpx<T>*)h->d_RX,
+                                                                 (const cpx<T>*)L.d_V, cc, (const cpx<T>*)h->d_yt, y);
+    CU(cudaGetLastError());
+}
 
 template <typename T>
 void launch_interp_two_pass(bi_handle_s* h, int l, int E, cudaStream_t s) {
@@ -1113,7 +1257,7 @@ void launch_all(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s,
             interp_t& I = h->itp[l];
             dim3 g1(Cc.nbox, nblk((int64_t)P.nth * Cc.nph * E, th));
             k_anterp_phi<T><<<g1, th, 0, s>>>(P.nth, P.nph, Cc.nph, E, I.d_tph_ptr, I.d_tph_dst, (const T*)I.d_tph_w,
-                                              Cc.d_parent, Cc.d_octant, (const C*)P.d_shift, (const C*)P.d_V, (C*)I.d_tmp);
+                                              Cc.d_parent, Cc.d_octant, (const C*)P.d_shift_dn, (const C*)P.d_V, (C*)I.d_tmp);
             CU(cudaGetLastError());
             dim3 g2(Cc.nbox, nblk((int64_t)Cc.K * E, th));
             k_anterp_theta<T><<<g2, th, 0, s>>>(P.nth, Cc.nth, Cc.nph, E, I.d_tth_ptr, I.d_tth_dst, I.d_tth_flip,
@@ -1250,7 +1394,7 @@ bool anterp_child(bi_handle_s* h, int l, int E, cudaStream_t s) {
     k_anterp_child<T><<<C.nbox, 256, smem, s>>>(C.nth, C.nph, P.nth, P.nph, E, (int)I.tph_dst.size(), (int)I.tth_dst.size(),
                                                 I.d_tph_ptr, I.d_tph_dst, (const T*)I.d_tph_w, I.d_tth_ptr, I.d_tth_dst,
                                                 I.d_tth_flip, (const T*)I.d_tth_w, C.d_parent, C.d_octant,
-                                                (const cpx<T>*)P.d_shift, (const cpx<T>*)P.d_V, (cpx<T>*)C.d_V);
+                                                (const cpx<T>*)P.d_shift_dn, (const cpx<T>*)P.d_V, (cpx<T>*)C.d_V);
     CU(cudaGetLastError());
     return true;
 }
@@ -1322,7 +1466,9 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
         return;
     }
     const int lf = h->leaf;
-    if (R < 8 && bi_leaf_aggregate_bulk(h, x, R, s)) {
+    if (h->ki != 0.0) {
+        launch_aggregate_full<T>(h, x, R, s);
+    } else if (R < 8 && bi_leaf_aggregate_bulk(h, x, R, s)) {
     } else if (R >= 8) {
         level_t& L = h->lev[lf];
         dim3 g(L.nbox, nblk(L.K / 2, 32));
@@ -1391,7 +1537,7 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
         interp_t& I = h->itp[l];
         dim3 g1(Cc.nbox, nblk((int64_t)P.nth * Cc.nph * E, th));
         k_anterp_phi<T><<<g1, th, 0, s>>>(P.nth, P.nph, Cc.nph, E, I.d_tph_ptr, I.d_tph_dst, (const T*)I.d_tph_w,
-                                          Cc.d_parent, Cc.d_octant, (const C*)P.d_shift, (const C*)P.d_V, (C*)I.d_tmp);
+                                          Cc.d_parent, Cc.d_octant, (const C*)P.d_shift_dn, (const C*)P.d_V, (C*)I.d_tmp);
         CU(cudaGetLastError());
         dim3 g2(Cc.nbox, nblk((int64_t)Cc.K * E, th));
         k_anterp_theta<T><<<g2, th, 0, s>>>(P.nth, Cc.nth, Cc.nph, E, I.d_tth_ptr, I.d_tth_dst, I.d_tth_flip,
@@ -1400,7 +1546,9 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
     }
     if (ev) CU(cudaEventRecord(ev[5], s));
     else CU(cudaStreamWaitEvent(s, h->ev_join, 0));
-    if (R >= 8 && launch_receive_tile<T>(h, x, y, R, s)) {
+    if (h->ki != 0.0) {
+        launch_receive_full<T>(h, y, R, s);
+    } else if (R >= 8 && launch_receive_tile<T>(h, x, y, R, s)) {
     } else if (R < 8 && bi_leaf_receive_bulk(h, y, R, s)) {
     } else {
         level_t& L = h->lev[lf];

@@ -333,6 +333,27 @@ def test_fused_kernels_match_two_pass_kernels(bi, mode, nrhs, monkeypatch):
     assert rel(ys[0], ys[1]) < 1e-12
 
 
+@pytest.mark.parametrize("mode,nrhs", [(0, 3), (1, 8), (0, 16)])
+def test_row_blocked_anterpolation_matches_two_pass_kernels(bi, mode, nrhs, monkeypatch):
+    """The row-blocked anterpolation (transposed theta step first, on the parent's columns; the
+    kernel of coarse levels whose shifted parent field does not fit one CTA), forced on every
+    level, against the two-pass reference kernels in FP64."""
+    v, t = icosphere(16, 1.0)
+    x = None
+    ys = []
+    for env in ({"BI_ANTERP_ROWS": "1"}, {"BI_TWO_PASS": "1"}):
+        for k2, v2 in env.items():
+            monkeypatch.setenv(k2, v2)
+        op = bi.Operator(v, t, K0, precision="fp64", op_mode=mode, max_rhs=nrhs)
+        if x is None:
+            x = complex_gaussian(op.n_unknowns, nrhs, seed=SEED_BASE + 15)
+        ys.append(op.matvec(torch.from_numpy(x).cuda()).cpu().numpy())
+        op.close()
+        for k2 in env:
+            monkeypatch.delenv(k2)
+    assert rel(ys[0], ys[1]) < 1e-12
+
+
 @pytest.mark.parametrize("precision,mode,nrhs", [("fp64", 0, 1), ("fp32", 0, 1), ("fp32", 0, 4), ("fp32", 1, 3),
                                                   ("fp64", 1, 7)])
 def test_bulk_leaf_kernels_match_plain_kernels(bi, precision, mode, nrhs, monkeypatch):
