@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--secondary", type=int, default=1, help="run the 61,440-unknown one-RHS section (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=64, help="RHS of the batched monostatic-sweep section (0: skip)")
+    ap.add_argument("--sweep", type=int, default=1, help="solve the 180-incidence sweep end to end (0: skip)")
     ap.add_argument("--serving", type=int, default=32, help="requests of the serving section (0: skip)")
     ap.add_argument("--serving-max-unknowns", type=int, default=40000)
     ap.add_argument("--serving-max-rhs", type=int, default=8)
@@ -184,13 +185,15 @@ def stage_roofline(info, nrhs, stages, hbm_gbs):
     return out
 
 
-def launches_per_step(info):
-    """Kernels of one product on this path: near (side stream), aggregation, one interpolation and one anterpolation per level pair, one translation per
-    level, receive."""
+def launches_per_step(info, nrhs=1):
+    """Kernels of one product on this path: near (side stream; with several right-hand sides
+    preceded by the gather of x into tree order), aggregation, one interpolation and one
+    anterpolation per level pair, one translation per level, receive."""
     lf = info["leaf_level"]
+    gather = 1 if nrhs > 1 else 0
     if lf < 2:
-        return 2
-    return 1 + 1 + (lf - 2) + (lf - 1) + (lf - 2) + 1
+        return 2 + gather
+    return 1 + 1 + (lf - 2) + (lf - 1) + (lf - 2) + 1 + gather
 
 
 def measured_traffic(name="dram_matvec_sphere_r2_61440.md"):
@@ -341,14 +344,58 @@ def run_batched(args):
     rows = sample_rows(op.n_unknowns, 64, seed=SEED_BASE + 12)
     _, _, err = oracle_rows_rate(v, t, rows, xb, yv)
     hbm, _ = peaks()
+    tuned = op.tuned_config()
     out = {"workload": "cube 5 lambda + cylinder, %d RWG (%d unknowns), %d levels, FP32" %
                        (info["n_rwg"], info["n_unknowns"], info["levels"]),
            "nrhs": R, "ms_per_product": ms, "value": info["n_unknowns"] * R / (ms * 1e-3), "unit": UNIT,
            "one_rhs_value": info["n_unknowns"] / (ms1 * 1e-3), "setup_ms": info["setup_ms"],
            "rel_err_vs_oracle": err, "oracle_rows": len(rows),
-           "stage_ms": stages, "stage_roofline": stage_roofline(info, R, stages, hbm)}
+           "stage_ms": stages, "stage_roofline": stage_roofline(info, R, stages, hbm),
+           "tuned_config": tuned.strip().splitlines()}
     op.close()
+    if args.sweep:
+        out["sweep"] = run_sweep(v, t, R)
     return out
+
+
+def run_sweep(v, t, R, n_inc=180, tol=1e-3):
+    """The monostatic sweep end to end: 180 plane waves over phi (2-degree steps, theta = 90 deg,
+    polarisation z), right-hand sides, GMRES solves and monostatic far fields on the GPU, in
+    batches of R columns (64 + 64 + 52), against the same sweep one incidence at a time."""
+    import torch
+    from paper_2210_04892_gb300 import bi
+
+    def sweep(op, batch, count=n_inc):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, sig = [], []
+        for i0 in range(0, count, batch):
+            ph = np.deg2rad(2.0 * np.arange(i0, min(count, i0 + batch)))
+            kh = -np.stack([np.cos(ph), np.sin(ph), 0 * ph], 1)
+            pp = np.tile([0.0, 0.0, 1.0], (len(ph), 1))
+            b = op.rhs_planewave(kh, pp)
+            x, it, rel = op.solve(b, tol=tol)
+            F = op.farfield(x, -kh)                       # back-scatter directions of the batch
+            diag = F[torch.arange(len(ph)), torch.arange(len(ph))]
+            sig.append((4 * np.pi * (diag.abs() ** 2).sum(-1)).cpu().numpy())
+            its.extend(int(i) for i in it)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        return dt, its, np.concatenate(sig)
+
+    ops = {}
+    for batch in (R, 1):
+        ops[batch] = bi.Operator(v, t, K0, digits=3, precision="fp32", op_mode=0, max_rhs=batch, gmres_restart=30,
+                                 gmres_maxit=300)
+        sweep(ops[batch], batch, count=batch)  # warm-up: graph capture and autotuning
+    dt_b, its_b, sig_b = sweep(ops[R], R)
+    dt_1, its_1, sig_1 = sweep(ops[1], 1)
+    for op in ops.values():
+        op.close()
+    return {"incidences": n_inc, "batch": R, "tol": tol, "seconds": dt_b, "gmres_iterations_mean": float(np.mean(its_b)),
+            "one_at_a_time_seconds": dt_1, "one_at_a_time_iterations_mean": float(np.mean(its_1)),
+            "monostatic_rcs_max_diff_db": float(np.max(np.abs(10 * np.log10(sig_b / sig_1)))),
+            "form": "RHS + GMRES + monostatic far field per batch, FP32 products"}
 
 
 # ---------------------------------------------------------------------------- serving stream
@@ -527,7 +574,7 @@ def run_gpu(args):
                       "l2": "inputs larger than L2 (near blocks + leaf patterns %.1f GB per step)" %
                             ((sr["near"]["bytes"] + sr["receive"]["bytes"]) / 1e9)},
            "roofline": roofline, "e2e": e2e, "clocks": clocks, "setup_ms": info["setup_ms"],
-           "gpu_launches": launches_per_step(info) * args.steps}
+           "gpu_launches": launches_per_step(info, R) * args.steps}
     out["rel_err_vs_oracle"] = golden_error(y_np)
     out["oracle_rows"] = "256 stored rows x 8 columns (tests/golden/c5_rows.json)"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -54,13 +54,34 @@ typedef enum {
 
 typedef enum { BI_PREC_FP64 = 0, BI_PREC_FP32 = 1 } bi_precision;
 
-/* op_mode 0: the C block of Eq. 42 (2N unknowns):
+/* op_mode 2: a homogeneous penetrable body of relative permittivity eps_r = eps_re + j eps_im
+ * (mu_r = 1) in free space, by the surface-only two-region (PMCHWT) equations -- tangential E
+ * and H continuous across the surface (the check the paper's Mie comparisons of Sec. III.A need
+ * without the HDG interior):
+ *     [ L0 + eta L1        -(K0 + K1)     ] [J]      L_i = <f_m, L f_n>, K_i = <f_m, Kbar f_n>
+ *     [ K0 + K1        L0 + L1 / eta      ] [M]      in medium i (k1 = k0 sqrt(eps_r), eta = 1/sqrt(eps_r)),
+ *   2N unknowns (J then M: the exterior equivalent currents).  Each medium gets its own
+ *   octree, sampling and near field; the two products are summed.  Right-hand sides of
+ *   bi_rhs_planewave are [-<f, E_inc>; -<f, H_inc>]; bi_farfield radiates J, M into free space.
+ *   precond must be 0 and k_im 0; bi_set_coupling is not available.
+ * op_mode 0: the C block of Eq. 42 (2N unknowns):
  *     [ G - P     X/2 - Q ] [J]      G = <f_m, f_n>, X = <f_m, n x f_n>,
  *     [   Q       G/2 - P ] [M]      P = <f_m, C f_n>, Q = <f_m, n x C f_n>,
  *   with C = 1/2 pi_tau L + 1/2 pi_x Kbar (Eq. 27, alpha = 1/2).
  * op_mode 1: PEC combined-field equation (Eqs. 24a/24b with M = 0, alpha = 1/2):
  *     G/4 - P  (N unknowns). */
-typedef enum { BI_MODE_CBLOCK = 0, BI_MODE_PEC = 1 } bi_op_mode;
+/* op_mode 4: a PEC core under a coat of relative permittivity eps_r (the coated sphere of
+ *   Sec. III.A, without the HDG interior): the mesh holds two closed surfaces, the coat's outer
+ *   surface S1 (the first nt - core_tris triangles) and the core S2 (the last core_tris), every
+ *   vertex of S1 numbered before every vertex of S2 (so the RWG functions of S1 come first).
+ *   Unknowns [J1, M1, J2] (2 N1 + N2): the exterior currents on S1 and J2 = n2 x H on the core
+ *   (n2 out of the core).  Rows: tangential E and H matched on S1, tangential E = 0 on S2:
+ *     [ L0 + eta L1_11      -(K0 + K1_11)       -eta L1_12 ]
+ *     [ K0 + K1_11         L0 + L1_11 / eta     -K1_12     ]
+ *     [ -eta L1_21          K1_21               eta L1_22  ]
+ *   with the free-space operators on S1 and the coat's on both surfaces.  Right-hand sides and
+ *   far fields as for op_mode 2 (zero on the core's rows). */
+typedef enum { BI_MODE_CBLOCK = 0, BI_MODE_PEC = 1, BI_MODE_TWO_REGION = 2, BI_MODE_COATED_PEC = 4 } bi_op_mode;
 
 typedef struct {
     int digits;             /* MLFMA accuracy digits d0 in the excess-bandwidth rule (default 3) */
@@ -86,6 +107,8 @@ typedef struct {
                                Hankel functions of complex argument, and the near field is integrated
                                in FP64 throughout.  bi_rhs_planewave, bi_farfield(_noalloc) and the
                                server take free-space handles only (BI_ERR_ARG otherwise). */
+    double eps_re, eps_im;  /* op_mode 2, 4: relative permittivity of the body or coat (default 1, 0); eps_im <= 0 */
+    int core_tris;          /* op_mode 4: triangles of the PEC core (the last ones of the mesh) */
 } bi_params;
 
 typedef struct {
@@ -297,6 +320,14 @@ void bi_plan_destroy(bi_plan p);
 
 /* Text of the last error on h (or, when h is NULL, of the calling thread's last failed bi_setup). */
 const char* bi_last_error(bi_handle h);
+
+/* Diagnostics (no counterpart in the paper): the kernel forms the autotuner chose for the level
+ * passes, one line per (pass, level, E): the first product with a given nrhs (bi_matvec,
+ * bi_solve, bi_profile_stages) times every applicable form of each translation, interpolation
+ * and anterpolation on the handle's buffers, synchronising the stream, and keeps the fastest
+ * (environment BI_AUTOTUNE=0 keeps the built-in choices).  buf: host, len bytes, NUL-terminated;
+ * BI_ERR_ARG when the text was cut. */
+int bi_tuned_config(bi_handle h, char* buf, int64_t len);
 
 /* Diagnostics (no counterpart in the paper): limit, in SM clock cycles, of the consumer waits of
  * the bulk-copy leaf kernels (aggregation and receive of one and few right-hand sides); cycles <= 0

@@ -27,7 +27,7 @@ _NAMES = {0: "BI_OK", -1: "BI_ERR_ARG", -2: "BI_ERR_MESH", -3: "BI_ERR_OOM", -4:
 
 # entry points declared in include/bi.h
 EXPORTS = ["bi_default_params", "bi_setup", "bi_num_unknowns", "bi_rwg_edges", "bi_get_info", "bi_matvec",
-           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_debug_set_wait_limit", "bi_profile_stages", "bi_stage_name", "bi_last_error", "bi_device_status", "bi_set_coupling", "bi_matvec_coupled", "bi_plan_create", "bi_plan_info", "bi_plan_get",
+           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_debug_set_wait_limit", "bi_tuned_config", "bi_profile_stages", "bi_stage_name", "bi_last_error", "bi_device_status", "bi_set_coupling", "bi_matvec_coupled", "bi_plan_create", "bi_plan_info", "bi_plan_get",
            "bi_plan_last_error", "bi_plan_destroy",
            "bi_destroy", "bi_server_default_params", "bi_server_create", "bi_submit", "bi_poll", "bi_result",
            "bi_release", "bi_server_last_error", "bi_server_destroy"]
@@ -55,7 +55,8 @@ class Params(ctypes.Structure):
     _fields_ = [("digits", ctypes.c_int), ("leaf_box", ctypes.c_double), ("levels", ctypes.c_int),
                 ("interp_order", ctypes.c_int), ("precision", ctypes.c_int), ("op_mode", ctypes.c_int),
                 ("max_rhs", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("precond", ctypes.c_int), ("k_im", ctypes.c_double)]
+                ("stream", ctypes.c_void_p), ("precond", ctypes.c_int), ("k_im", ctypes.c_double),
+                ("eps_re", ctypes.c_double), ("eps_im", ctypes.c_double), ("core_tris", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH):
     L.bi_farfield_noalloc.argtypes = [vp, vp, i, vp, i, vp]
     L.bi_debug_copy.argtypes = [vp, i, i, vp, i64]
     L.bi_debug_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+    L.bi_tuned_config.argtypes = [vp, ctypes.c_char_p, i64]
     L.bi_profile_stages.argtypes = [vp, vp, vp, i, i, vp]
     L.bi_stage_name.argtypes = [i]
     L.bi_stage_name.restype = ctypes.c_char_p
@@ -145,10 +147,13 @@ class Operator:
 
     op_mode 0: C block (2N unknowns, J then M); op_mode 1: PEC combined field (N).
     precision "fp32" (complex64 vectors) or "fp64" (complex128).  k0 may be complex
-    (k0.real > 0 >= k0.imag: a lossy medium); its imaginary part goes to bi_params.k_im."""
+    (k0.real > 0 >= k0.imag: a lossy medium); its imaginary part goes to bi_params.k_im.
+    op_mode 2: a homogeneous body of relative permittivity eps_r (two-region equations);
+    op_mode 4: a PEC core (the last core_tris triangles) under a coat of permittivity eps_r."""
 
     def __init__(self, verts, tris, k0, digits=3, precision="fp32", op_mode=0, leaf_box=0.25, levels=0,
-                 interp_order=10, max_rhs=1, gmres_restart=100, gmres_maxit=1000, stream=None, precond=0):
+                 interp_order=10, max_rhs=1, gmres_restart=100, gmres_maxit=1000, stream=None, precond=0,
+                 eps_r=1.0, core_tris=0):
         import torch
         L = load()
         p = default_params()
@@ -164,6 +169,9 @@ class Operator:
         p.precond = int(precond)
         k0 = complex(k0)
         p.k_im = k0.imag
+        eps_r = complex(eps_r)
+        p.eps_re, p.eps_im = eps_r.real, eps_r.imag
+        p.core_tris = int(core_tris)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -315,6 +323,12 @@ class Operator:
     def status(self):
         """Synchronise and raise BIError if a product kernel gave up a bounded device wait."""
         _check(load().bi_device_status(self.h), self.h)
+
+    def tuned_config(self):
+        """Kernel forms chosen by the autotuner (one line per pass, level and E)."""
+        buf = ctypes.create_string_buffer(1 << 16)
+        _check(load().bi_tuned_config(self.h, buf, len(buf)), self.h)
+        return buf.value.decode()
 
     def set_wait_limit(self, cycles):
         """Diagnostics: limit of the bulk-copy waits in SM cycles (<= 0: the default)."""

@@ -1,4 +1,5 @@
 // C-ABI entry points (include/bi.h): argument checks, handle lifecycle, error text.
+#include <complex>
 #include <map>
 #include <mutex>
 #include <chrono>
@@ -49,6 +50,7 @@ extern "C" void bi_default_params(bi_params* p) {
     p->gmres_restart = 100;
     p->gmres_maxit = 1000;
     p->stream = nullptr;
+    p->eps_re = 1.0;
 }
 
 static void release(bi_handle_s* h) {
@@ -71,15 +73,24 @@ static void release(bi_handle_s* h) {
 
 bool bi_params_valid(const bi_params& P) {
     return P.digits >= 1 && P.digits <= 8 && P.leaf_box > 0 && P.interp_order >= 2 && P.interp_order <= 32 &&
-           (P.precision == 0 || P.precision == 1) && (P.op_mode == 0 || P.op_mode == 1) && P.max_rhs >= 1 &&
+           (P.precision == 0 || P.precision == 1) && P.op_mode >= 0 && P.op_mode <= 4 && P.max_rhs >= 1 &&
            P.max_rhs <= 4096 && P.gmres_restart >= 1 && P.gmres_maxit >= 1 && P.levels >= 0 && P.levels <= 21 &&
            (P.precond == 0 || P.precond == 1) && P.k_im <= 0.0;
 }
 
-extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, double k0, int digits, const bi_params* opt,
-                        bi_handle* out) {
+static int setup_two_region(const double* verts, int nv, const int* tris, int nt, double k0, const bi_params& P,
+                            bi_handle* out);
+
+// One operator.  op_mode 3 (one medium of the two-region form) is built only by the two-region
+// set-up (internal = true).
+static int setup_handle(const double* verts, int nv, const int* tris, int nt, double k0, int digits, const bi_params* opt,
+                        bi_handle* out, bool internal) {
     if (!out) return BI_ERR_ARG;
     *out = nullptr;
+    if (opt && opt->op_mode == 3 && !internal) {
+        g_setup_error = "bi_setup: op_mode must be 0, 1 or 2";
+        return BI_ERR_ARG;
+    }
     if (!verts || !tris || nv < 3 || nt < 4 || !(k0 > 0)) {
         g_setup_error = "bi_setup: null mesh, fewer than 4 triangles, or k0 <= 0";
         return BI_ERR_ARG;
@@ -95,6 +106,11 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
         delete h;
         return BI_ERR_ARG;
     }
+    if (P.op_mode == 2 || P.op_mode == 4) {
+        const bi_params P2 = P;
+        delete h;
+        return setup_two_region(verts, nv, tris, nt, k0, P2, out);
+    }
     if (P.k_im < -k0) {
         g_setup_error = "bi_setup: k_im outside [-k0, 0]";
         delete h;
@@ -104,7 +120,8 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
     h->ki = P.k_im;
     h->prec = P.precision;
     h->csize = P.precision == 0 ? 16 : 8;
-    h->nX = P.op_mode == 0 ? 2 : 1;
+    h->nX = (P.op_mode == 0 || P.op_mode == 3) ? 2 : 1;
+    h->nF = P.op_mode == 3 ? 2 : 1;
     h->max_rhs = P.max_rhs;
     h->stream = (cudaStream_t)P.stream;
     const char* env = std::getenv("BI_NO_GRAPHS");
@@ -115,6 +132,8 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
     h->use_leaf_bulk = !(env3 && env3[0] == '0');
     const char* env4 = std::getenv("BI_ANTERP_ROWS");
     h->force_anterp_rows = env4 && env4[0] == '1';
+    const char* env5 = std::getenv("BI_AUTOTUNE");
+    h->autotune = !(env5 && env5[0] == '0') && !h->force_anterp_rows;
     try {
         bi_build_rwg(h, verts, nv, tris, nt);
         h->nun = h->nX * h->N;
@@ -177,6 +196,131 @@ extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, do
     return BI_OK;
 }
 
+extern "C" int bi_setup(const double* verts, int nv, const int* tris, int nt, double k0, int digits, const bi_params* opt,
+                        bi_handle* out) {
+    return setup_handle(verts, nv, tris, nt, k0, digits, opt, out, false);
+}
+
+// The two-region operator: one op_mode-3 handle per medium, the exterior at k0 (a = b = 1) and
+// the body at k1 = k0 sqrt(eps_r) (a = eta, b = 1/eta, eta = 1/sqrt(eps_r)); products summed.
+static int setup_two_region(const double* verts, int nv, const int* tris, int nt, double k0, const bi_params& P,
+                            bi_handle* out) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (P.precond != 0 || P.k_im != 0.0 || !(P.eps_im <= 0.0) || !(P.eps_re * P.eps_re + P.eps_im * P.eps_im > 0.0)) {
+        g_setup_error = "bi_setup: two-region needs precond 0, k_im 0, eps_im <= 0 and eps_r != 0";
+        return BI_ERR_ARG;
+    }
+    std::complex<double> n = std::sqrt(std::complex<double>(P.eps_re, P.eps_im));
+    if (n.real() < 0) n = -n;
+    const std::complex<double> k1 = k0 * n, eta = 1.0 / n;
+    if (!(k1.real() > 0) || -k1.imag() > k1.real()) {
+        g_setup_error = "bi_setup: the body's wavenumber k0 sqrt(eps_r) has |Im k| > Re k";
+        return BI_ERR_ARG;
+    }
+    const bool coated = P.op_mode == 4;
+    int nt_outer = nt;
+    if (coated) {
+        // the core: the last core_tris triangles; every vertex of the outer surface numbered first
+        if (P.core_tris < 4 || P.core_tris > nt - 4) {
+            g_setup_error = "bi_setup: coated body needs 4 <= core_tris <= nt - 4";
+            return BI_ERR_ARG;
+        }
+        nt_outer = nt - P.core_tris;
+        int max_outer = -1, min_core = nv;
+        for (int t = 0; t < nt; ++t)
+            for (int a = 0; a < 3; ++a) {
+                const int v = tris[3 * t + a];
+                if (t < nt_outer) max_outer = std::max(max_outer, v);
+                else min_core = std::min(min_core, v);
+            }
+        if (max_outer >= min_core) {
+            g_setup_error = "bi_setup: coated body: number the outer surface's vertices before the core's";
+            return BI_ERR_MESH;
+        }
+    }
+    bi_params P0 = P, P1 = P;
+    P0.op_mode = P1.op_mode = 3;
+    P0.k_im = 0.0;
+    P1.k_im = k1.imag();
+    bi_handle c0 = nullptr, c1 = nullptr;
+    int rc = setup_handle(verts, nv, tris, nt_outer, k0, 0, &P0, &c0, true);
+    if (rc != BI_OK) return rc;
+    rc = setup_handle(verts, nv, tris, nt, k1.real(), 0, &P1, &c1, true);
+    if (rc != BI_OK) {
+        bi_destroy(c0);
+        return rc;
+    }
+    if (coated) {
+        // the coat's RWG functions: those of the outer surface first, numbered as the outer medium's
+        bool same = c1->N > c0->N;
+        for (int i = 0; same && i < 2 * c0->N; ++i) same = c0->edges[i] == c1->edges[i];
+        if (!same) {
+            g_setup_error = "bi_setup: coated body: the outer surface's RWG functions do not come first";
+            bi_destroy(c0);
+            bi_destroy(c1);
+            return BI_ERR_MESH;
+        }
+    }
+    c1->pa[0] = eta.real();
+    c1->pa[1] = eta.imag();
+    c1->pb[0] = n.real();
+    c1->pb[1] = n.imag();
+    bi_handle_s* h = new bi_handle_s();
+    h->prm = P;
+    h->k = k0;
+    h->prec = P.precision;
+    h->csize = P.precision == 0 ? 16 : 8;
+    h->N = c0->N;
+    h->nun = c0->nun;
+    h->nX = 2;
+    h->nF = 2;
+    h->max_rhs = P.max_rhs;
+    h->stream = (cudaStream_t)P.stream;
+    h->device = c0->device;
+    h->med[0] = c0;
+    h->med[1] = c1;
+    h->edges = c0->edges;
+    if (coated) {
+        h->coated = 1;
+        h->N1 = c0->N;
+        h->N2 = c1->N - c0->N;
+        h->N = c1->N;
+        h->nun = 2 * h->N1 + h->N2;
+        h->edges = c1->edges;
+    }
+    try {
+        h->d_status = (int*)h->alloc(sizeof(int));
+        CU(cudaMemset(h->d_status, 0, sizeof(int)));
+        const size_t vec = (size_t)h->nun * h->max_rhs * h->csize;
+        h->d_sx = h->alloc(vec);
+        h->d_sy = h->alloc(vec);
+        h->d_ysum = h->alloc(vec);
+        if (coated) {
+            const size_t v0 = (size_t)c0->nun * h->max_rhs * h->csize, v1 = (size_t)c1->nun * h->max_rhs * h->csize;
+            h->d_xin0 = h->alloc(v0);
+            h->d_y0 = h->alloc(v0);
+            h->d_xin1 = h->alloc(v1);
+            h->d_y1 = h->alloc(v1);
+        }
+    } catch (const bi_error& e) {
+        g_setup_error = e.msg;
+        release(h);
+        delete h;
+        bi_destroy(c0);
+        bi_destroy(c1);
+        return e.code;
+    }
+    h->info = c0->info;
+    h->info.n_rwg = h->N;
+    h->info.n_unknowns = h->nun;
+    int64_t own = 0;
+    for (const dbuf& b : h->owned) own += (int64_t)b.bytes;
+    h->info.device_bytes = c0->info.device_bytes + c1->info.device_bytes + own;
+    h->info.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return BI_OK;
+}
+
 extern "C" int bi_num_unknowns(bi_handle h, int64_t* n_rwg, int64_t* n_unknowns) {
     if (!h) return BI_ERR_ARG;
     if (n_rwg) *n_rwg = h->N;
@@ -212,6 +356,11 @@ static int guarded(bi_handle h, F&& f) {
 
 // Read and clear the device status word (the caller has synchronised the work it checks).
 int bi_take_device_status(bi_handle_s* h) {
+    for (bi_handle_s* m : h->med)
+        if (m && bi_take_device_status(m) != BI_OK) {
+            h->err = m->err;
+            return BI_ERR_TIMEOUT;
+        }
     if (!h->d_status) return BI_OK;
     int st = 0;
     CU(cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -252,6 +401,10 @@ extern "C" int bi_set_coupling(bi_handle h, int64_t n_int, const int* dlx_ptr, c
                                const int* dxl_ptr, const int* dxl_col, const void* dxl_val, bi_qsolve_fn qsolve,
                                void* user) {
     if (!h) return BI_ERR_ARG;
+    if (h->med[0]) {
+        h->err = "bi_set_coupling: not available for the two-region operator";
+        return BI_ERR_ARG;
+    }
     if (qsolve && (n_int < 1 || !dlx_ptr || !dlx_col || !dlx_val || !dxl_ptr || !dxl_col || !dxl_val)) {
         h->err = "bi_set_coupling: n_int < 1 or a null CSR array";
         return BI_ERR_ARG;
@@ -304,8 +457,19 @@ extern "C" int bi_rhs_planewave(bi_handle h, const double* khat, const double* p
         h->err = "bi_rhs_planewave: null argument or nrhs < 1";
         return BI_ERR_ARG;
     }
+    if (nrhs > h->max_rhs && h->coated) {
+        h->err = "bi_rhs_planewave: nrhs above max_rhs (coated body)";
+        return BI_ERR_ARG;
+    }
     return guarded(h, [&] {
-        bi_rhs_launch(h, khat, phat, nrhs, b);
+        if (h->coated) {
+            // the outer surface's [-<f, E>; -<f, H>], zero on the core's rows
+            bi_rhs_launch(h->med[0], khat, phat, nrhs, h->d_y0);
+            bi_coated_rhs(h, b, nrhs, h->stream);
+            CU(cudaStreamSynchronize(h->stream));
+            return (int)BI_OK;
+        }
+        bi_rhs_launch(h->med[0] ? h->med[0] : h, khat, phat, nrhs, b);
         return (int)BI_OK;
     });
 }
@@ -323,6 +487,10 @@ extern "C" const char* bi_last_error(bi_handle h) { return h ? h->err.c_str() : 
 
 extern "C" void bi_destroy(bi_handle h) {
     if (!h) return;
+    for (bi_handle_s*& m : h->med) {
+        bi_destroy(m);
+        m = nullptr;
+    }
     cudaStreamSynchronize(h->stream);
     release(h);
     delete h;
@@ -330,6 +498,7 @@ extern "C" void bi_destroy(bi_handle h) {
 
 extern "C" int bi_debug_copy(bi_handle h, int what, int level, void* host, int64_t bytes) {
     if (!h || !host || bytes < 0) return BI_ERR_ARG;
+    if (h->med[0]) return bi_debug_copy(h->med[0], what, level, host, bytes);   // two-region: the exterior medium
     const void* src = nullptr;
     size_t need = 0;
     const bool far = h->leaf >= 2;
@@ -378,6 +547,21 @@ extern "C" int bi_profile_stages(bi_handle h, const void* x, void* y, int nrhs, 
         return BI_ERR_ARG;
     }
     return guarded(h, [&] {
+        if (h->med[0]) {
+            // two-region: the stages of both media, summed
+            double ms1[BI_NSTAGES];
+            if (h->coated) {
+                bi_coated_outer_currents(h, x, nrhs, h->stream);
+                bi_profile_impl(h->med[0], h->d_xin0, h->d_y0, nrhs, reps, stage_ms);
+                bi_profile_impl(h->med[1], h->d_xin1, h->d_y1, nrhs, reps, ms1);
+                for (int i = 0; i < BI_NSTAGES; ++i) stage_ms[i] += ms1[i];
+                return (int)BI_OK;
+            }
+            bi_profile_impl(h->med[0], x, y, nrhs, reps, stage_ms);
+            bi_profile_impl(h->med[1], x, h->d_ysum, nrhs, reps, ms1);
+            for (int i = 0; i < BI_NSTAGES; ++i) stage_ms[i] += ms1[i];
+            return (int)BI_OK;
+        }
         bi_profile_impl(h, x, y, nrhs, reps, stage_ms);
         return (int)BI_OK;
     });
@@ -385,11 +569,36 @@ extern "C" int bi_profile_stages(bi_handle h, const void* x, void* y, int nrhs, 
 
 extern "C" const char* bi_stage_name(int i) { return bi_stage_name_impl(i); }
 
+extern "C" int bi_tuned_config(bi_handle h, char* buf, int64_t len) {
+    if (!h || !buf || len < 1) return BI_ERR_ARG;
+    static const char* pass_name[3] = {"translate", "interpolate", "anterpolate"};
+    std::string out;
+    for (int m = 0; m < 2; ++m) {
+        const bi_handle_s* src = h->med[0] ? h->med[m] : (m == 0 ? h : nullptr);
+        if (!src) continue;
+        for (const auto& t : src->tuned) {
+            std::string form = t.pass == 0 ? (t.variant == 2 ? "2 pairs/thread" : "1 pair/thread")
+                               : t.variant == 2 ? "two-pass"
+                               : t.variant >= 200 ? "row blocks, chunk " + std::to_string(t.variant - 200)
+                               : t.pass == 1 ? "rows per CTA, chunk " + std::to_string(t.variant - 100)
+                                             : "per child, chunk " + std::to_string(t.variant - 100);
+            if (h->med[0]) out += "medium " + std::to_string(m) + " ";
+            out += std::string(pass_name[t.pass]) + " level " + std::to_string(t.level) + " E " + std::to_string(t.E) +
+                   ": " + form + " (" + std::to_string((int)t.us) + " us)\n";
+        }
+    }
+    std::strncpy(buf, out.c_str(), (size_t)len - 1);
+    buf[len - 1] = 0;
+    return (int64_t)out.size() < len ? BI_OK : BI_ERR_ARG;
+}
+
 extern "C" int bi_debug_set_wait_limit(bi_handle h, long long cycles) {
     if (!h) return BI_ERR_ARG;
     return guarded(h, [&] {
         CU(cudaStreamSynchronize(h->stream));
         h->wait_cycles = cycles > 0 ? cycles : (1ll << 31);
+        for (bi_handle_s* m : h->med)
+            if (m && bi_debug_set_wait_limit(m, cycles) != BI_OK) throw bi_error{BI_ERR_CUDA, m->err};
         // the captured products carry the old limit as a kernel argument
         for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
         h->graphs.clear();
@@ -398,6 +607,19 @@ extern "C" int bi_debug_set_wait_limit(bi_handle h, long long cycles) {
 }
 
 extern "C" int bi_farfield(bi_handle h, const void* x, int nrhs, const double* dirs, int ndir, void* F) {
+    if (h && h->coated) {
+        // the outer surface's currents radiate into free space
+        if (!x || nrhs < 1 || nrhs > h->max_rhs) {
+            h->err = "bi_farfield: null x or nrhs outside [1, max_rhs] (coated body)";
+            return BI_ERR_ARG;
+        }
+        const int rc = guarded(h, [&] {
+            bi_coated_outer_currents(h, x, nrhs, h->stream);
+            return (int)BI_OK;
+        });
+        return rc != BI_OK ? rc : bi_farfield(h->med[0], h->d_xin0, nrhs, dirs, ndir, F);
+    }
+    if (h && h->med[0]) return bi_farfield(h->med[0], x, nrhs, dirs, ndir, F);   // radiated into the exterior
     if (h && h->ki != 0.0) {
         h->err = "bi_farfield: the handle's medium is lossy (k_im != 0); a far field exists in free space only";
         return BI_ERR_ARG;

@@ -148,6 +148,11 @@ static __device__ __align__(256) double g_ff_noalloc_scratch[BI_FARFIELD_NOALLOC
 
 extern "C" int bi_farfield_noalloc(bi_handle h, const void* x, int nrhs, const double* dirs, int ndir, void* F) {
     if (!h) return BI_ERR_ARG;
+    if (h->coated) {
+        h->err = "bi_farfield_noalloc: use bi_farfield for the coated body";
+        return BI_ERR_ARG;
+    }
+    if (h->med[0]) return bi_farfield_noalloc(h->med[0], x, nrhs, dirs, ndir, F);   // two-region: the exterior
     if (!x || !dirs || !F || nrhs < 1 || ndir < 1 || nrhs > 65535 || ndir > 65535) {
         h->err = "bi_farfield_noalloc: null argument or nrhs/ndir outside [1, 65535]";
         return BI_ERR_ARG;

@@ -115,6 +115,34 @@ struct bi_handle_s {
     bi_params prm{};
     double k = 0;     // Re k: sets the sampling and the box sizes in wavelengths
     double ki = 0;    // Im k (<= 0: a lossy medium; 0: free space)
+    // one medium of the two-region form (op_mode 3): y_E = a L x_J - K x_M, y_H = K x_J + b L x_M
+    double pa[2] = {1.0, 0.0}, pb[2] = {1.0, 0.0};
+    int nF = 1;       // transverse fields per box and direction: 1, or 2 (op_mode 3: E and H)
+    // the two-region operator (op_mode 2): one handle per medium, products summed
+    bi_handle_s* med[2] = {nullptr, nullptr};
+    void* d_ysum = nullptr;             // [max_rhs][nun] the second medium's product
+    // Autotuned kernel forms of the level passes, per (pass, level, E): pass 0 translation
+    // (1 or 2 pairs of entries per thread), 1 interpolation (100 + EC: chunked; 2: two-pass),
+    // 2 anterpolation (100 + EC: per child; 200 + EC: row blocks; 2: two-pass); 0 = the built-in
+    // choice.  Filled by the first product with a given nrhs (bi_autotune) and reported by
+    // bi_tuned_config.
+    struct tune_entry {
+        int pass, level, E, variant;
+        double us;
+    };
+    std::vector<tune_entry> tuned;
+    std::vector<int> tuned_E;           // E values already tuned
+    bool autotune = true;
+    int variant_of(int pass, int level, int E) const {
+        for (const tune_entry& t : tuned)
+            if (t.pass == pass && t.level == level && t.E == E) return t.variant;
+        return 0;
+    }
+    int force_variant = -1;             // set by the tuner while it times one candidate
+    // the coated PEC body (op_mode 4): med[0] = free space on the outer surface (N1 RWG),
+    // med[1] = the coat on both surfaces (N1 + N2 RWG); unknowns [J1, M1, J2]
+    int coated = 0, N1 = 0, N2 = 0;
+    void *d_xin0 = nullptr, *d_xin1 = nullptr, *d_y0 = nullptr, *d_y1 = nullptr;
     int N = 0, nt = 0, nv = 0;
     int nun = 0;      // unknowns
     int nX = 2;       // currents per RWG (2 for op_mode 0, 1 for op_mode 1)
@@ -245,6 +273,10 @@ void bi_translation_series(const bi_handle_s* h, int l, std::vector<int>& dist_i
 void bi_alloc_work(bi_handle_s* h);
 void bi_matvec_launch(bi_handle_s* h, const void* x, void* y, int nrhs, cudaStream_t s);
 void bi_rhs_launch(bi_handle_s* h, const double* khat, const double* phat, int nrhs, void* b);
+// coated body: the outer surface's currents [J1; M1] of x into d_xin0; the outer medium's
+// right-hand sides (in d_y0) into b = [b_J1; b_M1; 0]
+void bi_coated_outer_currents(bi_handle_s* h, const void* x, int R, cudaStream_t s);
+void bi_coated_rhs(bi_handle_s* h, void* b, int R, cudaStream_t s);
 void bi_profile_impl(bi_handle_s* h, const void* x, void* y, int nrhs, int reps, double* ms);
 const char* bi_stage_name_impl(int i);
 bool bi_leaf_aggregate_bulk(bi_handle_s* h, const void* x, int R, cudaStream_t s);
@@ -252,6 +284,7 @@ bool bi_interp_level(bi_handle_s* h, int l, int E, cudaStream_t s);
 bool bi_anterp_level(bi_handle_s* h, int l, int E, cudaStream_t s);
 void bi_upload_taps(bi_handle_s* h);
 bool bi_translate_level(bi_handle_s* h, int l, int E, cudaStream_t s);
+void bi_autotune(bi_handle_s* h, int nrhs, cudaStream_t s);
 void bi_build_sai(bi_handle_s* h);
 void bi_operator_launch(bi_handle_s* h, const void* x, void* y, int R, cudaStream_t s);
 void bi_coupling_set(bi_handle_s* h, int64_t n_int, const int* lx_ptr, const int* lx_col, const void* lx_val,

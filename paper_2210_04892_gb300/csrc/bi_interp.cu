@@ -793,14 +793,14 @@ bool interp_t_p(bi_handle_s* h, int l, int E, cudaStream_t s) {
 // 8, 4, 2 that divides E and leaves room for at least one parent row of 8 children in about
 // 64 KB of shared memory; rows per CTA fill the rest.
 template <typename T, int P>
-bool interp_chunked(bi_handle_s* h, int l, int E, cudaStream_t s) {
+bool interp_chunked(bi_handle_s* h, int l, int E, cudaStream_t s, int ec_force = 0) {
     level_t& Pl = h->lev[l];
     level_t& C = h->lev[l + 1];
     interp_t& I = h->itp[l];
     const size_t budget = 64 * 1024;
     int EC = 0;
     for (int ec : {16, 8, 4, 2})
-        if (E % ec == 0 && (size_t)8 * C.nph * ec * sizeof(cpx<T>) <= budget / 2) {
+        if (E % ec == 0 && (size_t)8 * C.nph * ec * sizeof(cpx<T>) <= budget / 2 && (!ec_force || ec == ec_force)) {
             EC = ec;
             break;
         }
@@ -856,7 +856,7 @@ bool anterp_t_p(bi_handle_s* h, int l, int E, cudaStream_t s) {
 // 4, 2 dividing E whose shared memory (shifted parent field and transposed phi pass of the
 // chunk) stays within about 80 KB; false when even EC = 2 does not fit (coarse levels).
 template <typename T, int PT>
-bool anterp_chunked(bi_handle_s* h, int l, int E, cudaStream_t s) {
+bool anterp_chunked(bi_handle_s* h, int l, int E, cudaStream_t s, int ec_force = 0) {
     level_t& Pl = h->lev[l];
     level_t& C = h->lev[l + 1];
     interp_t& I = h->itp[l];
@@ -865,7 +865,7 @@ bool anterp_chunked(bi_handle_s* h, int l, int E, cudaStream_t s) {
     size_t smem = 0;
     for (int ec : {16, 8, 4, 2}) {
         const size_t sm = taps + ((size_t)Pl.K + (size_t)Pl.nth * C.nph) * ec * sizeof(cpx<T>);
-        if (E % ec == 0 && sm <= 80 * 1024) {
+        if (E % ec == 0 && sm <= (ec_force ? 160 : 80) * 1024 && (!ec_force || ec == ec_force)) {
             EC = ec;
             smem = sm;
             break;
@@ -886,14 +886,14 @@ bool anterp_chunked(bi_handle_s* h, int l, int E, cudaStream_t s) {
 // Coarse levels: the row-blocked kernel, EC the largest of 16, 8, 4, 2 dividing E with at least
 // one child row's parent-column field (nphp x EC) in about 48 KB; rows fill up to that.
 template <typename T, int PT>
-bool anterp_rows(bi_handle_s* h, int l, int E, cudaStream_t s) {
+bool anterp_rows(bi_handle_s* h, int l, int E, cudaStream_t s, int ec_force = 0) {
     level_t& Pl = h->lev[l];
     level_t& C = h->lev[l + 1];
     interp_t& I = h->itp[l];
     const size_t budget = 48 * 1024;
     int EC = 0;
     for (int ec : {16, 8, 4, 2})
-        if (E % ec == 0 && (size_t)Pl.nph * ec * sizeof(cpx<T>) * 2 <= budget) {
+        if (E % ec == 0 && (size_t)Pl.nph * ec * sizeof(cpx<T>) * 2 <= budget && (!ec_force || ec == ec_force)) {
             EC = ec;
             break;
         }
@@ -933,6 +933,9 @@ void bi_upload_taps(bi_handle_s* h) {
 bool bi_interp_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
     const interp_t& I = h->itp[l];
     if (I.p_th != 10 || I.p_ph != 10 || !I.d_th_tap) return false;
+    const int v = h->force_variant >= 0 ? h->force_variant : (E > 2 ? h->variant_of(1, l, E) : 0);
+    if (v >= 100) return h->prec == 0 ? interp_chunked<double, 10>(h, l, E, s, v - 100) : interp_chunked<float, 10>(h, l, E, s, v - 100);
+    if (v == 2) return h->prec == 0 ? interp_wide<double>(h, l, E, s) : interp_wide<float>(h, l, E, s);
     if (E > 2 && (h->prec == 0 ? interp_chunked<double, 10>(h, l, E, s) : interp_chunked<float, 10>(h, l, E, s)))
         return true;
     if (E >= 32) return h->prec == 0 ? interp_wide<double>(h, l, E, s) : interp_wide<float>(h, l, E, s);
@@ -942,6 +945,19 @@ bool bi_interp_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
 bool bi_anterp_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
     const interp_t& I = h->itp[l];
     if (!I.d_tth_pad) return false;
+    const int v = h->force_variant >= 0 ? h->force_variant : (E > 2 ? h->variant_of(2, l, E) : 0);
+    if (v != 0 && I.pt_th == I.pt_ph && (I.pt_th == 16 || I.pt_th == 24)) {
+        const bool p16 = I.pt_th == 16, dbl = h->prec == 0;
+        if (v >= 200)
+            return p16 ? (dbl ? anterp_rows<double, 16>(h, l, E, s, v - 200) : anterp_rows<float, 16>(h, l, E, s, v - 200))
+                       : (dbl ? anterp_rows<double, 24>(h, l, E, s, v - 200) : anterp_rows<float, 24>(h, l, E, s, v - 200));
+        if (v >= 100)
+            return p16 ? (dbl ? anterp_chunked<double, 16>(h, l, E, s, v - 100) : anterp_chunked<float, 16>(h, l, E, s, v - 100))
+                       : (dbl ? anterp_chunked<double, 24>(h, l, E, s, v - 100) : anterp_chunked<float, 24>(h, l, E, s, v - 100));
+        if (v == 2)
+            return p16 ? (dbl ? anterp_wide<double, 16>(h, l, E, s) : anterp_wide<float, 16>(h, l, E, s))
+                       : (dbl ? anterp_wide<double, 24>(h, l, E, s) : anterp_wide<float, 24>(h, l, E, s));
+    }
     if (E > 2 && I.pt_th == I.pt_ph) {
         const bool whole = !h->force_anterp_rows;
         if (whole && I.pt_th == 16 && (h->prec == 0 ? anterp_chunked<double, 16>(h, l, E, s) : anterp_chunked<float, 16>(h, l, E, s)))

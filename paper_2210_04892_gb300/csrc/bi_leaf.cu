@@ -24,15 +24,6 @@ namespace {
 
 constexpr int kBarBytes = 128;  // shared-memory header: up to 16 mbarriers
 
-// Thread 0, after a wait gave up: wait (bounded, with the default limit of about one second
-// whatever limit the consumers used) for the copies still in flight so that no copy lands
-// after the CTA has left, then record the failure.
-__device__ void give_up(uint64_t* bar, int first_chunk, int nch, int S, int* status) {
-    if (threadIdx.x != 0) return;
-    for (int c = first_chunk; c < min(first_chunk + S, nch); ++c) mbar_wait_bounded(&bar[c % S], (c / S) & 1);
-    atomicExch(status, BI_DEVSTATUS_TMA_TIMEOUT);
-}
-
 // CTA = one leaf box; thread slot = (stored direction kk, RHS r), SL slots per thread.
 template <typename T, int MODE, int SL>
 __global__ void __launch_bounds__(256) k_aggregate_bulk(int N, int K, int nph, int R, int nun, int G, int S,
@@ -73,7 +64,7 @@ __global__ void __launch_bounds__(256) k_aggregate_bulk(int N, int K, int nph, i
         const int st = c % S;
         const bool ok = mbar_wait_bounded(&bar[st], (c / S) & 1, wait);
         if (!__syncthreads_and(ok)) {
-            give_up(bar, c, nch, S, status);
+            bulk_give_up(bar, c, nch, S, status);
             return;
         }
         const cpx<T>* f = ring + st * stage;
@@ -155,7 +146,7 @@ __global__ void __launch_bounds__(256) k_receive_bulk(int N, int K, int nph, int
     __syncthreads();
     if (!__syncthreads_and(mbar_wait_bounded(&bar[S], 0, wait))) {
         if (threadIdx.x == 0) mbar_wait_bounded(&bar[S], 0);
-        give_up(bar, 0, nch, S, status);
+        bulk_give_up(bar, 0, nch, S, status);
         return;
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
@@ -163,7 +154,7 @@ __global__ void __launch_bounds__(256) k_receive_bulk(int N, int K, int nph, int
         const int st = c % S;
         const bool ok = mbar_wait_bounded(&bar[st], (c / S) & 1, wait);
         if (!__syncthreads_and(ok)) {
-            give_up(bar, c, nch, S, status);
+            bulk_give_up(bar, c, nch, S, status);
             return;
         }
         const cpx<T>* fst = ring + st * stage;

@@ -504,6 +504,8 @@ __global__ void __launch_bounds__(256, RT == 1 ? 6 : 1) k_near_stream(int N, int
 // tree-ordered copy xt [N][NX][R] (gathered once per product), so the x of one near box is one
 // contiguous chunk and its staging is coalesced; each warp owns one row at a time (RT RHS of J
 // and M in registers), lanes stride the row's columns with 16-byte block loads.
+// MODE 3 (one medium of the two-region form): entries (L, K) = (<f, L f>, <f, Kbar f>) and
+//   y_E = a L x_J - K x_M,   y_H = K x_J + b L x_M   (a, b: the medium's eta and 1/eta, or 1).
 template <typename T, int MODE, int RT>
 __global__ void __launch_bounds__(256, RT >= 8 ? 2 : 3) k_near_multi(int N, int R, int nun, const int* __restrict__ perm,
                                                       const int2* __restrict__ work,
@@ -513,8 +515,8 @@ __global__ void __launch_bounds__(256, RT >= 8 ? 2 : 3) k_near_multi(int N, int 
                                                       const cpx<T>* __restrict__ blocks, const int* __restrict__ gptr,
                                                       const int* __restrict__ gseg, const T* __restrict__ gval,
                                                       const cpx<T>* __restrict__ xt, cpx<T>* __restrict__ yt,
-                                                      cpx<T>* __restrict__ yuser) {
-    constexpr int NX = MODE == 0 ? 2 : 1;
+                                                      cpx<T>* __restrict__ yuser, cpx<T> pa, cpx<T> pb) {
+    constexpr int NX = (MODE == 0 || MODE == 3) ? 2 : 1;
     extern __shared__ unsigned char smem_raw[];
     cpx<T>* xs = reinterpret_cast<cpx<T>*>(smem_raw);  // [NX][RT][ncol]
     const int b = work[blockIdx.x].x, row0 = work[blockIdx.x].y;
@@ -539,15 +541,26 @@ __global__ void __launch_bounds__(256, RT >= 8 ? 2 : 3) k_near_multi(int N, int 
             }
         }
         __syncthreads();
-        const int stride = (MODE == 0 ? 2 : 1);
+        const int stride = ((MODE == 0 || MODE == 3) ? 2 : 1);
         for (int ml = row0 + warp; ml < row_end; ml += nwarp) {
-            cpx<T> aJ[RT], aM[RT];
+            cpx<T> aJ[RT], aM[RT], bJ[RT], bM[RT];   // b*: the second pair of sums of MODE 3
 #pragma unroll
-            for (int rr = 0; rr < RT; ++rr) { aJ[rr] = czero<T>(); aM[rr] = czero<T>(); }
+            for (int rr = 0; rr < RT; ++rr) { aJ[rr] = czero<T>(); aM[rr] = czero<T>(); bJ[rr] = czero<T>(); bM[rr] = czero<T>(); }
             const cpx<T>* row = blocks + stride * (seg + (int64_t)ml * ncol);
 #pragma unroll 2
             for (int c = lane; c < ncol; c += 32) {
-                if (MODE == 0) {
+                if (MODE == 3) {
+                    cpx<T> A, B;   // A = L, B = K
+                    load_pair(row + 2 * c, A, B);
+#pragma unroll
+                    for (int rr = 0; rr < RT; ++rr) {
+                        const cpx<T> xJ = xs[(size_t)rr * ncol + c], xM = xs[(size_t)(RT + rr) * ncol + c];
+                        cfma(aJ[rr], A, xJ);   // L x_J
+                        cfma(aM[rr], B, xM);   // K x_M
+                        cfma(bJ[rr], B, xJ);   // K x_J
+                        cfma(bM[rr], A, xM);   // L x_M
+                    }
+                } else if (MODE == 0) {
                     cpx<T> A, B;
                     load_pair(row + 2 * c, A, B);
 #pragma unroll
@@ -580,17 +593,25 @@ __global__ void __launch_bounds__(256, RT >= 8 ? 2 : 3) k_near_multi(int N, int 
             }
 #pragma unroll
             for (int rr = 0; rr < RT; ++rr) {
-                const cpx<T> sJ = warp_sum(aJ[rr]);
-                const cpx<T> sM = MODE == 0 ? warp_sum(aM[rr]) : czero<T>();
+                cpx<T> sJ = warp_sum(aJ[rr]);
+                cpx<T> sM = (MODE == 0 || MODE == 3) ? warp_sum(aM[rr]) : czero<T>();
+                if (MODE == 3) {
+                    // y_E = a L x_J - K x_M,  y_H = K x_J + b L x_M (stored so that the lines below,
+                    // which negate the first, write them)
+                    const cpx<T> kJ = warp_sum(bJ[rr]), lM = warp_sum(bM[rr]);
+                    const cpx<T> yE = csub(cmul(pa, sJ), sM), yH = cadd(kJ, cmul(pb, lM));
+                    sJ = cpx<T>{-yE.x, -yE.y};
+                    sM = yH;
+                }
                 if (lane == rr && rr < rn) {
                     const int r = r0 + rr;
                     const cpx<T> vJ = {-sJ.x, -sJ.y};
                     if (yuser) {
                         yuser[(int64_t)r * nun + perm[m]] = vJ;
-                        if (MODE == 0) yuser[(int64_t)r * nun + N + perm[m]] = sM;
+                        if (NX == 2) yuser[(int64_t)r * nun + N + perm[m]] = sM;
                     } else {
                         yt[((int64_t)m * NX + 0) * R + r] = vJ;
-                        if (MODE == 0) yt[((int64_t)m * NX + 1) * R + r] = sM;
+                        if (NX == 2) yt[((int64_t)m * NX + 1) * R + r] = sM;
                     }
                 }
             }
@@ -1047,22 +1068,31 @@ __global__ void __launch_bounds__(256) k_receive2(int N, int K, int nph, int R, 
 // pattern R_m(khat) = int f_m exp(-jk khat.(r - c)) is not conj F_m, but it is F_m at the
 // antipode -khat (theta-hat the same there, phi-hat reversed): R = (F_theta, -F_phi)(-khat).
 // Aggregation: U_b(k) = sum_n ( -x_J,n F_n(k) + x_M,n khat x F_n(k) ), thread per (direction, entry).
+// MODE 3 (one medium of the two-region form): two fields per box, E = 4R entries per direction,
+//   U_E = a x_J F - x_M khat x F,   U_H = x_J F - b x_M khat x F      ((khat x F) = (-F_phi, F_theta)).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_aggregate_full(int N, int K, int R, int nun, const int* __restrict__ perm,
                                                         const int* __restrict__ leaf_start, const cpx<T>* __restrict__ F,
-                                                        const cpx<T>* __restrict__ x, cpx<T>* __restrict__ U) {
+                                                        const cpx<T>* __restrict__ x, cpx<T>* __restrict__ U, cpx<T> pa,
+                                                        cpx<T> pb) {
     const int b = blockIdx.x;
-    const int E = 2 * R;
+    const int E = (MODE == 3 ? 4 : 2) * R;
     const int64_t idx = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)K * E) return;
     const int kk = (int)(idx / E), e = (int)(idx % E);
-    const int c = e / R, r = e % R;
+    const int c = (e / R) & 1, r = e % R, fld = e / (2 * R);
     cpx<T> acc = czero<T>();
     for (int n = leaf_start[b]; n < leaf_start[b + 1]; ++n) {
         const cpx<T> Ft = F[((int64_t)n * K + kk) * 2], Fp = F[((int64_t)n * K + kk) * 2 + 1];
         const int u = perm[n];
         const cpx<T> xJ = x[(int64_t)r * nun + u];
-        if (MODE == 0) {
+        if (MODE == 3) {
+            const cpx<T> xM = x[(int64_t)r * nun + N + u];
+            const cpx<T> sJ = fld == 0 ? cmul(pa, xJ) : xJ;    // coefficient of F
+            const cpx<T> sM = fld == 0 ? xM : cmul(pb, xM);    // coefficient of -khat x F
+            // theta: sJ Ft + sM Fp;  phi: sJ Fp - sM Ft
+            acc = c == 0 ? cadd(acc, cadd(cmul(sJ, Ft), cmul(sM, Fp))) : cadd(acc, csub(cmul(sJ, Fp), cmul(sM, Ft)));
+        } else if (MODE == 0) {
             const cpx<T> xM = x[(int64_t)r * nun + N + u];
             acc = c == 0 ? csub(acc, cadd(cmul(xJ, Ft), cmul(xM, Fp))) : cadd(acc, csub(cmul(xM, Ft), cmul(xJ, Fp)));
         } else {
@@ -1074,6 +1104,7 @@ __global__ void __launch_bounds__(256) k_aggregate_full(int N, int K, int R, int
 
 // Receive: y_J = yt_J - cc sum_k [ R.V - RX.(khat x V) ],  y_M = yt_M + cc sum_k [ -R.(khat x V) - RX.V ]
 // with the complex constant cc = k^2 / (32 pi^2); one warp per (tree RWG m, RHS r).
+// MODE 3: y_E = yt_E - cc sum_k R.V_E,  y_H = yt_H - cc sum_k R.(khat x V_H), cc = k^2 / (16 pi^2).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_receive_full(int N, int K, int nph, int R, int nun, const int* __restrict__ perm,
                                                       const int* __restrict__ leaf_of, const cpx<T>* __restrict__ F,
@@ -1084,24 +1115,34 @@ __global__ void __launch_bounds__(256) k_receive_full(int N, int K, int nph, int
     if (warp >= N * R) return;
     const int m = warp / R, r = warp % R;
     const int b = leaf_of[m];
-    const int E = 2 * R;
+    const int E = (MODE == 3 ? 4 : 2) * R;
     cpx<T> sJ = czero<T>(), sM = czero<T>();
     for (int kk = lane; kk < K; kk += 32) {
         const int ka = antipode(kk, K, nph);
         const cpx<T> Rt = F[((int64_t)m * K + ka) * 2];
         const cpx<T> Fa = F[((int64_t)m * K + ka) * 2 + 1];
         const cpx<T> Rp = {-Fa.x, -Fa.y};
+        if (MODE == 3) {
+            const cpx<T>* v = V + ((int64_t)b * K + kk) * E + r;
+            const cpx<T> Et = v[0], Ep = v[R], Ht = v[2 * R], Hp = v[3 * R];
+            sJ = cadd(sJ, cadd(cmul(Rt, Et), cmul(Rp, Ep)));   // R.V_E
+            sM = cadd(sM, csub(cmul(Rp, Ht), cmul(Rt, Hp)));   // R.(khat x V_H)
+            continue;
+        }
         const cpx<T> Xt = RX[((int64_t)m * K + kk) * 2], Xp = RX[((int64_t)m * K + kk) * 2 + 1];
         const cpx<T> Vt = V[((int64_t)b * K + kk) * E + r], Vp = V[((int64_t)b * K + kk) * E + R + r];
         sJ = cadd(sJ, cadd(csub(cadd(cmul(Rt, Vt), cmul(Rp, Vp)), cmul(Xp, Vt)), cmul(Xt, Vp)));
         if (MODE == 0) sM = cadd(sM, csub(csub(cmul(Rt, Vp), cmul(Rp, Vt)), cadd(cmul(Xt, Vt), cmul(Xp, Vp))));
     }
     sJ = warp_sum(sJ);
-    if (MODE == 0) sM = warp_sum(sM);
+    if (MODE == 0 || MODE == 3) sM = warp_sum(sM);
     if (lane == 0) {
         const int u = perm[m];
         const cpx<T> nc = {-cc.x, -cc.y};
-        if (MODE == 0) {
+        if (MODE == 3) {
+            y[(int64_t)r * nun + u] = cadd(yt[((int64_t)m * 2 + 0) * R + r], cmul(nc, sJ));
+            y[(int64_t)r * nun + N + u] = cadd(yt[((int64_t)m * 2 + 1) * R + r], cmul(nc, sM));
+        } else if (MODE == 0) {
             y[(int64_t)r * nun + u] = cadd(yt[((int64_t)m * 2 + 0) * R + r], cmul(nc, sJ));
             y[(int64_t)r * nun + N + u] = cadd(yt[((int64_t)m * 2 + 1) * R + r], cmul(cc, sM));
         } else {
@@ -1116,24 +1157,32 @@ inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) / th); 
 template <typename T>
 void launch_aggregate_full(bi_handle_s* h, const cpx<T>* x, int R, cudaStream_t s) {
     level_t& L = h->lev[h->leaf];
-    dim3 g(L.nbox, nblk((int64_t)L.K * 2 * R, 256));
-    if (h->prm.op_mode == 0)
+    dim3 g(L.nbox, nblk((int64_t)L.K * 2 * h->nF * R, 256));
+    const cpx<T> pa = {(T)h->pa[0], (T)h->pa[1]}, pb = {(T)h->pb[0], (T)h->pb[1]};
+    if (h->prm.op_mode == 3)
+        k_aggregate_full<T, 3><<<g, 256, 0, s>>>(h->N, L.K, R, h->nun, h->d_perm, h->d_leaf_start, (const cpx<T>*)h->d_F, x,
+                                                 (cpx<T>*)L.d_U, pa, pb);
+    else if (h->prm.op_mode == 0)
         k_aggregate_full<T, 0><<<g, 256, 0, s>>>(h->N, L.K, R, h->nun, h->d_perm, h->d_leaf_start, (const cpx<T>*)h->d_F, x,
-                                                 (cpx<T>*)L.d_U);
+                                                 (cpx<T>*)L.d_U, pa, pb);
     else
         k_aggregate_full<T, 1><<<g, 256, 0, s>>>(h->N, L.K, R, h->nun, h->d_perm, h->d_leaf_start, (const cpx<T>*)h->d_F, x,
-                                                 (cpx<T>*)L.d_U);
+                                                 (cpx<T>*)L.d_U, pa, pb);
     CU(cudaGetLastError());
 }
 template <typename T>
 void launch_receive_full(bi_handle_s* h, cpx<T>* y, int R, cudaStream_t s) {
     level_t& L = h->lev[h->leaf];
     const double pi = 3.14159265358979323846;
-    // k^2 / (32 pi^2) at complex k
-    const double kr = h->k, ki = h->ki;
-    const cpx<T> cc = {(T)((kr * kr - ki * ki) / (32.0 * pi * pi)), (T)(2.0 * kr * ki / (32.0 * pi * pi))};
+    // k^2 / (32 pi^2) at complex k (k^2 / (16 pi^2) for one medium of the two-region form)
+    const double kr = h->k, ki = h->ki, den = (h->prm.op_mode == 3 ? 16.0 : 32.0) * pi * pi;
+    const cpx<T> cc = {(T)((kr * kr - ki * ki) / den), (T)(2.0 * kr * ki / den)};
     const int64_t nthreads = (int64_t)h->N * R * 32;
-    if (h->prm.op_mode == 0)
+    if (h->prm.op_mode == 3)
+        k_receive_full<T, 3><<<nblk(nthreads, 256), 256, 0, s>>>(h->N, L.K, L.nph, R, h->nun, h->d_perm, h->d_leaf_of,
+                                                                 (const cpx<T>*)h->d_F, (const cpx<T>*)h->d_RX,
+                                                                 (const cpx<T>*)L.d_V, cc, (const cpx<T>*)h->d_yt, y);
+    else if (h->prm.op_mode == 0)
         k_receive_full<T, 0><<<nblk(nthreads, 256), 256, 0, s>>>(h->N, L.K, L.nph, R, h->nun, h->d_perm, h->d_leaf_of,
                                                                  (const cpx<T>*)h->d_F, (const cpx<T>*)h->d_RX,
                                                                  (const cpx<T>*)L.d_V, cc, (const cpx<T>*)h->d_yt, y);
@@ -1309,19 +1358,32 @@ void launch_near_stream(bi_handle_s* h, const cpx<T>* x, cpx<T>* yt, cpx<T>* yus
 
 template <typename T, int MODE, int RT>
 void launch_near_multi(bi_handle_s* h, cpx<T>* yt, cpx<T>* yuser, int R, cudaStream_t s) {
-    const int NX = MODE == 0 ? 2 : 1;
+    const int NX = (MODE == 0 || MODE == 3) ? 2 : 1;
     size_t smem = (size_t)h->near_ncol_max * NX * RT * sizeof(cpx<T>);
     auto kern = k_near_multi<T, MODE, RT>;
     bi_raise_smem(kern, smem);
     kern<<<h->near_nwork, 256, smem, s>>>(h->N, R, h->nun, h->d_perm, (const int2*)h->d_near_work, h->d_leaf_start,
                                           h->d_near_ptr, h->d_near_src, h->d_near_blk, h->d_near_col0, h->d_near_ncol,
                                           (const cpx<T>*)h->d_near, h->d_gram_ptr, h->d_gram_seg, (const T*)h->d_gram_val,
-                                          (const cpx<T>*)h->d_xt, yt, yuser);
+                                          (const cpx<T>*)h->d_xt, yt, yuser, cpx<T>{(T)h->pa[0], (T)h->pa[1]},
+                                          cpx<T>{(T)h->pb[0], (T)h->pb[1]});
     CU(cudaGetLastError());
 }
 
 template <typename T, int MODE>
 void launch_near_any(bi_handle_s* h, const cpx<T>* x, cpx<T>* yt, cpx<T>* yuser, int R, cudaStream_t s) {
+    if (MODE == 3) {
+        // one medium of the two-region form: the tree-ordered kernel for every R
+        if ((size_t)h->near_ncol_max * 2 * 4 * sizeof(cpx<T>) > 200 * 1024)
+            throw bi_error{BI_ERR_ARG, "two-region near field: a leaf box's near segment is too wide"};
+        const int64_t nvec = (int64_t)h->N * h->nX * R;
+        k_gather_x<T><<<nblk(nvec, 256), 256, 0, s>>>(h->N, h->nX, R, h->nun, h->d_perm, x, (cpx<T>*)h->d_xt);
+        CU(cudaGetLastError());
+        if (R == 1) launch_near_multi<T, 3, 1>(h, yt, yuser, R, s);
+        else if (R == 2) launch_near_multi<T, 3, 2>(h, yt, yuser, R, s);
+        else launch_near_multi<T, 3, 4>(h, yt, yuser, R, s);
+        return;
+    }
     if ((size_t)h->near_ncol_max * 2 * sizeof(cpx<T>) > 160 * 1024) {
         // rows of one box exceed the CTA: the row-per-thread kernel on tree-ordered vectors
         const int64_t nvec = (int64_t)h->N * h->nX * R;
@@ -1447,14 +1509,16 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
     const C* x = (const C*)xv;
     C* y = (C*)yv;
     C* yt = (C*)h->d_yt;
-    const int N = h->N, nun = h->nun, E = 2 * R, th = 256;
+    const int N = h->N, nun = h->nun, E = 2 * h->nF * R, th = 256;
     const bool far = h->leaf >= 2;
+    const bool full = h->ki != 0.0 || h->prm.op_mode == 3;   // every direction of the leaf patterns stored
     if (ev) CU(cudaEventRecord(ev[0], s));
     if (!ev) {
         CU(cudaEventRecord(h->ev_fork, s));
         CU(cudaStreamWaitEvent(side, h->ev_fork, 0));
     }
-    if (h->prm.op_mode == 0) launch_near_any<T, 0>(h, x, yt, far ? nullptr : y, R, side);
+    if (h->prm.op_mode == 3) launch_near_any<T, 3>(h, x, yt, far ? nullptr : y, R, side);
+    else if (h->prm.op_mode == 0) launch_near_any<T, 0>(h, x, yt, far ? nullptr : y, R, side);
     else launch_near_any<T, 1>(h, x, yt, far ? nullptr : y, R, side);
     if (ev) CU(cudaEventRecord(ev[1], s));
     else CU(cudaEventRecord(h->ev_join, side));
@@ -1466,7 +1530,7 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
         return;
     }
     const int lf = h->leaf;
-    if (h->ki != 0.0) {
+    if (full) {
         launch_aggregate_full<T>(h, x, R, s);
     } else if (R < 8 && bi_leaf_aggregate_bulk(h, x, R, s)) {
     } else if (R >= 8) {
@@ -1546,7 +1610,7 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
     }
     if (ev) CU(cudaEventRecord(ev[5], s));
     else CU(cudaStreamWaitEvent(s, h->ev_join, 0));
-    if (h->ki != 0.0) {
+    if (full) {
         launch_receive_full<T>(h, y, R, s);
     } else if (R >= 8 && launch_receive_tile<T>(h, x, y, R, s)) {
     } else if (R < 8 && bi_leaf_receive_bulk(h, y, R, s)) {
@@ -1571,6 +1635,72 @@ void launch_fast(bi_handle_s* h, const void* xv, void* yv, int R, cudaStream_t s
 
 }  // namespace
 
+// Autotuner of the level passes: the first product with a given E = 2 nF nrhs times every
+// applicable kernel form of each level pass once on the handle's own buffers (zeroed first:
+// the values do not change the timing) and keeps the fastest per (pass, level, E):
+//   translation: one or two pairs of entries per thread;
+//   interpolation: chunks of 16, 8, 4 or 2 entries, or the two-pass form;
+//   anterpolation: per child or in row blocks, chunks of 16, 8, 4 or 2 entries, or two-pass.
+// Every later launch (and every captured graph) uses the choice.  It synchronises the stream.
+void bi_autotune(bi_handle_s* h, int nrhs, cudaStream_t s) {
+    const int E = 2 * h->nF * nrhs;
+    if (!h->autotune || E <= 2 || h->leaf < 2) return;
+    if (std::find(h->tuned_E.begin(), h->tuned_E.end(), E) != h->tuned_E.end()) return;
+    h->tuned_E.push_back(E);
+    for (int l = 2; l <= h->leaf; ++l) {
+        const level_t& L = h->lev[l];
+        const size_t sz = (size_t)L.nbox * L.K * E * h->csize;
+        CU(cudaMemsetAsync(L.d_U, 0, sz, s));
+        CU(cudaMemsetAsync(L.d_V, 0, sz, s));
+    }
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    const std::vector<int> cand[3] = {{1, 2},
+                                      {116, 108, 104, 102, 2},
+                                      {116, 108, 104, 102, 216, 208, 204, 202, 2}};
+    try {
+        for (int pass = 0; pass < 3; ++pass) {
+            const int lmax = pass == 0 ? h->leaf : h->leaf - 1;
+            for (int l = 2; l <= lmax; ++l) {
+                int best = 0;
+                double best_us = 1e300;
+                for (int c : cand[pass]) {
+                    h->force_variant = c;
+                    auto run = [&] {
+                        return pass == 0 ? bi_translate_level(h, l, E, s)
+                                         : pass == 1 ? bi_interp_level(h, l, E, s) : bi_anterp_level(h, l, E, s);
+                    };
+                    if (!run()) continue;       // not applicable at this level (shared memory, E)
+                    double us = 1e300;
+                    for (int rep = 0; rep < 2; ++rep) {
+                        CU(cudaEventRecord(e0, s));
+                        run();
+                        CU(cudaEventRecord(e1, s));
+                        CU(cudaEventSynchronize(e1));
+                        float ms = 0;
+                        CU(cudaEventElapsedTime(&ms, e0, e1));
+                        us = std::min(us, 1e3 * ms);
+                    }
+                    if (us < best_us) {
+                        best_us = us;
+                        best = c;
+                    }
+                }
+                h->force_variant = -1;
+                if (best) h->tuned.push_back({pass, l, E, best, best_us});
+            }
+        }
+    } catch (...) {
+        h->force_variant = -1;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    CU(cudaEventDestroy(e0));
+    CU(cudaEventDestroy(e1));
+}
+
 // Enqueue one product on stream s (no graph).
 static void matvec_enqueue(bi_handle_s* h, const void* x, void* y, int nrhs, cudaStream_t s, cudaStream_t side) {
     if (h->use_fast) {
@@ -1582,8 +1712,106 @@ static void matvec_enqueue(bi_handle_s* h, const void* x, void* y, int nrhs, cud
     }
 }
 
-// One product: replayed from a CUDA graph captured on first use for this (x, y, nrhs).
+template <typename T>
+__global__ void k_add_vec(int64_t n, cpx<T>* __restrict__ y, const cpx<T>* __restrict__ a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = cadd(y[i], a[i]);
+}
+
+// Coated PEC body: inputs of the two media from x = [J1, M1, J2] (column-major [R][2 N1 + N2]):
+//   outer medium (S1):  [J1; M1];   coat (S1 and S2):  x_J = [J1; -J2],  x_M = [M1; 0]
+template <typename T>
+__global__ void k_coated_in(int N1, int N2, int R, const cpx<T>* __restrict__ x, cpx<T>* __restrict__ x0,
+                            cpx<T>* __restrict__ x1) {
+    const int nun = 2 * N1 + N2, n1 = 2 * (N1 + N2);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)R * n1) return;
+    const int r = (int)(i / n1), j = (int)(i % n1);
+    const cpx<T>* xr = x + (int64_t)r * nun;
+    cpx<T> v = czero<T>();
+    if (j < N1) v = xr[j];                                     // J1
+    else if (j < N1 + N2) v = cpx<T>{-xr[N1 + j].x, -xr[N1 + j].y};   // -J2 (x index 2 N1 + (j - N1))
+    else if (j < 2 * N1 + N2) v = xr[j - N2];                  // M1 (x index N1 + (j - N1 - N2))
+    x1[i] = v;
+    if (j < 2 * N1) x0[(int64_t)r * 2 * N1 + j] = xr[j];
+}
+// rows: E and H of S1 = outer + coat; the core's row (tangential E = 0 on S2) = -(coat's E rows of S2)
+template <typename T>
+__global__ void k_coated_out(int N1, int N2, int R, const cpx<T>* __restrict__ y0, const cpx<T>* __restrict__ y1,
+                             cpx<T>* __restrict__ y) {
+    const int nun = 2 * N1 + N2, n1 = 2 * (N1 + N2);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)R * nun) return;
+    const int r = (int)(i / nun), j = (int)(i % nun);
+    const cpx<T>* a = y0 + (int64_t)r * 2 * N1;
+    const cpx<T>* b = y1 + (int64_t)r * n1;
+    cpx<T> v;
+    if (j < N1) v = cadd(a[j], b[j]);
+    else if (j < 2 * N1) v = cadd(a[j], b[N2 + j]);           // H rows of S1: coat index N1 + N2 + (j - N1)
+    else v = cpx<T>{-b[j - N1].x, -b[j - N1].y};              // E rows of S2: coat index N1 + (j - 2 N1)
+    y[i] = v;
+}
+template <typename T>
+__global__ void k_coated_rhs(int N1, int N2, int R, const cpx<T>* __restrict__ b0, cpx<T>* __restrict__ b) {
+    const int nun = 2 * N1 + N2;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)R * nun) return;
+    const int r = (int)(i / nun), j = (int)(i % nun);
+    b[i] = j < 2 * N1 ? b0[(int64_t)r * 2 * N1 + j] : czero<T>();
+}
+
+void bi_coated_outer_currents(bi_handle_s* h, const void* x, int R, cudaStream_t s) {
+    const int64_t n = (int64_t)R * 2 * (h->N1 + h->N2);
+    if (h->prec == 0)
+        k_coated_in<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h->N1, h->N2, R, (const cpx<double>*)x,
+                                                                        (cpx<double>*)h->d_xin0, (cpx<double>*)h->d_xin1);
+    else
+        k_coated_in<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h->N1, h->N2, R, (const cpx<float>*)x,
+                                                                       (cpx<float>*)h->d_xin0, (cpx<float>*)h->d_xin1);
+    CU(cudaGetLastError());
+}
+
+void bi_coated_rhs(bi_handle_s* h, void* b, int R, cudaStream_t s) {
+    const int64_t n = (int64_t)R * h->nun;
+    if (h->prec == 0)
+        k_coated_rhs<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h->N1, h->N2, R, (const cpx<double>*)h->d_y0,
+                                                                         (cpx<double>*)b);
+    else
+        k_coated_rhs<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h->N1, h->N2, R, (const cpx<float>*)h->d_y0,
+                                                                        (cpx<float>*)b);
+    CU(cudaGetLastError());
+}
+
+// One product: replayed from a CUDA graph captured on first use for this (x, y, nrhs).  The
+// two-region operator sums the products of its two media; the coated body maps its unknowns to
+// and from theirs.
 void bi_matvec_launch(bi_handle_s* h, const void* x, void* y, int nrhs, cudaStream_t s) {
+    if (h->coated) {
+        bi_coated_outer_currents(h, x, nrhs, s);
+        bi_matvec_launch(h->med[0], h->d_xin0, h->d_y0, nrhs, s);
+        bi_matvec_launch(h->med[1], h->d_xin1, h->d_y1, nrhs, s);
+        const int64_t n = (int64_t)nrhs * h->nun;
+        if (h->prec == 0)
+            k_coated_out<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h->N1, h->N2, nrhs, (const cpx<double>*)h->d_y0,
+                                                                              (const cpx<double>*)h->d_y1, (cpx<double>*)y);
+        else
+            k_coated_out<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h->N1, h->N2, nrhs, (const cpx<float>*)h->d_y0,
+                                                                             (const cpx<float>*)h->d_y1, (cpx<float>*)y);
+        CU(cudaGetLastError());
+        return;
+    }
+    if (h->med[0]) {
+        bi_matvec_launch(h->med[0], x, y, nrhs, s);
+        bi_matvec_launch(h->med[1], x, h->d_ysum, nrhs, s);
+        const int64_t n = (int64_t)h->nun * nrhs;
+        if (h->prec == 0)
+            k_add_vec<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, (cpx<double>*)y, (const cpx<double>*)h->d_ysum);
+        else
+            k_add_vec<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, (cpx<float>*)y, (const cpx<float>*)h->d_ysum);
+        CU(cudaGetLastError());
+        return;
+    }
+    if (h->use_fast) bi_autotune(h, nrhs, s);
     if (!h->use_graphs) {
         matvec_enqueue(h, x, y, nrhs, s, h->side);
         return;
@@ -1620,6 +1848,7 @@ const char* bi_stage_name_impl(int i) { return (i >= 0 && i < BI_NSTAGES) ? kSta
 
 // Per-stage device time of `reps` products (serialised stages, CUDA events on the handle's stream).
 void bi_profile_impl(bi_handle_s* h, const void* x, void* y, int nrhs, int reps, double* ms) {
+    if (h->use_fast) bi_autotune(h, nrhs, h->stream);
     cudaEvent_t ev[BI_NSTAGES + 1];
     for (auto& e : ev) CU(cudaEventCreate(&e));
     for (int i = 0; i < BI_NSTAGES; ++i) ms[i] = 0.0;

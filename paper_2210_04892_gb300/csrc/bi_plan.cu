@@ -42,8 +42,8 @@ extern "C" int bi_plan_create(const double* verts, int nv, const int* tris, int 
     bi_handle_s* h = &p->h;
     if (opt) h->prm = *opt;
     else bi_default_params(&h->prm);
-    if (!bi_params_valid(h->prm)) {
-        g_plan_error = "bi_plan_create: parameter out of range";
+    if (!bi_params_valid(h->prm) || h->prm.op_mode > 1) {
+        g_plan_error = "bi_plan_create: parameter out of range (op_mode 0 or 1)";
         delete p;
         return BI_ERR_ARG;
     }

@@ -267,9 +267,9 @@ extern "C" int bi_submit(bi_server S, const double* verts, int nv, const int* tr
                          int64_t* req) {
     if (!S || !verts || !tris || nv < 3 || nt < 4 || !(k0 > 0) || nrhs < 1 || !khat || !phat || !(tol > 0) || !req)
         return BI_ERR_ARG;
-    if (opt && opt->k_im != 0.0) {
+    if (opt && (opt->k_im != 0.0 || opt->op_mode > 1)) {
         std::lock_guard<std::mutex> lk(S->mu);
-        S->err = "bi_submit: plane-wave requests are for free space (k_im = 0)";
+        S->err = "bi_submit: requests are free-space C-block or PEC operators (k_im = 0, op_mode 0 or 1)";
         return BI_ERR_ARG;
     }
     std::unique_ptr<request> r;

@@ -755,7 +755,7 @@ __global__ void k_near_fill(int nblk, const int* __restrict__ blk_box, const int
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
         int ml = e % mb, nl = e / mb;
         int m = m0 + ml, n = n0 + nl;
-        zd P = zmk(0, 0), Q = zmk(0, 0);
+        zd P = zmk(0, 0), Q = zmk(0, 0), Lm = zmk(0, 0), Km = zmk(0, 0);
         double G = 0, X = 0;
         for (int sm = 0; sm < 2; ++sm) {
             dtri Tm;
@@ -771,6 +771,8 @@ __global__ void k_near_fill(int nblk, const int* __restrict__ blk_box, const int
                 double c = 0.5 * cm * cn;
                 P = zadd(P, zscale(zadd(r.L, r.NK), c));
                 Q = zadd(Q, zscale(zadd(r.NL, zscale(r.K, -1.0)), c));
+                Lm = zadd(Lm, zscale(r.L, cm * cn));
+                Km = zadd(Km, zscale(r.K, cm * cn));
                 if (tm == tn) {
                     // Gram integrals are exact with the edge-midpoint rule (degree-2 integrand)
                     double gg = 0, gx = 0;
@@ -790,12 +792,17 @@ __global__ void k_near_fill(int nblk, const int* __restrict__ blk_box, const int
                 }
             }
         }
-        // A = P - g G,  B = Q - X/2  (g = 1 for the C block, 1/4 for PEC)
+        // A = P - g G,  B = Q - X/2  (g = 1 for the C block, 1/4 for PEC); one medium of the
+        // two-region form (mode 3): A = <f_m, L f_n>, B = <f_m, Kbar f_n>, no identity terms
         double gA = (mode == 0) ? 1.0 : 0.25;
         zd A = zmk(P.x - gA * G, P.y);
         zd B = zmk(Q.x - 0.5 * X, Q.y);
+        if (mode == 3) {
+            A = Lm;
+            B = Km;
+        }
         int64_t o = seg + (int64_t)ml * ncol + c0 + nl;
-        if (mode == 0) {
+        if (mode == 0 || mode == 3) {
             out[4 * o + 0] = (T)A.x;
             out[4 * o + 1] = (T)A.y;
             out[4 * o + 2] = (T)B.x;
@@ -819,8 +826,9 @@ template <typename T>
 __global__ void k_patterns(int N, int K, int nph, const double* __restrict__ theta, const int* __restrict__ leaf_of,
                            const double* __restrict__ centers, const int* __restrict__ rwg_t, const int* __restrict__ rwg_l,
                            const double* __restrict__ rwg_len, const double* __restrict__ tri, const double* __restrict__ nrm,
-                           const double* __restrict__ area, double k, double ki, T* __restrict__ F, T* __restrict__ RX) {
-    const int Kh = ki != 0.0 ? K : K / 2;
+                           const double* __restrict__ area, double k, double ki, int full, T* __restrict__ F,
+                           T* __restrict__ RX) {
+    const int Kh = full ? K : K / 2;
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)N * Kh) return;
     int n = (int)(idx / Kh), kk = (int)(idx % Kh);
@@ -1172,10 +1180,10 @@ void bi_fill_near(bi_handle_s* h) {
     for (int b = 0; b < LF.nbox; ++b)
         for (int q = h->near_ptr[b]; q < h->near_ptr[b + 1]; ++q) blk_box[q] = b;
     int* d_blk_box = h->upload(blk_box);
-    size_t per = (h->prm.op_mode == 0 ? 2 : 1) * h->csize;
+    size_t per = (h->prm.op_mode == 0 || h->prm.op_mode == 3 ? 2 : 1) * h->csize;
     h->d_near = h->alloc(per * (size_t)std::max<int64_t>(h->near_nnz, 1));
     const char* env_fill = std::getenv("BI_NEAR_FILL_SINGLE_PASS");
-    const bool two_pass = !(env_fill && env_fill[0] == '1') && h->ki == 0.0;
+    const bool two_pass = !(env_fill && env_fill[0] == '1') && h->ki == 0.0 && h->prm.op_mode != 3;
     if (nblk > 0 && two_pass) {
         // per-class lists of singular / near-singular triangle pairs, counted first and sized exactly
         unsigned long long* d_count = nullptr;
@@ -1346,7 +1354,9 @@ void bi_fill_patterns(bi_handle_s* h) {
     if (h->leaf < 2) return;
     const level_t& LF = h->lev[h->leaf];
     double* d_theta = h->upload(LF.theta);
-    const int Ks = h->ki != 0.0 ? LF.K : LF.K / 2;   // stored directions (all of them at complex k)
+    // stored directions: all of them at complex k and for one medium of the two-region form
+    const int full = (h->ki != 0.0 || h->prm.op_mode == 3) ? 1 : 0;
+    const int Ks = full ? LF.K : LF.K / 2;
     size_t nel = (size_t)h->N * Ks * 2;
     h->d_F = h->alloc(nel * h->csize);
     h->d_RX = h->alloc(nel * h->csize);
@@ -1356,11 +1366,11 @@ void bi_fill_patterns(bi_handle_s* h) {
     if (h->prec == 0)
         k_patterns<double><<<(unsigned)nb, th, 0, h->stream>>>(h->N, LF.K, LF.nph, d_theta, h->d_leaf_of, h->d_leaf_center,
                                                                 h->d_rwg_t, h->d_rwg_l, h->d_rwg_len, h->d_tri, h->d_tri_n,
-                                                                h->d_tri_area, h->k, h->ki, (double*)h->d_F, (double*)h->d_RX);
+                                                                h->d_tri_area, h->k, h->ki, full, (double*)h->d_F, (double*)h->d_RX);
     else
         k_patterns<float><<<(unsigned)nb, th, 0, h->stream>>>(h->N, LF.K, LF.nph, d_theta, h->d_leaf_of, h->d_leaf_center,
                                                                h->d_rwg_t, h->d_rwg_l, h->d_rwg_len, h->d_tri, h->d_tri_n,
-                                                               h->d_tri_area, h->k, h->ki, (float*)h->d_F, (float*)h->d_RX);
+                                                               h->d_tri_area, h->k, h->ki, full, (float*)h->d_F, (float*)h->d_RX);
     CU(cudaGetLastError());
 }
 
@@ -1471,7 +1481,7 @@ void bi_alloc_work(bi_handle_s* h) {
     h->d_yfar = h->alloc(vec);
     h->d_sx = h->alloc((size_t)h->nun * R * h->csize);
     h->d_sy = h->alloc((size_t)h->nun * R * h->csize);
-    const int E = 2 * R;
+    const int E = 2 * h->nF * R;
     for (int l = 2; l <= h->leaf; ++l) {
         level_t& L = h->lev[l];
         size_t sz = (size_t)L.nbox * L.K * E * h->csize;

@@ -23,7 +23,7 @@ template <typename T>
 __global__ void k_rhs(int N, int nX, int nun, int nrhs, const int* __restrict__ perm, const int* __restrict__ rwg_t,
                       const int* __restrict__ rwg_l, const double* __restrict__ rwg_len, const double* __restrict__ tri,
                       const double* __restrict__ nrm, const double* __restrict__ area, const double* __restrict__ kp, double k,
-                      T* __restrict__ b) {
+                      int two_region, T* __restrict__ b) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= N * nrhs) return;
     int t = idx % N, s = idx / N;
@@ -56,8 +56,14 @@ __global__ void k_rhs(int N, int nX, int nun, int nrhs, const int* __restrict__ 
             }
             double sn, cs;
             sincos(-k * (kh[0] * r[0] + kh[1] * r[1] + kh[2] * r[2]), &sn, &cs);
-            double vJ = 0.5 * (f[0] * (ph[0] + nH[0]) + f[1] * (ph[1] + nH[1]) + f[2] * (ph[2] + nH[2]));
-            double vM = 0.5 * (f[0] * (hp[0] - nE[0]) + f[1] * (hp[1] - nE[1]) + f[2] * (hp[2] - nE[2]));
+            double vJ, vM;
+            if (two_region) {   // -<f, E_inc>, -<f, H_inc>: tangential E and H matched across the surface
+                vJ = -(f[0] * ph[0] + f[1] * ph[1] + f[2] * ph[2]);
+                vM = -(f[0] * hp[0] + f[1] * hp[1] + f[2] * hp[2]);
+            } else {
+                vJ = 0.5 * (f[0] * (ph[0] + nH[0]) + f[1] * (ph[1] + nH[1]) + f[2] * (ph[2] + nH[2]));
+                vM = 0.5 * (f[0] * (hp[0] - nE[0]) + f[1] * (hp[1] - nE[1]) + f[2] * (hp[2] - nE[2]));
+            }
             bJr += vJ * cs; bJi += vJ * sn;
             bMr += vM * cs; bMi += vM * sn;
         }
@@ -248,11 +254,11 @@ void bi_rhs_launch(bi_handle_s* h, const double* khat, const double* phat, int n
     if (h->prec == 0)
         k_rhs<double><<<nb(tot, 128), 128, 0, h->stream>>>(h->N, h->nX, h->nun, nrhs, h->d_perm, h->d_rwg_t, h->d_rwg_l,
                                                             h->d_rwg_len, h->d_tri, h->d_tri_n, h->d_tri_area, d_kp, h->k,
-                                                            (double*)b);
+                                                            h->prm.op_mode == 3, (double*)b);
     else
         k_rhs<float><<<nb(tot, 128), 128, 0, h->stream>>>(h->N, h->nX, h->nun, nrhs, h->d_perm, h->d_rwg_t, h->d_rwg_l,
                                                            h->d_rwg_len, h->d_tri, h->d_tri_n, h->d_tri_area, d_kp, h->k,
-                                                           (float*)b);
+                                                           h->prm.op_mode == 3, (float*)b);
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(h->stream));
     // the small parameter buffer is released with the handle's other scratch at bi_destroy

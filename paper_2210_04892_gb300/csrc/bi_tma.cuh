@@ -74,3 +74,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 // Device status word of a handle: 0 while healthy; kernels that give up a wait store a code.
 #define BI_DEVSTATUS_TMA_TIMEOUT 1
+
+// Thread 0 of a CTA whose ring of S stages (one mbarrier each, chunk c on stage c % S with
+// parity (c / S) & 1) gave up waiting at chunk `first`: wait again, with the default limit of
+// about one second, for the chunks still in flight so that no copy lands after the CTA has
+// left, then record the failure in the status word.
+__device__ __forceinline__ void bulk_give_up(uint64_t* bar, int first, int nchunks, int S, int* status) {
+    if (threadIdx.x != 0) return;
+    for (int c = first; c < first + S && c < nchunks; ++c) mbar_wait_bounded(&bar[c % S], (c / S) & 1);
+    atomicExch(status, BI_DEVSTATUS_TMA_TIMEOUT);
+}

@@ -10,9 +10,9 @@
 // in shared memory; every child's V is written once, without atomics.  One right-hand side
 // (E = 2): each lane carries both components of its direction.
 //
-// Several right-hand sides (E = 2R > 2): thread = (direction k, pair of adjacent entries of
-// the E-vector of k), so a CTA reads a contiguous tile of D directions x E entries of each
-// source and the R threads of a direction share every operator value (one broadcast load).
+// Several right-hand sides (E = 2R > 2): thread = (direction k, one or two pairs of adjacent
+// entries of the E-vector of k), so a CTA reads a contiguous tile of D directions x E entries of
+// each source and the threads of a direction share every operator value (one broadcast load).
 // CTAs run parents fastest: the CTAs resident at one time work on one direction tile of
 // neighbouring parents, whose sources and the tile of the 343 operators stay in L2/L1.
 #include <algorithm>
@@ -94,60 +94,95 @@ __device__ __forceinline__ void store_pair(cpx<float>* p, cpx<float> a, cpx<floa
     *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
 }
 
-template <typename T>
+template <typename T, int VP>
 __global__ void __launch_bounds__(256) k_translate_pcE(int K, int R, int D, int np, const int* __restrict__ cptr,
                                                        const int* __restrict__ tptr, const int* __restrict__ src,
                                                        const uint4* __restrict__ codes, const cpx<T>* __restrict__ Top,
                                                        const cpx<T>* __restrict__ U, cpx<T>* __restrict__ V) {
+    // thread = (direction, VP consecutive pairs of entries); the next source's entries and
+    // offset codes are loaded one iteration ahead
     const int p = (int)(blockIdx.x % (unsigned)np);
     const int chunk = (int)(blockIdx.x / (unsigned)np);
-    const int d = threadIdx.x / R, j = threadIdx.x - d * R;
+    const int TPD = R / VP;                    // threads per direction
+    const int d = threadIdx.x / TPD, j = threadIdx.x - d * TPD;
     const int k = chunk * D + d;
     if (d >= D || k >= K) return;   // no barrier below
     const int64_t E = 2 * R;
     const int c0 = cptr[p], nc = cptr[p + 1] - c0;
-    cpx<T> a0[8], a1[8];
+    cpx<T> acc[8][2 * VP];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) a0[i] = a1[i] = czero<T>();
-    const cpx<T>* ub = U + (int64_t)k * E + 2 * j;
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int v = 0; v < 2 * VP; ++v) acc[i][v] = czero<T>();
+    const cpx<T>* ub = U + (int64_t)k * E + 2 * VP * j;
     const cpx<T>* tk = Top + k;
     const int64_t box = (int64_t)K * E;
-#pragma unroll 4
-    for (int q = tptr[p]; q < tptr[p + 1]; ++q) {
-        const int s = src[q];
-        const uint4 cw = codes[q];
-        const unsigned cc[4] = {cw.x, cw.y, cw.z, cw.w};
-        cpx<T> u0, u1;
-        load_pair(ub + (int64_t)s * box, u0, u1);
+    const int q0 = tptr[p], q1 = tptr[p + 1];
+    cpx<T> un[2 * VP];
+    uint4 cn = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+    if (q0 < q1) {
+        const cpx<T>* us = ub + (int64_t)src[q0] * box;
+#pragma unroll
+        for (int v = 0; v < VP; ++v) load_pair(us + 2 * v, un[2 * v], un[2 * v + 1]);
+        cn = codes[q0];
+    }
+    for (int q = q0; q < q1; ++q) {
+        cpx<T> u[2 * VP];
+#pragma unroll
+        for (int v = 0; v < 2 * VP; ++v) u[v] = un[v];
+        const unsigned cc[4] = {cn.x, cn.y, cn.z, cn.w};
+        if (q + 1 < q1) {
+            const cpx<T>* us = ub + (int64_t)src[q + 1] * box;
+#pragma unroll
+            for (int v = 0; v < VP; ++v) load_pair(us + 2 * v, un[2 * v], un[2 * v + 1]);
+            cn = codes[q + 1];
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const unsigned code = (cc[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
             if (code != kNone) {
                 const cpx<T> t = ldg_cpx(tk + (int64_t)code * K);
-                cfma(a0[i], t, u0);
-                cfma(a1[i], t, u1);
+#pragma unroll
+                for (int v = 0; v < 2 * VP; ++v) cfma(acc[i][v], t, u[v]);
             }
         }
     }
-    cpx<T>* vb = V + (int64_t)c0 * box + (int64_t)k * E + 2 * j;
+    cpx<T>* vb = V + (int64_t)c0 * box + (int64_t)k * E + 2 * VP * j;
 #pragma unroll
     for (int i = 0; i < 8; ++i)
-        if (i < nc) store_pair(vb + i * box, a0[i], a1[i]);
+        if (i < nc)
+#pragma unroll
+            for (int v = 0; v < VP; ++v) store_pair(vb + i * box + 2 * v, acc[i][2 * v], acc[i][2 * v + 1]);
 }
 
 template <typename T>
-void launch_tE(bi_handle_s* h, int l, int E, cudaStream_t s) {
+bool launch_tE(bi_handle_s* h, int l, int E, cudaStream_t s, int vp_force) {
     level_t& L = h->lev[l];
     const int R = E / 2;
-    const int D = std::max(1, 256 / R);
-    const int threads = std::min(1024, (D * R + 31) / 32 * 32);
+    // two pairs per thread when R is even (FP32): the code decode and operator loads serve twice
+    // the multiply-adds
+    int VP = (R % 2 == 0 && sizeof(T) == 4) ? 2 : 1;
+    if (vp_force == 1) VP = 1;
+    if (vp_force == 2) {
+        if (R % 2 != 0) return false;
+        VP = 2;
+    }
+    const int TPD = R / VP;
+    const int D = std::max(1, 256 / TPD);
+    const int threads = std::min(1024, (D * TPD + 31) / 32 * 32);
     const int64_t nchunk = (L.K + D - 1) / D;
     const int64_t blocks = nchunk * L.tp_np;
     if (blocks > 0x7fffffffLL) throw bi_error{BI_ERR_ARG, "translation grid too large"};
-    k_translate_pcE<T><<<(unsigned)blocks, threads, 0, s>>>(L.K, R, D, L.tp_np, L.d_tp_cptr, L.d_tp_ptr, L.d_tp_src,
-                                                             (const uint4*)L.d_tp_code, (const cpx<T>*)L.d_T,
-                                                             (const cpx<T>*)L.d_U, (cpx<T>*)L.d_V);
+    if (VP == 2)
+        k_translate_pcE<T, 2><<<(unsigned)blocks, threads, 0, s>>>(L.K, R, D, L.tp_np, L.d_tp_cptr, L.d_tp_ptr, L.d_tp_src,
+                                                                    (const uint4*)L.d_tp_code, (const cpx<T>*)L.d_T,
+                                                                    (const cpx<T>*)L.d_U, (cpx<T>*)L.d_V);
+    else
+        k_translate_pcE<T, 1><<<(unsigned)blocks, threads, 0, s>>>(L.K, R, D, L.tp_np, L.d_tp_cptr, L.d_tp_ptr, L.d_tp_src,
+                                                                    (const uint4*)L.d_tp_code, (const cpx<T>*)L.d_T,
+                                                                    (const cpx<T>*)L.d_U, (cpx<T>*)L.d_V);
     CU(cudaGetLastError());
+    return true;
 }
 
 template <typename T>
@@ -243,8 +278,8 @@ bool bi_translate_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
         if (h->prec == 0) launch_t<double>(h, l, s);
         else launch_t<float>(h, l, s);
     } else if (E <= 512) {
-        if (h->prec == 0) launch_tE<double>(h, l, E, s);
-        else launch_tE<float>(h, l, E, s);
+        const int v = h->force_variant >= 0 ? h->force_variant : h->variant_of(0, l, E);
+        return h->prec == 0 ? launch_tE<double>(h, l, E, s, v) : launch_tE<float>(h, l, E, s, v);
     } else {
         return false;
     }

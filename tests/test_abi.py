@@ -78,6 +78,7 @@ def test_every_entry_point_rejects_null_handles():
     assert L.bi_farfield_noalloc(None, None, 1, None, 1, None) == E
     assert L.bi_debug_copy(None, 0, 0, None, 0) == E
     assert L.bi_debug_set_wait_limit(None, 1) == E
+    assert L.bi_tuned_config(None, None, 0) == E
     assert L.bi_profile_stages(None, None, None, 1, 1, None) == E
     assert L.bi_device_status(None) == E
     L.bi_destroy(None)
