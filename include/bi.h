@@ -175,6 +175,18 @@ int bi_rhs_planewave(bi_handle h, const double* khat, const double* phat, int nr
  * column missed tol (x holds the last iterate). */
 int bi_solve(bi_handle h, const void* rhs, void* x, int nrhs, double tol, int* iters, double* relres);
 
+/* Mixed-precision iterative refinement of C x = rhs (Sec. II.E's GMRES, no counterpart in the
+ * paper for the precision split): each step solves C d = r with h's GMRES to 1e-3 of r (h
+ * normally FP32), adds d to x in FP64, and recomputes r = rhs - C x with the FP64 handle h_ref
+ * of the same surface, wavenumber and operator mode; it stops when ||r|| / ||rhs|| <= tol for
+ * every column or after 20 steps.  Reaches tolerances below the working product's rounding floor
+ * (about 1e-4 in FP32).  rhs, x: device complex128, column-major [nrhs][n_unknowns];
+ * iters: host [nrhs] inner GMRES iterations in total; relres: host [nrhs] the final FP64
+ * residuals.  Allocates its work vectors for the call.  BI_ERR_NOT_CONVERGED when a column
+ * missed tol; BI_ERR_ARG when h_ref is not FP64 or does not match h. */
+int bi_solve_refined(bi_handle h, bi_handle h_ref, const void* rhs, void* x, int nrhs, double tol, int* iters,
+                     double* relres);
+
 /* Coupling with an interior discretisation (Eq. 52; Sec. II.E steps 2(a)-(e)).  Once set,
  * bi_solve solves the reduced system (C - D^{X Lambda} Q^{-1} D^{Lambda X}) x = rhs and
  * bi_matvec_coupled applies that operator; bi_matvec keeps applying C alone.

@@ -27,7 +27,7 @@ _NAMES = {0: "BI_OK", -1: "BI_ERR_ARG", -2: "BI_ERR_MESH", -3: "BI_ERR_OOM", -4:
 
 # entry points declared in include/bi.h
 EXPORTS = ["bi_default_params", "bi_setup", "bi_num_unknowns", "bi_rwg_edges", "bi_get_info", "bi_matvec",
-           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_debug_set_wait_limit", "bi_tuned_config", "bi_profile_stages", "bi_stage_name", "bi_last_error", "bi_device_status", "bi_set_coupling", "bi_matvec_coupled", "bi_plan_create", "bi_plan_info", "bi_plan_get",
+           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_solve_refined", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_debug_set_wait_limit", "bi_tuned_config", "bi_profile_stages", "bi_stage_name", "bi_last_error", "bi_device_status", "bi_set_coupling", "bi_matvec_coupled", "bi_plan_create", "bi_plan_info", "bi_plan_get",
            "bi_plan_last_error", "bi_plan_destroy",
            "bi_destroy", "bi_server_default_params", "bi_server_create", "bi_submit", "bi_poll", "bi_result",
            "bi_release", "bi_server_last_error", "bi_server_destroy"]
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
     L.bi_matvec_host.argtypes = [vp, vp, vp, i]
     L.bi_rhs_planewave.argtypes = [vp, vp, vp, i, vp]
     L.bi_solve.argtypes = [vp, vp, vp, i, d, vp, vp]
+    L.bi_solve_refined.argtypes = [vp, vp, vp, vp, i, d, vp, vp]
     L.bi_farfield.argtypes = [vp, vp, i, vp, i, vp]
     L.bi_farfield_noalloc.argtypes = [vp, vp, i, vp, i, vp]
     L.bi_debug_copy.argtypes = [vp, i, i, vp, i64]
@@ -263,6 +264,24 @@ class Operator:
         its = np.zeros(R, np.int32)
         rel = np.zeros(R, np.float64)
         rc = load().bi_solve(self.h, b.data_ptr(), x.data_ptr(), R, float(tol), its.ctypes.data, rel.ctypes.data)
+        if rc not in (BI_OK, BI_ERR_NOT_CONVERGED):
+            _check(rc, self.h)
+        return x, its, rel
+
+    def solve_refined(self, ref, b, tol=1e-4):
+        """Iterative refinement: inner GMRES on this operator, residuals with the FP64 operator
+        `ref` of the same surface; b complex128 on the GPU.  Returns (x complex128, iterations,
+        relative FP64 residuals)."""
+        import torch
+        b = b.to(torch.complex128).contiguous()
+        if b.dim() == 1:
+            b = b.view(1, -1)
+        x = torch.empty_like(b)
+        R = b.shape[0]
+        its = np.zeros(R, np.int32)
+        rel = np.zeros(R, np.float64)
+        rc = load().bi_solve_refined(self.h, ref.h, b.data_ptr(), x.data_ptr(), R, float(tol), its.ctypes.data,
+                                     rel.ctypes.data)
         if rc not in (BI_OK, BI_ERR_NOT_CONVERGED):
             _check(rc, self.h)
         return x, its, rel

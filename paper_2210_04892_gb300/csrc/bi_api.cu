@@ -483,6 +483,18 @@ extern "C" int bi_solve(bi_handle h, const void* rhs, void* x, int nrhs, double 
     return guarded(h, [&] { return bi_gmres(h, rhs, x, nrhs, tol, iters, relres); });
 }
 
+extern "C" int bi_solve_refined(bi_handle h, bi_handle h_ref, const void* rhs, void* x, int nrhs, double tol, int* iters,
+                                double* relres) {
+    if (!h || !h_ref) return BI_ERR_ARG;
+    if (!rhs || !x || nrhs < 1 || nrhs > h->max_rhs || nrhs > h_ref->max_rhs || !(tol > 0) || h_ref->prec != 0 ||
+        h_ref->nun != h->nun || h_ref->prm.op_mode != h->prm.op_mode || h_ref->N != h->N) {
+        h->err = "bi_solve_refined: null vector, nrhs outside [1, max_rhs], tol <= 0, or h_ref not an FP64 handle of "
+                 "the same operator";
+        return BI_ERR_ARG;
+    }
+    return guarded(h, [&] { return bi_solve_refined_impl(h, h_ref, rhs, x, nrhs, tol, iters, relres); });
+}
+
 extern "C" const char* bi_last_error(bi_handle h) { return h ? h->err.c_str() : g_setup_error.c_str(); }
 
 extern "C" void bi_destroy(bi_handle h) {

@@ -299,6 +299,8 @@ size_t bi_farfield_scratch_bytes(const bi_handle_s* h, int nrhs, int ndir);
 void bi_farfield_launch(bi_handle_s* h, const void* x, int nrhs, const double* dirs, int ndir, void* F, double* part,
                         cudaStream_t s);
 int bi_gmres(bi_handle_s* h, const void* rhs, void* x, int nrhs, double tol, int* iters, double* relres);
+int bi_solve_refined_impl(bi_handle_s* h, bi_handle_s* href, const void* rhs, void* x, int R, double tol, int* iters,
+                          double* relres);
 // resumable GMRES (serving loop)
 struct gmres_ctx;
 gmres_ctx* bi_gmres_create(bi_handle_s* h, const void* rhs, int nrhs, double tol, cudaStream_t s);

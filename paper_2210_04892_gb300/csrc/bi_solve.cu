@@ -528,3 +528,89 @@ int bi_gmres(bi_handle_s* h, const void* rhs, void* xout, int R, double tol, int
     }
     return c.finish(xout, iters, relres);
 }
+
+// ---------------------------------------------------------------------------------
+// Mixed-precision iterative refinement: the working handle's GMRES (FP32 products) solves the
+// correction equation C d = r to a loose tolerance, d is added to x in FP64, and the residual
+// r = b - C x is recomputed with an FP64 handle of the same operator.  The working product's
+// rounding floor (about 1e-4 in FP32) then limits only the inner solves, not the solution.
+namespace {
+template <typename T>
+__global__ void k_add_to64(int64_t n, const T* __restrict__ d, z2* __restrict__ x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        x[i].x += (double)d[2 * i];
+        x[i].y += (double)d[2 * i + 1];
+    }
+}
+}  // namespace
+
+int bi_solve_refined_impl(bi_handle_s* h, bi_handle_s* href, const void* rhs, void* xout, int R, double tol, int* iters,
+                          double* relres) {
+    const int64_t nun = h->nun, nv = nun * R;
+    const int th = 256;
+    cudaStream_t s = href->stream;
+    std::vector<void*> bufs;
+    auto A = [&](size_t bytes) {
+        void* p = nullptr;
+        CU(cudaMalloc(&p, bytes));
+        bufs.push_back(p);
+        return p;
+    };
+    int status = BI_OK;
+    try {
+        z2* b = (z2*)rhs;
+        z2* x = (z2*)xout;
+        z2* r = (z2*)A(sizeof(z2) * nv);
+        z2* ax = (z2*)A(sizeof(z2) * nv);
+        void* rl = A(h->csize * nv);
+        void* d = A(h->csize * nv);
+        double* nrm = (double*)A(sizeof(double) * R);
+        std::vector<double> bn(R), rn(R);
+        CU(cudaMemsetAsync(x, 0, sizeof(z2) * nv, s));
+        CU(cudaMemcpyAsync(r, b, sizeof(z2) * nv, cudaMemcpyDeviceToDevice, s));
+        k_norms<<<R, 256, 0, s>>>((int)nun, b, nrm);
+        CU(cudaMemcpyAsync(bn.data(), nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        std::vector<int> its(R, 0), it1(R);
+        std::vector<double> rel1(R);
+        rn = bn;
+        for (int step = 0; step < 20; ++step) {
+            bool done = true;
+            for (int c = 0; c < R; ++c) done = done && (bn[c] == 0.0 || rn[c] <= tol * bn[c]);
+            if (done) break;
+            // C d = r in the working precision, to 1e-3 of r (above its rounding floor)
+            if (h->prec == 0) k_cvt_to<double><<<nb(nv, th), th, 0, s>>>(nv, r, (double*)rl);
+            else k_cvt_to<float><<<nb(nv, th), th, 0, s>>>(nv, r, (float*)rl);
+            CU(cudaGetLastError());
+            CU(cudaStreamSynchronize(s));
+            const int st = bi_gmres(h, rl, d, R, 1e-3, it1.data(), rel1.data());
+            if (st != BI_OK && st != BI_ERR_NOT_CONVERGED) throw bi_error{st, h->err};
+            for (int c = 0; c < R; ++c) its[c] += it1[c];
+            CU(cudaStreamSynchronize(h->stream));
+            if (h->prec == 0) k_add_to64<double><<<nb(nv, th), th, 0, s>>>(nv, (const double*)d, x);
+            else k_add_to64<float><<<nb(nv, th), th, 0, s>>>(nv, (const float*)d, x);
+            CU(cudaGetLastError());
+            // r = b - C x with the FP64 product
+            bi_operator_launch(href, x, ax, R, s);
+            k_residual<<<nb(nv, th), th, 0, s>>>(nv, b, ax, r);
+            k_norms<<<R, 256, 0, s>>>((int)nun, r, nrm);
+            CU(cudaMemcpyAsync(rn.data(), nrm, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+        }
+        status = bi_take_device_status(href);
+        if (status == BI_OK) status = bi_take_device_status(h);
+        for (int c = 0; c < R; ++c) {
+            const double rel = bn[c] > 0 ? rn[c] / bn[c] : 0.0;
+            if (iters) iters[c] = its[c];
+            if (relres) relres[c] = rel;
+            if (status == BI_OK && rel > tol * 1.0001 + 1e-15) status = BI_ERR_NOT_CONVERGED;
+        }
+    } catch (...) {
+        for (void* p : bufs) cudaFree(p);
+        throw;
+    }
+    for (void* p : bufs) cudaFree(p);
+    return status;
+}
+

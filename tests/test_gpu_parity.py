@@ -414,6 +414,32 @@ def test_pec_sphere_solve_rcs_vs_mie(bi, nu, radius, tol):
     op.close()
 
 
+@pytest.mark.parametrize("mode,tol", [(1, 1e-5), (0, 1e-4)])
+def test_c2_refined_solve_below_the_fp32_floor(bi, mode, tol):
+    """Iterative refinement on the 61,440-unknown sphere (r = 2 lambda): FP32 GMRES corrections,
+    residuals from an FP64 operator of the same surface.  The true residual, recomputed here
+    by the FP64 product, meets tol below the FP32 product's rounding floor; for the PEC
+    operator the RCS still matches the Mie series."""
+    from oracle import mie
+    v, t = icosphere(32, 2.0)
+    op = bi.Operator(v, t, K0, precision="fp32", op_mode=mode, max_rhs=1)
+    ref = bi.Operator(v, t, K0, precision="fp64", op_mode=mode, max_rhs=1)
+    b = ref.rhs_planewave([0, 0, 1.0], [1.0, 0, 0])
+    x, its, relres = op.solve_refined(ref, b, tol=tol)
+    assert relres[0] <= tol * 1.001
+    r = ref.matvec(x) - b
+    assert float(r.norm() / b.norm()) <= tol * 1.001
+    if mode == 1:
+        th = np.deg2rad(np.arange(0, 181))
+        dirs = np.stack([np.sin(th), 0 * th, np.cos(th)], 1)
+        s = ref.rcs(x, dirs)[0]
+        sm = mie.rcs_pec(K0, 2.0, th)
+        mask = 10 * np.log10(sm) >= 10 * np.log10(sm.max()) - 20
+        assert np.abs(10 * np.log10(s / sm))[mask].max() < 0.5
+    op.close()
+    ref.close()
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_two_pass_near_fill_matches_single_pass(bi, mode, monkeypatch):
     """The default near-field fill (separated triangle pairs in FP32, the rest in FP64) against
