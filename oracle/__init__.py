@@ -19,6 +19,8 @@ Functions (each cites the passage it follows):
                               operators at k0, interior at k1 = k0 sqrt(eps_r mu_r)
   coated_pec(...)             the same for a PEC core under a coat (the object of Sec. III.A)
 Mie series for PEC, dielectric and coated PEC spheres: oracle.mie.
+Coupling blocks D^{X Lambda}, D^{Lambda X} of the hybrid system (Eqs. 40a/b, 47, 48):
+oracle.coupling.
 
 Complex wavenumbers (lossy media, Im k < 0 with exp(j w t)) are accepted by fill, rows,
 operators and pair_blocks.
