@@ -204,6 +204,26 @@ int bi_solve_refined(bi_handle h, bi_handle h_ref, const void* rhs, void* x, int
 typedef void (*bi_qsolve_fn)(void* user, const void* in, void* out, int nrhs, void* stream);
 int bi_set_coupling(bi_handle h, int64_t n_int, const int* dlx_ptr, const int* dlx_col, const void* dlx_val,
                     const int* dxl_ptr, const int* dxl_col, const void* dxl_val, bi_qsolve_fn qsolve, void* user);
+/* The coupling blocks of Eq. 42 on the handle's surface, in the CSR form bi_set_coupling takes:
+ *   D^{X Lambda} = [D^{J Lambda}; D^{M Lambda}], n_unknowns rows (J rows then M rows):
+ *     D^{J Lambda}_mn = -1/2 <f_m, n x eta_n>   (Eq. 47),  D^{M Lambda}_mn = 1/2 <f_m, eta_n>  (Eq. 48);
+ *   D^{Lambda X} = [D^{Lambda J}, D^{Lambda M}], n_lambda rows, columns [0, n_unknowns):
+ *     D^{Lambda J}_mn = -<eta_m, n x f_n>       (Eq. 40a), D^{Lambda M}_mn = -<eta_m, f_n>     (Eq. 40b).
+ * f are the RWG functions of bi_rwg_edges; eta the zeroth-order edge functions of Eq. exp3 on
+ * the surface triangles, eta = l_ab (lambda_a grad lambda_b - lambda_b grad lambda_a) for the
+ * edge (a, b), a the smaller vertex number (tangential component 1 from a to b); n the outward
+ * normal.  conforming = 0: one eta per (triangle t, local edge k opposite vertex k of t),
+ * n_lambda = 3 nt, index 3 t + k (the face-wise trace space of a hybridised method);
+ * conforming = 1: one eta per mesh edge in the RWG order, the sum of its two face functions,
+ * n_lambda = N.  op_mode 0 only.
+ * sizes: host int64 [3], set to (n_lambda, nnz of D^{X Lambda}, nnz of D^{Lambda X}).  With
+ * all six arrays null only the sizes are returned; otherwise all six are device arrays:
+ * *_ptr int32 [rows + 1], *_col int32 [nnz] (ascending within a row), *_val complex [nnz] of
+ * the handle precision (imaginary parts 0).  Computed on the handle's stream; returns once
+ * the arrays are written.  BI_ERR_ARG for another op_mode, bad conforming or a partial set
+ * of arrays. */
+int bi_coupling_blocks(bi_handle h, int conforming, int64_t* sizes, int* dxl_ptr, int* dxl_col, void* dxl_val,
+                       int* dlx_ptr, int* dlx_col, void* dlx_val);
 /* y = (C - D^{X Lambda} Q^{-1} D^{Lambda X}) x, the product of steps 2(a)-(e); same
  * arguments and stream behaviour as bi_matvec.  BI_ERR_ARG when no coupling is set. */
 int bi_matvec_coupled(bi_handle h, const void* x, void* y, int nrhs);

@@ -27,7 +27,7 @@ _NAMES = {0: "BI_OK", -1: "BI_ERR_ARG", -2: "BI_ERR_MESH", -3: "BI_ERR_OOM", -4:
 
 # entry points declared in include/bi.h
 EXPORTS = ["bi_default_params", "bi_setup", "bi_num_unknowns", "bi_rwg_edges", "bi_get_info", "bi_matvec",
-           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_solve_refined", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_debug_set_wait_limit", "bi_tuned_config", "bi_profile_stages", "bi_stage_name", "bi_last_error", "bi_device_status", "bi_set_coupling", "bi_matvec_coupled", "bi_plan_create", "bi_plan_info", "bi_plan_get",
+           "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_solve_refined", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_debug_set_wait_limit", "bi_tuned_config", "bi_profile_stages", "bi_stage_name", "bi_last_error", "bi_device_status", "bi_set_coupling", "bi_coupling_blocks", "bi_matvec_coupled", "bi_plan_create", "bi_plan_info", "bi_plan_get",
            "bi_plan_last_error", "bi_plan_destroy",
            "bi_destroy", "bi_server_default_params", "bi_server_create", "bi_submit", "bi_poll", "bi_result",
            "bi_release", "bi_server_last_error", "bi_server_destroy"]
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH):
     L.bi_last_error.restype = ctypes.c_char_p
     L.bi_device_status.argtypes = [vp]
     L.bi_set_coupling.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, QSOLVE, vp]
+    L.bi_coupling_blocks.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp]
     L.bi_matvec_coupled.argtypes = [vp, vp, vp, i]
     L.bi_plan_create.argtypes = [vp, i, vp, i, d, ctypes.POINTER(Params), ctypes.POINTER(vp)]
     L.bi_plan_info.argtypes = [vp, ctypes.POINTER(Info)]
@@ -295,6 +296,25 @@ class Operator:
         _check(load().bi_profile_stages(self.h, x.data_ptr(), y.data_ptr(), x.shape[0], int(reps), ms.ctypes.data),
                self.h)
         return {load().bi_stage_name(i).decode(): float(ms[i]) for i in range(8)}
+
+    def coupling_blocks(self, conforming=False):
+        """The coupling blocks of Eqs. 40a/b, 47, 48 on this surface, computed on the GPU:
+        returns (n_lambda, dlx, dxl) with dlx = (ptr, col, val) of D^{Lambda X} and dxl of
+        D^{X Lambda} as CUDA tensors, ready for set_coupling."""
+        import torch
+        L = load()
+        sizes = np.zeros(3, np.int64)
+        _check(L.bi_coupling_blocks(self.h, int(bool(conforming)), sizes.ctypes.data, None, None, None, None, None,
+                                    None), self.h)
+        nL, nxl, nlx = (int(v) for v in sizes)
+        i32 = dict(dtype=torch.int32, device="cuda")
+        xl = (torch.empty(self.n_unknowns + 1, **i32), torch.empty(nxl, **i32),
+              torch.empty(nxl, dtype=self.cdtype, device="cuda"))
+        lx = (torch.empty(nL + 1, **i32), torch.empty(nlx, **i32), torch.empty(nlx, dtype=self.cdtype, device="cuda"))
+        _check(L.bi_coupling_blocks(self.h, int(bool(conforming)), sizes.ctypes.data, xl[0].data_ptr(),
+                                    xl[1].data_ptr(), xl[2].data_ptr(), lx[0].data_ptr(), lx[1].data_ptr(),
+                                    lx[2].data_ptr()), self.h)
+        return nL, lx, xl
 
     def set_coupling(self, n_int, dlx, dxl, qsolve):
         """Couple to an interior discretisation (Eq. 52).  dlx = (ptr, col, val) of

@@ -415,6 +415,25 @@ extern "C" int bi_set_coupling(bi_handle h, int64_t n_int, const int* dlx_ptr, c
     });
 }
 
+extern "C" int bi_coupling_blocks(bi_handle h, int conforming, int64_t* sizes, int* dxl_ptr, int* dxl_col,
+                                  void* dxl_val, int* dlx_ptr, int* dlx_col, void* dlx_val) {
+    if (!h) return BI_ERR_ARG;
+    if (h->med[0] || h->prm.op_mode != 0) {
+        h->err = "bi_coupling_blocks: needs the C-block operator (op_mode 0: unknowns [J; M])";
+        return BI_ERR_ARG;
+    }
+    const bool none = !dxl_ptr && !dxl_col && !dxl_val && !dlx_ptr && !dlx_col && !dlx_val;
+    const bool all = dxl_ptr && dxl_col && dxl_val && dlx_ptr && dlx_col && dlx_val;
+    if (!sizes || (conforming != 0 && conforming != 1) || !(none || all)) {
+        h->err = "bi_coupling_blocks: null sizes, conforming not 0 or 1, or some but not all CSR arrays null";
+        return BI_ERR_ARG;
+    }
+    return guarded(h, [&] {
+        bi_coupling_blocks_impl(h, conforming, sizes, dxl_ptr, dxl_col, dxl_val, dlx_ptr, dlx_col, dlx_val);
+        return (int)BI_OK;
+    });
+}
+
 extern "C" int bi_matvec_coupled(bi_handle h, const void* x, void* y, int nrhs) {
     if (!h) return BI_ERR_ARG;
     if (!h->cpl.qsolve) {

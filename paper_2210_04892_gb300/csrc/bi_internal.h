@@ -287,6 +287,8 @@ bool bi_translate_level(bi_handle_s* h, int l, int E, cudaStream_t s);
 void bi_autotune(bi_handle_s* h, int nrhs, cudaStream_t s);
 void bi_build_sai(bi_handle_s* h);
 void bi_operator_launch(bi_handle_s* h, const void* x, void* y, int R, cudaStream_t s);
+void bi_coupling_blocks_impl(bi_handle_s* h, int conforming, int64_t* sizes, int* xl_ptr, int* xl_col, void* xl_val,
+                             int* lx_ptr, int* lx_col, void* lx_val);
 void bi_coupling_set(bi_handle_s* h, int64_t n_int, const int* lx_ptr, const int* lx_col, const void* lx_val,
                      const int* xl_ptr, const int* xl_col, const void* xl_val, bi_qsolve_fn qsolve, void* user);
 void bi_sai_apply(bi_handle_s* h, const void* x, void* y, int R, cudaStream_t s);
