@@ -56,9 +56,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=64, help="RHS of the batched monostatic-sweep section (0: skip)")
     ap.add_argument("--sweep", type=int, default=1, help="solve the 180-incidence sweep end to end (0: skip)")
-    ap.add_argument("--serving", type=int, default=32, help="requests of the serving section (0: skip)")
-    ap.add_argument("--serving-max-unknowns", type=int, default=40000)
-    ap.add_argument("--serving-max-rhs", type=int, default=8)
+    ap.add_argument("--serving", type=int, default=64, help="requests of the serving section (0: skip)")
+    ap.add_argument("--serving-max-unknowns", type=int, default=50000)
+    ap.add_argument("--serving-max-rhs", type=int, default=32)
     return ap.parse_args()
 
 
@@ -170,8 +170,18 @@ def stage_flops(info, nrhs, p=10):
 
 def stage_roofline(info, nrhs, stages, hbm_gbs):
     """Per stage: the bound (HBM bytes or FP32 flops, whichever takes longer at the peaks),
-    the achieved rate and its fraction of that peak."""
+    the achieved rate and its fraction of that peak.  Where the product fuses the gather of x
+    into the near stage and the scatter of y into the receive (the gather and scatter stages
+    then time as empty), their bytes move to those stages and they are not reported apart."""
     sb, sf = stage_bytes(info, nrhs), stage_flops(info, nrhs)
+    stages = dict(stages)
+    vec = info["n_unknowns"] * nrhs * 8
+    if "gather" in stages and stages["gather"] < 0.01 * max(stages.get("near", 0.0), 1e-9):
+        stages.pop("gather")
+        sb["near"] += sb["gather"]
+    if "scatter" in stages and stages["scatter"] < 0.01 * max(stages.get("receive", 0.0), 1e-9):
+        stages.pop("scatter")
+        sb["receive"] += vec          # the receive also reads the near part of y and writes y
     out = {}
     for k, ms in stages.items():
         t_hbm = sb[k] / (hbm_gbs * 1e9)
@@ -399,62 +409,92 @@ def run_sweep(v, t, R, n_inc=180, tol=1e-3):
 
 
 # ---------------------------------------------------------------------------- serving stream
-def _serve(bi, reqs, arrivals, max_active, split_rhs, tol):
-    """Submit requests at the given arrival times (s) and wait for all; returns per-request
-    latency (s, from arrival to the last solved column), makespan (s) and setup ms."""
-    srv = bi.Server(max_active=max_active)
+def _serve(bi, reqs, arrivals, tol, share=True, max_active=8):
+    """Submit requests to a server at the given arrival times (s) and wait for all; returns
+    per-request latency (s, arrival to solution), makespan (s), mean operator set-up ms, whether
+    every request converged or reported, and the server's counters."""
+    srv = bi.Server(max_active=max_active, share_operators=share)
     t0 = time.perf_counter()
-    pending = {}
-    order = []
-    for i, (q, ta) in enumerate(zip(reqs, arrivals)):
+    ids = []
+    for q, ta in zip(reqs, arrivals):
         while time.perf_counter() - t0 < ta:
             time.sleep(0.0005)
-        cols = [(q["khat"][c:c + 1], q["phat"][c:c + 1]) for c in range(len(q["khat"]))] if split_rhs else \
-            [(q["khat"], q["phat"])]
-        for kh, ph in cols:
-            rid = srv.submit(q["verts"], q["tris"], q["k0"], kh, ph, tol=tol, op_mode=q["op_mode"])
-            pending[rid] = i
-            order.append(rid)
-    done_at = {}
-    setup = []
-    status_ok = True
-    for rid in order:
+        ids.append(srv.submit(q["verts"], q["tris"], q["k0"], q["khat"], q["phat"], tol=tol, op_mode=q["op_mode"]))
+    lat, setup, ok = [], [], True
+    for rid in ids:
         r = srv.wait(rid, timeout=3600)
-        status_ok = status_ok and r["status"] in (bi.BI_OK, bi.BI_ERR_NOT_CONVERGED)
-        i = pending[rid]
-        # latency of a request = submission (its arrival) to its last solved column; in the
-        # split form all of a request's columns are submitted at its arrival
-        done_at[i] = max(done_at.get(i, 0.0), r["latency_ms"] / 1e3)
+        ok = ok and r["status"] in (bi.BI_OK, bi.BI_ERR_NOT_CONVERGED)
+        lat.append(r["latency_ms"] / 1e3)
         setup.append(r["setup_ms"])
     makespan = time.perf_counter() - t0
+    stats = srv.stats()
     srv.close()
-    lat = np.array([done_at[i] for i in range(len(reqs))])
-    return lat, makespan, float(np.mean(setup)), status_ok
+    built = [s for s in setup if s > 0]
+    return np.array(lat), makespan, float(np.mean(built)) if built else 0.0, ok, stats
+
+
+def _plain_fifo(bi, reqs, arrivals, tol):
+    """The plain form: one request at a time in arrival order, its operator set up, then its
+    right-hand sides solved one at a time (FP32, one-RHS products).  Each request's service time
+    is measured; latencies follow from the arrivals of a single first-come-first-served server."""
+    import torch
+    service, ok = [], True
+    for q in reqs:
+        t0 = time.perf_counter()
+        op = bi.Operator(q["verts"], q["tris"], q["k0"], precision="fp32", op_mode=q["op_mode"], max_rhs=1)
+        for c in range(len(q["khat"])):
+            b = op.rhs_planewave(q["khat"][c], q["phat"][c])
+            x, its, rel = op.solve(b, tol=tol)
+            ok = ok and bool(np.all(np.isfinite(rel)))
+        torch.cuda.synchronize()
+        op.close()
+        service.append(time.perf_counter() - t0)
+    finish, lat = 0.0, []
+    for ta, sv in zip(arrivals, service):
+        finish = max(finish, ta) + sv
+        lat.append(finish - ta)
+    return np.array(lat), finish - arrivals[0], ok
 
 
 def run_serving(args):
-    """Serving stream (Poisson arrivals at about 75% of the measured capacity): p50/p99
-    latency and solved unknowns*RHS per second of the continuous-batching server, against the
-    plain form (one request at a time, one right-hand side at a time) on the same arrivals."""
+    """Serving stream after c4 (request mix of inputs.serving_requests: spheres, ellipsoids and
+    cubes, PEC or C block, plane waves; Poisson arrivals at 75% of the batched server's measured
+    capacity): p50/p99 latency and solved unknowns*RHS per second of
+      - the batched server (operators shared and cached, requests on one operator merged into
+        one GMRES whose products are single batched launches),
+      - the same server with one operator per request (requests overlap on the device but
+        share no launch),
+      - the plain form (one request at a time, one right-hand side at a time)."""
     from paper_2210_04892_gb300 import bi
     from paper_2210_04892_gb300.inputs import serving_requests
     reqs = serving_requests(args.serving, 2000, args.serving_max_unknowns, args.serving_max_rhs)
     tol = 1e-3
     work = sum((len(q["tris"]) * 3 // 2) * (2 if q["op_mode"] == 0 else 1) * len(q["khat"]) for q in reqs)
-    # capacity: everything submitted at once
-    lat0, span0, _, _ = _serve(bi, reqs, [0.0] * len(reqs), 8, False, tol)
-    rate = 0.75 * len(reqs) / span0
+    n = len(reqs)
+    _, span0, _, _, _ = _serve(bi, reqs, [0.0] * n, tol)
+    rate = 0.75 * n / span0
     rng = np.random.default_rng(20221011 + 31)
-    arrivals = list(np.cumsum(rng.exponential(1.0 / rate, len(reqs))))
+    arrivals = list(np.cumsum(rng.exponential(1.0 / rate, n)))
     arrivals = [a - arrivals[0] for a in arrivals]
-    lat, span, setup_ms, ok = _serve(bi, reqs, arrivals, 8, False, tol)
-    lat_p, span_p, _, ok_p = _serve(bi, reqs, arrivals, 1, True, tol)
-    return {"requests": len(reqs), "unknowns_range": [2000, args.serving_max_unknowns], "max_rhs": args.serving_max_rhs,
-            "tol": tol, "arrival_rate_per_s": rate, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-            "p99_ms": 1e3 * float(np.percentile(lat, 99)), "throughput": work / span, "unit": "unknowns*RHS solved/s",
-            "mean_setup_ms": setup_ms, "all_converged_or_reported": bool(ok and ok_p),
-            "plain": {"p50_ms": 1e3 * float(np.percentile(lat_p, 50)), "p99_ms": 1e3 * float(np.percentile(lat_p, 99)),
-                      "throughput": work / span_p, "form": "one request at a time, one RHS at a time"}}
+
+    def summary(lat, span):
+        return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "throughput": work / span}
+    lat, span, setup_ms, ok, stats = _serve(bi, reqs, arrivals, tol)
+    lat_u, span_u, setup_u, ok_u, stats_u = _serve(bi, reqs, arrivals, tol, share=False)
+    lat_p, span_p, ok_p = _plain_fifo(bi, reqs, arrivals, tol)
+    out = {"requests": n, "unknowns_range": [2000, args.serving_max_unknowns], "max_rhs": args.serving_max_rhs,
+           "distinct_operators": len({(q["shape"], len(q["tris"]), q["op_mode"]) for q in reqs}), "tol": tol,
+           "arrival_rate_per_s": rate, "unit": "unknowns*RHS solved/s", "all_converged_or_reported": bool(ok and ok_u and ok_p),
+           "capacity_makespan_s": span0}
+    out.update(summary(lat, span))
+    out.update({"mean_setup_ms": setup_ms, "server_stats": {k: v for k, v in stats.items() if k != "held_bytes"},
+                "form": "operators shared and cached; requests on one operator merged into one batched GMRES"})
+    out["unshared"] = dict(summary(lat_u, span_u), mean_setup_ms=setup_u,
+                           form="one operator per request; requests overlap on the device, no shared launch")
+    out["plain"] = dict(summary(lat_p, span_p), form="one request at a time (first come first served), one RHS at a "
+                        "time; latencies from each request's measured service time on the same arrivals")
+    return out
 
 
 # ---------------------------------------------------------------------------- GPU arm
@@ -557,6 +597,7 @@ def run_gpu(args):
     hbm, peak_kind = peaks()
     sr = stage_roofline(info, R, stages, hbm)
     dom = max((k for k in sr if k not in ("gather", "scatter")), key=lambda k: sr[k]["ms"])
+    stages = {k: v for k, v in stages.items() if k in sr}
     tr = measured_traffic("dram_matvec_sphere_r20_3484860.md").get(dom)
     roofline = {"bound": sr[dom]["bound"], "kernel": dom, "achieved": sr[dom]["achieved"], "peak": sr[dom]["peak"],
                 "unit": sr[dom]["unit"], "frac": sr[dom]["frac"],

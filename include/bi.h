@@ -247,8 +247,10 @@ int bi_farfield(bi_handle h, const void* x, int nrhs, const double* dirs, int nd
  * ceil(N / 256) * nrhs * ndir * 96 bytes; larger requests return BI_ERR_ARG (split the
  * directions over several calls).  The call allocates nothing.  The handle's device (the one
  * current at bi_setup) must be current: otherwise BI_ERR_ARG.  The first call on each handle
- * looks up the array's device address (cudaGetSymbolAddress) and keeps it in the handle; make
- * that first call before any stream capture.  All calls on a device share the array, which
+ * looks up the array's device address (cudaGetSymbolAddress) and keeps it in the handle with
+ * the id of the current CUDA context; a later call under another context (the device reset
+ * and its context created anew) looks it up again.  Make the first call before any stream
+ * capture.  All calls on a device share the array, which
  * keeps the last call's partial sums (each call writes every slot it reads): calls whose work
  * overlaps on the GPU (different streams, or different handles on one device) race on it --
  * order them on one stream or synchronise between them.  The handle itself must already
@@ -279,18 +281,39 @@ const char* bi_stage_name(int i);
 
 /* ---- Serving: continuous batching of solves ------------------------------------------
  * A server owns two host threads.  bi_submit queues a solve request (mesh, k0, parameters,
- * nrhs plane waves, tolerance); requests are admitted in arrival order while fewer than
- * max_active are running and the device-memory estimate fits mem_budget_bytes.  An admitted
- * request gets its own stream, operator (bi_setup, run on a setup thread so that setups
- * overlap running solves) and GMRES state; the serving thread advances every running solve
- * by one iteration per pass, so their matvecs and Krylov kernels overlap on the device, and
- * requests join or leave between passes.  Latency = submit to solution on the host. */
+ * nrhs plane waves, tolerance).  Requests on the same operator (identical vertices,
+ * triangles, k0 and parameters) share one set-up operator and are merged into one job: one
+ * GMRES over the columns of all of them (each column keeps its request's tolerance), so each
+ * product of the job is one batched bi_matvec for all its requests.  A job takes every waiting
+ * request of its operator up to max_batch_rhs columns, including requests that arrive while
+ * its operator is set up; later requests of a busy operator wait for the next job.  After its
+ * job an operator stays cached (idle operators are dropped, oldest first, when the memory
+ * budget needs room).  Jobs are admitted while fewer than max_active are set up or running
+ * and the device-memory estimate fits mem_budget_bytes; a setup thread builds operators and
+ * GMRES states so that set-ups overlap running solves, and the serving thread advances every
+ * running job by one iteration per pass, so their products and Krylov kernels overlap on the
+ * device.  Latency = submit to solution on the host. */
 typedef struct bi_server_s* bi_server;
 typedef struct {
-    int64_t mem_budget_bytes;   /* device bytes for admitted requests; 0 = 80% of free memory */
-    int max_active;             /* requests set up or iterating at once (default 8) */
+    int64_t mem_budget_bytes;   /* device bytes for operators and jobs; 0 = 80% of free memory */
+    int max_active;             /* jobs set up or iterating at once (default 8) */
     int queue_capacity;         /* waiting requests before bi_submit returns BI_ERR_BUSY (default 4096) */
+    int share_operators;        /* 1 (default): cache operators and merge requests on one operator into
+                                   jobs; 0: every request builds its own operator and runs alone */
+    int max_batch_rhs;          /* columns of one job, and max_rhs of the operators (default 64) */
 } bi_server_params;
+
+/* bi_server_stats counters */
+enum {
+    BI_STAT_JOBS = 0,              /* jobs started */
+    BI_STAT_OPERATORS_BUILT = 1,   /* bi_setup calls */
+    BI_STAT_CACHE_HITS = 2,        /* jobs started on a cached operator */
+    BI_STAT_MERGED_REQUESTS = 3,   /* requests that joined another request's job */
+    BI_STAT_EVICTIONS = 4,         /* cached operators dropped for memory */
+    BI_STAT_CACHED_OPERATORS = 5,  /* idle operators held now */
+    BI_STAT_HELD_BYTES = 6,        /* device bytes held now (operators and jobs) */
+    BI_SERVER_NSTATS = 7
+};
 
 void bi_server_default_params(bi_server_params* p);
 /* Create a server on the current CUDA device. */
@@ -308,6 +331,8 @@ int bi_poll(bi_server s, int64_t req, int* done, int* status);
  * finished.  Any output pointer may be NULL. */
 int bi_result(bi_server s, int64_t req, void* x_host, int64_t x_bytes, int* iters, double* relres, double* latency_ms,
               double* setup_ms);
+/* Copy the first n counters (BI_STAT_*) into out. */
+int bi_server_stats(bi_server s, int64_t* out, int n);
 /* Forget a finished request (frees its host result). */
 int bi_release(bi_server s, int64_t req);
 const char* bi_server_last_error(bi_server s);

@@ -30,7 +30,7 @@ EXPORTS = ["bi_default_params", "bi_setup", "bi_num_unknowns", "bi_rwg_edges", "
            "bi_matvec_host", "bi_rhs_planewave", "bi_solve", "bi_solve_refined", "bi_farfield", "bi_farfield_noalloc", "bi_debug_copy", "bi_debug_set_wait_limit", "bi_tuned_config", "bi_profile_stages", "bi_stage_name", "bi_last_error", "bi_device_status", "bi_set_coupling", "bi_coupling_blocks", "bi_matvec_coupled", "bi_plan_create", "bi_plan_info", "bi_plan_get",
            "bi_plan_last_error", "bi_plan_destroy",
            "bi_destroy", "bi_server_default_params", "bi_server_create", "bi_submit", "bi_poll", "bi_result",
-           "bi_release", "bi_server_last_error", "bi_server_destroy"]
+           "bi_release", "bi_server_last_error", "bi_server_stats", "bi_server_destroy"]
 
 
 # qsolve(user, in, out, nrhs, stream) of bi_set_coupling
@@ -69,7 +69,12 @@ class Info(ctypes.Structure):
 
 
 class ServerParams(ctypes.Structure):
-    _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_active", ctypes.c_int), ("queue_capacity", ctypes.c_int)]
+    _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_active", ctypes.c_int), ("queue_capacity", ctypes.c_int),
+                ("share_operators", ctypes.c_int), ("max_batch_rhs", ctypes.c_int)]
+
+
+SERVER_STATS = ("jobs", "operators_built", "cache_hits", "merged_requests", "evictions", "cached_operators",
+                "held_bytes")
 
 
 _lib = None
@@ -123,6 +128,7 @@ def load(path: str = LIB_PATH):
     L.bi_server_create.argtypes = [ctypes.POINTER(ServerParams), ctypes.POINTER(vp)]
     L.bi_submit.argtypes = [vp, vp, i, vp, i, d, ctypes.POINTER(Params), i, vp, vp, d, ctypes.POINTER(i64)]
     L.bi_poll.argtypes = [vp, i64, ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.bi_server_stats.argtypes = [vp, vp, i]
     L.bi_result.argtypes = [vp, i64, vp, i64, vp, vp, ctypes.POINTER(d), ctypes.POINTER(d)]
     L.bi_release.argtypes = [vp, i64]
     L.bi_server_last_error.argtypes = [vp]
@@ -420,13 +426,15 @@ class Operator:
 class Server:
     """Continuous-batching solve server (bi_server_* in include/bi.h)."""
 
-    def __init__(self, mem_budget_bytes=0, max_active=8, queue_capacity=4096):
+    def __init__(self, mem_budget_bytes=0, max_active=8, queue_capacity=4096, share_operators=True, max_batch_rhs=64):
         L = load()
         p = ServerParams()
         L.bi_server_default_params(ctypes.byref(p))
         p.mem_budget_bytes = int(mem_budget_bytes)
         p.max_active = int(max_active)
         p.queue_capacity = int(queue_capacity)
+        p.share_operators = int(bool(share_operators))
+        p.max_batch_rhs = int(max_batch_rhs)
         h = ctypes.c_void_p()
         rc = L.bi_server_create(ctypes.byref(p), ctypes.byref(h))
         if rc != BI_OK:
@@ -485,6 +493,12 @@ class Server:
             if time.time() - t0 > timeout:
                 raise TimeoutError("request %d not finished" % req)
             time.sleep(0.002)
+
+    def stats(self):
+        """Server counters (SERVER_STATS names)."""
+        out = np.zeros(len(SERVER_STATS), np.int64)
+        _check(load().bi_server_stats(self.h, out.ctypes.data, len(out)), None)
+        return dict(zip(SERVER_STATS, (int(v) for v in out)))
 
     def release(self, req):
         load().bi_release(self.h, int(req))

@@ -7,6 +7,9 @@
 // scratch memory), then one thread per (rhs, direction) adds the chunks and projects.
 #include <cmath>
 
+#include <cuda.h>
+#include <mutex>
+
 #include "bi_internal.h"
 
 namespace {
@@ -146,6 +149,32 @@ void bi_farfield_launch(bi_handle_s* h, const void* x, int nrhs, const double* d
 // the process exits; all calls on one device share it.
 static __device__ __align__(256) double g_ff_noalloc_scratch[BI_FARFIELD_NOALLOC_MAX_BYTES / sizeof(double)];
 
+// Unique id of the calling thread's current CUDA context (0 when none or unknown), through
+// the driver entry points the runtime hands out, so the library needs no link to libcuda.
+static unsigned long long current_context_id() {
+    typedef CUresult (*get_current_t)(CUcontext*);
+    typedef CUresult (*get_id_t)(CUcontext, unsigned long long*);
+    static get_current_t get_current = nullptr;
+    static get_id_t get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (get_current_t)p;
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (get_id_t)p;
+        cudaGetLastError();
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS) return id;
+    return 0;
+}
+
 extern "C" int bi_farfield_noalloc(bi_handle h, const void* x, int nrhs, const double* dirs, int ndir, void* F) {
     if (!h) return BI_ERR_ARG;
     if (h->coated) {
@@ -178,13 +207,16 @@ extern "C" int bi_farfield_noalloc(bi_handle h, const void* x, int nrhs, const d
                      ") is not the handle's device (" + std::to_string(h->device) + "); make it current first";
             return BI_ERR_ARG;
         }
-        if (!h->ff_noalloc_part) {
-            // Host code cannot use the array's name as an address: look the address up on the
-            // handle's first call, with its device current.  The handle's lifetime is bounded by
-            // its device context, so the cached address cannot outlive the context it belongs to.
+        const unsigned long long ctx = current_context_id();
+        if (!h->ff_noalloc_part || ctx != h->ff_noalloc_ctx || ctx == 0) {
+            // Host code cannot use the array's name as an address: look the address up with the
+            // handle's device current, and again whenever the current context is not the one the
+            // kept address belongs to (a context destroyed and recreated, e.g. after
+            // cudaDeviceReset, places the array anew; an unknown context is never trusted).
             void* p = nullptr;
             CU(cudaGetSymbolAddress(&p, g_ff_noalloc_scratch));
             h->ff_noalloc_part = (double*)p;
+            h->ff_noalloc_ctx = ctx;
         }
         // every partial-sum slot used by this call is written by the first pass before the
         // second pass reads it, so nothing needs clearing

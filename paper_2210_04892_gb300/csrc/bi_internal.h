@@ -159,6 +159,9 @@ struct bi_handle_s {
     bool use_graphs = true;
     bool use_fast = true;               // fused kernels (false: two-pass reference kernels)
     bool use_leaf_bulk = true;          // bulk-copy pipelines for leaf aggregation and receive
+    int translate_variant = 0;          // translation kernel form forced on every level (test switch
+                                        // BI_TRANSLATE_VARIANT=1..4; 0: tuned)
+    bool near_rb = true;                // row-blocked near kernel for R >= 3 (test switch BI_NEAR_RB=0)
     bool force_anterp_rows = false;     // row-blocked anterpolation on every level (test switch)
     int* d_status = nullptr;            // device status word (0: healthy; see bi_tma.cuh)
     long long wait_cycles = 1ll << 31;  // limit of the bulk-copy waits of the leaf kernels (SM clocks)
@@ -180,6 +183,7 @@ struct bi_handle_s {
     int num_sms = 152;
     int device = -1;                    // CUDA device current at bi_setup (the handle's buffers live there)
     double* ff_noalloc_part = nullptr;  // device address of the allocation-free far-field array on that device
+    unsigned long long ff_noalloc_ctx = 0;  // id of the CUDA context that address belongs to
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // host mesh / RWG in user order
@@ -305,7 +309,8 @@ int bi_solve_refined_impl(bi_handle_s* h, bi_handle_s* href, const void* rhs, vo
                           double* relres);
 // resumable GMRES (serving loop)
 struct gmres_ctx;
-gmres_ctx* bi_gmres_create(bi_handle_s* h, const void* rhs, int nrhs, double tol, cudaStream_t s);
+// tol: host [nrhs], one tolerance per column (columns of different requests may share a context)
+gmres_ctx* bi_gmres_create(bi_handle_s* h, const void* rhs, int nrhs, const double* tol, cudaStream_t s);
 int bi_gmres_advance(gmres_ctx* c);
 int bi_gmres_finish(gmres_ctx* c, void* xout, int* iters, double* relres);
 void bi_gmres_destroy(gmres_ctx* c);

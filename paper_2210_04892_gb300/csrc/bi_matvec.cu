@@ -619,6 +619,144 @@ __global__ void __launch_bounds__(256, RT >= 8 ? 2 : 3) k_near_multi(int N, int 
     }
 }
 
+// ------------------------------------------------------------------ near field, row pairs
+// Several RHS (R >= 3, MODE 0 or 1), the work items and staged x of k_near_multi: each warp
+// takes two rows of its work item at once, its lanes split as 16 column lanes x 2 halves of
+// the RT right-hand sides.  A lane's staged x values (RT/2 RHS of J and M) serve both rows, so
+// shared-memory reads per multiply-add are half those of k_near_multi, and the row sums meet
+// over 16 lanes (4 shuffle steps) for RT/2 RHS per lane instead of 32 lanes for RT.
+template <typename T, int MODE, int RT>
+__global__ void __launch_bounds__(256, 2) k_near_rb(int N, int R, int nun, const int* __restrict__ perm,
+                                                    const int2* __restrict__ work, const int* __restrict__ leaf_start,
+                                                    const int* __restrict__ near_ptr, const int* __restrict__ near_src,
+                                                    const int64_t* __restrict__ near_blk, const int* __restrict__ near_col0,
+                                                    const int* __restrict__ near_ncol, const cpx<T>* __restrict__ blocks,
+                                                    const int* __restrict__ gptr, const int* __restrict__ gseg,
+                                                    const T* __restrict__ gval, const cpx<T>* __restrict__ xt,
+                                                    cpx<T>* __restrict__ yt, cpx<T>* __restrict__ yuser) {
+    constexpr int NX = MODE == 0 ? 2 : 1;
+    constexpr int RH = RT / 2;           // RHS per lane
+    extern __shared__ unsigned char smem_raw[];
+    cpx<T>* xs = reinterpret_cast<cpx<T>*>(smem_raw);  // [NX][RT][ncol]
+    const int b = work[blockIdx.x].x, row0 = work[blockIdx.x].y;
+    const int m0 = leaf_start[b], mb = leaf_start[b + 1] - m0;
+    const int q0 = near_ptr[b], q1 = near_ptr[b + 1];
+    const int64_t seg = near_blk[q0];
+    const int ncol = near_ncol[b];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const int cl = lane & 15, hh = lane >> 4;      // column lane, RHS half
+    const int row_end = min(mb, row0 + 16);       // a work item holds up to 16 rows of its box
+    for (int r0 = 0; r0 < R; r0 += RT) {
+        const int rn = min(RT, R - r0);
+        __syncthreads();
+        for (int q = q0 + warp; q < q1; q += nwarp) {
+            const int s = near_src[q];
+            const int n0 = leaf_start[s], nbs = leaf_start[s + 1] - n0;
+            const int c0 = near_col0[q];
+            const cpx<T>* xb = xt + (int64_t)n0 * NX * R + r0;
+            for (int i = lane; i < nbs * NX * RT; i += 32) {
+                const int rr = i % RT, X = (i / RT) % NX, n = i / (RT * NX);
+                xs[((size_t)X * RT + rr) * ncol + c0 + n] = rr < rn ? xb[((int64_t)n * NX + X) * R + rr] : czero<T>();
+            }
+        }
+        __syncthreads();
+        const cpx<T>* xJs = xs + (size_t)(hh * RH) * ncol;
+        const cpx<T>* xMs = xs + (size_t)(RT + hh * RH) * ncol;
+        for (int ml = row0 + 2 * warp; ml < row_end; ml += 2 * nwarp) {
+            const bool two = ml + 1 < row_end;
+            cpx<T> a0[RH][NX], a1[RH][NX];
+#pragma unroll
+            for (int j = 0; j < RH; ++j)
+#pragma unroll
+                for (int X = 0; X < NX; ++X) { a0[j][X] = czero<T>(); a1[j][X] = czero<T>(); }
+            const cpx<T>* rowA = blocks + (int64_t)NX * (seg + (int64_t)ml * ncol);
+            const cpx<T>* rowB = two ? rowA + (int64_t)NX * ncol : rowA;   // a lone last row reads its own row twice
+#pragma unroll 2
+            for (int c = cl; c < ncol; c += 16) {
+                if (MODE == 0) {
+                    cpx<T> A0, B0, A1, B1;
+                    load_pair(rowA + 2 * c, A0, B0);
+                    load_pair(rowB + 2 * c, A1, B1);
+#pragma unroll
+                    for (int j = 0; j < RH; ++j) {
+                        const cpx<T> xJ = xJs[(size_t)j * ncol + c], xM = xMs[(size_t)j * ncol + c];
+                        const cpx<T> nxM = {-xM.x, -xM.y};
+                        cfma(a0[j][0], A0, xJ);
+                        cfma(a0[j][0], B0, xM);
+                        cfma(a0[j][NX - 1], B0, xJ);
+                        cfma(a0[j][NX - 1], A0, nxM);
+                        cfma(a1[j][0], A1, xJ);
+                        cfma(a1[j][0], B1, xM);
+                        cfma(a1[j][NX - 1], B1, xJ);
+                        cfma(a1[j][NX - 1], A1, nxM);
+                    }
+                } else {
+                    const cpx<T> A0 = ldg_cpx(rowA + c), A1 = ldg_cpx(rowB + c);
+#pragma unroll
+                    for (int j = 0; j < RH; ++j) {
+                        const cpx<T> xJ = xJs[(size_t)j * ncol + c];
+                        cfma(a0[j][0], A0, xJ);
+                        cfma(a1[j][0], A1, xJ);
+                    }
+                }
+            }
+            if (MODE == 0) {
+                // Gram terms of the M rows: 1/2 (X x_J - G x_M), lanes over the row's entries
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    if (t == 1 && !two) break;
+                    const int m = m0 + ml + t;
+                    const int g0 = gptr[m], gn = gptr[m + 1] - g0;
+                    for (int qq = cl; qq < gn; qq += 16) {
+                        const int c = gseg[g0 + qq];
+                        const T gg = gval[2 * (g0 + qq)], xx = gval[2 * (g0 + qq) + 1];
+#pragma unroll
+                        for (int j = 0; j < RH; ++j) {
+                            const cpx<T> xJ = xJs[(size_t)j * ncol + c], xM = xMs[(size_t)j * ncol + c];
+                            cpx<T>& acc = t == 0 ? a0[j][NX - 1] : a1[j][NX - 1];
+                            acc.x += T(0.5) * (xx * xJ.x - gg * xM.x);
+                            acc.y += T(0.5) * (xx * xJ.y - gg * xM.y);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < RH; ++j)
+#pragma unroll
+                for (int X = 0; X < NX; ++X)
+#pragma unroll
+                    for (int o = 1; o < 16; o <<= 1) {
+                        a0[j][X].x += __shfl_xor_sync(0xffffffffu, a0[j][X].x, o);
+                        a0[j][X].y += __shfl_xor_sync(0xffffffffu, a0[j][X].y, o);
+                        a1[j][X].x += __shfl_xor_sync(0xffffffffu, a1[j][X].x, o);
+                        a1[j][X].y += __shfl_xor_sync(0xffffffffu, a1[j][X].y, o);
+                    }
+            // lane cl of each half writes RHS hh*RH + cl (cl < RH) of both rows
+#pragma unroll
+            for (int j = 0; j < RH; ++j) {
+                const int rr = hh * RH + j;
+                if (cl == j && rr < rn) {
+                    const int r = r0 + rr;
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        if (t == 1 && !two) break;
+                        const int m = m0 + ml + t;
+                        const cpx<T> sJ = t == 0 ? a0[j][0] : a1[j][0];
+                        const cpx<T> vJ = {-sJ.x, -sJ.y};
+                        if (yuser) {
+                            yuser[(int64_t)r * nun + perm[m]] = vJ;
+                            if (NX == 2) yuser[(int64_t)r * nun + N + perm[m]] = t == 0 ? a0[j][NX - 1] : a1[j][NX - 1];
+                        } else {
+                            yt[((int64_t)m * NX + 0) * R + r] = vJ;
+                            if (NX == 2) yt[((int64_t)m * NX + 1) * R + r] = t == 0 ? a0[j][NX - 1] : a1[j][NX - 1];
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ leaf aggregation (fused gather)
 // thread per (stored direction kk, RHS r): both components from one 16-byte pattern load give
 // U at kk and at its antipode.
@@ -1370,6 +1508,21 @@ void launch_near_multi(bi_handle_s* h, cpx<T>* yt, cpx<T>* yuser, int R, cudaStr
     CU(cudaGetLastError());
 }
 
+template <typename T, int MODE, int RT>
+bool launch_near_rb(bi_handle_s* h, cpx<T>* yt, cpx<T>* yuser, int R, cudaStream_t s) {
+    constexpr int NX = MODE == 0 ? 2 : 1;
+    const size_t smem = (size_t)h->near_ncol_max * RT * NX * sizeof(cpx<T>);
+    if (smem > 110 * 1024) return false;
+    auto kern = k_near_rb<T, MODE, RT>;
+    bi_raise_smem(kern, smem);
+    kern<<<h->near_nwork, 256, smem, s>>>(h->N, R, h->nun, h->d_perm, (const int2*)h->d_near_work, h->d_leaf_start,
+                                          h->d_near_ptr, h->d_near_src, h->d_near_blk, h->d_near_col0, h->d_near_ncol,
+                                          (const cpx<T>*)h->d_near, h->d_gram_ptr, h->d_gram_seg, (const T*)h->d_gram_val,
+                                          (const cpx<T>*)h->d_xt, yt, yuser);
+    CU(cudaGetLastError());
+    return true;
+}
+
 template <typename T, int MODE>
 void launch_near_any(bi_handle_s* h, const cpx<T>* x, cpx<T>* yt, cpx<T>* yuser, int R, cudaStream_t s) {
     if (MODE == 3) {
@@ -1404,6 +1557,12 @@ void launch_near_any(bi_handle_s* h, const cpx<T>* x, cpx<T>* yt, cpx<T>* yuser,
     const int64_t nvec = (int64_t)h->N * h->nX * R;
     k_gather_x<T><<<nblk(nvec, 256), 256, 0, s>>>(h->N, h->nX, R, h->nun, h->d_perm, x, (cpx<T>*)h->d_xt);
     CU(cudaGetLastError());
+    if constexpr (MODE == 0 || MODE == 1) {
+        if (h->near_rb && R >= 3) {
+            if (R >= 6 && launch_near_rb<T, MODE, 8>(h, yt, yuser, R, s)) return;
+            if (launch_near_rb<T, MODE, 4>(h, yt, yuser, R, s)) return;
+        }
+    }
     if (R == 2) launch_near_multi<T, MODE, 2>(h, yt, yuser, R, s);
     else if (R <= 4 || (size_t)h->near_ncol_max * 2 * 8 * sizeof(cpx<T>) > 160 * 1024) launch_near_multi<T, MODE, 4>(h, yt, yuser, R, s);
     else launch_near_multi<T, MODE, 8>(h, yt, yuser, R, s);
@@ -1656,7 +1815,7 @@ void bi_autotune(bi_handle_s* h, int nrhs, cudaStream_t s) {
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    const std::vector<int> cand[3] = {{1, 2},
+    const std::vector<int> cand[3] = {{1, 2, 3, 4},
                                       {116, 108, 104, 102, 2},
                                       {116, 108, 104, 102, 216, 208, 204, 202, 2}};
     try {

@@ -1,16 +1,21 @@
-// Continuous-batching solve server: requests (mesh, wavenumber, plane-wave excitations,
-// tolerance) are admitted as device memory and slots allow; each admitted request gets its
-// own stream, operator (bi_setup, on a setup worker thread so that setups overlap the
-// iterations of running solves) and resumable GMRES context.  The serving thread advances
-// every running solve by one iteration per pass -- their matvec graphs and Krylov kernels
-// are queued on their own streams and overlap on the device -- retires finished requests
-// and admits waiting ones between passes.
+// Continuous-batching solve server.  A request is a surface, a wavenumber, nrhs plane waves and
+// a tolerance.  Requests on the same operator (identical surface, wavenumber and parameters)
+// share one set-up operator, kept in a cache after its requests finish, and are merged into
+// one job: one resumable GMRES context over the columns of all of them, so every product of
+// the job is one batched bi_matvec -- one launch per kernel of the product for all its
+// requests.  A job takes every waiting request of its operator (up to max_batch_rhs columns),
+// including those that arrive while the operator is being set up.  Jobs are admitted as device
+// memory and slots allow; a setup thread builds operators and GMRES contexts so that set-ups
+// overlap running solves, and the serving thread advances every running job by one iteration
+// per pass (their products are queued on their own streams and overlap on the device),
+// retires finished jobs and admits waiting requests between passes.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
-#include <exception>
 #include <cstring>
 #include <deque>
+#include <exception>
+#include <list>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -24,6 +29,9 @@ namespace {
 using clk = std::chrono::steady_clock;
 
 enum req_state { RQ_QUEUED = 0, RQ_SETUP = 1, RQ_RUNNING = 2, RQ_DONE = 3 };
+enum op_state { OP_BUILDING = 0, OP_IDLE = 1, OP_BUSY = 2 };
+
+struct job;
 
 struct request {
     int64_t id = 0;
@@ -31,24 +39,109 @@ struct request {
     std::vector<int> tris;
     double k0 = 0;
     bi_params prm{};
+    uint64_t key = 0;
     int nrhs = 1;
     std::vector<double> khat, phat;
     double tol = 1e-3;
-    int64_t est_bytes = 0, held_bytes = 0;
-    clk::time_point t_submit, t_start, t_done;
+    clk::time_point t_submit, t_done;
     std::atomic<int> state{RQ_QUEUED};
     int status = BI_OK;
     std::string err;
-    cudaStream_t stream = nullptr;
-    bi_handle_s* op = nullptr;
-    void* d_rhs = nullptr;
-    void* d_x = nullptr;
-    gmres_ctx* ctx = nullptr;
+    job* jb = nullptr;
+    int col0 = 0;                       // first column of this request in its job
     std::vector<unsigned char> x_host;  // result, handle precision
     std::vector<int> iters;
     std::vector<double> relres;
-    double setup_ms = 0;
+    double setup_ms = 0;                // operator set-up time, when this request's job built it
 };
+
+// One set-up operator and the identity it was built for.
+struct op_entry {
+    uint64_t key = 0;
+    std::vector<double> verts;
+    std::vector<int> tris;
+    double k0 = 0;
+    bi_params prm{};
+    int max_rhs = 1;
+    int state = OP_BUILDING;
+    bi_handle_s* h = nullptr;
+    cudaStream_t stream = nullptr;
+    int64_t bytes = 0;                  // device bytes held (estimate until built)
+    double setup_ms = 0;
+    clk::time_point last_use;
+};
+
+struct job {
+    op_entry* op = nullptr;
+    std::vector<request*> reqs;
+    bool sealed = false;                // columns fixed (no more requests join)
+    bool builds_op = false;             // this job triggered the operator's set-up
+    int R = 0;
+    void* d_rhs = nullptr;
+    void* d_x = nullptr;
+    gmres_ctx* ctx = nullptr;
+    int64_t est_bytes = 0, held_bytes = 0;
+};
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// Operator identity: the surface, the wavenumber and every parameter that changes the operator
+// or its solver (stream and max_rhs excluded: the server sets them).
+uint64_t operator_key(const request* r) {
+    uint64_t h = 1469598103934665603ull;
+    h = fnv1a(h, r->verts.data(), r->verts.size() * sizeof(double));
+    h = fnv1a(h, r->tris.data(), r->tris.size() * sizeof(int));
+    h = fnv1a(h, &r->k0, sizeof(double));
+    const bi_params& p = r->prm;
+    const double dv[] = {p.leaf_box, p.k_im, p.eps_re, p.eps_im};
+    const int iv[] = {p.digits, p.levels, p.interp_order, p.precision, p.op_mode, p.gmres_restart, p.gmres_maxit,
+                      p.precond, p.core_tris};
+    h = fnv1a(h, dv, sizeof(dv));
+    h = fnv1a(h, iv, sizeof(iv));
+    return h;
+}
+
+bool same_operator(const op_entry* e, const request* r) {
+    const bi_params &a = e->prm, &b = r->prm;
+    return e->key == r->key && e->k0 == r->k0 && e->verts == r->verts && e->tris == r->tris &&
+           a.leaf_box == b.leaf_box && a.digits == b.digits && a.levels == b.levels &&
+           a.interp_order == b.interp_order && a.precision == b.precision && a.op_mode == b.op_mode &&
+           a.gmres_restart == b.gmres_restart && a.gmres_maxit == b.gmres_maxit && a.precond == b.precond &&
+           a.k_im == b.k_im && a.eps_re == b.eps_re && a.eps_im == b.eps_im && a.core_tris == b.core_tris &&
+           r->nrhs <= e->max_rhs;
+}
+
+int64_t n_unknowns_of(const request* r) {
+    const int64_t N = (int64_t)r->tris.size() / 3 * 3 / 2;
+    return N * (r->prm.op_mode == 0 ? 2 : 1);
+}
+
+// Device bytes of an operator: near blocks (~420 near pairs per RWG at a 0.25-wavelength
+// leaf), leaf patterns, far-field buffers and work vectors for max_rhs columns; a 1.5x margin
+// covers the tree and scratch.
+int64_t estimate_op_bytes(const request* r, int max_rhs) {
+    const int64_t N = (int64_t)r->tris.size() / 3 * 3 / 2;
+    const int nX = r->prm.op_mode == 0 ? 2 : 1;
+    const int64_t cs = r->prm.precision == 0 ? 16 : 8;
+    const int64_t near = N * 420 * cs * nX;
+    const int64_t pat = N * 300 * 4 * cs;
+    const int64_t far = N * 300 * 2 * (int64_t)max_rhs * cs * 2;
+    return (near + pat + far + N * nX * max_rhs * cs * 4) * 3 / 2 + (64 << 20);
+}
+
+// Device bytes of a job's GMRES state and vectors for R columns.
+int64_t estimate_job_bytes(const request* r, int R) {
+    const int64_t nun = n_unknowns_of(r);
+    const int64_t cs = r->prm.precision == 0 ? 16 : 8;
+    return bi_gmres_estimate_bytes(nun, R, r->prm.gmres_restart) + 2 * nun * R * cs;
+}
 
 }  // namespace
 
@@ -57,116 +150,276 @@ struct bi_server_s {
     int device = 0;
     std::mutex mu;
     std::condition_variable cv;
-    std::deque<request*> queue;          // waiting for admission
-    std::deque<request*> to_setup;       // admitted, waiting for the setup worker
-    std::vector<request*> running;       // set up, iterating (serving thread only)
-    std::deque<request*> ready;          // set up, waiting to join `running`
+    std::deque<request*> queue;          // waiting for a job
+    std::deque<job*> to_setup;           // admitted, waiting for the setup worker
+    std::vector<job*> pending;           // jobs whose columns are still open (setting up)
+    std::vector<job*> running;           // iterating (serving thread only)
+    std::deque<job*> ready;              // set up, waiting to join `running`
+    std::list<op_entry*> ops;            // every operator, in order of last use (front: oldest)
     std::unordered_map<int64_t, request*> all;
     int64_t next_id = 1;
-    int64_t held_bytes = 0;
-    int active = 0;                      // admitted and not finished
+    int64_t held_bytes = 0;              // operators (cached or in use) plus jobs
+    int active = 0;                      // jobs admitted and not finished
     bool stop = false;
     std::thread serve_thread, setup_thread;
     std::string err;
+    int64_t stats[BI_SERVER_NSTATS] = {};
 };
 
-static int64_t estimate_request_bytes(const request* r) {
-    // near blocks (~400 near pairs per RWG at a 0.25-wavelength leaf), patterns, far-field
-    // buffers and the Krylov basis; a 1.5x margin covers the tree and scratch
-    const int64_t nt = (int64_t)r->tris.size() / 3;
-    const int64_t N = nt * 3 / 2;
-    const int nX = r->prm.op_mode == 0 ? 2 : 1;
-    const int64_t cs = r->prm.precision == 0 ? 16 : 8;
-    const int64_t nun = N * nX;
-    const int64_t near = N * 420 * cs * nX;
-    const int64_t pat = N * 300 * 4 * cs;
-    const int64_t far = N * 300 * 2 * r->nrhs * cs * 2;
-    const int64_t kry = bi_gmres_estimate_bytes(nun, r->nrhs, r->prm.gmres_restart);
-    return (near + pat + far + kry + nun * r->nrhs * cs * 6) * 3 / 2 + (64 << 20);
+namespace {
+
+void destroy_op(op_entry* e) {
+    if (e->h) bi_destroy(e->h);
+    if (e->stream) cudaStreamDestroy(e->stream);
+    delete e;
 }
 
-static void fail_request(bi_server_s* S, request* r, int code, const std::string& msg) {
-    r->status = code;
-    r->err = msg;
-    r->t_done = clk::now();
-    if (r->ctx) { bi_gmres_destroy(r->ctx); r->ctx = nullptr; }
-    if (r->op) { bi_destroy(r->op); r->op = nullptr; }
-    if (r->d_rhs) { cudaFree(r->d_rhs); r->d_rhs = nullptr; }
-    if (r->d_x) { cudaFree(r->d_x); r->d_x = nullptr; }
-    if (r->stream) { cudaStreamDestroy(r->stream); r->stream = nullptr; }
+// Drop idle cached operators, oldest first, until `need` more bytes fit the budget.
+void evict_locked(bi_server_s* S, int64_t need) {
+    for (auto it = S->ops.begin(); it != S->ops.end() && S->held_bytes + need > S->prm.mem_budget_bytes;) {
+        op_entry* e = *it;
+        if (e->state == OP_IDLE) {
+            S->held_bytes -= e->bytes;
+            it = S->ops.erase(it);
+            destroy_op(e);
+            S->stats[BI_STAT_EVICTIONS] += 1;
+        } else {
+            ++it;
+        }
+    }
+}
+
+// Finish every request of a job with the same status; frees the job and releases its operator
+// (destroyed when operators are not shared, or when it failed to build).
+void finish_job(bi_server_s* S, job* jb, int code, const std::string& msg) {
+    if (jb->ctx) bi_gmres_destroy(jb->ctx);
+    if (jb->d_rhs) cudaFree(jb->d_rhs);
+    if (jb->d_x) cudaFree(jb->d_x);
     std::lock_guard<std::mutex> lk(S->mu);
-    S->held_bytes -= r->held_bytes;
-    r->held_bytes = 0;
+    const clk::time_point now = clk::now();
+    for (request* r : jb->reqs) {
+        if (code != BI_OK && r->status == BI_OK) {
+            r->status = code;
+            r->err = msg;
+        }
+        r->t_done = now;
+        r->jb = nullptr;
+        r->state = RQ_DONE;
+    }
+    S->held_bytes -= jb->held_bytes;
     S->active -= 1;
-    r->state = RQ_DONE;
+    op_entry* e = jb->op;
+    if (e) {
+        e->last_use = now;
+        const bool keep = S->prm.share_operators && e->h && code != BI_ERR_CUDA;
+        if (keep) {
+            e->state = OP_IDLE;
+            S->ops.remove(e);
+            S->ops.push_back(e);
+        } else {
+            S->held_bytes -= e->bytes;
+            S->ops.remove(e);
+            destroy_op(e);
+        }
+    }
+    for (auto it = S->pending.begin(); it != S->pending.end(); ++it)
+        if (*it == jb) {
+            S->pending.erase(it);
+            break;
+        }
+    delete jb;
     S->cv.notify_all();
 }
 
-// admit queued requests in arrival order while slots and the memory budget allow
-static void admit_locked(bi_server_s* S) {
-    while (!S->queue.empty() && S->active < S->prm.max_active) {
-        request* r = S->queue.front();
-        if (S->held_bytes + r->est_bytes > S->prm.mem_budget_bytes && S->active > 0) break;
-        S->queue.pop_front();
-        r->held_bytes = r->est_bytes;
-        S->held_bytes += r->held_bytes;
+// Admit waiting requests in arrival order.  A request joins the open job of its operator
+// when one is setting up and has room; else it starts a job on its idle cached operator; else
+// it starts a job that builds a new operator; a request whose operator is busy with a job
+// that no longer takes columns waits for that job to finish.
+void admit_locked(bi_server_s* S) {
+    const int cap = std::max(1, S->prm.max_batch_rhs);
+    for (auto it = S->queue.begin(); it != S->queue.end();) {
+        request* r = *it;
+        op_entry* e = nullptr;
+        if (S->prm.share_operators)
+            for (op_entry* o : S->ops)
+                if (same_operator(o, r)) {
+                    e = o;
+                    break;
+                }
+        if (e && e->state == OP_BUSY) {
+            job* open = nullptr;
+            for (job* jb : S->pending)
+                if (jb->op == e && !jb->sealed) open = jb;
+            int cols = 0;
+            if (open)
+                for (request* q : open->reqs) cols += q->nrhs;
+            if (open && cols + r->nrhs <= cap) {
+                const int64_t more = estimate_job_bytes(r, cols + r->nrhs) - open->est_bytes;
+                if (S->held_bytes + more <= S->prm.mem_budget_bytes) {
+                    open->reqs.push_back(r);
+                    open->est_bytes += more;
+                    open->held_bytes += more;
+                    S->held_bytes += more;
+                    r->jb = open;
+                    r->state = RQ_SETUP;
+                    S->stats[BI_STAT_MERGED_REQUESTS] += 1;
+                    it = S->queue.erase(it);
+                    continue;
+                }
+            }
+            ++it;   // waits for the operator's current job
+            continue;
+        }
+        if (S->active >= S->prm.max_active) break;
+        const int max_rhs = std::max(cap, r->nrhs);
+        const int64_t op_bytes = e ? 0 : estimate_op_bytes(r, max_rhs);
+        const int64_t jb_bytes = estimate_job_bytes(r, r->nrhs);
+        if (e) e->state = OP_BUSY;      // not evictable while this request may use it
+        if (S->held_bytes + op_bytes + jb_bytes > S->prm.mem_budget_bytes) evict_locked(S, op_bytes + jb_bytes);
+        if (S->held_bytes + op_bytes + jb_bytes > S->prm.mem_budget_bytes && S->active > 0) {
+            if (e) e->state = OP_IDLE;
+            break;
+        }
+        job* jb = new job();
+        if (!e) {
+            e = new op_entry();
+            e->key = r->key;
+            e->verts = r->verts;
+            e->tris = r->tris;
+            e->k0 = r->k0;
+            e->prm = r->prm;
+            e->max_rhs = max_rhs;
+            e->bytes = op_bytes;
+            S->held_bytes += op_bytes;
+            S->ops.push_back(e);
+            jb->builds_op = true;
+            S->stats[BI_STAT_OPERATORS_BUILT] += 1;
+        } else {
+            S->stats[BI_STAT_CACHE_HITS] += 1;
+        }
+        e->state = OP_BUSY;
+        jb->op = e;
+        jb->reqs.push_back(r);
+        jb->est_bytes = jb->held_bytes = jb_bytes;
+        S->held_bytes += jb_bytes;
         S->active += 1;
+        S->stats[BI_STAT_JOBS] += 1;
+        r->jb = jb;
         r->state = RQ_SETUP;
-        S->to_setup.push_back(r);
+        S->pending.push_back(jb);
+        S->to_setup.push_back(jb);
+        it = S->queue.erase(it);
         S->cv.notify_all();
     }
 }
 
-static void setup_worker(bi_server_s* S) {
+// Build the job's operator if needed, then close its columns and create its right-hand sides
+// and GMRES context (setup thread).
+void setup_job(bi_server_s* S, job* jb) {
+    op_entry* e = jb->op;
+    if (jb->builds_op) {
+        CU(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
+        bi_params p = e->prm;
+        p.stream = e->stream;
+        p.max_rhs = e->max_rhs;
+        bi_handle h = nullptr;
+        const int rc = bi_setup(e->verts.data(), (int)e->verts.size() / 3, e->tris.data(), (int)e->tris.size() / 3,
+                                e->k0, 0, &p, &h);
+        if (rc != BI_OK) throw bi_error{rc, std::string("setup: ") + bi_last_error(nullptr)};
+        e->h = h;
+        bi_info_t inf;
+        bi_get_info(h, &inf);
+        e->setup_ms = inf.setup_ms;
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->held_bytes += inf.device_bytes - e->bytes;
+        e->bytes = inf.device_bytes;
+    }
+    std::vector<request*> reqs;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        jb->sealed = true;
+        reqs = jb->reqs;
+    }
+    bi_handle_s* h = e->h;
+    int R = 0;
+    for (request* r : reqs) {
+        r->col0 = R;
+        R += r->nrhs;
+    }
+    jb->R = R;
+    const size_t vb = (size_t)h->nun * R * h->csize;
+    CU(cudaMalloc(&jb->d_rhs, vb));
+    CU(cudaMalloc(&jb->d_x, vb));
+    std::vector<double> tolv;
+    for (request* r : reqs) {
+        const int rc = bi_rhs_planewave(h, r->khat.data(), r->phat.data(), r->nrhs,
+                                        (char*)jb->d_rhs + (size_t)r->col0 * h->nun * h->csize);
+        if (rc != BI_OK) throw bi_error{rc, bi_last_error(h)};
+        tolv.insert(tolv.end(), r->nrhs, r->tol);
+        r->setup_ms = jb->builds_op ? e->setup_ms : 0.0;
+    }
+    jb->ctx = bi_gmres_create(h, jb->d_rhs, R, tolv.data(), e->stream);
+    const int64_t actual = bi_gmres_bytes(jb->ctx) + 2 * (int64_t)vb;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->held_bytes += actual - jb->held_bytes;
+    jb->held_bytes = actual;
+    for (request* r : reqs) r->state = RQ_RUNNING;
+    S->ready.push_back(jb);
+}
+
+void setup_worker(bi_server_s* S) {
     cudaSetDevice(S->device);
     for (;;) {
-        request* r = nullptr;
+        job* jb = nullptr;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv.wait(lk, [&] { return S->stop || !S->to_setup.empty(); });
             if (S->stop) return;
-            r = S->to_setup.front();
+            jb = S->to_setup.front();
             S->to_setup.pop_front();
         }
-        r->t_start = clk::now();
         try {
-            CU(cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking));
-            bi_params p = r->prm;
-            p.stream = r->stream;
-            p.max_rhs = std::max(p.max_rhs, r->nrhs);
-            bi_handle h = nullptr;
-            int rc = bi_setup(r->verts.data(), (int)r->verts.size() / 3, r->tris.data(), (int)r->tris.size() / 3, r->k0,
-                              0, &p, &h);
-            if (rc != BI_OK) throw bi_error{rc, std::string("setup: ") + bi_last_error(nullptr)};
-            r->op = h;
-            bi_info_t inf;
-            bi_get_info(h, &inf);
-            r->setup_ms = inf.setup_ms;
-            const size_t vb = (size_t)h->nun * r->nrhs * h->csize;
-            CU(cudaMalloc(&r->d_rhs, vb));
-            CU(cudaMalloc(&r->d_x, vb));
-            rc = bi_rhs_planewave(h, r->khat.data(), r->phat.data(), r->nrhs, r->d_rhs);
-            if (rc != BI_OK) throw bi_error{rc, bi_last_error(h)};
-            r->ctx = bi_gmres_create(h, r->d_rhs, r->nrhs, r->tol, r->stream);
-            const int64_t actual = inf.device_bytes + bi_gmres_bytes(r->ctx) + 2 * (int64_t)vb;
-            {
-                std::lock_guard<std::mutex> lk(S->mu);
-                S->held_bytes += actual - r->held_bytes;
-                r->held_bytes = actual;
-                r->state = RQ_RUNNING;
-                S->ready.push_back(r);
-            }
+            setup_job(S, jb);
             S->cv.notify_all();
         } catch (const bi_error& e) {
-            fail_request(S, r, e.code, e.msg);
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                jb->sealed = true;
+            }
+            finish_job(S, jb, e.code, e.msg);
         } catch (const std::exception& e) {
-            // host allocation failure: fail this request, keep the worker alive
-            fail_request(S, r, BI_ERR_OOM, std::string("setup: ") + e.what());
+            // host allocation failure: fail this job, keep the worker alive
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                jb->sealed = true;
+            }
+            finish_job(S, jb, BI_ERR_OOM, std::string("setup: ") + e.what());
         }
     }
 }
 
-static void serve_loop(bi_server_s* S) {
+// Results of a finished job, split into its requests.
+void retire_job(bi_server_s* S, job* jb) {
+    bi_handle_s* h = jb->op->h;
+    std::vector<int> its(jb->R, 0);
+    std::vector<double> rel(jb->R, 0.0);
+    const int st = bi_gmres_finish(jb->ctx, jb->d_x, its.data(), rel.data());
+    const size_t col = (size_t)h->nun * h->csize;
+    for (request* r : jb->reqs) {
+        r->x_host.resize(col * r->nrhs);
+        CU(cudaMemcpy(r->x_host.data(), (const char*)jb->d_x + col * r->col0, col * r->nrhs, cudaMemcpyDeviceToHost));
+        r->iters.assign(its.begin() + r->col0, its.begin() + r->col0 + r->nrhs);
+        r->relres.assign(rel.begin() + r->col0, rel.begin() + r->col0 + r->nrhs);
+        r->status = BI_OK;
+        for (int c = 0; c < r->nrhs; ++c)
+            if (r->relres[c] > r->tol * 1.0001 + 1e-12) r->status = BI_ERR_NOT_CONVERGED;
+        if (st != BI_OK && st != BI_ERR_NOT_CONVERGED) r->status = st;
+        if (r->status == BI_ERR_NOT_CONVERGED) r->err = "GMRES did not reach tol";
+    }
+    finish_job(S, jb, BI_OK, "");
+}
+
+void serve_loop(bi_server_s* S) {
     cudaSetDevice(S->device);
     for (;;) {
         {
@@ -181,29 +434,22 @@ static void serve_loop(bi_server_s* S) {
                 S->ready.pop_front();
             }
         }
-        // one pass: every running solve advances as far as its completed work allows
+        // one pass: every running job advances as far as its completed work allows
         for (size_t i = 0; i < S->running.size();) {
-            request* r = S->running[i];
+            job* jb = S->running[i];
             try {
-                int fin = bi_gmres_advance(r->ctx);
-                if (fin) {
-                    r->iters.assign(r->nrhs, 0);
-                    r->relres.assign(r->nrhs, 0.0);
-                    int st = bi_gmres_finish(r->ctx, r->d_x, r->iters.data(), r->relres.data());
-                    const size_t vb = (size_t)r->op->nun * r->nrhs * r->op->csize;
-                    r->x_host.resize(vb);
-                    CU(cudaMemcpy(r->x_host.data(), r->d_x, vb, cudaMemcpyDeviceToHost));
-                    fail_request(S, r, st, st == BI_OK ? "" : "GMRES did not reach tol");
+                if (bi_gmres_advance(jb->ctx)) {
                     S->running.erase(S->running.begin() + i);
+                    retire_job(S, jb);
                     continue;
                 }
             } catch (const bi_error& e) {
-                fail_request(S, r, e.code, e.msg);
                 S->running.erase(S->running.begin() + i);
+                finish_job(S, jb, e.code, e.msg);
                 continue;
             } catch (const std::exception& e) {
-                fail_request(S, r, BI_ERR_OOM, std::string("solve: ") + e.what());
                 S->running.erase(S->running.begin() + i);
+                finish_job(S, jb, BI_ERR_OOM, std::string("solve: ") + e.what());
                 continue;
             }
             ++i;
@@ -212,12 +458,16 @@ static void serve_loop(bi_server_s* S) {
     }
 }
 
+}  // namespace
+
 extern "C" void bi_server_default_params(bi_server_params* p) {
     if (!p) return;
     std::memset(p, 0, sizeof(*p));
     p->mem_budget_bytes = 0;
     p->max_active = 8;
     p->queue_capacity = 4096;
+    p->share_operators = 1;
+    p->max_batch_rhs = 64;
 }
 
 extern "C" int bi_server_create(const bi_server_params* prm, bi_server* out) {
@@ -227,7 +477,8 @@ extern "C" int bi_server_create(const bi_server_params* prm, bi_server* out) {
     if (!S) return BI_ERR_OOM;
     if (prm) S->prm = *prm;
     else bi_server_default_params(&S->prm);
-    if (S->prm.max_active < 1 || S->prm.queue_capacity < 1 || S->prm.mem_budget_bytes < 0) {
+    if (S->prm.max_active < 1 || S->prm.queue_capacity < 1 || S->prm.mem_budget_bytes < 0 ||
+        S->prm.max_batch_rhs < 1 || (S->prm.share_operators != 0 && S->prm.share_operators != 1)) {
         delete S;
         return BI_ERR_ARG;
     }
@@ -285,13 +536,16 @@ extern "C" int bi_submit(bi_server S, const double* verts, int nv, const int* tr
     r->k0 = k0;
     if (opt) r->prm = *opt;
     else bi_default_params(&r->prm);
+    r->prm.stream = nullptr;
     r->nrhs = nrhs;
     r->tol = tol;
+    r->key = operator_key(r.get());
     r->t_submit = clk::now();
-    r->est_bytes = estimate_request_bytes(r.get());
+    const int64_t need = estimate_op_bytes(r.get(), std::max(S->prm.max_batch_rhs, nrhs)) +
+                         estimate_job_bytes(r.get(), nrhs);
     std::lock_guard<std::mutex> lk(S->mu);
     if ((int)S->queue.size() >= S->prm.queue_capacity) return BI_ERR_BUSY;
-    if (r->est_bytes > S->prm.mem_budget_bytes) {
+    if (need > S->prm.mem_budget_bytes) {
         S->err = "bi_submit: request needs more device memory than the whole budget";
         return BI_ERR_OOM;
     }
@@ -346,6 +600,19 @@ extern "C" int bi_result(bi_server S, int64_t req, void* x_host, int64_t x_bytes
     return r->status;
 }
 
+extern "C" int bi_server_stats(bi_server S, int64_t* out, int n) {
+    if (!S || !out || n < 1) return BI_ERR_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    int64_t cached = 0;
+    for (op_entry* e : S->ops) cached += e->state == OP_IDLE;
+    int64_t v[BI_SERVER_NSTATS];
+    std::memcpy(v, S->stats, sizeof(v));
+    v[BI_STAT_CACHED_OPERATORS] = cached;
+    v[BI_STAT_HELD_BYTES] = S->held_bytes;
+    for (int i = 0; i < n && i < BI_SERVER_NSTATS; ++i) out[i] = v[i];
+    return BI_OK;
+}
+
 extern "C" int bi_release(bi_server S, int64_t req) {
     if (!S) return BI_ERR_ARG;
     std::lock_guard<std::mutex> lk(S->mu);
@@ -368,24 +635,17 @@ extern "C" void bi_server_destroy(bi_server S) {
     if (S->serve_thread.joinable()) S->serve_thread.join();
     if (S->setup_thread.joinable()) S->setup_thread.join();
     cudaSetDevice(S->device);
-    for (request* r : S->running) {
-        if (r->ctx) bi_gmres_destroy(r->ctx);
-        if (r->op) bi_destroy(r->op);
-        if (r->d_rhs) cudaFree(r->d_rhs);
-        if (r->d_x) cudaFree(r->d_x);
-        if (r->stream) cudaStreamDestroy(r->stream);
-        r->ctx = nullptr;
-        r->op = nullptr;
+    // jobs still set up or running; the threads are gone, so nothing else touches them
+    std::vector<job*> jobs(S->running.begin(), S->running.end());
+    jobs.insert(jobs.end(), S->ready.begin(), S->ready.end());
+    jobs.insert(jobs.end(), S->to_setup.begin(), S->to_setup.end());
+    for (job* jb : jobs) {
+        if (jb->ctx) bi_gmres_destroy(jb->ctx);
+        if (jb->d_rhs) cudaFree(jb->d_rhs);
+        if (jb->d_x) cudaFree(jb->d_x);
+        delete jb;
     }
-    for (request* r : S->ready) {
-        if (r->ctx) bi_gmres_destroy(r->ctx);
-        if (r->op) bi_destroy(r->op);
-        if (r->d_rhs) cudaFree(r->d_rhs);
-        if (r->d_x) cudaFree(r->d_x);
-        if (r->stream) cudaStreamDestroy(r->stream);
-        r->ctx = nullptr;
-        r->op = nullptr;
-    }
+    for (op_entry* e : S->ops) destroy_op(e);
     for (auto& kv : S->all) delete kv.second;
     delete S;
 }

@@ -277,7 +277,7 @@ __global__ void k_add_inplace(int64_t n, z2* __restrict__ a, const z2* __restric
 struct gmres_ctx_impl {
     bi_handle_s* h = nullptr;
     int R = 1, m = 1, maxit = 1;
-    double tol = 1e-3;
+    std::vector<double> tolv;           // per-column tolerance
     int64_t nun = 0, nv = 0;
     cudaStream_t s = nullptr;
     std::vector<void*> mem;
@@ -326,10 +326,11 @@ struct gmres_ctx_impl {
         else k_cvt_from<float><<<nb(nv, th), th, 0, s>>>(nv, (const float*)yout, out);
     }
     // allocate, x0 = 0, |b| (synchronises the stream once)
-    void init(bi_handle_s* hh, const void* rhs, int nrhs, double tol_, cudaStream_t st, void* xin_, void* yout_) {
+    void init(bi_handle_s* hh, const void* rhs, int nrhs, const double* tol_, cudaStream_t st, void* xin_,
+              void* yout_) {
         h = hh;
         R = nrhs;
-        tol = tol_;
+        tolv.assign(tol_, tol_ + nrhs);
         s = st;
         m = std::max(1, h->prm.gmres_restart);
         maxit = std::max(1, h->prm.gmres_maxit);
@@ -389,7 +390,7 @@ struct gmres_ctx_impl {
             double rel = beta[r] / std::max(bnorm[r], 1e-300);
             // the true residual decides; a column whose true residual did not drop over a
             // whole cycle by 1% has stagnated (matvec rounding floor) and stops
-            if (bnorm[r] == 0.0 || rel <= tol) done[r] = 1;
+            if (bnorm[r] == 0.0 || rel <= tolv[r]) done[r] = 1;
             else if (done[r] == 0 && rel > 0.99 * last_true[r]) done[r] = 2;
             else if (done[r] == 1) done[r] = 0;
             last_true[r] = rel;
@@ -436,7 +437,7 @@ struct gmres_ctx_impl {
             if (a[r]) {
                 kcols[r] = j + 1;
                 its[r] += 1;
-                if (h_res[r] / std::max(bnorm[r], 1e-300) <= tol) a[r] = 0;
+                if (h_res[r] / std::max(bnorm[r], 1e-300) <= tolv[r]) a[r] = 0;
                 any = any || a[r];
             }
         ++j;
@@ -472,14 +473,14 @@ struct gmres_ctx_impl {
             double rel = bnorm[r] > 0 ? rr[r] / bnorm[r] : 0.0;
             if (iters) iters[r] = its[r];
             if (relres) relres[r] = rel;
-            if (status == BI_OK && rel > tol * 1.0001 + 1e-12) status = BI_ERR_NOT_CONVERGED;
+            if (status == BI_OK && rel > tolv[r] * 1.0001 + 1e-12) status = BI_ERR_NOT_CONVERGED;
         }
         finished = true;
         return status;
     }
 };
 
-gmres_ctx* bi_gmres_create(bi_handle_s* h, const void* rhs, int nrhs, double tol, cudaStream_t s) {
+gmres_ctx* bi_gmres_create(bi_handle_s* h, const void* rhs, int nrhs, const double* tol, cudaStream_t s) {
     gmres_ctx_impl* c = new gmres_ctx_impl();
     try {
         c->init(h, rhs, nrhs, tol, s, nullptr, nullptr);
@@ -517,7 +518,8 @@ int bi_gmres_finish(gmres_ctx* cc, void* xout, int* iters, double* relres) {
 
 int bi_gmres(bi_handle_s* h, const void* rhs, void* xout, int R, double tol, int* iters, double* relres) {
     gmres_ctx_impl c;
-    c.init(h, rhs, R, tol, h->stream, h->d_sx, h->d_sy);
+    const std::vector<double> tolv(R, tol);
+    c.init(h, rhs, R, tolv.data(), h->stream, h->d_sx, h->d_sy);
     while (c.start_cycle()) {
         for (;;) {
             c.enqueue_iteration();

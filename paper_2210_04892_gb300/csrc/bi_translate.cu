@@ -94,24 +94,28 @@ __device__ __forceinline__ void store_pair(cpx<float>* p, cpx<float> a, cpx<floa
     *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
 }
 
-template <typename T, int VP>
+template <typename T, int VP, int CH>
 __global__ void __launch_bounds__(256) k_translate_pcE(int K, int R, int D, int np, const int* __restrict__ cptr,
                                                        const int* __restrict__ tptr, const int* __restrict__ src,
                                                        const uint4* __restrict__ codes, const cpx<T>* __restrict__ Top,
                                                        const cpx<T>* __restrict__ U, cpx<T>* __restrict__ V) {
-    // thread = (direction, VP consecutive pairs of entries); the next source's entries and
-    // offset codes are loaded one iteration ahead
+    // thread = (direction, VP consecutive pairs of entries, CH of the parent's 8 child slots);
+    // the next source's entries and offset codes are loaded one iteration ahead.  CH = 4 halves
+    // the accumulators (more resident warps) at the price of loading each source twice.
+    constexpr int NH = 8 / CH;                 // threads sharing one (direction, pairs)
     const int p = (int)(blockIdx.x % (unsigned)np);
     const int chunk = (int)(blockIdx.x / (unsigned)np);
-    const int TPD = R / VP;                    // threads per direction
-    const int d = threadIdx.x / TPD, j = threadIdx.x - d * TPD;
+    const int TPP = R / VP;                    // pair groups per direction
+    const int TPD = TPP * NH;                  // threads per direction
+    const int d = threadIdx.x / TPD, jj = threadIdx.x - d * TPD;
+    const int j = jj % TPP, half = jj / TPP;
     const int k = chunk * D + d;
     if (d >= D || k >= K) return;   // no barrier below
     const int64_t E = 2 * R;
     const int c0 = cptr[p], nc = cptr[p + 1] - c0;
-    cpx<T> acc[8][2 * VP];
+    cpx<T> acc[CH][2 * VP];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < CH; ++i)
 #pragma unroll
         for (int v = 0; v < 2 * VP; ++v) acc[i][v] = czero<T>();
     const cpx<T>* ub = U + (int64_t)k * E + 2 * VP * j;
@@ -130,7 +134,9 @@ __global__ void __launch_bounds__(256) k_translate_pcE(int K, int R, int D, int 
         cpx<T> u[2 * VP];
 #pragma unroll
         for (int v = 0; v < 2 * VP; ++v) u[v] = un[v];
-        const unsigned cc[4] = {cn.x, cn.y, cn.z, cn.w};
+        // the 16-bit codes of this thread's child slots, indexed at compile time only
+        const unsigned w0 = CH == 8 ? cn.x : (half ? cn.z : cn.x), w1 = CH == 8 ? cn.y : (half ? cn.w : cn.y);
+        const unsigned w2 = cn.z, w3 = cn.w;
         if (q + 1 < q1) {
             const cpx<T>* us = ub + (int64_t)src[q + 1] * box;
 #pragma unroll
@@ -138,8 +144,9 @@ __global__ void __launch_bounds__(256) k_translate_pcE(int K, int R, int D, int 
             cn = codes[q + 1];
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const unsigned code = (cc[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
+        for (int i = 0; i < CH; ++i) {
+            const unsigned w = (i >> 1) == 0 ? w0 : (i >> 1) == 1 ? w1 : (i >> 1) == 2 ? w2 : w3;
+            const unsigned code = (w >> ((i & 1) * 16)) & 0xFFFFu;
             if (code != kNone) {
                 const cpx<T> t = ldg_cpx(tk + (int64_t)code * K);
 #pragma unroll
@@ -149,38 +156,42 @@ __global__ void __launch_bounds__(256) k_translate_pcE(int K, int R, int D, int 
     }
     cpx<T>* vb = V + (int64_t)c0 * box + (int64_t)k * E + 2 * VP * j;
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-        if (i < nc)
+    for (int i = 0; i < CH; ++i) {
+        const int ci = (CH == 8 ? 0 : half * CH) + i;
+        if (ci < nc)
 #pragma unroll
-            for (int v = 0; v < VP; ++v) store_pair(vb + i * box + 2 * v, acc[i][2 * v], acc[i][2 * v + 1]);
+            for (int v = 0; v < VP; ++v) store_pair(vb + ci * box + 2 * v, acc[i][2 * v], acc[i][2 * v + 1]);
+    }
 }
 
+// Variant codes (autotuner): 1 / 2 = one / two pairs of entries per thread over all 8 child
+// slots; 3 / 4 = the same with the child slots split over two threads (4 each).
 template <typename T>
-bool launch_tE(bi_handle_s* h, int l, int E, cudaStream_t s, int vp_force) {
+bool launch_tE(bi_handle_s* h, int l, int E, cudaStream_t s, int variant) {
     level_t& L = h->lev[l];
     const int R = E / 2;
     // two pairs per thread when R is even (FP32): the code decode and operator loads serve twice
     // the multiply-adds
     int VP = (R % 2 == 0 && sizeof(T) == 4) ? 2 : 1;
-    if (vp_force == 1) VP = 1;
-    if (vp_force == 2) {
+    int CH = 8;
+    if (variant == 1 || variant == 3) VP = 1;
+    if (variant == 2 || variant == 4) {
         if (R % 2 != 0) return false;
         VP = 2;
     }
-    const int TPD = R / VP;
+    if (variant == 3 || variant == 4) CH = 4;
+    const int TPD = R / VP * (8 / CH);
+    if (TPD > 256) return false;
     const int D = std::max(1, 256 / TPD);
     const int threads = std::min(1024, (D * TPD + 31) / 32 * 32);
     const int64_t nchunk = (L.K + D - 1) / D;
     const int64_t blocks = nchunk * L.tp_np;
     if (blocks > 0x7fffffffLL) throw bi_error{BI_ERR_ARG, "translation grid too large"};
-    if (VP == 2)
-        k_translate_pcE<T, 2><<<(unsigned)blocks, threads, 0, s>>>(L.K, R, D, L.tp_np, L.d_tp_cptr, L.d_tp_ptr, L.d_tp_src,
-                                                                    (const uint4*)L.d_tp_code, (const cpx<T>*)L.d_T,
-                                                                    (const cpx<T>*)L.d_U, (cpx<T>*)L.d_V);
-    else
-        k_translate_pcE<T, 1><<<(unsigned)blocks, threads, 0, s>>>(L.K, R, D, L.tp_np, L.d_tp_cptr, L.d_tp_ptr, L.d_tp_src,
-                                                                    (const uint4*)L.d_tp_code, (const cpx<T>*)L.d_T,
-                                                                    (const cpx<T>*)L.d_U, (cpx<T>*)L.d_V);
+    auto kern = VP == 2 ? (CH == 8 ? k_translate_pcE<T, 2, 8> : k_translate_pcE<T, 2, 4>)
+                        : (CH == 8 ? k_translate_pcE<T, 1, 8> : k_translate_pcE<T, 1, 4>);
+    kern<<<(unsigned)blocks, threads, 0, s>>>(L.K, R, D, L.tp_np, L.d_tp_cptr, L.d_tp_ptr, L.d_tp_src,
+                                              (const uint4*)L.d_tp_code, (const cpx<T>*)L.d_T, (const cpx<T>*)L.d_U,
+                                              (cpx<T>*)L.d_V);
     CU(cudaGetLastError());
     return true;
 }
@@ -278,7 +289,8 @@ bool bi_translate_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
         if (h->prec == 0) launch_t<double>(h, l, s);
         else launch_t<float>(h, l, s);
     } else if (E <= 512) {
-        const int v = h->force_variant >= 0 ? h->force_variant : h->variant_of(0, l, E);
+        const int v = h->force_variant >= 0 ? h->force_variant
+                      : h->translate_variant > 0 ? h->translate_variant : h->variant_of(0, l, E);
         return h->prec == 0 ? launch_tE<double>(h, l, E, s, v) : launch_tE<float>(h, l, E, s, v);
     } else {
         return false;

@@ -74,6 +74,7 @@ def test_every_entry_point_rejects_null_handles():
     assert L.bi_solve(None, None, None, 1, 1e-3, None, None) == E
     assert L.bi_solve_refined(None, None, None, None, 1, 1e-3, None, None) == E
     assert L.bi_coupling_blocks(None, 0, None, None, None, None, None, None, None) == E
+    assert L.bi_server_stats(None, None, 0) == E
     assert L.bi_set_coupling(None, 1, None, None, None, None, None, None, bi.QSOLVE(), None) == E
     assert L.bi_matvec_coupled(None, None, None, 1) == E
     assert L.bi_farfield(None, None, 1, None, 1, None) == E

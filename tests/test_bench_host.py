@@ -64,6 +64,19 @@ def test_stage_roofline_picks_the_slower_bound(bench_info):
     assert sr["near"]["bound"] == "alu"
 
 
+def test_fused_gather_and_scatter_fold_into_their_stages(bench_info):
+    """When the gather of x and the scatter of y time as empty (fused into the near and the
+    receive kernels), their bytes count in those stages and they get no fraction of their own."""
+    bench, info = bench_info
+    sb = bench.stage_bytes(info, 8)
+    stages = {k: 1.0 for k in sb}
+    stages["gather"] = stages["scatter"] = 0.0
+    sr = bench.stage_roofline(info, 8, stages, 6000.0)
+    assert "gather" not in sr and "scatter" not in sr
+    assert sr["near"]["bytes"] == sb["near"] + sb["gather"]
+    assert sr["receive"]["bytes"] == sb["receive"] + info["n_unknowns"] * 8 * 8
+
+
 def test_measured_traffic_matches_the_byte_model(bench_info):
     """Every HBM-bound kernel of the roofline has a committed per-launch DRAM figure that fits
     the algorithmic bytes of its stage: at most 5% above (the kernels re-read nothing), and

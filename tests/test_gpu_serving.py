@@ -73,10 +73,11 @@ def test_same_result_alone_and_in_the_mix(bi):
     mix.close()
     for r in res:
         assert r["status"] == bi.BI_OK
-    # Each request builds its own operator.  The near-field set-up adds the up-to-four
+    # The two servers build their own operators.  The near-field set-up adds the up-to-four
     # triangle-pair contributions of an entry with atomics, so two set-ups of one surface may
-    # differ in the last bit of an entry; the products themselves are deterministic (no
-    # atomics).  With the same GMRES iteration count the solutions agree to that rounding as
+    # differ in the last bit of an entry; and in the mix the two copies of the request share
+    # one job with more columns, whose products take other kernel forms (other summation
+    # orders).  With the same GMRES iteration count the solutions agree to that rounding as
     # GMRES amplifies it (measured 2.2e-5 in FP32); in any case both meet the stated tolerance.
     for r in (res[1], res[4]):
         assert rel(r["x"], a["x"]) < TOL
@@ -92,7 +93,8 @@ def test_admission_limits(bi):
         small.submit(v, t, K0, [0, 0, 1.0], [1.0, 0, 0], tol=TOL)
     assert e.value.code == bi.BI_ERR_OOM
     small.close()
-    srv = bi.Server(max_active=1, queue_capacity=1)
+    # requests that cannot merge (no operator sharing) fill the queue behind the running one
+    srv = bi.Server(max_active=1, queue_capacity=1, share_operators=False)
     codes = []
     ids = []
     for _ in range(4):
@@ -103,4 +105,49 @@ def test_admission_limits(bi):
     assert bi.BI_ERR_BUSY in codes
     for i in ids:
         assert srv.wait(i)["status"] == bi.BI_OK
+    srv.close()
+
+
+def test_requests_on_one_operator_share_it_and_merge(bi):
+    """Requests on the same surface share one operator and one job (columns of all of them in
+    one GMRES, one batched product per iteration), each column keeps its own tolerance, the
+    results equal direct solves, and a later request reuses the cached operator."""
+    v, t = icosphere(8, 0.5)
+    kh = np.array([[0, 0, 1.0], [1.0, 0, 0], [0, 1.0, 0]])
+    ph = np.array([[1.0, 0, 0], [0, 0, 1.0], [1.0, 0, 0]])
+    tols = [1e-3, 2e-4, 5e-4]
+    srv = bi.Server(max_active=4)
+    ids = [srv.submit(v, t, K0, kh[i:i + 1], ph[i:i + 1], tol=tols[i], op_mode=1) for i in range(3)]
+    e1 = ellipsoid(10, (1.0, 0.75, 0.5))
+    other = srv.submit(*e1, K0, kh[:1], ph[:1], tol=TOL, op_mode=1)
+    res = [srv.wait(i) for i in ids]
+    assert srv.wait(other)["status"] == bi.BI_OK
+    st = srv.stats()
+    assert st["operators_built"] == 2
+    assert st["merged_requests"] + st["cache_hits"] >= 2
+    assert st["jobs"] <= 3
+    op = bi.Operator(v, t, K0, op_mode=1, max_rhs=1)
+    for i, r in enumerate(res):
+        assert r["status"] == bi.BI_OK
+        assert r["relres"][0] <= tols[i] * 1.001
+        b = op.rhs_planewave(kh[i], ph[i])
+        x, its, relres = op.solve(b, tol=tols[i])
+        assert rel(r["x"][0], x.cpu().numpy()[0]) < 10 * tols[i]
+    op.close()
+    # the cached operator serves a later request without a set-up
+    again = srv.wait(srv.submit(v, t, K0, kh[:1], ph[:1], tol=TOL, op_mode=1))
+    assert again["status"] == bi.BI_OK and again["setup_ms"] == 0.0
+    assert srv.stats()["cache_hits"] >= 1
+    srv.close()
+
+
+def test_unshared_server_builds_one_operator_per_request(bi):
+    v, t = icosphere(6, 0.5)
+    srv = bi.Server(max_active=4, share_operators=False)
+    ids = [srv.submit(v, t, K0, [0, 0, 1.0], [1.0, 0, 0], tol=TOL, op_mode=1) for _ in range(3)]
+    res = [srv.wait(i) for i in ids]
+    st = srv.stats()
+    assert st["operators_built"] == 3 and st["merged_requests"] == 0 and st["cached_operators"] == 0
+    for r in res:
+        assert r["status"] == bi.BI_OK and r["setup_ms"] > 0
     srv.close()
