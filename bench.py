@@ -59,6 +59,11 @@ def parse():
     ap.add_argument("--serving", type=int, default=64, help="requests of the serving section (0: skip)")
     ap.add_argument("--serving-max-unknowns", type=int, default=50000)
     ap.add_argument("--serving-max-rhs", type=int, default=32)
+    ap.add_argument("--serving-plain", type=int, default=1, help="time the plain one-at-a-time form too (0: skip)")
+    ap.add_argument("--profile-one", choices=["headline", "secondary", "cube_cylinder"],
+                    help="profiling aid: set up the named workload, run a few products, then bracket ONE "
+                         "product with cudaProfilerStart/Stop (for ncu --profile-from-start off) and exit")
+    ap.add_argument("--nrhs", type=int, default=0, help="with --profile-one: right-hand sides (0: the workload's)")
     return ap.parse_args()
 
 
@@ -436,7 +441,8 @@ def _serve(bi, reqs, arrivals, tol, share=True, max_active=8):
 def _plain_fifo(bi, reqs, arrivals, tol):
     """The plain form: one request at a time in arrival order, its operator set up, then its
     right-hand sides solved one at a time (FP32, one-RHS products).  Each request's service time
-    is measured; latencies follow from the arrivals of a single first-come-first-served server."""
+    is measured; latencies follow from the arrivals of a single first-come-first-served server,
+    and its capacity makespan (everything submitted at once) is the sum of the service times."""
     import torch
     service, ok = [], True
     for q in reqs:
@@ -453,7 +459,7 @@ def _plain_fifo(bi, reqs, arrivals, tol):
     for ta, sv in zip(arrivals, service):
         finish = max(finish, ta) + sv
         lat.append(finish - ta)
-    return np.array(lat), finish - arrivals[0], ok
+    return np.array(lat), finish - arrivals[0], ok, float(sum(service))
 
 
 def run_serving(args):
@@ -472,6 +478,7 @@ def run_serving(args):
     work = sum((len(q["tris"]) * 3 // 2) * (2 if q["op_mode"] == 0 else 1) * len(q["khat"]) for q in reqs)
     n = len(reqs)
     _, span0, _, _, _ = _serve(bi, reqs, [0.0] * n, tol)
+    _, span0_u, _, _, _ = _serve(bi, reqs, [0.0] * n, tol, share=False)
     rate = 0.75 * n / span0
     rng = np.random.default_rng(20221011 + 31)
     arrivals = list(np.cumsum(rng.exponential(1.0 / rate, n)))
@@ -482,18 +489,23 @@ def run_serving(args):
                 "throughput": work / span}
     lat, span, setup_ms, ok, stats = _serve(bi, reqs, arrivals, tol)
     lat_u, span_u, setup_u, ok_u, stats_u = _serve(bi, reqs, arrivals, tol, share=False)
-    lat_p, span_p, ok_p = _plain_fifo(bi, reqs, arrivals, tol)
+    lat_p, span_p, ok_p, cap_p = _plain_fifo(bi, reqs, arrivals, tol) if args.serving_plain else (None, None, True, None)
     out = {"requests": n, "unknowns_range": [2000, args.serving_max_unknowns], "max_rhs": args.serving_max_rhs,
            "distinct_operators": len({(q["shape"], len(q["tris"]), q["op_mode"]) for q in reqs}), "tol": tol,
            "arrival_rate_per_s": rate, "unit": "unknowns*RHS solved/s", "all_converged_or_reported": bool(ok and ok_u and ok_p),
-           "capacity_makespan_s": span0}
+           "capacity_makespan_s": span0, "capacity_throughput": work / span0,
+           "note": "throughput under the Poisson stream is bounded by the arrivals (75% of the batched server's "
+                   "capacity); capacity_throughput (every request submitted at once) compares the forms"}
     out.update(summary(lat, span))
     out.update({"mean_setup_ms": setup_ms, "server_stats": {k: v for k, v in stats.items() if k != "held_bytes"},
                 "form": "operators shared and cached; requests on one operator merged into one batched GMRES"})
-    out["unshared"] = dict(summary(lat_u, span_u), mean_setup_ms=setup_u,
+    out["unshared"] = dict(summary(lat_u, span_u), mean_setup_ms=setup_u, capacity_makespan_s=span0_u,
+                           capacity_throughput=work / span0_u,
                            form="one operator per request; requests overlap on the device, no shared launch")
-    out["plain"] = dict(summary(lat_p, span_p), form="one request at a time (first come first served), one RHS at a "
-                        "time; latencies from each request's measured service time on the same arrivals")
+    if lat_p is not None:
+        out["plain"] = dict(summary(lat_p, span_p), capacity_makespan_s=cap_p, capacity_throughput=work / cap_p,
+                            form="one request at a time (first come first served), one RHS at a time; latencies "
+                                 "from each request's measured service time on the same arrivals")
     return out
 
 
@@ -642,8 +654,40 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def profile_one(args):
+    """One product of a workload between cudaProfilerStart and cudaProfilerStop, after set-up,
+    tuning and warm-up products, so that ncu --profile-from-start off sees exactly one product."""
+    import torch
+    from paper_2210_04892_gb300 import bi
+    from paper_2210_04892_gb300.inputs import SEED_BASE, complex_gaussian, cube_with_cylinder
+    if args.profile_one == "cube_cylinder":
+        v, t = cube_with_cylinder()
+        R = args.nrhs or 8
+    else:
+        w = HEADLINE if args.profile_one == "headline" else SECONDARY
+        v, t, _ = workload_mesh(w["name"])
+        R = args.nrhs or w["nrhs"]
+    op = bi.Operator(v, t, K0, digits=3, precision="fp32", op_mode=0, max_rhs=R)
+    x = torch.from_numpy(complex_gaussian(op.n_unknowns, R, seed=SEED_BASE + 1).astype(np.complex64)).cuda()
+    y = torch.empty_like(x)
+    for _ in range(max(3, args.warmup)):
+        op.matvec(x, out=y)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    op.matvec(x, out=y)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    op.status()
+    print(json.dumps({"profiled": args.profile_one, "n_unknowns": op.n_unknowns, "nrhs": R,
+                      "tuned": op.tuned_config().strip().splitlines()}))
+    op.close()
+
+
 def main():
     args = parse()
+    if args.profile_one:
+        profile_one(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -289,8 +289,9 @@ const char* bi_stage_name(int i);
  * its operator is set up; later requests of a busy operator wait for the next job.  After its
  * job an operator stays cached (idle operators are dropped, oldest first, when the memory
  * budget needs room).  Jobs are admitted while fewer than max_active are set up or running
- * and the device-memory estimate fits mem_budget_bytes; a setup thread builds operators and
- * GMRES states so that set-ups overlap running solves, and the serving thread advances every
+ * and the device-memory estimate fits mem_budget_bytes; setup threads build operators and
+ * GMRES states (and tune the kernel forms for the job's column count) so that set-ups
+ * overlap running solves, and the serving thread advances every
  * running job by one iteration per pass, so their products and Krylov kernels overlap on the
  * device.  Latency = submit to solution on the host. */
 typedef struct bi_server_s* bi_server;
@@ -301,6 +302,7 @@ typedef struct {
     int share_operators;        /* 1 (default): cache operators and merge requests on one operator into
                                    jobs; 0: every request builds its own operator and runs alone */
     int max_batch_rhs;          /* columns of one job, and max_rhs of the operators (default 64) */
+    int setup_threads;          /* host threads that build operators and jobs, 1-16 (default 2) */
 } bi_server_params;
 
 /* bi_server_stats counters */

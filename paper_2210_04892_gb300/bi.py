@@ -70,7 +70,7 @@ class Info(ctypes.Structure):
 
 class ServerParams(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_active", ctypes.c_int), ("queue_capacity", ctypes.c_int),
-                ("share_operators", ctypes.c_int), ("max_batch_rhs", ctypes.c_int)]
+                ("share_operators", ctypes.c_int), ("max_batch_rhs", ctypes.c_int), ("setup_threads", ctypes.c_int)]
 
 
 SERVER_STATS = ("jobs", "operators_built", "cache_hits", "merged_requests", "evictions", "cached_operators",
@@ -426,7 +426,8 @@ class Operator:
 class Server:
     """Continuous-batching solve server (bi_server_* in include/bi.h)."""
 
-    def __init__(self, mem_budget_bytes=0, max_active=8, queue_capacity=4096, share_operators=True, max_batch_rhs=64):
+    def __init__(self, mem_budget_bytes=0, max_active=8, queue_capacity=4096, share_operators=True, max_batch_rhs=64,
+                 setup_threads=2):
         L = load()
         p = ServerParams()
         L.bi_server_default_params(ctypes.byref(p))
@@ -435,6 +436,7 @@ class Server:
         p.queue_capacity = int(queue_capacity)
         p.share_operators = int(bool(share_operators))
         p.max_batch_rhs = int(max_batch_rhs)
+        p.setup_threads = int(setup_threads)
         h = ctypes.c_void_p()
         rc = L.bi_server_create(ctypes.byref(p), ctypes.byref(h))
         if rc != BI_OK:

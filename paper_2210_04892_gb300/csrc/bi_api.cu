@@ -134,9 +134,10 @@ static int setup_handle(const double* verts, int nv, const int* tris, int nt, do
     h->force_anterp_rows = env4 && env4[0] == '1';
     const char* env7 = std::getenv("BI_TRANSLATE_VARIANT");
     h->translate_variant = env7 ? std::atoi(env7) : 0;
-    if (h->translate_variant < 0 || h->translate_variant > 4) h->translate_variant = 0;
+    if (h->translate_variant < 0 || h->translate_variant > 9) h->translate_variant = 0;
     const char* env6 = std::getenv("BI_NEAR_RB");
-    h->near_rb = !(env6 && env6[0] == '0');
+    h->near_rb = env6 ? std::atoi(env6) : 1;
+    if (h->near_rb < 0 || h->near_rb > 2) h->near_rb = 1;
     const char* env5 = std::getenv("BI_AUTOTUNE");
     h->autotune = !(env5 && env5[0] == '0') && !h->force_anterp_rows;
     try {
@@ -613,8 +614,12 @@ extern "C" int bi_tuned_config(bi_handle h, char* buf, int64_t len) {
         const bi_handle_s* src = h->med[0] ? h->med[m] : (m == 0 ? h : nullptr);
         if (!src) continue;
         for (const auto& t : src->tuned) {
-            std::string form = t.pass == 0 ? (std::string(t.variant % 2 == 0 ? "2 pairs/thread" : "1 pair/thread") +
-                                              (t.variant >= 3 ? ", 4 child slots/thread" : ""))
+            std::string form = t.pass == 0 ? (t.variant >= 6 ? std::string(t.variant % 2 ? "2" : "1") +
+                                                                    " pair(s)/thread, " + (t.variant <= 7 ? "4" : "8") +
+                                                                    " child slots, pipelined loads"
+                                              : t.variant == 5 ? std::string("staged sources, thread per child slot")
+                                              : std::string(t.variant % 2 == 0 ? "2 pairs/thread" : "1 pair/thread") +
+                                                    (t.variant >= 3 ? ", 4 child slots/thread" : ""))
                                : t.variant == 2 ? "two-pass"
                                : t.variant >= 200 ? "row blocks, chunk " + std::to_string(t.variant - 200)
                                : t.pass == 1 ? "rows per CTA, chunk " + std::to_string(t.variant - 100)

@@ -57,7 +57,7 @@ struct level_t {
     // interaction list (levels >= 2)
     std::vector<int> il_ptr, il_src, il_off;
     // device
-    void* d_T = nullptr;                // translation operators [343][K] complex (weights folded)
+    void* d_T = nullptr;                // translation operators [344][K] complex (weights folded; row 343 zero)
     int* d_il_ptr = nullptr;
     int* d_il_src = nullptr;
     int* d_il_off = nullptr;
@@ -160,8 +160,9 @@ struct bi_handle_s {
     bool use_fast = true;               // fused kernels (false: two-pass reference kernels)
     bool use_leaf_bulk = true;          // bulk-copy pipelines for leaf aggregation and receive
     int translate_variant = 0;          // translation kernel form forced on every level (test switch
-                                        // BI_TRANSLATE_VARIANT=1..4; 0: tuned)
-    bool near_rb = true;                // row-blocked near kernel for R >= 3 (test switch BI_NEAR_RB=0)
+                                        // BI_TRANSLATE_VARIANT=1..9; 0: tuned)
+    int near_rb = 1;                    // near kernel for 3 <= R <= 8: 1 row pairs, 2 row pairs with
+                                        // cp.async-pipelined block entries, 0 per-row (switch BI_NEAR_RB)
     bool force_anterp_rows = false;     // row-blocked anterpolation on every level (test switch)
     int* d_status = nullptr;            // device status word (0: healthy; see bi_tma.cuh)
     long long wait_cycles = 1ll << 31;  // limit of the bulk-copy waits of the leaf kernels (SM clocks)

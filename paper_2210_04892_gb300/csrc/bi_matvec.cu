@@ -757,6 +757,153 @@ __global__ void __launch_bounds__(256, 2) k_near_rb(int N, int R, int nun, const
     }
 }
 
+// ------------------------------------------------------------------ near field, row pairs, pipelined
+// The row-pair kernel above (MODE 0, FP32) with the block entries brought into shared memory by
+// per-lane cp.async copies NS column steps ahead of their use: lane (t, cl) copies the 16-byte
+// (A, B) entry of row t of the pair at column step + cl into the warp's ring, so the registers
+// hold no loads in flight and each warp keeps NS x 512 bytes of the block stream in flight.
+__device__ __forceinline__ void near_cp16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+template <int RT, int NS>
+__global__ void __launch_bounds__(256, 2) k_near_rbp(int N, int R, int nun, const int* __restrict__ perm,
+                                                     const int2* __restrict__ work, const int* __restrict__ leaf_start,
+                                                     const int* __restrict__ near_ptr, const int* __restrict__ near_src,
+                                                     const int64_t* __restrict__ near_blk,
+                                                     const int* __restrict__ near_col0, const int* __restrict__ near_ncol,
+                                                     const cpx<float>* __restrict__ blocks, const int* __restrict__ gptr,
+                                                     const int* __restrict__ gseg, const float* __restrict__ gval,
+                                                     const cpx<float>* __restrict__ xt, cpx<float>* __restrict__ yt,
+                                                     cpx<float>* __restrict__ yuser) {
+    typedef cpx<float> C;
+    constexpr int NX = 2, RH = RT / 2;
+    extern __shared__ float4 smem_rbp[];
+    float4* ring = smem_rbp;                                    // [8 warps][NS][32]
+    C* xs = reinterpret_cast<C*>(smem_rbp + 8 * NS * 32);      // [NX][RT][ncol]
+    const int b = work[blockIdx.x].x, row0 = work[blockIdx.x].y;
+    const int m0 = leaf_start[b], mb = leaf_start[b + 1] - m0;
+    const int q0 = near_ptr[b], q1 = near_ptr[b + 1];
+    const int64_t seg = near_blk[q0];
+    const int ncol = near_ncol[b];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const int cl = lane & 15, hh = lane >> 4;
+    const int row_end = min(mb, row0 + 16);
+    float4* wr = ring + warp * NS * 32;
+    const int nstep = (ncol + 15) / 16;
+    for (int r0 = 0; r0 < R; r0 += RT) {
+        const int rn = min(RT, R - r0);
+        __syncthreads();
+        for (int q = q0 + warp; q < q1; q += nwarp) {
+            const int s = near_src[q];
+            const int n0 = leaf_start[s], nbs = leaf_start[s + 1] - n0;
+            const int c0 = near_col0[q];
+            const C* xb = xt + (int64_t)n0 * NX * R + r0;
+            for (int i = lane; i < nbs * NX * RT; i += 32) {
+                const int rr = i % RT, X = (i / RT) % NX, n = i / (RT * NX);
+                xs[((size_t)X * RT + rr) * ncol + c0 + n] = rr < rn ? xb[((int64_t)n * NX + X) * R + rr] : czero<float>();
+            }
+        }
+        __syncthreads();
+        const C* xJs = xs + (size_t)(hh * RH) * ncol;
+        const C* xMs = xs + (size_t)(RT + hh * RH) * ncol;
+        for (int ml = row0 + 2 * warp; ml < row_end; ml += 2 * nwarp) {
+            const bool two = ml + 1 < row_end;
+            // this lane copies row (ml + hh) of the pair (a lone last row: row ml twice)
+            const C* crow = blocks + 2 * (seg + (int64_t)(two ? ml + hh : ml) * ncol);
+            auto issue = [&](int st) {
+                const int c = st * 16 + cl;
+                if (st < nstep) near_cp16(&wr[(st % NS) * 32 + lane], crow + 2 * min(c, ncol - 1), c < ncol ? 16 : 0);
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            };
+#pragma unroll
+            for (int st = 0; st < NS - 1; ++st) issue(st);
+            C a0[RH][NX], a1[RH][NX];
+#pragma unroll
+            for (int j = 0; j < RH; ++j)
+#pragma unroll
+                for (int X = 0; X < NX; ++X) { a0[j][X] = czero<float>(); a1[j][X] = czero<float>(); }
+            for (int st = 0; st < nstep; ++st) {
+                issue(st + NS - 1);
+                asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1) : "memory");
+                __syncwarp();
+                const int c = st * 16 + cl;
+                if (c < ncol) {
+                    const float4 e0 = wr[(st % NS) * 32 + cl], e1 = wr[(st % NS) * 32 + 16 + cl];
+                    const C A0 = {e0.x, e0.y}, B0 = {e0.z, e0.w}, A1 = {e1.x, e1.y}, B1 = {e1.z, e1.w};
+#pragma unroll
+                    for (int j = 0; j < RH; ++j) {
+                        const C xJ = xJs[(size_t)j * ncol + c], xM = xMs[(size_t)j * ncol + c];
+                        const C nxM = {-xM.x, -xM.y};
+                        cfma(a0[j][0], A0, xJ);
+                        cfma(a0[j][0], B0, xM);
+                        cfma(a0[j][1], B0, xJ);
+                        cfma(a0[j][1], A0, nxM);
+                        cfma(a1[j][0], A1, xJ);
+                        cfma(a1[j][0], B1, xM);
+                        cfma(a1[j][1], B1, xJ);
+                        cfma(a1[j][1], A1, nxM);
+                    }
+                }
+                __syncwarp();   // the slot is refilled by the copy issued next step
+            }
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                if (t == 1 && !two) break;
+                const int m = m0 + ml + t;
+                const int g0 = gptr[m], gn = gptr[m + 1] - g0;
+                for (int qq = cl; qq < gn; qq += 16) {
+                    const int c = gseg[g0 + qq];
+                    const float gg = gval[2 * (g0 + qq)], xx = gval[2 * (g0 + qq) + 1];
+#pragma unroll
+                    for (int j = 0; j < RH; ++j) {
+                        const C xJ = xJs[(size_t)j * ncol + c], xM = xMs[(size_t)j * ncol + c];
+                        C& acc = t == 0 ? a0[j][1] : a1[j][1];
+                        acc.x += 0.5f * (xx * xJ.x - gg * xM.x);
+                        acc.y += 0.5f * (xx * xJ.y - gg * xM.y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < RH; ++j)
+#pragma unroll
+                for (int X = 0; X < NX; ++X)
+#pragma unroll
+                    for (int o = 1; o < 16; o <<= 1) {
+                        a0[j][X].x += __shfl_xor_sync(0xffffffffu, a0[j][X].x, o);
+                        a0[j][X].y += __shfl_xor_sync(0xffffffffu, a0[j][X].y, o);
+                        a1[j][X].x += __shfl_xor_sync(0xffffffffu, a1[j][X].x, o);
+                        a1[j][X].y += __shfl_xor_sync(0xffffffffu, a1[j][X].y, o);
+                    }
+#pragma unroll
+            for (int j = 0; j < RH; ++j) {
+                const int rr = hh * RH + j;
+                if (cl == j && rr < rn) {
+                    const int r = r0 + rr;
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        if (t == 1 && !two) break;
+                        const int m = m0 + ml + t;
+                        const C sJ = t == 0 ? a0[j][0] : a1[j][0];
+                        const C vJ = {-sJ.x, -sJ.y};
+                        const C vM = t == 0 ? a0[j][1] : a1[j][1];
+                        if (yuser) {
+                            yuser[(int64_t)r * nun + perm[m]] = vJ;
+                            yuser[(int64_t)r * nun + N + perm[m]] = vM;
+                        } else {
+                            yt[((int64_t)m * NX + 0) * R + r] = vJ;
+                            yt[((int64_t)m * NX + 1) * R + r] = vM;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // ------------------------------------------------------------------ leaf aggregation (fused gather)
 // thread per (stored direction kk, RHS r): both components from one 16-byte pattern load give
 // U at kk and at its antipode.
@@ -1557,8 +1704,26 @@ void launch_near_any(bi_handle_s* h, const cpx<T>* x, cpx<T>* yt, cpx<T>* yuser,
     const int64_t nvec = (int64_t)h->N * h->nX * R;
     k_gather_x<T><<<nblk(nvec, 256), 256, 0, s>>>(h->N, h->nX, R, h->nun, h->d_perm, x, (cpx<T>*)h->d_xt);
     CU(cudaGetLastError());
+    if constexpr (MODE == 0 && sizeof(T) == 4) {
+        if (h->near_rb == 2 && R >= 6 && R <= 8) {
+            constexpr int NS = 6;
+            const size_t smem = (size_t)8 * NS * 32 * 16 + (size_t)h->near_ncol_max * 8 * 2 * sizeof(cpx<T>);
+            if (smem <= 110 * 1024) {
+                bi_raise_smem(k_near_rbp<8, NS>, smem);
+                k_near_rbp<8, NS><<<h->near_nwork, 256, smem, s>>>(
+                    h->N, R, h->nun, h->d_perm, (const int2*)h->d_near_work, h->d_leaf_start, h->d_near_ptr,
+                    h->d_near_src, h->d_near_blk, h->d_near_col0, h->d_near_ncol, (const cpx<float>*)h->d_near,
+                    h->d_gram_ptr, h->d_gram_seg, (const float*)h->d_gram_val, (const cpx<float>*)h->d_xt,
+                    (cpx<float>*)yt, (cpx<float>*)yuser);
+                CU(cudaGetLastError());
+                return;
+            }
+        }
+    }
     if constexpr (MODE == 0 || MODE == 1) {
-        if (h->near_rb && R >= 3) {
+        // the row-pair kernel for one chunk of right-hand sides (measured: 25% faster than the
+        // per-row kernel at R = 8, 10% slower at R = 64, where x is restaged per chunk)
+        if (h->near_rb && R >= 3 && R <= 8) {
             if (R >= 6 && launch_near_rb<T, MODE, 8>(h, yt, yuser, R, s)) return;
             if (launch_near_rb<T, MODE, 4>(h, yt, yuser, R, s)) return;
         }
@@ -1815,7 +1980,7 @@ void bi_autotune(bi_handle_s* h, int nrhs, cudaStream_t s) {
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    const std::vector<int> cand[3] = {{1, 2, 3, 4},
+    const std::vector<int> cand[3] = {{1, 2, 3, 4, 5, 6, 7, 8, 9},
                                       {116, 108, 104, 102, 2},
                                       {116, 108, 104, 102, 216, 208, 204, 202, 2}};
     try {

@@ -5,8 +5,8 @@
 // the job is one batched bi_matvec -- one launch per kernel of the product for all its
 // requests.  A job takes every waiting request of its operator (up to max_batch_rhs columns),
 // including those that arrive while the operator is being set up.  Jobs are admitted as device
-// memory and slots allow; a setup thread builds operators and GMRES contexts so that set-ups
-// overlap running solves, and the serving thread advances every running job by one iteration
+// memory and slots allow; setup threads build operators and GMRES contexts (and tune the
+// kernel forms for the job's column count) so that set-ups overlap running solves, and the serving thread advances every running job by one iteration
 // per pass (their products are queued on their own streams and overlap on the device),
 // retires finished jobs and admits waiting requests between passes.
 #include <atomic>
@@ -161,7 +161,8 @@ struct bi_server_s {
     int64_t held_bytes = 0;              // operators (cached or in use) plus jobs
     int active = 0;                      // jobs admitted and not finished
     bool stop = false;
-    std::thread serve_thread, setup_thread;
+    std::thread serve_thread;
+    std::vector<std::thread> setup_threads;
     std::string err;
     int64_t stats[BI_SERVER_NSTATS] = {};
 };
@@ -359,6 +360,11 @@ void setup_job(bi_server_s* S, job* jb) {
         r->setup_ms = jb->builds_op ? e->setup_ms : 0.0;
     }
     jb->ctx = bi_gmres_create(h, jb->d_rhs, R, tolv.data(), e->stream);
+    // tune the level passes for this column count here, off the serving thread (the first
+    // product of a new column count would otherwise time every kernel form while the other
+    // jobs wait)
+    if (h->use_fast) bi_autotune(h, R, e->stream);
+    CU(cudaStreamSynchronize(e->stream));
     const int64_t actual = bi_gmres_bytes(jb->ctx) + 2 * (int64_t)vb;
     std::lock_guard<std::mutex> lk(S->mu);
     S->held_bytes += actual - jb->held_bytes;
@@ -468,6 +474,7 @@ extern "C" void bi_server_default_params(bi_server_params* p) {
     p->queue_capacity = 4096;
     p->share_operators = 1;
     p->max_batch_rhs = 64;
+    p->setup_threads = 2;
 }
 
 extern "C" int bi_server_create(const bi_server_params* prm, bi_server* out) {
@@ -478,7 +485,8 @@ extern "C" int bi_server_create(const bi_server_params* prm, bi_server* out) {
     if (prm) S->prm = *prm;
     else bi_server_default_params(&S->prm);
     if (S->prm.max_active < 1 || S->prm.queue_capacity < 1 || S->prm.mem_budget_bytes < 0 ||
-        S->prm.max_batch_rhs < 1 || (S->prm.share_operators != 0 && S->prm.share_operators != 1)) {
+        S->prm.max_batch_rhs < 1 || (S->prm.share_operators != 0 && S->prm.share_operators != 1) ||
+        S->prm.setup_threads < 1 || S->prm.setup_threads > 16) {
         delete S;
         return BI_ERR_ARG;
     }
@@ -495,16 +503,17 @@ extern "C" int bi_server_create(const bi_server_params* prm, bi_server* out) {
         S->prm.mem_budget_bytes = (int64_t)(fr * 0.8);
     }
     try {
-        S->setup_thread = std::thread(setup_worker, S);
+        for (int i = 0; i < S->prm.setup_threads; ++i) S->setup_threads.emplace_back(setup_worker, S);
         S->serve_thread = std::thread(serve_loop, S);
     } catch (const std::exception&) {
-        // a thread could not be started: stop the one that may have started, then give up
+        // a thread could not be started: stop those that started, then give up
         {
             std::lock_guard<std::mutex> lk(S->mu);
             S->stop = true;
         }
         S->cv.notify_all();
-        if (S->setup_thread.joinable()) S->setup_thread.join();
+        for (std::thread& t : S->setup_threads)
+            if (t.joinable()) t.join();
         if (S->serve_thread.joinable()) S->serve_thread.join();
         delete S;
         return BI_ERR_OOM;
@@ -633,7 +642,8 @@ extern "C" void bi_server_destroy(bi_server S) {
     }
     S->cv.notify_all();
     if (S->serve_thread.joinable()) S->serve_thread.join();
-    if (S->setup_thread.joinable()) S->setup_thread.join();
+    for (std::thread& t : S->setup_threads)
+        if (t.joinable()) t.join();
     cudaSetDevice(S->device);
     // jobs still set up or running; the threads are gone, so nothing else touches them
     std::vector<job*> jobs(S->running.begin(), S->running.end());

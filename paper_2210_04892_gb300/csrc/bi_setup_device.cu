@@ -1384,7 +1384,10 @@ void bi_fill_translations(bi_handle_s* h) {
         double* d_wth = h->upload(L.wtheta);
         int* d_di = h->upload(dist_idx);
         double* d_hk = h->upload(hk);
-        L.d_T = h->alloc((size_t)343 * L.K * h->csize);
+        // 343 offset codes plus a zero row (code 343) that lets a translation kernel run every
+        // child slot without a branch: a slot without an interaction reads zeros
+        L.d_T = h->alloc((size_t)344 * L.K * h->csize);
+        CU(cudaMemsetAsync((char*)L.d_T + (size_t)343 * L.K * h->csize, 0, (size_t)L.K * h->csize, h->stream));
         int64_t tot = (int64_t)343 * L.K;
         unsigned nb = (unsigned)((tot + 255) / 256);
         if (h->prec == 0)

@@ -164,12 +164,238 @@ __global__ void __launch_bounds__(256) k_translate_pcE(int K, int R, int D, int 
     }
 }
 
+// Pipelined form of the above: the offset codes are loaded two sources ahead, the operator
+// values T[code](k) and the source entries one source ahead, so no load is consumed in the
+// iteration that issues it.  A child slot without an interaction reads the zero row 343 of T,
+// so every slot runs the same multiply-adds without a branch.  CH = 4 or 8 child slots per
+// thread.
+template <typename T, int VP, int CH>
+__global__ void __launch_bounds__(256, CH == 4 ? 3 : 2) k_translate_pp(int K, int R, int D, int np,
+                                                                       const int* __restrict__ cptr,
+                                                                       const int* __restrict__ tptr,
+                                                                       const int* __restrict__ src,
+                                                                       const uint4* __restrict__ codes,
+                                                                       const cpx<T>* __restrict__ Top,
+                                                                       const cpx<T>* __restrict__ U, cpx<T>* __restrict__ V) {
+    constexpr int NH = 8 / CH;
+    const int p = (int)(blockIdx.x % (unsigned)np);
+    const int chunk = (int)(blockIdx.x / (unsigned)np);
+    const int TPP = R / VP;
+    const int TPD = TPP * NH;
+    const int d = threadIdx.x / TPD, jj = threadIdx.x - d * TPD;
+    const int j = jj % TPP, half = jj / TPP;
+    const int k = chunk * D + d;
+    if (d >= D || k >= K) return;   // no barrier below
+    const int64_t E = 2 * R;
+    const int c0 = cptr[p], nc = cptr[p + 1] - c0;
+    cpx<T> acc[CH][2 * VP];
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+#pragma unroll
+        for (int v = 0; v < 2 * VP; ++v) acc[i][v] = czero<T>();
+    const cpx<T>* ub = U + (int64_t)k * E + 2 * VP * j;
+    const cpx<T>* tk = Top + k;
+    const int64_t box = (int64_t)K * E;
+    const int q0 = tptr[p], q1 = tptr[p + 1];
+    // this thread's code words (CH slots) of a source record; past the list: no interaction
+    auto words = [&](int q, unsigned* w) {
+        if (q < q1) {
+            const uint4 c = codes[q];
+            if (CH == 8) {
+                w[0] = c.x; w[1] = c.y; w[2] = c.z; w[3] = c.w;
+            } else {
+                w[0] = half ? c.z : c.x;
+                w[1] = half ? c.w : c.y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < CH / 2; ++i) w[i] = 0xFFFFFFFFu;
+        }
+    };
+    auto load_t = [&](const unsigned* w, cpx<T>* t) {
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const unsigned code = min((w[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu, 343u);
+            t[i] = ldg_cpx(tk + (int64_t)code * K);
+        }
+    };
+    auto load_u = [&](int q, cpx<T>* u) {
+        if (q < q1) {
+            const cpx<T>* us = ub + (int64_t)src[q] * box;
+#pragma unroll
+            for (int v = 0; v < VP; ++v) load_pair(us + 2 * v, u[2 * v], u[2 * v + 1]);
+        }
+    };
+    unsigned w1[CH / 2], w2[CH / 2];
+    cpx<T> t1[CH], u1[2 * VP];
+    words(q0, w1);
+    words(q0 + 1, w2);
+    load_t(w1, t1);
+    load_u(q0, u1);
+    for (int q = q0; q < q1; ++q) {
+        cpx<T> t[CH], u[2 * VP];
+#pragma unroll
+        for (int i = 0; i < CH; ++i) t[i] = t1[i];
+#pragma unroll
+        for (int v = 0; v < 2 * VP; ++v) u[v] = u1[v];
+        // issue the next source's operator values and entries, and the codes after that
+        load_t(w2, t1);
+        load_u(q + 1, u1);
+        words(q + 2, w2);
+#pragma unroll
+        for (int i = 0; i < CH; ++i)
+#pragma unroll
+            for (int v = 0; v < 2 * VP; ++v) cfma(acc[i][v], t[i], u[v]);
+    }
+    cpx<T>* vb = V + (int64_t)c0 * box + (int64_t)k * E + 2 * VP * j;
+#pragma unroll
+    for (int i = 0; i < CH; ++i) {
+        const int ci = (CH == 8 ? 0 : half * CH) + i;
+        if (ci < nc)
+#pragma unroll
+            for (int v = 0; v < VP; ++v) store_pair(vb + ci * box + 2 * v, acc[i][2 * v], acc[i][2 * v + 1]);
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Staged form (FP32): CTA = (parent p, 32 directions, one group of EP entries); thread =
+// (direction, child slot) with the EP entries of its group in registers.  The sources' entries
+// for the CTA's directions are copied into shared memory, KS sources per stage and two stages in
+// flight (cp.async), so each source value is read from global memory once per CTA and then by
+// the 8 child-slot threads of its direction from shared memory (a broadcast); every operator
+// value T[code](k) serves EP multiply-adds.  Rows are padded by 16 bytes so the 4 directions
+// of a warp read distinct banks.
+constexpr int kTrDir = 32, kTrStage = 8;
+template <int EP>
+__global__ void __launch_bounds__(256, 3) k_translate_sm(int K, int E, int np, const int* __restrict__ cptr,
+                                                         const int* __restrict__ tptr, const int* __restrict__ src,
+                                                         const uint4* __restrict__ codes,
+                                                         const cpx<float>* __restrict__ Top,
+                                                         const cpx<float>* __restrict__ U, cpx<float>* __restrict__ V) {
+    constexpr int ROW = EP + 2;                    // complex values per staged row (16-byte pad)
+    extern __shared__ float4 smem_tr[];
+    cpx<float>* buf = reinterpret_cast<cpx<float>*>(smem_tr);   // [2][kTrStage][kTrDir][ROW]
+    const int p = (int)(blockIdx.x % (unsigned)np);
+    const int k0 = (int)(blockIdx.x / (unsigned)np) * kTrDir;
+    const int e0 = blockIdx.y * EP;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int dl = warp * 4 + (lane & 3), slot = lane >> 2;
+    const int k = k0 + dl;
+    const int q0 = tptr[p], q1 = tptr[p + 1];
+    const int c0 = cptr[p], nc = cptr[p + 1] - c0;
+    const int64_t box = (int64_t)K * E;
+    cpx<float> acc[EP];
+#pragma unroll
+    for (int e = 0; e < EP; ++e) acc[e] = czero<float>();
+    // copy sources qs .. qs + n - 1 (n <= kTrStage) into stage st: 16-byte chunks of (source,
+    // direction, entry pair); directions past K are zero-filled
+    auto stage = [&](int st, int qs) {
+        const int n = min(kTrStage, q1 - qs);
+        const int chunks = n * kTrDir * (EP / 2);
+        for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
+            const int h = i % (EP / 2), d = (i / (EP / 2)) % kTrDir, sq = i / (kTrDir * (EP / 2));
+            cpx<float>* dst = buf + ((size_t)(st * kTrStage + sq) * kTrDir + d) * ROW + 2 * h;
+            if (k0 + d < K)
+                cp_async16(dst, U + (int64_t)src[qs + sq] * box + (int64_t)(k0 + d) * E + e0 + 2 * h);
+            else
+                *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        cp_async_commit();
+    };
+    if (q0 < q1) stage(0, q0);
+    for (int qs = q0, it = 0; qs < q1; qs += kTrStage, ++it) {
+        const int st = it & 1;
+        if (qs + kTrStage < q1) {
+            stage(st ^ 1, qs + kTrStage);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const int n = min(kTrStage, q1 - qs);
+        for (int sq = 0; sq < n; ++sq) {
+            const uint4 cw = codes[qs + sq];
+            const unsigned long long half = slot < 4 ? ((unsigned long long)cw.y << 32 | cw.x)
+                                                     : ((unsigned long long)cw.w << 32 | cw.z);
+            const unsigned code = (unsigned)(half >> (16 * (slot & 3))) & 0xFFFFu;
+            if (code != kNone && k < K) {
+                const cpx<float> t = ldg_cpx(Top + (int64_t)code * K + k);
+                const cpx<float>* u = buf + ((size_t)(st * kTrStage + sq) * kTrDir + dl) * ROW;
+#pragma unroll
+                for (int e = 0; e < EP; e += 2) {
+                    cpx<float> a, b;
+                    lds_pair(u + e, a, b);
+                    cfma(acc[e], t, a);
+                    cfma(acc[e + 1], t, b);
+                }
+            }
+        }
+        __syncthreads();   // stage st is refilled by the copy issued in the next iteration
+    }
+    if (slot < nc && k < K) {
+        cpx<float>* vb = V + (int64_t)(c0 + slot) * box + (int64_t)k * E + e0;
+#pragma unroll
+        for (int e = 0; e < EP; e += 2) store_pair(vb + e, acc[e], acc[e + 1]);
+    }
+}
+
+template <int EP>
+bool launch_tsm(level_t& L, int E, cudaStream_t s) {
+    const size_t smem = (size_t)2 * kTrStage * kTrDir * (EP + 2) * sizeof(cpx<float>);
+    bi_raise_smem(k_translate_sm<EP>, smem);
+    const int64_t nchunk = (L.K + kTrDir - 1) / kTrDir;
+    const int64_t blocks = nchunk * L.tp_np;
+    if (blocks > 0x7fffffffLL) throw bi_error{BI_ERR_ARG, "translation grid too large"};
+    dim3 g((unsigned)blocks, E / EP);
+    k_translate_sm<EP><<<g, 256, smem, s>>>(L.K, E, L.tp_np, L.d_tp_cptr, L.d_tp_ptr, L.d_tp_src,
+                                            (const uint4*)L.d_tp_code, (const cpx<float>*)L.d_T,
+                                            (const cpx<float>*)L.d_U, (cpx<float>*)L.d_V);
+    CU(cudaGetLastError());
+    return true;
+}
+
 // Variant codes (autotuner): 1 / 2 = one / two pairs of entries per thread over all 8 child
-// slots; 3 / 4 = the same with the child slots split over two threads (4 each).
+// slots; 3 / 4 = the same with the child slots split over two threads (4 each); 5 = the staged
+// form (FP32, E a multiple of 4); 6 / 7 = the pipelined form with 4 child slots per thread, one
+// or two pairs; 8 / 9 = the pipelined form with all 8 child slots, one or two pairs.
 template <typename T>
 bool launch_tE(bi_handle_s* h, int l, int E, cudaStream_t s, int variant) {
     level_t& L = h->lev[l];
+    if (variant == 5) {
+        if (sizeof(T) != 4 || E % 4 != 0) return false;
+        return E % 16 == 0 ? launch_tsm<16>(L, E, s) : E % 8 == 0 ? launch_tsm<8>(L, E, s) : launch_tsm<4>(L, E, s);
+    }
     const int R = E / 2;
+    if (variant >= 6 && variant <= 9) {
+        const int VP = (variant == 7 || variant == 9) ? 2 : 1;
+        const int CH = variant <= 7 ? 4 : 8;
+        if (R % VP != 0) return false;
+        const int TPD = R / VP * (8 / CH);
+        if (TPD > 256) return false;
+        const int D = std::max(1, 256 / TPD);
+        const int threads = std::min(1024, (D * TPD + 31) / 32 * 32);
+        const int64_t blocks = (int64_t)((L.K + D - 1) / D) * L.tp_np;
+        if (blocks > 0x7fffffffLL) throw bi_error{BI_ERR_ARG, "translation grid too large"};
+        // FP64 runs only the one-pair forms: two pairs would not fit the register bounds
+        auto kern = CH == 4 ? k_translate_pp<T, 1, 4> : k_translate_pp<T, 1, 8>;
+        if constexpr (sizeof(T) == 4) {
+            if (VP == 2) kern = CH == 4 ? k_translate_pp<T, 2, 4> : k_translate_pp<T, 2, 8>;
+        } else {
+            if (VP == 2) return false;
+        }
+        kern<<<(unsigned)blocks, threads, 0, s>>>(L.K, R, D, L.tp_np, L.d_tp_cptr, L.d_tp_ptr, L.d_tp_src,
+                                                  (const uint4*)L.d_tp_code, (const cpx<T>*)L.d_T, (const cpx<T>*)L.d_U,
+                                                  (cpx<T>*)L.d_V);
+        CU(cudaGetLastError());
+        return true;
+    }
     // two pairs per thread when R is even (FP32): the code decode and operator loads serve twice
     // the multiply-adds
     int VP = (R % 2 == 0 && sizeof(T) == 4) ? 2 : 1;

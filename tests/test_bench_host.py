@@ -117,3 +117,21 @@ def test_peaks_are_the_measured_file_when_present(bench_info):
         assert kind == "measured" and peak == float(json.load(open(path))["hbm_gbs"])
     else:
         assert kind == "fallback" and peak == 6800.0
+
+
+@pytest.mark.slow
+def test_headline_traffic_matches_the_byte_model():
+    """The committed one-product DRAM capture of the headline workload has one `traffic:` line
+    per stage, each within 0.95-1.35 of the stage's algorithmic bytes at 8 RHS (the gather of x
+    counted in the near stage, the scatter of y in the receive): the product re-reads little
+    from HBM, and the summary belongs to this workload."""
+    import bench
+    bench, info = _plan_info(bench.HEADLINE["name"])
+    traffic = bench.measured_traffic("dram_matvec_sphere_r20_3484860.md")
+    sb = bench.stage_bytes(info, 8)
+    sb["near"] += sb["gather"]
+    sb["receive"] += info["n_unknowns"] * 8 * 8
+    assert set(traffic) == {"near", "aggregate", "interpolate", "translate", "anterpolate", "receive"}
+    for stage, (kernel, nbytes) in traffic.items():
+        assert kernel.startswith("k_")
+        assert 0.95 * sb[stage] <= nbytes <= 1.35 * sb[stage], (stage, nbytes, sb[stage])

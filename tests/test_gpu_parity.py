@@ -320,13 +320,14 @@ def test_c2_sampled_rows(bi):
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("mode,nrhs", [(0, 3), (0, 8), (0, 13), (1, 4), (1, 6), (1, 16)])
 def test_row_blocked_near_matches_per_row_kernel(bi, nu, precision, mode, nrhs, monkeypatch):
-    """The row-blocked near kernel (lanes split RHS and columns, row sums in registers) against
-    the per-row kernel, on a one-level mesh (near field only, written to the user vector) and a
-    multilevel one: the products agree to the rounding of the summation order."""
+    """The row-pair near kernels (lanes split RHS and columns, two rows per warp; plain loads or
+    cp.async-pipelined block entries) against the per-row kernel, on a one-level mesh (near
+    field only, written to the user vector) and a multilevel one: the products agree to the
+    rounding of the summation order."""
     v, t = icosphere(nu, 0.5)
     x = complex_gaussian(oracle.num_unknowns(v, t, mode), nrhs, seed=SEED_BASE + 71)
     ys = []
-    for flag in ("0", "1"):
+    for flag in ("0", "1", "2"):
         monkeypatch.setenv("BI_NEAR_RB", flag)
         op = bi.Operator(v, t, K0, precision=precision, op_mode=mode, max_rhs=nrhs)
         ys.append(op.matvec(torch.from_numpy(x.astype(op.np_cdtype)).cuda()).cpu().numpy())
@@ -334,24 +335,27 @@ def test_row_blocked_near_matches_per_row_kernel(bi, nu, precision, mode, nrhs, 
     tol = 2e-6 if precision == "fp32" else 1e-13
     for r in range(nrhs):
         assert rel(ys[1][r], ys[0][r]) < tol
+        assert rel(ys[2][r], ys[0][r]) < tol
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 @pytest.mark.parametrize("mode,nrhs", [(0, 2), (0, 8), (1, 3), (1, 16)])
 def test_translation_variants_agree(bi, precision, mode, nrhs, monkeypatch):
     """Every form of the batched translation kernel (one or two pairs of entries per thread,
-    all 8 child slots or 4 per thread) gives the same product on a 5-level sphere, to the
-    rounding of the summation order."""
+    all 8 child slots or 4 per thread, and the staged FP32 form) gives the same product on a
+    5-level sphere, to the rounding of the summation order.  (A forced form that does not
+    apply to E falls back to the tuned one.)"""
     v, t = icosphere(32, 2.0)
     x = complex_gaussian(oracle.num_unknowns(v, t, mode), nrhs, seed=SEED_BASE + 73)
     ys = {}
-    for var in ("1", "2", "3", "4"):
+    variants = tuple(str(v) for v in range(1, 10)) if precision == "fp32" else ("1", "2", "3", "4", "6", "8")
+    for var in variants:
         monkeypatch.setenv("BI_TRANSLATE_VARIANT", var)
         op = bi.Operator(v, t, K0, precision=precision, op_mode=mode, max_rhs=nrhs)
         ys[var] = op.matvec(torch.from_numpy(x.astype(op.np_cdtype)).cuda()).cpu().numpy()
         op.close()
     tol = 2e-6 if precision == "fp32" else 1e-13
-    for var in ("2", "3", "4"):
+    for var in variants[1:]:
         for r in range(nrhs):
             assert rel(ys[var][r], ys["1"][r]) < tol, (var, r)
 

@@ -11,22 +11,28 @@ narrower format and accumulated exactly:
   receive    leaf incoming patterns and the receive patterns R
 
 Formats: FP32; TF32 (10-bit mantissa); FP16 with one scale per box pattern (10-bit mantissa,
-range kept by the scale); BF16 (7-bit mantissa).  The error is relative to the FP64 far part.
-Measured (far part, 7680 RWG, 4 levels):
+range kept by the scale); BF16 (7-bit mantissa); and two split forms that run FP32 products on
+tensor cores, modelled by their product error (the operands rounded to the equivalent
+mantissa):
+  split16  three BF16 products per FP32 product (hi*hi + hi*mid + mid*hi of a three-term BF16
+           split; Henry, Tang and Heinecke 2019): dropped terms ~2^-16;
+  split21  error-corrected TF32 (hi*hi + hi*lo + lo*hi of a two-term TF32 split; Ootomo and
+           Yokota 2022): the dropped lo*lo term ~2^-22.
+The error is relative to the FP64 far part.  Measured (far part, 7680 RWG, 4 levels):
 
-  | stage     | fp32    | tf32    | fp16_scaled | bf16    |
-  | aggregate | 1.9e-05 | 1.5e-01 | 1.3e-01     | 1.2e+00 |
-  | interp    | 1.0e-05 | 4.3e-02 | 3.1e-02     | 3.4e-01 |
-  | translate | 2.9e-05 | 2.7e-01 | 3.6e-01     | 2.1e+00 |
-  | anterp    | 1.1e-05 | 5.5e-02 | 4.5e-02     | 4.3e-01 |
-  | receive   | 2.6e-05 | 2.1e-01 | 1.9e-01     | 1.6e+00 |
+  | stage     | fp32    | tf32    | fp16_scaled | bf16    | split16 | split21 |
+  | aggregate | 1.9e-05 | 1.5e-01 | 1.3e-01     | 1.2e+00 | 2.4e-03 | 8.2e-05 |
+  | interp    | 1.0e-05 | 4.3e-02 | 3.1e-02     | 3.4e-01 | 8.6e-04 | 1.7e-05 |
+  | translate | 2.9e-05 | 2.7e-01 | 3.6e-01     | 2.1e+00 | 3.5e-03 | 1.3e-04 |
+  | anterp    | 1.1e-05 | 5.5e-02 | 4.5e-02     | 4.3e-01 | 1.0e-03 | 2.5e-05 |
+  | receive   | 2.6e-05 | 2.1e-01 | 1.9e-01     | 1.6e+00 | 3.2e-03 | 1.1e-04 |
 
 Every stage amplifies its operands' relative rounding by about 400: the far-field sum over the
 directions cancels heavily for quarter-wavelength boxes (the translation operators' high-order
 terms), on the incoming side as much as on the outgoing side.  FP32 keeps every stage 30x or
-more inside the 1e-3 bar; TF32, scaled FP16 and BF16 operands break it at every stage, so the
-product computes in FP32 throughout (tensor-core inputs of those formats would need a split
-representation to reach FP32 accuracy).
+more inside the 1e-3 bar; TF32, scaled FP16 and BF16 operands break it at every stage, and so
+does the three-product BF16 split; error-corrected TF32 (three TF32 products per FP32 product)
+holds it with a 7x margin at its worst stage.
 
   python tests/test_precision_study.py      prints the table (a few minutes)
 """
@@ -42,7 +48,7 @@ sys.path.insert(0, os.path.dirname(HERE))
 
 K0 = 2 * np.pi
 STAGES = ("aggregate", "interp", "translate", "anterp", "receive")
-FORMATS = ("fp32", "tf32", "fp16_scaled", "bf16")
+FORMATS = ("fp32", "tf32", "fp16_scaled", "bf16", "split16", "split21")
 
 
 def _round_mantissa(a, bits):
@@ -67,6 +73,14 @@ def rnd(x, fmt):
         return _round_mantissa(x, 10)
     if fmt == "bf16":
         return _round_mantissa(x, 7)
+    if fmt == "split16":
+        # product error of three BF16 products per FP32 product (hi*hi + hi*mid + mid*hi of a
+        # three-term BF16 split, Henry, Tang and Heinecke 2019): the dropped terms are ~2^-16
+        return _round_mantissa(x, 16)
+    if fmt == "split21":
+        # error-corrected TF32 (hi*hi + hi*lo + lo*hi of a two-term TF32 split, Ootomo and Yokota
+        # 2022): the dropped lo*lo term is ~2^-22
+        return _round_mantissa(x, 21)
     if fmt == "fp16_scaled":
         s = float(np.abs(x).max()) or 1.0
         return (x / s).astype(np.float16).astype(np.float64) * s
