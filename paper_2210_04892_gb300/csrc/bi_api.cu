@@ -132,12 +132,16 @@ static int setup_handle(const double* verts, int nv, const int* tris, int nt, do
     h->use_leaf_bulk = !(env3 && env3[0] == '0');
     const char* env4 = std::getenv("BI_ANTERP_ROWS");
     h->force_anterp_rows = env4 && env4[0] == '1';
+    const char* env8 = std::getenv("BI_INTERP_VARIANT");
+    h->interp_variant = env8 ? std::atoi(env8) : 0;
+    const char* env9 = std::getenv("BI_ANTERP_VARIANT");
+    h->anterp_variant = env9 ? std::atoi(env9) : 0;
     const char* env7 = std::getenv("BI_TRANSLATE_VARIANT");
     h->translate_variant = env7 ? std::atoi(env7) : 0;
     if (h->translate_variant < 0 || h->translate_variant > 9) h->translate_variant = 0;
     const char* env6 = std::getenv("BI_NEAR_RB");
-    h->near_rb = env6 ? std::atoi(env6) : 1;
-    if (h->near_rb < 0 || h->near_rb > 2) h->near_rb = 1;
+    h->near_rb = env6 ? std::atoi(env6) : 2;
+    if (h->near_rb < 0 || h->near_rb > 2) h->near_rb = 2;
     const char* env5 = std::getenv("BI_AUTOTUNE");
     h->autotune = !(env5 && env5[0] == '0') && !h->force_anterp_rows;
     try {
@@ -621,6 +625,7 @@ extern "C" int bi_tuned_config(bi_handle h, char* buf, int64_t len) {
                                               : std::string(t.variant % 2 == 0 ? "2 pairs/thread" : "1 pair/thread") +
                                                     (t.variant >= 3 ? ", 4 child slots/thread" : ""))
                                : t.variant == 2 ? "two-pass"
+                               : t.variant == 3 ? "two-pass, entry pairs"
                                : t.variant >= 200 ? "row blocks, chunk " + std::to_string(t.variant - 200)
                                : t.pass == 1 ? "rows per CTA, chunk " + std::to_string(t.variant - 100)
                                              : "per child, chunk " + std::to_string(t.variant - 100);

@@ -159,10 +159,13 @@ struct bi_handle_s {
     bool use_graphs = true;
     bool use_fast = true;               // fused kernels (false: two-pass reference kernels)
     bool use_leaf_bulk = true;          // bulk-copy pipelines for leaf aggregation and receive
+    int interp_variant = 0, anterp_variant = 0;   // level-pass forms forced on every level (test
+                                                  // switches BI_INTERP_VARIANT, BI_ANTERP_VARIANT)
     int translate_variant = 0;          // translation kernel form forced on every level (test switch
                                         // BI_TRANSLATE_VARIANT=1..9; 0: tuned)
-    int near_rb = 1;                    // near kernel for 3 <= R <= 8: 1 row pairs, 2 row pairs with
-                                        // cp.async-pipelined block entries, 0 per-row (switch BI_NEAR_RB)
+    int near_rb = 2;                    // near kernel for 3 <= R <= 8: 2 row pairs with cp.async-pipelined
+                                        // block entries (FP32 C block, 6-8 RHS; else 1), 1 row pairs,
+                                        // 0 per-row (switch BI_NEAR_RB)
     bool force_anterp_rows = false;     // row-blocked anterpolation on every level (test switch)
     int* d_status = nullptr;            // device status word (0: healthy; see bi_tma.cuh)
     long long wait_cycles = 1ll << 31;  // limit of the bulk-copy waits of the leaf kernels (SM clocks)

@@ -692,6 +692,185 @@ __global__ void __launch_bounds__(256) k_anterp_theta_w(int nthc, int nphc, int 
     }
 }
 
+// ---------------------------------------------------------------- two passes, entry pairs
+// The two-pass forms above with each thread on one pair of adjacent entries (a 16-byte load in
+// FP32) and E/2 pair lanes per column, so every tap reads whole contiguous E-vectors and no
+// lane idles for E < 32; zero-weight entries of the padded transposed tap lists are skipped.
+// For the coarse levels (few boxes, many directions), where the per-CTA forms leave most SMs
+// idle or read the parent field once per tap.
+template <typename T>
+__device__ __forceinline__ void st_pair(cpx<T>* p, cpx<T> a, cpx<T> b) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+    } else {
+        p[0] = a;
+        p[1] = b;
+    }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_interp_theta_p2(int nthc, int nphc, int nthp, int E, const tap<T>* __restrict__ th_tap,
+                                                         const cpx<T>* __restrict__ Uc, cpx<T>* __restrict__ tmp) {
+    const int cb = blockIdx.x / nthp, ip = blockIdx.x - cb * nthp;
+    const int PE = E / 2, le = threadIdx.x % PE, col0 = threadIdx.x / PE, ncols = blockDim.x / PE;
+    const int half = nphc / 2, Kc = nthc * nphc;
+    int code[P];
+    T w[P];
+#pragma unroll
+    for (int t = 0; t < P; ++t) {
+        const tap<T> q = th_tap[ip * P + t];
+        code[t] = q.c;
+        w[t] = q.w;
+    }
+    const cpx<T>* u = Uc + (int64_t)cb * Kc * E + 2 * le;
+    cpx<T>* out = tmp + (((int64_t)cb * nthp + ip) * nphc) * E + 2 * le;
+    for (int jc = col0; jc < nphc; jc += ncols) {
+        const int jf = jc + half < nphc ? jc + half : jc + half - nphc;
+        cpx<T> a = czero<T>(), b = czero<T>();
+#pragma unroll
+        for (int t = 0; t < P; ++t) {
+            cpx<T> va, vb;
+            load_pair(u + ((int64_t)(code[t] >> 1) * nphc + ((code[t] & 1) ? jf : jc)) * E, va, vb);
+            fma_pair(w[t], va, vb, a, b);
+        }
+        st_pair(out + (int64_t)jc * E, a, b);
+    }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) k_interp_phi_p2(int nthp, int nphp, int nphc, int E, const tap<T>* __restrict__ ph_tap,
+                                                       const int* __restrict__ child_ptr, const int* __restrict__ octant,
+                                                       const cpx<T>* __restrict__ shift, const cpx<T>* __restrict__ tmp,
+                                                       cpx<T>* __restrict__ Up) {
+    const int pb = blockIdx.x / nthp, ip = blockIdx.x - pb * nthp;
+    const int PE = E / 2, le = threadIdx.x % PE, col0 = threadIdx.x / PE, ncols = blockDim.x / PE;
+    const int Kp = nthp * nphp;
+    const int c0 = child_ptr[pb], nc = child_ptr[pb + 1] - c0;
+    for (int jp = col0; jp < nphp; jp += ncols) {
+        int src[P];
+        T w[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const tap<T> tq = ph_tap[jp * P + q];
+            src[q] = tq.c;
+            w[q] = tq.w;
+        }
+        cpx<T> A = czero<T>(), B = czero<T>();
+        for (int c = 0; c < nc; ++c) {
+            const cpx<T>* row = tmp + (((int64_t)(c0 + c) * nthp + ip) * nphc) * E + 2 * le;
+            cpx<T> a = czero<T>(), b = czero<T>();
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                cpx<T> va, vb;
+                load_pair(row + (int64_t)src[q] * E, va, vb);
+                fma_pair(w[q], va, vb, a, b);
+            }
+            const cpx<T> z = ldg_c(shift + (int64_t)octant[c0 + c] * Kp + ip * nphp + jp);
+            cfma(A, z, a);
+            cfma(B, z, b);
+        }
+        st_pair(Up + ((int64_t)pb * Kp + ip * nphp + jp) * E + 2 * le, A, B);
+    }
+}
+
+template <typename T, int PT>
+__global__ void __launch_bounds__(256) k_anterp_phi_p2(int nthp, int nphp, int nphc, int E, const tap<T>* __restrict__ tph_pad,
+                                                       const int* __restrict__ parent, const int* __restrict__ octant,
+                                                       const cpx<T>* __restrict__ shift, const cpx<T>* __restrict__ Vp,
+                                                       cpx<T>* __restrict__ tmp) {
+    const int cb = blockIdx.x / nthp, ip = blockIdx.x - cb * nthp;
+    const int PE = E / 2, le = threadIdx.x % PE, col0 = threadIdx.x / PE, ncols = blockDim.x / PE;
+    const int Kp = nthp * nphp;
+    const int pb = parent[cb];
+    const cpx<T>* sh = shift + (int64_t)octant[cb] * Kp + ip * nphp;
+    const cpx<T>* vp = Vp + ((int64_t)pb * Kp + ip * nphp) * E + 2 * le;
+    cpx<T>* out = tmp + (((int64_t)cb * nthp + ip) * nphc) * E + 2 * le;
+    for (int jc = col0; jc < nphc; jc += ncols) {
+        cpx<T> a = czero<T>(), b = czero<T>();
+#pragma unroll
+        for (int q = 0; q < PT; ++q) {
+            const tap<T> tq = tph_pad[jc * PT + q];
+            if (tq.w == T(0)) continue;      // padding of the transposed list
+            const cpx<T> z = ldg_c(sh + tq.c);
+            const cpx<T> sc = {tq.w * z.x, -tq.w * z.y};   // w conj(shift)
+            cpx<T> va, vb;
+            load_pair(vp + (int64_t)tq.c * E, va, vb);
+            cfma(a, sc, va);
+            cfma(b, sc, vb);
+        }
+        st_pair(out + (int64_t)jc * E, a, b);
+    }
+}
+
+template <typename T, int PT>
+__global__ void __launch_bounds__(256) k_anterp_theta_p2(int nthc, int nphc, int nthp, int E, const tap<T>* __restrict__ tth_pad,
+                                                         const cpx<T>* __restrict__ tmp, cpx<T>* __restrict__ Vc) {
+    const int cb = blockIdx.x / nthc, ic = blockIdx.x - cb * nthc;
+    const int PE = E / 2, le = threadIdx.x % PE, col0 = threadIdx.x / PE, ncols = blockDim.x / PE;
+    const int half = nphc / 2, Kc = nthc * nphc;
+    int code[PT];
+    T w[PT];
+    int nq = 0;
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+        const tap<T> tq = tth_pad[ic * PT + q];
+        code[q] = tq.c;
+        w[q] = tq.w;
+        if (tq.w != T(0)) nq = q + 1;
+    }
+    const cpx<T>* t0 = tmp + (int64_t)cb * nthp * nphc * E + 2 * le;
+    cpx<T>* vc = Vc + ((int64_t)cb * Kc + ic * nphc) * E + 2 * le;
+    for (int jc = col0; jc < nphc; jc += ncols) {
+        const int jf = jc + half < nphc ? jc + half : jc + half - nphc;
+        cpx<T> a = czero<T>(), b = czero<T>();
+#pragma unroll
+        for (int q = 0; q < PT; ++q) {
+            if (q >= nq) break;
+            cpx<T> va, vb;
+            load_pair(t0 + ((int64_t)(code[q] >> 1) * nphc + ((code[q] & 1) ? jf : jc)) * E, va, vb);
+            fma_pair(w[q], va, vb, a, b);
+        }
+        cpx<T>* g = vc + (int64_t)jc * E;
+        cpx<T> ga, gb;
+        load_pair(g, ga, gb);
+        st_pair(g, cadd(ga, a), cadd(gb, b));
+    }
+}
+
+template <typename T>
+bool interp_pairs(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    level_t& Pl = h->lev[l];
+    level_t& C = h->lev[l + 1];
+    interp_t& I = h->itp[l];
+    if (!I.d_tmp || E % 2 != 0 || E / 2 > 256) return false;
+    const int PE = E / 2, threads = (256 / PE) * PE;
+    k_interp_theta_p2<T, 10><<<(unsigned)((int64_t)C.nbox * Pl.nth), threads, 0, s>>>(
+        C.nth, C.nph, Pl.nth, E, (const tap<T>*)I.d_th_tap, (const cpx<T>*)C.d_U, (cpx<T>*)I.d_tmp);
+    CU(cudaGetLastError());
+    k_interp_phi_p2<T, 10><<<(unsigned)((int64_t)Pl.nbox * Pl.nth), threads, 0, s>>>(
+        Pl.nth, Pl.nph, C.nph, E, (const tap<T>*)I.d_ph_tap, Pl.d_child_ptr, C.d_octant, (const cpx<T>*)Pl.d_shift,
+        (const cpx<T>*)I.d_tmp, (cpx<T>*)Pl.d_U);
+    CU(cudaGetLastError());
+    return true;
+}
+
+template <typename T, int PT>
+bool anterp_pairs(bi_handle_s* h, int l, int E, cudaStream_t s) {
+    level_t& Pl = h->lev[l];
+    level_t& C = h->lev[l + 1];
+    interp_t& I = h->itp[l];
+    if (!I.d_tmp || E % 2 != 0 || E / 2 > 256) return false;
+    const int PE = E / 2, threads = (256 / PE) * PE;
+    k_anterp_phi_p2<T, PT><<<(unsigned)((int64_t)C.nbox * Pl.nth), threads, 0, s>>>(
+        Pl.nth, Pl.nph, C.nph, E, (const tap<T>*)I.d_tph_pad, C.d_parent, C.d_octant, (const cpx<T>*)Pl.d_shift_dn,
+        (const cpx<T>*)Pl.d_V, (cpx<T>*)I.d_tmp);
+    CU(cudaGetLastError());
+    k_anterp_theta_p2<T, PT><<<(unsigned)((int64_t)C.nbox * C.nth), threads, 0, s>>>(
+        C.nth, C.nph, Pl.nth, E, (const tap<T>*)I.d_tth_pad, (const cpx<T>*)I.d_tmp, (cpx<T>*)C.d_V);
+    CU(cudaGetLastError());
+    return true;
+}
+
 template <typename T>
 bool interp_wide(bi_handle_s* h, int l, int E, cudaStream_t s) {
     level_t& Pl = h->lev[l];
@@ -933,9 +1112,11 @@ void bi_upload_taps(bi_handle_s* h) {
 bool bi_interp_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
     const interp_t& I = h->itp[l];
     if (I.p_th != 10 || I.p_ph != 10 || !I.d_th_tap) return false;
-    const int v = h->force_variant >= 0 ? h->force_variant : (E > 2 ? h->variant_of(1, l, E) : 0);
+    const int v = h->force_variant >= 0 ? h->force_variant
+                  : E > 2 && h->interp_variant > 0 ? h->interp_variant : (E > 2 ? h->variant_of(1, l, E) : 0);
     if (v >= 100) return h->prec == 0 ? interp_chunked<double, 10>(h, l, E, s, v - 100) : interp_chunked<float, 10>(h, l, E, s, v - 100);
     if (v == 2) return h->prec == 0 ? interp_wide<double>(h, l, E, s) : interp_wide<float>(h, l, E, s);
+    if (v == 3) return h->prec == 0 ? interp_pairs<double>(h, l, E, s) : interp_pairs<float>(h, l, E, s);
     if (E > 2 && (h->prec == 0 ? interp_chunked<double, 10>(h, l, E, s) : interp_chunked<float, 10>(h, l, E, s)))
         return true;
     if (E >= 32) return h->prec == 0 ? interp_wide<double>(h, l, E, s) : interp_wide<float>(h, l, E, s);
@@ -945,7 +1126,8 @@ bool bi_interp_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
 bool bi_anterp_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
     const interp_t& I = h->itp[l];
     if (!I.d_tth_pad) return false;
-    const int v = h->force_variant >= 0 ? h->force_variant : (E > 2 ? h->variant_of(2, l, E) : 0);
+    const int v = h->force_variant >= 0 ? h->force_variant
+                  : E > 2 && h->anterp_variant > 0 ? h->anterp_variant : (E > 2 ? h->variant_of(2, l, E) : 0);
     if (v != 0 && I.pt_th == I.pt_ph && (I.pt_th == 16 || I.pt_th == 24)) {
         const bool p16 = I.pt_th == 16, dbl = h->prec == 0;
         if (v >= 200)
@@ -957,6 +1139,9 @@ bool bi_anterp_level(bi_handle_s* h, int l, int E, cudaStream_t s) {
         if (v == 2)
             return p16 ? (dbl ? anterp_wide<double, 16>(h, l, E, s) : anterp_wide<float, 16>(h, l, E, s))
                        : (dbl ? anterp_wide<double, 24>(h, l, E, s) : anterp_wide<float, 24>(h, l, E, s));
+        if (v == 3)
+            return p16 ? (dbl ? anterp_pairs<double, 16>(h, l, E, s) : anterp_pairs<float, 16>(h, l, E, s))
+                       : (dbl ? anterp_pairs<double, 24>(h, l, E, s) : anterp_pairs<float, 24>(h, l, E, s));
     }
     if (E > 2 && I.pt_th == I.pt_ph) {
         const bool whole = !h->force_anterp_rows;

@@ -1981,8 +1981,8 @@ void bi_autotune(bi_handle_s* h, int nrhs, cudaStream_t s) {
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     const std::vector<int> cand[3] = {{1, 2, 3, 4, 5, 6, 7, 8, 9},
-                                      {116, 108, 104, 102, 2},
-                                      {116, 108, 104, 102, 216, 208, 204, 202, 2}};
+                                      {116, 108, 104, 102, 2, 3},
+                                      {116, 108, 104, 102, 216, 208, 204, 202, 2, 3}};
     try {
         for (int pass = 0; pass < 3; ++pass) {
             const int lmax = pass == 0 ? h->leaf : h->leaf - 1;

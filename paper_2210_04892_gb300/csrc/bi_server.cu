@@ -194,8 +194,9 @@ void evict_locked(bi_server_s* S, int64_t need) {
 // (destroyed when operators are not shared, or when it failed to build).
 void finish_job(bi_server_s* S, job* jb, int code, const std::string& msg) {
     if (jb->ctx) bi_gmres_destroy(jb->ctx);
-    if (jb->d_rhs) cudaFree(jb->d_rhs);
-    if (jb->d_x) cudaFree(jb->d_x);
+    cudaStream_t st = jb->op ? jb->op->stream : nullptr;
+    if (jb->d_rhs) cudaFreeAsync(jb->d_rhs, st);
+    if (jb->d_x) cudaFreeAsync(jb->d_x, st);
     std::lock_guard<std::mutex> lk(S->mu);
     const clk::time_point now = clk::now();
     for (request* r : jb->reqs) {
@@ -349,8 +350,10 @@ void setup_job(bi_server_s* S, job* jb) {
     }
     jb->R = R;
     const size_t vb = (size_t)h->nun * R * h->csize;
-    CU(cudaMalloc(&jb->d_rhs, vb));
-    CU(cudaMalloc(&jb->d_x, vb));
+    // stream-ordered: allocating and freeing a job's vectors (and its GMRES state) does not
+    // synchronise the device while other jobs run
+    CU(cudaMallocAsync(&jb->d_rhs, vb, e->stream));
+    CU(cudaMallocAsync(&jb->d_x, vb, e->stream));
     std::vector<double> tolv;
     for (request* r : reqs) {
         const int rc = bi_rhs_planewave(h, r->khat.data(), r->phat.data(), r->nrhs,
@@ -493,6 +496,16 @@ extern "C" int bi_server_create(const bi_server_params* prm, bi_server* out) {
     if (cudaGetDevice(&S->device) != cudaSuccess) {
         delete S;
         return BI_ERR_CUDA;
+    }
+    {
+        // keep stream-ordered memory that jobs free in the device's pool (no unmap and remap
+        // of every job's GMRES state at the next synchronisation); process-local pool setting
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, S->device) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
     }
     if (S->prm.mem_budget_bytes == 0) {
         size_t fr = 0, tot = 0;
@@ -651,10 +664,12 @@ extern "C" void bi_server_destroy(bi_server S) {
     jobs.insert(jobs.end(), S->to_setup.begin(), S->to_setup.end());
     for (job* jb : jobs) {
         if (jb->ctx) bi_gmres_destroy(jb->ctx);
-        if (jb->d_rhs) cudaFree(jb->d_rhs);
-        if (jb->d_x) cudaFree(jb->d_x);
+        cudaStream_t st = jb->op ? jb->op->stream : nullptr;
+        if (jb->d_rhs) cudaFreeAsync(jb->d_rhs, st);
+        if (jb->d_x) cudaFreeAsync(jb->d_x, st);
         delete jb;
     }
+    cudaDeviceSynchronize();
     for (op_entry* e : S->ops) destroy_op(e);
     for (auto& kv : S->all) delete kv.second;
     delete S;

@@ -295,15 +295,18 @@ struct gmres_ctx_impl {
     bool in_cycle = false, finished = false;
     int64_t bytes = 0;
 
+    // Stream-ordered allocations on the context's stream: creating and freeing a context does
+    // not synchronise the device, so the contexts of concurrent solves (the server) come and go
+    // while other solves' kernels run.
     void* A(size_t n) {
         void* p = nullptr;
-        CU(cudaMalloc(&p, n));
+        CU(cudaMallocAsync(&p, n, s));
         mem.push_back(p);
         bytes += (int64_t)n;
         return p;
     }
     ~gmres_ctx_impl() {
-        for (void* p : mem) cudaFree(p);
+        for (void* p : mem) cudaFreeAsync(p, s);
         if (h_res) cudaFreeHost(h_res);
         if (ev) cudaEventDestroy(ev);
     }

@@ -360,6 +360,27 @@ def test_translation_variants_agree(bi, precision, mode, nrhs, monkeypatch):
             assert rel(ys[var][r], ys["1"][r]) < tol, (var, r)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("mode,nrhs", [(0, 3), (0, 8), (1, 16)])
+@pytest.mark.parametrize("variant", ["2", "3"])
+def test_two_pass_level_forms_agree(bi, precision, mode, nrhs, variant, monkeypatch):
+    """The two-pass interpolation and anterpolation forms (one entry per lane, and entry pairs
+    with the zero taps of the padded lists skipped), forced on every level of a 5-level sphere,
+    give the tuned product to the rounding of the summation order."""
+    v, t = icosphere(32, 2.0)
+    x = complex_gaussian(oracle.num_unknowns(v, t, mode), nrhs, seed=SEED_BASE + 75)
+    ys = []
+    for var in ("", variant):
+        monkeypatch.setenv("BI_INTERP_VARIANT", var or "0")
+        monkeypatch.setenv("BI_ANTERP_VARIANT", var or "0")
+        op = bi.Operator(v, t, K0, precision=precision, op_mode=mode, max_rhs=nrhs)
+        ys.append(op.matvec(torch.from_numpy(x.astype(op.np_cdtype)).cuda()).cpu().numpy())
+        op.close()
+    tol = 2e-6 if precision == "fp32" else 1e-13
+    for r in range(nrhs):
+        assert rel(ys[1][r], ys[0][r]) < tol, r
+
+
 @pytest.mark.parametrize("mode,nrhs", [(0, 1), (0, 3), (1, 5), (0, 16), (1, 20)])
 def test_fused_kernels_match_two_pass_kernels(bi, mode, nrhs, monkeypatch):
     """The fused/streaming kernels and the two-pass reference kernels give the same product
