@@ -60,10 +60,15 @@ def parse():
     ap.add_argument("--serving-max-unknowns", type=int, default=50000)
     ap.add_argument("--serving-max-rhs", type=int, default=32)
     ap.add_argument("--serving-plain", type=int, default=1, help="time the plain one-at-a-time form too (0: skip)")
+    ap.add_argument("--serving-unshared", type=int, default=1,
+                    help="time the server with one operator per request too (0: skip)")
     ap.add_argument("--profile-one", choices=["headline", "secondary", "cube_cylinder"],
                     help="profiling aid: set up the named workload, run a few products, then bracket ONE "
                          "product with cudaProfilerStart/Stop (for ncu --profile-from-start off) and exit")
     ap.add_argument("--nrhs", type=int, default=0, help="with --profile-one: right-hand sides (0: the workload's)")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run only the serving section (e.g. the full c4 stream: --serving 500 "
+                         "--serving-max-unknowns 200000 --serving-plain 0) and print its JSON")
     return ap.parse_args()
 
 
@@ -478,7 +483,7 @@ def run_serving(args):
     work = sum((len(q["tris"]) * 3 // 2) * (2 if q["op_mode"] == 0 else 1) * len(q["khat"]) for q in reqs)
     n = len(reqs)
     _, span0, _, _, _ = _serve(bi, reqs, [0.0] * n, tol)
-    _, span0_u, _, _, _ = _serve(bi, reqs, [0.0] * n, tol, share=False)
+    span0_u = _serve(bi, reqs, [0.0] * n, tol, share=False)[1] if args.serving_unshared else None
     rate = 0.75 * n / span0
     rng = np.random.default_rng(20221011 + 31)
     arrivals = list(np.cumsum(rng.exponential(1.0 / rate, n)))
@@ -488,7 +493,8 @@ def run_serving(args):
         return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
                 "throughput": work / span}
     lat, span, setup_ms, ok, stats = _serve(bi, reqs, arrivals, tol)
-    lat_u, span_u, setup_u, ok_u, stats_u = _serve(bi, reqs, arrivals, tol, share=False)
+    lat_u, span_u, setup_u, ok_u, stats_u = (_serve(bi, reqs, arrivals, tol, share=False) if args.serving_unshared
+                                             else (None, None, None, True, None))
     lat_p, span_p, ok_p, cap_p = _plain_fifo(bi, reqs, arrivals, tol) if args.serving_plain else (None, None, True, None)
     out = {"requests": n, "unknowns_range": [2000, args.serving_max_unknowns], "max_rhs": args.serving_max_rhs,
            "distinct_operators": len({(q["shape"], len(q["tris"]), q["op_mode"]) for q in reqs}), "tol": tol,
@@ -499,9 +505,10 @@ def run_serving(args):
     out.update(summary(lat, span))
     out.update({"mean_setup_ms": setup_ms, "server_stats": {k: v for k, v in stats.items() if k != "held_bytes"},
                 "form": "operators shared and cached; requests on one operator merged into one batched GMRES"})
-    out["unshared"] = dict(summary(lat_u, span_u), mean_setup_ms=setup_u, capacity_makespan_s=span0_u,
-                           capacity_throughput=work / span0_u,
-                           form="one operator per request; requests overlap on the device, no shared launch")
+    if lat_u is not None:
+        out["unshared"] = dict(summary(lat_u, span_u), mean_setup_ms=setup_u, capacity_makespan_s=span0_u,
+                               capacity_throughput=work / span0_u,
+                               form="one operator per request; requests overlap on the device, no shared launch")
     if lat_p is not None:
         out["plain"] = dict(summary(lat_p, span_p), capacity_makespan_s=cap_p, capacity_throughput=work / cap_p,
                             form="one request at a time (first come first served), one RHS at a time; latencies "
@@ -687,6 +694,9 @@ def main():
     args = parse()
     if args.profile_one:
         profile_one(args)
+        return
+    if args.serving_only:
+        print(json.dumps({"serving": run_serving(args)}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -376,7 +376,11 @@ def test_two_pass_level_forms_agree(bi, precision, mode, nrhs, variant, monkeypa
         op = bi.Operator(v, t, K0, precision=precision, op_mode=mode, max_rhs=nrhs)
         ys.append(op.matvec(torch.from_numpy(x.astype(op.np_cdtype)).cuda()).cpu().numpy())
         op.close()
-    tol = 2e-6 if precision == "fp32" else 1e-13
+    # the forms take theta and phi in different orders (anterpolation: phi first in the
+    # two-pass forms, theta first in the row-block form), so their FP32 intermediates round
+    # differently; the far part amplifies operand rounding about 400 times (the precision
+    # study), which puts FP32 differences at a few 1e-6
+    tol = 2e-5 if precision == "fp32" else 1e-13
     for r in range(nrhs):
         assert rel(ys[1][r], ys[0][r]) < tol, r
 
