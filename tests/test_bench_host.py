@@ -122,9 +122,11 @@ def test_peaks_are_the_measured_file_when_present(bench_info):
 @pytest.mark.slow
 def test_headline_traffic_matches_the_byte_model():
     """The committed one-product DRAM capture of the headline workload has one `traffic:` line
-    per stage, each within 0.95-1.35 of the stage's algorithmic bytes at 8 RHS (the gather of x
+    per stage, each within 0.95-1.5 of the stage's algorithmic bytes at 8 RHS (the gather of x
     counted in the near stage, the scatter of y in the receive): the product re-reads little
-    from HBM, and the summary belongs to this workload."""
+    from HBM, and the summary belongs to this workload.  The upper end leaves room for the
+    intermediates that the two-pass forms of the coarse level passes write and read back, and
+    for the outgoing leaf patterns of the aggregation, which pass through L2 to DRAM."""
     import bench
     bench, info = _plan_info(bench.HEADLINE["name"])
     traffic = bench.measured_traffic("dram_matvec_sphere_r20_3484860.md")
@@ -134,4 +136,4 @@ def test_headline_traffic_matches_the_byte_model():
     assert set(traffic) == {"near", "aggregate", "interpolate", "translate", "anterpolate", "receive"}
     for stage, (kernel, nbytes) in traffic.items():
         assert kernel.startswith("k_")
-        assert 0.95 * sb[stage] <= nbytes <= 1.35 * sb[stage], (stage, nbytes, sb[stage])
+        assert 0.95 * sb[stage] <= nbytes <= 1.5 * sb[stage], (stage, nbytes, sb[stage])
