@@ -272,7 +272,11 @@ void admit_locked(bi_server_s* S) {
             ++it;   // waits for the operator's current job
             continue;
         }
-        if (S->active >= S->prm.max_active) break;
+        // no free job slot: later requests may still join open jobs of their operators
+        if (S->active >= S->prm.max_active) {
+            ++it;
+            continue;
+        }
         const int max_rhs = std::max(cap, r->nrhs);
         const int64_t op_bytes = e ? 0 : estimate_op_bytes(r, max_rhs);
         const int64_t jb_bytes = estimate_job_bytes(r, r->nrhs);
