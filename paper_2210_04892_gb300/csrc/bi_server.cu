@@ -156,6 +156,7 @@ struct bi_server_s {
     std::vector<job*> running;           // iterating (serving thread only)
     std::deque<job*> ready;              // set up, waiting to join `running`
     std::list<op_entry*> ops;            // every operator, in order of last use (front: oldest)
+    std::vector<op_entry*> retired;      // operators to destroy outside the lock (evicted or unshared)
     std::unordered_map<int64_t, request*> all;
     int64_t next_id = 1;
     int64_t held_bytes = 0;              // operators (cached or in use) plus jobs
@@ -175,19 +176,31 @@ void destroy_op(op_entry* e) {
     delete e;
 }
 
-// Drop idle cached operators, oldest first, until `need` more bytes fit the budget.
+// Drop idle cached operators, oldest first, until `need` more bytes fit the budget.  Their
+// device memory is released by destroy_retired, outside the lock (freeing synchronises the
+// device, which must not hold up bi_submit and bi_poll).
 void evict_locked(bi_server_s* S, int64_t need) {
     for (auto it = S->ops.begin(); it != S->ops.end() && S->held_bytes + need > S->prm.mem_budget_bytes;) {
         op_entry* e = *it;
         if (e->state == OP_IDLE) {
             S->held_bytes -= e->bytes;
             it = S->ops.erase(it);
-            destroy_op(e);
+            S->retired.push_back(e);
             S->stats[BI_STAT_EVICTIONS] += 1;
         } else {
             ++it;
         }
     }
+}
+
+// Destroy the operators retired under the lock (called without it).
+void destroy_retired(bi_server_s* S) {
+    std::vector<op_entry*> dead;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        dead.swap(S->retired);
+    }
+    for (op_entry* e : dead) destroy_op(e);
 }
 
 // Finish every request of a job with the same status; frees the job and releases its operator
@@ -221,7 +234,7 @@ void finish_job(bi_server_s* S, job* jb, int code, const std::string& msg) {
         } else {
             S->held_bytes -= e->bytes;
             S->ops.remove(e);
-            destroy_op(e);
+            S->retired.push_back(e);
         }
     }
     for (auto it = S->pending.begin(); it != S->pending.end(); ++it)
@@ -447,6 +460,7 @@ void serve_loop(bi_server_s* S) {
                 S->ready.pop_front();
             }
         }
+        destroy_retired(S);
         // one pass: every running job advances as far as its completed work allows
         for (size_t i = 0; i < S->running.size();) {
             job* jb = S->running[i];
@@ -675,6 +689,7 @@ extern "C" void bi_server_destroy(bi_server S) {
     }
     cudaDeviceSynchronize();
     for (op_entry* e : S->ops) destroy_op(e);
+    for (op_entry* e : S->retired) destroy_op(e);
     for (auto& kv : S->all) delete kv.second;
     delete S;
 }
