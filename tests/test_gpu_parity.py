@@ -303,13 +303,13 @@ def test_cblock_solve_converges(bi, sphere_c1):
 
 def test_c2_sampled_rows(bi):
     """Coated-sphere outer surface r = 2 lambda (20480 triangles, 61440 unknowns), 5 levels,
-    FP32, one RHS: 96 seeded sampled rows computed one by one by the oracle."""
+    FP32, one RHS: 256 seeded sampled rows computed one by one by the oracle."""
     v, t = icosphere(32, 2.0)
     op = bi.Operator(v, t, K0, digits=3, precision="fp32", op_mode=0, max_rhs=1)
     assert op.info()["levels"] == 5
     x = complex_gaussian(op.n_unknowns, 1, seed=SEED_BASE + 1)
     y = op.matvec(torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()[0]
-    rows = sample_rows(op.n_unknowns, 96, seed=SEED_BASE + 11)
+    rows = sample_rows(op.n_unknowns, 256, seed=SEED_BASE + 11)
     Zr = oracle.rows(v, t, K0, 0, rows)
     ref = Zr @ x[0]
     assert rel(y[rows], ref) < 1e-3
