@@ -153,6 +153,98 @@ def test_near_and_interactions_cover_every_pair_once(geo_plan):
     assert np.all(cover == 1), np.unique(cover, return_counts=True)
 
 
+def _neighbour_pairs(coords):
+    """(box, other) index pairs of the boxes of one level at Chebyshev distance <= 1 (the box
+    itself included), from their integer cell coordinates."""
+    key = (coords[:, 0].astype(np.int64) << 40) | (coords[:, 1].astype(np.int64) << 20) | coords[:, 2]
+    order = np.argsort(key)
+    skey = key[order]
+    a_all, b_all = [], []
+    for d in np.array(np.meshgrid([-1, 0, 1], [-1, 0, 1], [-1, 0, 1], indexing="ij")).reshape(3, -1).T:
+        c = coords + d
+        ok = np.all(c >= 0, axis=1)
+        k = (c[:, 0].astype(np.int64) << 40) | (c[:, 1].astype(np.int64) << 20) | c[:, 2]
+        i = np.minimum(np.searchsorted(skey, k), len(skey) - 1)
+        hit = ok & (skey[i] == k)
+        a_all.append(np.flatnonzero(hit))
+        b_all.append(order[i[hit]])
+    return np.concatenate(a_all), np.concatenate(b_all)
+
+
+@pytest.mark.slow
+def test_headline_tree_lists_at_full_size(bi):
+    """The set-up lists of the large scatterer itself (sphere of radius 20 wavelengths,
+    1,742,430 RWG, 9 levels, 110,456 leaf boxes), checked exhaustively rather than by sampled
+    rows, from the boxes' cell coordinates alone:
+    - every RWG sits in the leaf box of its midpoint's cell, and every child in its parent;
+    - the near list of each leaf box is exactly its existing neighbours (Chebyshev distance
+      <= 1, itself included);
+    - on every level l >= 2, the children of the neighbours of a box's parent split exactly
+      into the box's own neighbours and its interaction list (Sec. II.D), with no entry twice;
+    - the offset codes are the coordinate differences, and the parent-centred lists hold the
+      same (box, source, code) triples as the per-box lists.
+    With level 1 (whose boxes all touch) as the start, the split on every level covers each
+    pair of leaf boxes exactly once: by a near block if the two touch, else by the one
+    translation between their ancestors on the finest level where those do not touch."""
+    v, t, meta = inputs.workload("sphere_r20_nu241")
+    p = bi.Plan(v, t, K0, digits=3)
+    info = p.info()
+    lf = info["leaf_level"]
+    assert info["levels"] == 9 and info["n_rwg"] == 1742430 and info["boxes"][lf] == 110456
+    # octree membership, vectorised over the RWGs
+    perm, start = p.get(12), p.get(0)
+    edges = p.get(13).reshape(-1, 2)
+    mid = 0.5 * (v[edges[:, 0]] + v[edges[:, 1]])
+    lo = 0.5 * (mid.min(0) + mid.max(0)) - 0.5 * info["root_size"]
+    a = info["root_size"] / 2 ** lf
+    cell = np.clip(np.floor((mid - lo) / a).astype(np.int64), 0, 2 ** lf - 1)
+    box_of_tree_pos = np.repeat(np.arange(len(start) - 1), np.diff(start))
+    coords = {l: p.get(3, l).reshape(-1, 3).astype(np.int64) for l in range(lf + 1)}
+    assert np.array_equal(cell[perm], coords[lf][box_of_tree_pos])
+    for l in range(1, lf + 1):
+        assert np.array_equal(coords[l] >> 1, coords[l - 1][p.get(4, l)])
+    # near lists at the leaf level = existing neighbours
+    nb = info["boxes"][lf]
+    na, nn = _neighbour_pairs(coords[lf])
+    nptr, nsrc = p.get(1), p.get(2)
+    near = np.repeat(np.arange(nb), np.diff(nptr)).astype(np.int64) * nb + nsrc
+    assert len(np.unique(near)) == len(near)
+    assert np.array_equal(np.sort(near), np.sort(na.astype(np.int64) * nb + nn))
+    for l in range(2, lf + 1):
+        n_l = info["boxes"][l]
+        cp = p.get(5, l - 1)                      # children of each box of level l - 1
+        # children of the parent's neighbours, for every box of level l
+        qa, qb = _neighbour_pairs(coords[l - 1])
+        nq, nr = np.diff(cp)[qa], np.diff(cp)[qb]
+        cnt = nq * nr
+        grp = np.repeat(np.arange(len(qa)), cnt)
+        k = np.arange(cnt.sum()) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+        c = cp[qa][grp] + k // nr[grp]
+        s = cp[qb][grp] + k % nr[grp]
+        cand = np.sort(c.astype(np.int64) * n_l + s)
+        assert len(np.unique(cand)) == len(cand)
+        la, lb = _neighbour_pairs(coords[l])
+        nbr = la.astype(np.int64) * n_l + lb
+        ptr, src, off = p.get(6, l), p.get(7, l), p.get(8, l)
+        recv = np.repeat(np.arange(n_l), np.diff(ptr)).astype(np.int64)
+        il = recv * n_l + src
+        assert info["interactions"][l] == len(il) and len(np.unique(il)) == len(il), l
+        assert np.array_equal(np.sort(np.concatenate([nbr, il])), cand), l
+        o = coords[l][recv] - coords[l][src]
+        assert np.array_equal(off, (o[:, 0] + 3) * 49 + (o[:, 1] + 3) * 7 + (o[:, 2] + 3)), l
+        # parent-centred lists: the same (box, source, code) triples
+        tptr, tsrc = p.get(9, l), p.get(10, l)
+        tcode = p.get(11, l).reshape(-1, 8).astype(np.int64)
+        par_of_row = np.repeat(np.arange(len(tptr) - 1), np.diff(tptr))
+        slot_box = cp[par_of_row][:, None] + np.arange(8)[None, :]
+        live = tcode != NONE
+        assert np.all(slot_box[live] < cp[par_of_row + 1][np.nonzero(live)[0]]), l
+        pc_keys = (slot_box[live].astype(np.int64) * n_l + np.repeat(tsrc, 8).reshape(-1, 8)[live]) * 344 + tcode[live]
+        pl_keys = il * 344 + off
+        assert np.array_equal(np.sort(pc_keys), np.sort(pl_keys)), l
+    p.close()
+
+
 def test_interaction_offsets_match_box_coordinates(geo_plan):
     plan = geo_plan[3]
     info = plan.info()

@@ -87,10 +87,15 @@ def rnd(x, fmt):
     raise ValueError(fmt)
 
 
-def _far_product(m, x, fmt, stage):
+def _far_product(m, x, fmt, stage, level=None):
     """Far part of <f, L f> x with one stage's operands rounded to fmt (the model's propagate
-    restated with rounding hooks)."""
+    restated with rounding hooks).  With `level`, a level pass is rounded on that level only:
+    interp on the step into parent level `level`, translate on level `level`, anterp on the
+    step out of parent level `level`."""
     q = (lambda a: rnd(a, fmt)) if fmt != "fp64" else (lambda a: a)
+
+    def hit(st, l):
+        return stage == st and (level is None or level == l)
     p, info, lf, k, cen, grids = m.p, m.info, m.lf, m.k, m.cen, m.grids
     F = m.F
     xa = x
@@ -105,7 +110,7 @@ def _far_product(m, x, fmt, stage):
     U = {lf: U_leaf}
     for l in range(lf - 1, 1, -1):
         A, B = m.interp[l]
-        if stage == "interp":
+        if hit("interp", l):
             A, B = q(A), q(B)
         nphc = grids[l + 1][1]
         nthp, nphp, khp = grids[l][:3]
@@ -115,23 +120,23 @@ def _far_product(m, x, fmt, stage):
             for c in range(cp[b], cp[b + 1]):
                 sh = np.exp(1j * k * (khp @ (cen[l + 1][c] - cen[l][b])))
                 for i in range(2):
-                    uc = q(U[l + 1][c, i]) if stage == "interp" else U[l + 1][c, i]
+                    uc = q(U[l + 1][c, i]) if hit("interp", l) else U[l + 1][c, i]
                     U[l][b, i] += ((A @ uc).reshape(nthp, nphc) @ B.T).reshape(-1) * sh
     V = {l: np.zeros_like(U[l]) for l in U}
     for l in range(2, lf + 1):
         ptr, src, off = p.get(6, l), p.get(7, l), p.get(8, l)
-        Uq = [[q(U[l][s, i]) for i in range(2)] for s in range(info["boxes"][l])] if stage == "translate" else None
+        Uq = [[q(U[l][s, i]) for i in range(2)] for s in range(info["boxes"][l])] if hit("translate", l) else None
         for b in range(info["boxes"][l]):
             for e in range(ptr[b], ptr[b + 1]):
                 T = m._translation(l, int(off[e]))
-                if stage == "translate":
+                if hit("translate", l):
                     T = q(T)
                     V[l][b] += T[None] * np.stack(Uq[src[e]])
                 else:
                     V[l][b] += T[None] * U[l][src[e]]
     for l in range(2, lf):
         A, B = m.interp[l]
-        if stage == "anterp":
+        if hit("anterp", l):
             A, B = q(A), q(B)
         nthp, nphp, khp = grids[l][:3]
         cp = p.get(5, l)
@@ -140,7 +145,7 @@ def _far_product(m, x, fmt, stage):
                 sh = np.exp(-1j * k * (khp @ (cen[l + 1][c] - cen[l][b])))
                 for i in range(2):
                     s = V[l][b, i] * sh
-                    if stage == "anterp":
+                    if hit("anterp", l):
                         s = q(s)
                     V[l + 1][c, i] += A.T @ (s.reshape(nthp, nphp) @ B).reshape(-1)
     Vl = V[lf]
@@ -172,6 +177,33 @@ def precision_table(nu=16, radius=1.0, formats=FORMATS, stages=STAGES):
     return m.info, out
 
 
+LEVEL_STAGES = ("interp", "translate", "anterp")
+LEVEL_FORMATS = ("fp32", "fp16_scaled", "bf16", "split16")
+
+
+def precision_by_level(nu=32, radius=2.0, formats=LEVEL_FORMATS, stages=LEVEL_STAGES, leaf=0.25, digits=3,
+                       mesh=None):
+    """The far part with one level pass rounded on ONE level only, every other operand FP64:
+    which levels, if any, could take a narrower format.  Default mesh: the 5-level sphere of
+    radius 2 wavelengths (30,720 RWG), whose translations run on three levels (1, 0.5 and
+    0.25 wavelength boxes); `mesh` = (verts, tris) replaces the sphere."""
+    from paper_2210_04892_gb300 import bi, inputs
+    import test_plan
+    bi.load()
+    v, t = mesh if mesh is not None else inputs.icosphere(nu, radius)
+    m = test_plan._MultilevelModel(bi, v, t, K0, leaf, digits)
+    rng = np.random.default_rng(inputs.SEED_BASE + 82)
+    x = rng.normal(size=m.N) + 1j * rng.normal(size=m.N)
+    ref = _far_product(m, x, "fp64", None)
+    out = {}
+    for st in stages:
+        for l in range(2, m.lf + 1 if st == "translate" else m.lf):
+            for fmt in formats:
+                y = _far_product(m, x, fmt, st, level=l)
+                out[(st, l, fmt)] = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+    return m.info, out
+
+
 @pytest.mark.slow
 def test_precision_policy_of_the_product():
     info, e = precision_table(formats=("fp32", "bf16"), stages=("interp", "translate", "anterp"))
@@ -183,6 +215,16 @@ def test_precision_policy_of_the_product():
 
 
 if __name__ == "__main__":
+    if "--by-level" in sys.argv:
+        info, e = precision_by_level()
+        nl = info["levels"]
+        print("levels %d, N %d, box size per level %s, K per level %s" % (
+            nl, info["n_rwg"], [info["root_size"] / 2 ** l for l in range(nl)], info["K"][:nl]))
+        print("| stage | level | " + " | ".join(LEVEL_FORMATS) + " |")
+        print("|---|---:|" + "---:|" * len(LEVEL_FORMATS))
+        for (st, l) in sorted({(s_, l_) for (s_, l_, _) in e}, key=lambda a: (LEVEL_STAGES.index(a[0]), a[1])):
+            print("| %s | %d | " % (st, l) + " | ".join("%.1e" % e[(st, l, f)] for f in LEVEL_FORMATS) + " |")
+        sys.exit(0)
     info, e = precision_table()
     print("levels %d, N %d, K per level %s" % (info["levels"], info["n_rwg"], info["K"][:info["levels"]]))
     print("| stage | " + " | ".join(FORMATS) + " |")
