@@ -649,12 +649,17 @@ def run_gpu(args):
         out["rel_err_cpu_sample"] = err
     op.close()
     del x, y
-    if args.secondary and rank == 0:
-        out["secondary"] = run_secondary(args, bi)
-    if args.batched and rank == 0:
-        out["batched"] = run_batched(args)
-    if args.serving and rank == 0:
-        out["serving"] = run_serving(args)
+    # the further sections are context for the headline: a failure in one is reported in its
+    # place and does not cost the headline line
+    for key, on, fn in (("secondary", args.secondary, lambda: run_secondary(args, bi)),
+                        ("batched", args.batched, lambda: run_batched(args)),
+                        ("serving", args.serving, lambda: run_serving(args))):
+        if on and rank == 0:
+            try:
+                out[key] = fn()
+            except Exception as e:  # noqa: BLE001 - any failure of a context section
+                out[key] = {"error": "%s: %s" % (type(e).__name__, str(e)[:300])}
+                print("bench: %s section failed: %r" % (key, e), file=sys.stderr, flush=True)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
