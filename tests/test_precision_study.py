@@ -34,7 +34,26 @@ more inside the 1e-3 bar; TF32, scaled FP16 and BF16 operands break it at every 
 does the three-product BF16 split; error-corrected TF32 (three TF32 products per FP32 product)
 holds it with a 7x margin at its worst stage.
 
-  python tests/test_precision_study.py      prints the table (a few minutes)
+Per level (precision_by_level: one level pass rounded on ONE level, everything else FP64), on
+the 5-level sphere of radius 2 wavelengths (30,720 RWG; boxes 1, 0.5, 0.25 wavelength on
+levels 2, 3, 4):
+
+  | pass      | level | fp32    | fp16_scaled | bf16    | split16 |
+  | interp    | 2     | 1.2e-06 | 1.1e-02     | 7.5e-02 | 1.8e-04 |
+  | interp    | 3     | 1.1e-05 | 3.2e-02     | 3.3e-01 | 8.7e-04 |
+  | translate | 2     | 1.8e-06 | 1.5e-02     | 1.2e-01 | 2.2e-04 |
+  | translate | 3     | 7.5e-06 | 5.4e-02     | 7.4e-01 | 9.0e-04 |
+  | translate | 4     | 2.5e-05 | 3.3e-01     | 1.8e+00 | 3.3e-03 |
+  | anterp    | 2     | 1.5e-06 | 1.3e-02     | 9.2e-02 | 2.2e-04 |
+  | anterp    | 3     | 1.2e-05 | 4.4e-02     | 4.0e-01 | 1.0e-03 |
+
+The amplification falls as the boxes grow (about 400, 130 and 30 at 0.25, 0.5 and 1
+wavelength); with 0.125-wavelength leaves (1280-triangle sphere, 4 digits) it is about 2.5e4,
+and FP32 translations on the finest level alone cost 1.5e-3.  Only the split forms hold the
+bar, and the three-product BF16 split only from 1-wavelength boxes upward.
+
+  python tests/test_precision_study.py              prints the per-stage table (a few minutes)
+  python tests/test_precision_study.py --by-level   prints the per-level table (about 10 minutes)
 """
 import os
 import sys
