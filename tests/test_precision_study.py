@@ -47,13 +47,18 @@ levels 2, 3, 4):
   | anterp    | 2     | 1.5e-06 | 1.3e-02     | 9.2e-02 | 2.2e-04 |
   | anterp    | 3     | 1.2e-05 | 4.4e-02     | 4.0e-01 | 1.0e-03 |
 
-The amplification falls as the boxes grow (about 400, 130 and 30 at 0.25, 0.5 and 1
+On the 6-level sphere of radius 4 wavelengths (122,880 RWG; --by-level 64 4) the 2-wavelength
+boxes of level 2 add: interp 2.5e-07 / 2.3e-03 / 2.3e-02 / 2.6e-05, translate 2.7e-07 /
+2.2e-03 / 1.7e-02 / 4.1e-05, anterp 2.9e-07 / 2.7e-03 / 2.5e-02 / 3.3e-05 (same columns), and
+its finer levels repeat the figures above at equal box sizes.
+The amplification falls as the boxes grow (about 400, 130, 30 and 4 at 0.25, 0.5, 1 and 2
 wavelength); with 0.125-wavelength leaves (1280-triangle sphere, 4 digits) it is about 2.5e4,
-and FP32 translations on the finest level alone cost 1.5e-3.  Only the split forms hold the
+and FP32 translations on the finest level alone cost 1.5e-3.  Of the narrower forms only the splits hold the
 bar, and the three-product BF16 split only from 1-wavelength boxes upward.
 
   python tests/test_precision_study.py              prints the per-stage table (a few minutes)
   python tests/test_precision_study.py --by-level   prints the per-level table (about 10 minutes)
+  python tests/test_precision_study.py --by-level 64 4                         (about an hour)
 """
 import os
 import sys
@@ -235,7 +240,10 @@ def test_precision_policy_of_the_product():
 
 if __name__ == "__main__":
     if "--by-level" in sys.argv:
-        info, e = precision_by_level()
+        # optional: --by-level NU RADIUS (geodesic sphere; the default is nu 32, radius 2)
+        i = sys.argv.index("--by-level")
+        nu_r = sys.argv[i + 1:i + 3]
+        info, e = precision_by_level(*(int(nu_r[0]), float(nu_r[1])) if len(nu_r) == 2 else ())
         nl = info["levels"]
         print("levels %d, N %d, box size per level %s, K per level %s" % (
             nl, info["n_rwg"], [info["root_size"] / 2 ** l for l in range(nl)], info["K"][:nl]))
