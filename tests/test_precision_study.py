@@ -53,8 +53,8 @@ boxes of level 2 add: interp 2.5e-07 / 2.3e-03 / 2.3e-02 / 2.6e-05, translate 2.
 its finer levels repeat the figures above at equal box sizes.
 The amplification falls as the boxes grow (about 400, 130, 30 and 4 at 0.25, 0.5, 1 and 2
 wavelength); with 0.125-wavelength leaves (1280-triangle sphere, 4 digits) it is about 2.5e4,
-and FP32 translations on the finest level alone cost 1.5e-3.  Of the narrower forms only the splits hold the
-bar, and the three-product BF16 split only from 1-wavelength boxes upward.
+and FP32 translations on the finest level alone cost 1.5e-3.  Of the narrower forms only the
+splits hold the bar, and the three-product BF16 split only from 1-wavelength boxes upward.
 
   python tests/test_precision_study.py              prints the per-stage table (a few minutes)
   python tests/test_precision_study.py --by-level   prints the per-level table (about 10 minutes)
