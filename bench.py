@@ -205,15 +205,20 @@ def stage_roofline(info, nrhs, stages, hbm_gbs):
     return out
 
 
-def launches_per_step(info, nrhs=1):
+def launches_per_step(info, nrhs=1, tuned=""):
     """Kernels of one product on this path: near (side stream; with several right-hand sides
     preceded by the gather of x into tree order), aggregation, one interpolation and one
-    anterpolation per level pair, one translation per level, receive."""
+    anterpolation per level pair, one translation per level, receive.  `tuned` is the handle's
+    tuned-form report (bi_tuned_config): a level pass tuned to a two-pass form launches two
+    kernels (the theta pass and the phi pass)."""
     lf = info["leaf_level"]
     gather = 1 if nrhs > 1 else 0
     if lf < 2:
         return 2 + gather
-    return 1 + 1 + (lf - 2) + (lf - 1) + (lf - 2) + 1 + gather
+    E = " E %d:" % (2 * nrhs)
+    two_pass = sum(1 for line in tuned.splitlines()
+                   if E in line and line.startswith(("interpolate", "anterpolate")) and "two-pass" in line)
+    return 1 + 1 + (lf - 2) + (lf - 1) + (lf - 2) + 1 + gather + two_pass
 
 
 def measured_traffic(name="dram_matvec_sphere_r2_61440.md"):
@@ -634,7 +639,7 @@ def run_gpu(args):
                       "l2": "inputs larger than L2 (near blocks + leaf patterns %.1f GB per step)" %
                             ((sr["near"]["bytes"] + sr["receive"]["bytes"]) / 1e9)},
            "roofline": roofline, "e2e": e2e, "clocks": clocks, "setup_ms": info["setup_ms"],
-           "gpu_launches": launches_per_step(info, R) * args.steps}
+           "gpu_launches": launches_per_step(info, R, op.tuned_config()) * args.steps}
     out["rel_err_vs_oracle"] = golden_error(y_np)
     out["oracle_rows"] = "256 stored rows x 8 columns (tests/golden/c5_rows.json)"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -108,6 +108,32 @@ def test_launch_count_matches_the_launch_summary(bench_info):
     assert abs(launches / products - n) < 0.1 * n
 
 
+@pytest.mark.slow
+def test_headline_launch_count_matches_the_launch_summary():
+    """Kernels per product of the headline workload (9 levels, 8 RHS): the gather of x, near,
+    aggregation, 7 translations, 6 interpolation and 6 anterpolation steps, receive (23), plus
+    one more launch for each level pass tuned to a two-pass form.  The committed launch list of
+    one product holds 27 launches, of which the two-pass forms are the theta/phi pairs (`_p2`);
+    the count built from those tuned forms matches it."""
+    import bench
+    bench, info = _plan_info(bench.HEADLINE["name"])
+    text = open(os.path.join(ROOT, "profiles", "launches_matvec_sphere_r20_3484860.md")).read()
+    order = re.findall(r"^\| \d+ \| (k_\w+)<", text, re.M)
+    assert len(order) == 27
+    n_int = order.count("k_interp_theta_p2")
+    n_ant = order.count("k_anterp_theta_p2")
+    assert order.count("k_interp_phi_p2") == n_int and order.count("k_anterp_phi_p2") == n_ant
+    tuned = "\n".join(["translate level %d E 16: 2 pairs/thread (1 us)" % l for l in range(2, 9)] +
+                      ["interpolate level %d E 16: two-pass, entry pairs (1 us)" % (2 + i) for i in range(n_int)] +
+                      ["interpolate level %d E 16: rows per CTA, chunk 16 (1 us)" % (2 + n_int + i)
+                       for i in range(6 - n_int)] +
+                      ["anterpolate level %d E 16: two-pass, entry pairs (1 us)" % (2 + i) for i in range(n_ant)] +
+                      ["anterpolate level %d E 16: per child, chunk 8 (1 us)" % (2 + n_ant + i) for i in range(6 - n_ant)] +
+                      ["interpolate level 2 E 128: two-pass (1 us)"])     # another column count: not counted
+    assert bench.launches_per_step(info, 8) == 23
+    assert bench.launches_per_step(info, 8, tuned) == len(order)
+
+
 def test_peaks_are_the_measured_file_when_present(bench_info):
     bench, _ = bench_info
     peak, kind = bench.peaks()
