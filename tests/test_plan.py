@@ -464,6 +464,50 @@ def test_plan_rejects_open_and_bad_meshes(bi):
     p.close()
 
 
+def test_plan_rejects_degenerate_inputs_and_accepts_the_smallest_surface(bi):
+    """The error contract of the set-up on degenerate input (the same checks run in bi_setup
+    before any device work): an empty mesh, vertex indices outside the vertex array, non-finite
+    coordinates, a triangle with a repeated or collinear vertex (zero area), and edges shared
+    by more than two triangles are refused with BI_ERR_ARG or BI_ERR_MESH; the smallest closed
+    surface, a tetrahedron, is accepted with its 6 RWG functions."""
+    v, t = inputs.icosphere(4)
+    cases = {"empty mesh": (v, np.zeros((0, 3), np.int32))}
+    t2 = t.copy()
+    t2[0, 1] = len(v) + 5
+    cases["index past the vertices"] = (v, t2)
+    t2 = t.copy()
+    t2[0, 1] = -1
+    cases["negative index"] = (v, t2)
+    for bad in (np.nan, np.inf):
+        v2 = v.copy()
+        v2[3] = bad
+        cases["vertex %r" % bad] = (v2, t)
+    t2 = t.copy()
+    t2[0, 1] = t2[0, 0]
+    cases["repeated vertex"] = (v, t2)
+    v2 = v.copy()
+    a, b, c = t[0]
+    v2[c] = 0.5 * (v2[a] + v2[b])
+    cases["collinear triangle"] = (v2, t)
+    cases["duplicated triangle"] = (v, np.concatenate([t, t[:1]]))
+    tv = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]]) * 0.1
+    tt = np.array([[0, 2, 1], [0, 1, 3], [0, 3, 2], [1, 2, 3]], np.int32)
+    # a second tetrahedron on the edge (0, 1): four triangles on one edge
+    V = np.concatenate([tv, [[0, -0.1, 0], [0, 0, -0.1]]])
+    T = np.concatenate([tt, np.array([[0, 4, 1], [0, 1, 5], [0, 5, 4], [1, 4, 5]], np.int32)])
+    cases["non-manifold edge"] = (V, T)
+    for name, (vv, ttt) in cases.items():
+        with pytest.raises(bi.BIError) as e:
+            bi.Plan(vv, ttt, K0)
+        assert e.value.code in (bi.BI_ERR_ARG, bi.BI_ERR_MESH), name
+    with pytest.raises(bi.BIError):
+        bi.Plan(v, t, float("nan"))
+    p = bi.Plan(tv, tt, K0)
+    info = p.info()
+    assert info["n_rwg"] == 6 and info["levels"] == 1
+    p.close()
+
+
 @pytest.mark.parametrize("digits,leaf_box", [(3, 0.25), (6, 0.125)])
 def test_translation_hankel_table(bi, sphere, digits, leaf_box):
     """Spherical Hankel functions h_n^(2)(k|X|) = j_n - i y_n behind the translation operators
