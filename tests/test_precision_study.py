@@ -184,20 +184,29 @@ def _far_product(m, x, fmt, stage, level=None):
     return y
 
 
-def precision_table(nu=16, radius=1.0, formats=FORMATS, stages=STAGES):
+def _model(nu, radius, leaf=0.25, digits=3, mesh=None):
+    """The numpy model of the chain on a geodesic sphere (or `mesh`), a seeded x and the FP64
+    far part."""
     from paper_2210_04892_gb300 import bi, inputs
     import test_plan
     bi.load()
-    v, t = inputs.icosphere(nu, radius)
-    m = test_plan._MultilevelModel(bi, v, t, K0, 0.25, 3)
+    v, t = mesh if mesh is not None else inputs.icosphere(nu, radius)
+    m = test_plan._MultilevelModel(bi, v, t, K0, leaf, digits)
     rng = np.random.default_rng(inputs.SEED_BASE + 82)
     x = rng.normal(size=m.N) + 1j * rng.normal(size=m.N)
-    ref = _far_product(m, x, "fp64", None)
+    return m, x, _far_product(m, x, "fp64", None)
+
+
+def _rel(y, ref):
+    return float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+
+
+def precision_table(nu=16, radius=1.0, formats=FORMATS, stages=STAGES, model=None):
+    m, x, ref = model or _model(nu, radius)
     out = {}
     for st in stages:
         for fmt in formats:
-            y = _far_product(m, x, fmt, st)
-            out[(st, fmt)] = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+            out[(st, fmt)] = _rel(_far_product(m, x, fmt, st), ref)
     return m.info, out
 
 
@@ -206,36 +215,36 @@ LEVEL_FORMATS = ("fp32", "fp16_scaled", "bf16", "split16")
 
 
 def precision_by_level(nu=32, radius=2.0, formats=LEVEL_FORMATS, stages=LEVEL_STAGES, leaf=0.25, digits=3,
-                       mesh=None):
+                       mesh=None, model=None):
     """The far part with one level pass rounded on ONE level only, every other operand FP64:
     which levels, if any, could take a narrower format.  Default mesh: the 5-level sphere of
     radius 2 wavelengths (30,720 RWG), whose translations run on three levels (1, 0.5 and
     0.25 wavelength boxes); `mesh` = (verts, tris) replaces the sphere."""
-    from paper_2210_04892_gb300 import bi, inputs
-    import test_plan
-    bi.load()
-    v, t = mesh if mesh is not None else inputs.icosphere(nu, radius)
-    m = test_plan._MultilevelModel(bi, v, t, K0, leaf, digits)
-    rng = np.random.default_rng(inputs.SEED_BASE + 82)
-    x = rng.normal(size=m.N) + 1j * rng.normal(size=m.N)
-    ref = _far_product(m, x, "fp64", None)
+    m, x, ref = model or _model(nu, radius, leaf, digits, mesh)
     out = {}
     for st in stages:
         for l in range(2, m.lf + 1 if st == "translate" else m.lf):
             for fmt in formats:
-                y = _far_product(m, x, fmt, st, level=l)
-                out[(st, l, fmt)] = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+                out[(st, l, fmt)] = _rel(_far_product(m, x, fmt, st, level=l), ref)
     return m.info, out
 
 
 @pytest.mark.slow
 def test_precision_policy_of_the_product():
-    info, e = precision_table(formats=("fp32", "bf16"), stages=("interp", "translate", "anterp"))
+    """On the 4-level sphere of radius 1 wavelength: FP32 operands keep every level pass far
+    inside the 1e-3 bar and BF16 operands break it; per level, the amplification of rounding
+    is larger on the 0.25-wavelength boxes (level 3) than on the 0.5-wavelength ones (level 2),
+    for FP32 and for the three-product BF16 split alike."""
+    model = _model(16, 1.0)
+    info, e = precision_table(formats=("fp32", "bf16"), stages=("interp", "translate", "anterp"), model=model)
     assert info["levels"] == 4
     for st in ("interp", "translate", "anterp"):
         assert e[(st, "fp32")] < 1e-4, (st, e)
         # BF16 operands break the 1e-3 bar of the product at every level pass
         assert e[(st, "bf16")] > 1e-2, (st, e)
+    _, el = precision_by_level(formats=("fp32", "split16"), stages=("translate",), model=model)
+    for fmt in ("fp32", "split16"):
+        assert el[("translate", 3, fmt)] > 2 * el[("translate", 2, fmt)], el
 
 
 if __name__ == "__main__":
